@@ -1,0 +1,162 @@
+"""Joint cost, Gauss-Newton, marginalisation and the per-frame tracker.
+
+Oracle code (test infrastructure only).
+
+Cost (Eq. 6): photometric + ICP + IMU terms and the marginalisation prior
+  (x_0 boxminus xbar_0 - H*^-1 b*)^T H* (x_0 boxminus xbar_0 - H*^-1 b*).
+System (Eq. 7): H dx = b over dx = [dx_0; dx_1] (34-D), H = sum J^T W J,
+b = -sum J^T W e; solved by dense Cholesky; both states updated with boxplus
+after each iteration (Sec. IV-D), coarse-to-fine over the pyramid levels.
+
+Prior (reading of Eq. 9, whose Delta x is not defined): the prior adds H* to
+H_00 and b* - H* (x_0 boxminus xbar_0) to b_0.  This is the gradient of Eq. 6's
+prior term (its Jacobian taken as the identity) and equals Eq. 9b with
+Delta x := xbar_0 boxminus x_0.
+
+Marginalisation (Eq. 8): after the last update the last system is moved to the
+new point to first order (b <- b - H dx_last) and x_0 is removed with the Schur
+complement H* = H_11 - H_10 H_00^-1 H_01, b* = b_1 - H_10 H_00^-1 b_0; xbar := x_1.
+
+Frame loop (reading; the paper does not state the initialisation): x_0 := the
+previous x_1, x_1 := the IMU prediction x^_1(x_0); W_IMU computed there.  The
+first frame only initialises: x_1 := x_init (identity pose, W = first camera
+frame, Sec. II), the diagonal first-frame prior, and the frame becomes the
+reference.  After every tracked frame the live frame's maps become the next
+reference at the final T_WC1.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import imu as imu_mod
+from .maps import frame_levels, reference_from_frame
+from .photogeo import linearise
+from .so3 import State, boxminus, boxplus
+
+POSE0 = slice(0, 6)
+POSE1 = slice(17, 23)
+
+
+def first_prior(cfg):
+    s = cfg.prior_sigma
+    sig = np.concatenate([[s["pose"]] * 6, [s["v"]] * 3, [s["bg"]] * 3, [s["ba"]] * 3,
+                          [s["grav"]] * 2])
+    return np.diag(1.0 / sig ** 2), np.zeros(17)
+
+
+def prior_terms(x0, xbar, Hs, bs):
+    """Contribution of the prior to (H_00, b_0)."""
+    d = boxminus(x0, xbar)
+    return Hs, bs - Hs @ d
+
+
+def prior_cost(x0, xbar, Hs, bs):
+    d = boxminus(x0, xbar) - np.linalg.solve(Hs, bs)
+    return float(d @ Hs @ d)
+
+
+def assemble(lin, J_imu, e_imu, W_imu, x0, xbar, Hs, bs):
+    """The 34 x 34 Gauss-Newton system of Eq. 7."""
+    H = np.zeros((34, 34))
+    b = np.zeros(34)
+    idx = np.r_[0:6, 17:23]
+    H[np.ix_(idx, idx)] += lin["H_rgb"]
+    b[idx] += lin["b_rgb"]
+    H[POSE1, POSE1] += lin["H_icp"]
+    b[POSE1] += lin["b_icp"]
+    H += J_imu.T @ W_imu @ J_imu
+    b += -J_imu.T @ W_imu @ e_imu
+    Hp, bp = prior_terms(x0, xbar, Hs, bs)
+    H[0:17, 0:17] += Hp
+    b[0:17] += bp
+    return H, b
+
+
+def cholesky_solve(H, b):
+    L = np.linalg.cholesky(H)
+    y = np.linalg.solve(L, b)
+    return np.linalg.solve(L.T, y)
+
+
+def schur(H, b):
+    """Eq. 8: marginalise the first 17 coordinates."""
+    H00, H01, H10, H11 = H[:17, :17], H[:17, 17:], H[17:, :17], H[17:, 17:]
+    X = np.linalg.solve(H00, np.column_stack([H01, b[:17]]))
+    return H11 - H10 @ X[:, :17], b[17:] - H10 @ X[:, 17]
+
+
+class TrackingLost(RuntimeError):
+    pass
+
+
+class Tracker:
+    """Per-stream FP64 tracker: the oracle of one dri_track call per frame."""
+
+    def __init__(self, cfg, x_init, t_init=None):
+        self.cfg = cfg
+        self.x = State.from_dict(x_init) if isinstance(x_init, dict) else x_init.copy()
+        self.t = t_init
+        self.ref = None
+        self.T_ref = None
+        self.Hs, self.bs = first_prior(cfg)
+        self.xbar = self.x.copy()
+        self.imu = np.zeros((0, 7))
+
+    def push_imu(self, samples):
+        self.imu = np.concatenate([self.imu, np.asarray(samples, dtype=np.float64)])
+
+    def linearise_all(self, levels, l, x0, x1, t0, t1, W_imu):
+        """All terms of Eq. 6 at (x0, x1) on level l: returns (H, b, parts)."""
+        cfg = self.cfg
+        lin = linearise(levels[l], self.ref[l], self.T_ref[0], self.T_ref[1], x0, x1, cfg)
+        pre = imu_mod.preintegrate(self.imu, t0, t1, x0.bg, x0.ba)
+        e, pr = imu_mod.residual(x0, x1, pre, cfg)
+        J = imu_mod.jacobian(x0, x1, pre, cfg, e, pr)
+        H, b = assemble(lin, J, e, W_imu, x0, self.xbar, self.Hs, self.bs)
+        parts = dict(lin=lin, e_imu=e, J_imu=J, cost_imu=float(e @ W_imu @ e))
+        return H, b, parts
+
+    def track(self, depth, intensity, t):
+        cfg = self.cfg
+        levels = frame_levels(depth, intensity, cfg)
+        if self.ref is None:                       # first frame: initialise only
+            self.t = t
+            self.T_ref = (self.x.R, self.x.r.copy())
+            self.ref = reference_from_frame(levels, *self.T_ref)
+            self.xbar = self.x.copy()
+            return dict(status="init", x1=self.x.copy())
+        t0, t1 = self.t, t
+        x0 = self.x.copy()
+        W_imu, _ = imu_mod.weight(x0, self.imu, t0, t1, cfg)
+        pre = imu_mod.preintegrate(self.imu, t0, t1, x0.bg, x0.ba)
+        pr = imu_mod.predict(x0, pre, cfg)
+        from .so3 import rot_to_quat
+        x1 = State(pr["r"], rot_to_quat(pr["R"]), pr["v"], x0.bg.copy(), x0.ba.copy(),
+                   x0.qg.copy())
+        counts = {}
+        H = b = d = None
+        for l in range(cfg.levels - 1, -1, -1):
+            for _ in range(cfg.iters[l]):
+                H, b, parts = self.linearise_all(levels, l, x0, x1, t0, t1, W_imu)
+                counts[l] = (parts["lin"]["n_icp"], parts["lin"]["n_rgb"])
+                try:
+                    d = cholesky_solve(H, b)
+                except np.linalg.LinAlgError as exc:
+                    raise TrackingLost("Cholesky failed") from exc
+                if not np.all(np.isfinite(d)):
+                    raise TrackingLost("non-finite step")
+                x0 = boxplus(x0, d[:17])
+                x1 = boxplus(x1, d[17:])
+        if counts[0][0] + counts[0][1] < cfg.min_valid:
+            raise TrackingLost("too few correspondences")
+        Hs, bs = schur(H, b - H @ d)
+        self.Hs, self.bs = Hs, bs
+        self.xbar = x1.copy()
+        self.x = x1.copy()
+        self.t = t1
+        self.T_ref = (x1.R, x1.r.copy())
+        self.ref = reference_from_frame(levels, *self.T_ref)
+        keep = np.searchsorted(self.imu[:, 0], t1, side="right") - 1
+        self.imu = self.imu[max(keep, 0):]
+        return dict(status="ok", x0=x0, x1=x1, counts=counts, H=H, b=b, d_last=d,
+                    H_prior=Hs, b_prior=bs)

@@ -1,0 +1,138 @@
+"""Image pyramid, vertex / normal / intensity-gradient maps and reference maps.
+
+Oracle code (test infrastructure only).  The paper minimises its cost "with a
+three level coarse-to-fine pyramid scheme" (Sec. IV-D) and evaluates Eq. 3
+(photometric) and Eq. 4 (point-to-plane ICP) on vertex, normal and intensity
+maps, without describing how they are built.  Readings used here:
+
+* Pyramid: level l halves level l-1 (floor of odd sizes).  Depth is the mean
+  of the samples > 0 in each 2x2 block (0 if none); intensity is the plain
+  2x2 mean.  Intrinsics scale as f_l = f / 2^l, c_l = (c + 0.5) / 2^l - 0.5.
+* Vertex map: v = d K_l^-1 [u, v, 1]^T for depths in [depth_min, depth_max].
+* Normal map: n = normalise((v(x+1,y) - v) x (v(x,y+1) - v)), flipped so that
+  n . v < 0 (facing the camera); invalid on the last row / column, where a
+  neighbour is invalid, or where the cross product vanishes.
+* Intensity gradient: central differences (I(x+1) - I(x-1)) / 2 and
+  (I(y+1) - I(y-1)) / 2; zero on the one-pixel border.
+* Reference maps (the "global model" of Eq. 4, here the previous frame's maps
+  moved into W with its final pose): V_W = R_ref v + r_ref, N_W = R_ref n,
+  intensity and its gradient, and the pose T_ref they were made at.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+def downsample_depth(d):
+    """2x2 mean of the valid (> 0) samples; 0 where none is valid."""
+    d = np.asarray(d, dtype=np.float64)
+    h, w = d.shape[0] // 2, d.shape[1] // 2
+    blk = d[: 2 * h, : 2 * w].reshape(h, 2, w, 2)
+    valid = blk > 0
+    s = np.where(valid, blk, 0.0).sum(axis=(1, 3))
+    n = valid.sum(axis=(1, 3))
+    return np.where(n > 0, s / np.maximum(n, 1), 0.0)
+
+
+def downsample_intensity(img):
+    img = np.asarray(img, dtype=np.float64)
+    h, w = img.shape[0] // 2, img.shape[1] // 2
+    return img[: 2 * h, : 2 * w].reshape(h, 2, w, 2).mean(axis=(1, 3))
+
+
+def pyramid(depth, intensity, levels):
+    ds = [np.asarray(depth, dtype=np.float64)]
+    Is = [np.asarray(intensity, dtype=np.float64)]
+    for _ in range(1, levels):
+        ds.append(downsample_depth(ds[-1]))
+        Is.append(downsample_intensity(Is[-1]))
+    return ds, Is
+
+
+def depth_valid(d, cfg):
+    return (d >= cfg.depth_min) & (d <= cfg.depth_max)
+
+
+def vertex_map(d, cam, cfg):
+    """Back-projection rho(u, d) = d K^-1 [u, v, 1]^T (Eq. 3), camera frame."""
+    h, w = d.shape
+    u = np.arange(w, dtype=np.float64)[None, :]
+    v = np.arange(h, dtype=np.float64)[:, None]
+    V = np.stack(np.broadcast_arrays(d * (u - cam["cx"]) / cam["fx"],
+                                     d * (v - cam["cy"]) / cam["fy"], d), axis=-1)
+    valid = depth_valid(d, cfg)
+    return V, valid
+
+
+def normal_map(V, valid):
+    """Normalised cross product of forward differences, facing the camera."""
+    h, w, _ = V.shape
+    N = np.zeros_like(V)
+    ok = np.zeros((h, w), dtype=bool)
+    dx = V[:-1, 1:] - V[:-1, :-1]
+    dy = V[1:, :-1] - V[:-1, :-1]
+    c = np.cross(dx, dy)
+    nrm = np.linalg.norm(c, axis=-1)
+    good = valid[:-1, :-1] & valid[:-1, 1:] & valid[1:, :-1] & (nrm > 0)
+    n = c / np.where(nrm > 0, nrm, 1.0)[..., None]
+    flip = np.sum(n * V[:-1, :-1], axis=-1) > 0
+    n = np.where(flip[..., None], -n, n)
+    N[:-1, :-1] = np.where(good[..., None], n, 0.0)
+    ok[:-1, :-1] = good
+    return N, ok
+
+
+def gradient_map(img):
+    img = np.asarray(img, dtype=np.float64)
+    g = np.zeros(img.shape + (2,))
+    g[1:-1, 1:-1, 0] = 0.5 * (img[1:-1, 2:] - img[1:-1, :-2])
+    g[1:-1, 1:-1, 1] = 0.5 * (img[2:, 1:-1] - img[:-2, 1:-1])
+    return g
+
+
+@dataclass
+class FrameLevel:
+    """Maps of the live frame at one pyramid level (camera frame C1)."""
+    cam: dict
+    depth: np.ndarray
+    V: np.ndarray
+    V_valid: np.ndarray
+    N: np.ndarray
+    N_valid: np.ndarray
+    I: np.ndarray
+
+
+@dataclass
+class RefLevel:
+    """Reference maps at one level, vertices and normals in W (Eq. 4)."""
+    cam: dict
+    V_W: np.ndarray
+    N_W: np.ndarray
+    valid: np.ndarray        # vertex and normal both valid
+    I: np.ndarray
+    G: np.ndarray            # intensity gradient (gx, gy) per pixel
+    depth: np.ndarray        # kept for the margin test of the association
+
+
+def frame_levels(depth, intensity, cfg):
+    ds, Is = pyramid(depth, intensity, cfg.levels)
+    out = []
+    for l in range(cfg.levels):
+        cam = cfg.level_camera(l)
+        V, vv = vertex_map(ds[l], cam, cfg)
+        N, nv = normal_map(V, vv)
+        out.append(FrameLevel(cam=cam, depth=ds[l], V=V, V_valid=vv, N=N, N_valid=nv, I=Is[l]))
+    return out
+
+
+def reference_from_frame(levels, R_ref, r_ref):
+    """The live frame's maps become the next reference, moved into W with T_ref."""
+    out = []
+    for fl in levels:
+        V_W = fl.V @ R_ref.T + r_ref
+        N_W = fl.N @ R_ref.T
+        out.append(RefLevel(cam=fl.cam, V_W=V_W, N_W=N_W, valid=fl.V_valid & fl.N_valid,
+                            I=fl.I, G=gradient_map(fl.I), depth=fl.depth))
+    return out

@@ -1,0 +1,74 @@
+"""Constants and tracker configuration of the oracle.
+
+Oracle code (test infrastructure only).
+
+Table I (Sec. VI), synthetic-dataset column: noise densities, bias priors,
+bias random walks ("drift noise density"), gravity and IMU rate.  Saturation
+limits (7.8 rad/s, 176 m/s^2) are never reached by the synthetic workloads and
+are not applied.
+
+Readings where the paper is silent (Sec. IV-B/D give no thresholds, weights
+or schedule):
+* W_RGB = 1 / sigma_I^2 with sigma_I = 0.01 (intensity in [0, 1]) and
+  W_ICP = 1 / sigma_d^2 with sigma_d = 0.002 m: the inverse covariances the
+  text asks for (Sec. III, Sec. IV-D), constant per pixel.  Table I's
+  "intensity noise 4.0" (no units) and "disparity noise 5.5 px" do not map onto
+  these synthetic images.
+* Data association: nearest reference pixel floor(x + 0.5), accepted when
+  the points are closer than 0.10 m and their normals differ by less than
+  20 degrees; depths are valid in [0.3, 8.0] m.  No robust kernel, no
+  occlusion test, no photometric gradient threshold.
+* Prior for the first frame (W is the first camera frame, Sec. II): diagonal
+  with pose 1e-6 (m, rad), velocity 0.1 m/s, gyro / accelerometer bias
+  0.03 rad/s and 0.1 m/s^2 (Table I bias priors), gravity direction 0.1 rad.
+* Gravity-direction process noise between consecutive frames: 1e-4 rad.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+GRAVITY = 9.81                 # Table I, m s^-2
+GYR_NOISE_DENSITY = 12.0e-4    # Table I, rad s^-1 Hz^-0.5
+ACC_NOISE_DENSITY = 8.0e-3     # Table I, m s^-2 Hz^-0.5
+GYR_BIAS_PRIOR = 0.03          # Table I, rad s^-1
+ACC_BIAS_PRIOR = 0.1           # Table I, m s^-2
+GYR_DRIFT_DENSITY = 4.0e-6     # Table I, rad s^-2 Hz^-0.5
+ACC_DRIFT_DENSITY = 2.0e-5     # Table I, m s^-3 Hz^-0.5
+IMU_RATE = 200.0               # Table I, Hz
+
+
+@dataclass
+class TrackerConfig:
+    width: int
+    height: int
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    levels: int = 3
+    iters: tuple = (10, 5, 4)           # iterations per level, index 0 = finest
+    R_CS: object = None                 # 3x3, IMU frame S in camera frame C
+    r_CS: object = None                 # position of S in C
+    sigma_I: float = 0.01
+    sigma_d: float = 0.002
+    gyr_nd: float = GYR_NOISE_DENSITY
+    acc_nd: float = ACC_NOISE_DENSITY
+    gyr_rw: float = GYR_DRIFT_DENSITY
+    acc_rw: float = ACC_DRIFT_DENSITY
+    g: float = GRAVITY
+    sigma_grav_rw: float = 1e-4
+    icp_dist_thr: float = 0.10
+    icp_angle_thr_deg: float = 20.0
+    depth_min: float = 0.3
+    depth_max: float = 8.0
+    prior_sigma: dict = field(default_factory=lambda: dict(
+        pose=1e-6, v=0.1, bg=GYR_BIAS_PRIOR, ba=ACC_BIAS_PRIOR, grav=0.1))
+    min_valid: int = 64                 # level-0 correspondences below this: tracking lost
+
+    def level_camera(self, level):
+        """Intrinsics at pyramid level l: f_l = f / 2^l, c_l = (c + 0.5) / 2^l - 0.5
+        (the centre of a 2x2 block of the finer level)."""
+        s = 2.0 ** level
+        return dict(width=self.width >> level, height=self.height >> level,
+                    fx=self.fx / s, fy=self.fy / s,
+                    cx=(self.cx + 0.5) / s - 0.5, cy=(self.cy + 0.5) / s - 0.5)

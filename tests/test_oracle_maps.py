@@ -1,0 +1,108 @@
+"""Pins of the oracle's pyramid and map construction (Sec. IV-D pyramid; Eq. 3-4 inputs)."""
+import numpy as np
+
+from oracle import maps
+from oracle.params import TrackerConfig
+
+
+def _cfg(w=16, h=12, f=14.0):
+    return TrackerConfig(w, h, f, f, w / 2.0, h / 2.0, levels=3, iters=(1, 1, 1),
+                         R_CS=np.eye(3), r_CS=np.zeros(3))
+
+
+def test_depth_downsample_means_valid_samples():
+    d = np.array([[1.0, 3.0, 0.0, 0.0],
+                  [0.0, 2.0, 0.0, 5.0],
+                  [1.0, 1.0, 2.0, 4.0],
+                  [1.0, 1.0, 6.0, 0.0]])
+    out = maps.downsample_depth(d)
+    np.testing.assert_array_equal(out, [[2.0, 5.0], [1.0, 4.0]])
+    assert maps.downsample_depth(np.zeros((4, 4))).sum() == 0.0
+
+
+def test_intensity_downsample_is_block_mean_and_odd_sizes_floor():
+    img = np.arange(35, dtype=np.float64).reshape(5, 7)
+    out = maps.downsample_intensity(img)
+    assert out.shape == (2, 3)
+    np.testing.assert_allclose(out[0, 0], (0 + 1 + 7 + 8) / 4.0)
+    np.testing.assert_allclose(out[1, 2], (18 + 19 + 25 + 26) / 4.0)
+
+
+def test_level_intrinsics_match_block_centres():
+    """A 3-D point seen at level-(l-1) pixel x sits at (x - 0.5) / 2 on level l."""
+    cfg = _cfg(640, 480, 554.0)
+    rng = np.random.default_rng(0)
+    P = rng.uniform([-1, -1, 1], [1, 1, 3], size=(50, 3))
+    for l in range(1, 3):
+        a, b = cfg.level_camera(l - 1), cfg.level_camera(l)
+        xa = a["fx"] * P[:, 0] / P[:, 2] + a["cx"]
+        xb = b["fx"] * P[:, 0] / P[:, 2] + b["cx"]
+        ya = a["fy"] * P[:, 1] / P[:, 2] + a["cy"]
+        yb = b["fy"] * P[:, 1] / P[:, 2] + b["cy"]
+        np.testing.assert_allclose(xb, (xa - 0.5) / 2.0, atol=1e-12)
+        np.testing.assert_allclose(yb, (ya - 0.5) / 2.0, atol=1e-12)
+        assert b["width"] == a["width"] // 2 and b["height"] == a["height"] // 2
+
+
+def _plane_depth(cam, n, dist):
+    """Exact z-depth of the plane n . X = dist seen by the camera."""
+    u = np.arange(cam["width"], dtype=np.float64)[None, :]
+    v = np.arange(cam["height"], dtype=np.float64)[:, None]
+    rx = (u - cam["cx"]) / cam["fx"]
+    ry = (v - cam["cy"]) / cam["fy"]
+    return dist / (n[0] * rx + n[1] * ry + n[2])
+
+
+def test_vertex_and_normal_of_a_tilted_plane():
+    cfg = _cfg()
+    cam = cfg.level_camera(0)
+    n = np.array([0.2, -0.3, 1.0])
+    n /= np.linalg.norm(n)
+    d = _plane_depth(cam, n, 2.0)
+    V, vv = maps.vertex_map(d, cam, cfg)
+    assert vv.all()
+    np.testing.assert_allclose(V @ n, 2.0, atol=1e-12)        # every vertex on the plane
+    np.testing.assert_allclose(V[..., 2], d)
+    N, nv = maps.normal_map(V, vv)
+    assert nv[:-1, :-1].all() and not nv[-1].any() and not nv[:, -1].any()
+    np.testing.assert_allclose(N[:-1, :-1], np.broadcast_to(-n, N[:-1, :-1].shape), atol=1e-12)
+
+
+def test_normal_invalid_next_to_missing_depth_and_out_of_range():
+    cfg = _cfg()
+    cam = cfg.level_camera(0)
+    d = np.full((12, 16), 2.0)
+    d[5, 7] = 0.0
+    d[2, 2] = 9.0               # beyond depth_max = 8
+    V, vv = maps.vertex_map(d, cam, cfg)
+    N, nv = maps.normal_map(V, vv)
+    assert not vv[5, 7] and not vv[2, 2]
+    for (y, x) in [(5, 7), (5, 6), (4, 7), (2, 2), (2, 1), (1, 2)]:
+        assert not nv[y, x]
+    assert nv[6, 8] and nv[0, 0]
+
+
+def test_gradient_of_a_ramp_is_exact_inside_and_zero_on_border():
+    u = np.arange(16, dtype=np.float64)[None, :]
+    v = np.arange(12, dtype=np.float64)[:, None]
+    img = 0.1 + 0.02 * u - 0.03 * v + 0 * u * v
+    G = maps.gradient_map(img)
+    np.testing.assert_allclose(G[1:-1, 1:-1, 0], 0.02, atol=1e-15)
+    np.testing.assert_allclose(G[1:-1, 1:-1, 1], -0.03, atol=1e-15)
+    assert np.all(G[0] == 0) and np.all(G[-1] == 0) and np.all(G[:, 0] == 0) and np.all(G[:, -1] == 0)
+
+
+def test_reference_maps_are_moved_into_world():
+    cfg = _cfg()
+    rng = np.random.default_rng(3)
+    d = rng.uniform(1.0, 3.0, (12, 16))
+    I = rng.uniform(0, 1, (12, 16))
+    lv = maps.frame_levels(d, I, cfg)
+    from oracle.so3 import exp_so3
+    R = exp_so3([0.1, -0.2, 0.3])
+    r = np.array([0.5, -1.0, 2.0])
+    ref = maps.reference_from_frame(lv, R, r)
+    for fl, rl in zip(lv, ref):
+        np.testing.assert_allclose(rl.V_W, fl.V @ R.T + r, atol=1e-14)
+        np.testing.assert_allclose(np.linalg.norm(rl.N_W[rl.valid], axis=-1), 1.0, atol=1e-14)
+        np.testing.assert_allclose((rl.N_W @ R)[rl.valid], fl.N[rl.valid], atol=1e-14)
