@@ -1,0 +1,195 @@
+/*
+ * dri.h -- C ABI of the GB300 dense RGB-D-inertial tracking library.
+ *
+ * The library tracks camera streams with the tightly coupled photometric +
+ * point-to-plane ICP + inertial Gauss-Newton of Laidlow et al., "Dense
+ * RGB-D-Inertial SLAM with Map Deformations" (IROS 2017), Sec. IV: per frame it
+ * estimates the current state x1 and refines the previous state x0 (Sec. IV-A),
+ * over a coarse-to-fine image pyramid (Sec. IV-D), and marginalises x0 into a
+ * prior for the next frame (Sec. IV-E, Eq. 8-9).  Every step of a frame runs in
+ * the library's CUDA kernels on one GPU; the host only copies inputs in and
+ * results out.
+ *
+ * Conventions (Sec. II).  Frames: W world (= first camera frame), I inertial
+ * (gravity aligned, z up, shares W's origin), C camera, S IMU sensor.  Poses
+ * T_AB map B coordinates into A.  Quaternions are Hamilton, stored (w, x, y, z).
+ * Images are row-major FP32, depth in metres (<= 0 or outside
+ * [depth_min, depth_max] is invalid), intensity in [0, 1].
+ *
+ * Errors.  Every call returns an int status (DRI_OK = 0 or a negative DRI_E*
+ * code).  No call throws across the ABI.  On error the stream's state is left
+ * as it was before the call unless the description says otherwise.
+ *
+ * Threads.  A stream handle is used by one host thread at a time.  Different
+ * streams may be driven from different threads.
+ */
+#ifndef DRI_H
+#define DRI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define DRI_OK          0
+#define DRI_EINVAL    (-1)   /* bad size, pointer, configuration or IMU order   */
+#define DRI_ENOMEM    (-2)   /* device or host allocation failed; workspace too small */
+#define DRI_EADMIT    (-3)   /* over the server's HBM budget                     */
+#define DRI_ENOTREADY (-4)   /* no frame uploaded, or IMU does not cover [t0, t1] */
+#define DRI_ELOST     (-5)   /* tracking failure; the stream keeps its last good state */
+#define DRI_ETIMEDOUT (-6)   /* a bounded wait expired                           */
+#define DRI_ECUDA     (-7)   /* a CUDA runtime call failed                       */
+
+/* ---- memory kinds for uploads ------------------------------------------ */
+#define DRI_HOST   0
+#define DRI_DEVICE 1
+
+/* ---- precision flags (dri_stream_config.precision_flags) --------------- */
+#define DRI_FP16_MAPS     1  /* normal and intensity-gradient maps stored in FP16 */
+#define DRI_FP32_PARTIALS 2  /* per-block partial sums in FP32 instead of FP64     */
+
+#define DRI_MAX_LEVELS 4
+
+typedef struct dri_stream_s* dri_stream;
+
+/* Per-stream configuration.  dri_config_default fills every field with the
+ * values of the synthetic-dataset column of Table I (Sec. VI) and the readings
+ * documented beside each field. */
+typedef struct {
+    double fx, fy, cx, cy;         /* level-0 intrinsics, pixels                     */
+    int32_t width, height;         /* level-0 image size (>= 8 x 8, <= 8192 x 8192)  */
+    int32_t levels;                /* pyramid levels, 1..DRI_MAX_LEVELS (Sec. IV-D)  */
+    int32_t iters[DRI_MAX_LEVELS]; /* Gauss-Newton iterations per level, [0] finest  */
+    double T_CS[7];                /* IMU in camera: r_CS (3), q_CS (w, x, y, z)      */
+    double sigma_I;                /* photometric noise, W_RGB = 1/sigma_I^2 (Eq. 6)  */
+    double sigma_d;                /* point-to-plane noise, W_ICP = 1/sigma_d^2       */
+    double gyr_nd, acc_nd;         /* IMU white-noise densities (Table I)            */
+    double gyr_rw, acc_rw;         /* bias random-walk densities (Table I)           */
+    double g;                      /* gravity magnitude (Table I)                     */
+    double sigma_grav_rw;          /* gravity-direction noise between frames, rad     */
+    double prior_sigma[5];         /* first-frame prior: pose, v, b_g, b_a, gravity   */
+    double icp_dist_thr;           /* ICP association distance threshold, m           */
+    double icp_angle_thr_deg;      /* ICP normal-angle threshold, degrees             */
+    double depth_min, depth_max;   /* valid depth range, m                            */
+    int32_t min_valid;             /* level-0 correspondences below this: DRI_ELOST   */
+    int32_t precision_flags;       /* DRI_FP16_MAPS | DRI_FP32_PARTIALS               */
+    int32_t max_imu;               /* IMU samples one frame interval may span         */
+    int32_t reserved;
+} dri_stream_config;
+
+/* One IMU sample: time (s), gyro (rad/s) and accelerometer (m/s^2) in S. */
+typedef struct { double t; double gyr[3]; double acc[3]; } dri_imu_sample;
+
+/* State x of Eq. 1: r_WC, q_WC, v_IS (in I), b_g, b_a, q_IW, and its time. */
+typedef struct {
+    double r_WC[3];
+    double q_WC[4];
+    double v_I[3];
+    double bg[3];
+    double ba[3];
+    double q_IW[4];
+    double t;
+} dri_state;
+
+/* Result of one tracked frame.  n_icp / n_rgb are the valid correspondence
+ * counts of the last iteration at each level; cost is Eq. 6 at the last
+ * linearisation (data + IMU terms, prior excluded); status is the frame's
+ * DRI_* code (DRI_OK, or DRI_ELOST with x1 = the previous state). */
+typedef struct {
+    dri_state x1;
+    dri_state x0;
+    int32_t n_icp[DRI_MAX_LEVELS];
+    int32_t n_rgb[DRI_MAX_LEVELS];
+    double cost;
+    int32_t status;
+    int32_t initialised;           /* 1 if this call only initialised the stream     */
+} dri_track_result;
+
+/* Debug / parity output of dri_linearise: every term of Eq. 6 linearised at
+ * one (x0, x1) on one pyramid level, in world coordinates, with H dx = b and
+ * b = -sum J^T W e (Eq. 7).  Matrices are row-major. */
+typedef struct {
+    double H[34 * 34];             /* assembled joint system over [dx0; dx1]          */
+    double b[34];
+    double H_icp[36], b_icp[6];    /* ICP term on x1's pose (dr1, da1)                */
+    double H_rgb[36], b_rgb[6];    /* photometric term, x1 pose block                 */
+    double cost_icp, cost_rgb, cost_imu;
+    double e_imu[18];              /* IMU error x^1(x0) boxminus x1                   */
+    int64_t n_icp, n_rgb;
+} dri_linearisation;
+
+/* Fills *cfg with defaults for a width x height stream: intrinsics scaled from
+ * 277 px focal per 320 px width with the principal point at the image centre,
+ * 3 levels with 10/5/4 iterations, identity T_CS, Table I noise (synthetic),
+ * sigma_I 0.01, sigma_d 0.002 m, ICP thresholds 0.10 m / 20 deg, depth range
+ * [0.3, 8] m.  Returns DRI_EINVAL for a NULL cfg or a size out of range. */
+int dri_config_default(int32_t width, int32_t height, dri_stream_config* cfg);
+
+/* Device bytes one stream needs for its maps, partials and state (the
+ * workspace passed to dri_create_stream).  DRI_EINVAL for a bad config. */
+int dri_stream_workspace_bytes(const dri_stream_config* cfg, size_t* bytes);
+
+/* Creates a stream.  cfg and x_init are copied.  cuda_stream is the
+ * cudaStream_t every operation of this stream is ordered on (NULL = legacy
+ * default stream).  workspace is caller-owned device memory of at least
+ * dri_stream_workspace_bytes(cfg) bytes, 256-byte aligned, kept alive until
+ * dri_destroy_stream; if NULL the library allocates (and frees) it.  The first
+ * dri_track call only initialises: x1 := x_init, the first-frame prior, and the
+ * frame becomes the reference (W = first camera frame, Sec. II). */
+int dri_create_stream(const dri_stream_config* cfg, const dri_state* x_init, void* cuda_stream,
+                      void* workspace, size_t workspace_bytes, dri_stream* out);
+
+/* Waits for the stream's work, frees what the library allocated. */
+int dri_destroy_stream(dri_stream s);
+
+/* Uploads the live frame at time t (seconds, strictly increasing): depth and
+ * intensity, height rows of width floats, rows pitch_bytes apart (0 = packed),
+ * on the host (DRI_HOST, copied before the call returns its staging) or on the
+ * device (DRI_DEVICE, copied stream-ordered).  The caller keeps ownership. */
+int dri_upload_frame(dri_stream s, double t, const float* depth, const float* intensity,
+                     size_t pitch_bytes, int32_t mem_kind);
+
+/* Appends IMU samples (host memory, n >= 0) with strictly increasing times,
+ * later than every sample already pushed.  DRI_EINVAL otherwise. */
+int dri_push_imu(dri_stream s, const dri_imu_sample* samples, size_t n);
+
+/* Tracks the uploaded frame (Sec. IV): IMU pre-integration, coarse-to-fine
+ * Gauss-Newton over x0 and x1 with the photometric, ICP, IMU and prior terms,
+ * marginalisation of x0 and the swap of the reference to this frame.
+ * out != NULL: waits and fills *out, returning DRI_OK or the frame's error.
+ * out == NULL: returns after enqueuing; read the state with dri_get_state.
+ * DRI_ENOTREADY when no new frame is uploaded or the IMU samples do not cover
+ * [t_previous_frame, t_frame]. */
+int dri_track(dri_stream s, dri_track_result* out);
+
+/* Waits for the stream and copies out x1 and, when non-NULL, the prior
+ * H* (17 x 17, row-major) and b* (17) that the next frame will use. */
+int dri_get_state(dri_stream s, dri_state* x1, double* H_prior, double* b_prior);
+
+/* Replaces x1 and, when non-NULL, the prior (checkpoint / resume).  The prior
+ * mean becomes x1. */
+int dri_set_state(dri_stream s, const dri_state* x1, const double* H_prior, const double* b_prior);
+
+/* Parity / debug entry: linearises every term of Eq. 6 at the given (x0, x1)
+ * on pyramid level `level` of the uploaded frame against the stream's
+ * reference, prior and IMU, without changing the stream.  W_IMU is taken at x0.
+ * flags (nullable, host, width_l * height_l bytes) receives per pixel
+ * bit 0 = ICP correspondence valid, bit 1 = photometric valid. */
+int dri_linearise(dri_stream s, int32_t level, const dri_state* x0, const dri_state* x1,
+                  dri_linearisation* out, uint8_t* flags);
+
+/* Static description of a status code. */
+const char* dri_status_string(int code);
+
+/* Kernel launches this stream has issued since creation (all kernels of the
+ * library, counted on the host at launch). */
+int dri_launch_count(dri_stream s, int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DRI_H */

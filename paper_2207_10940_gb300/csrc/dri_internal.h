@@ -1,0 +1,143 @@
+// Internal layout shared by the host API and the kernels of the tracking library.
+//
+// Device memory of one stream (one workspace allocation, 256-byte aligned parts):
+//   Ctrl           FP64 state block: x, the iterates x0 / x1, the prior (H*, b*, xbar),
+//                  W_IMU, the reference pose, the per-iteration pixel transforms, the
+//                  folded sums and the last joint system (Sec. IV-D/E).
+//   ImuBuf         header (t0, t1, n) + the samples covering [t0, t1].
+//   input depth/I  level-0 upload target (fixed address, so uploads never race the
+//                  buffer-set flip decided on the device).
+//   2 map sets     per level: depth, normal (3 planes), intensity, gradient (2 planes).
+//                  Set ctrl.ref_index is the reference, the other the live frame; a
+//                  tracked frame flips the index on the device (no host round trip).
+//   partials       per-block sums of the pixel kernel (FP64 or FP32).
+//   flags          per-pixel validity bytes for the parity entry point.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dri.h"
+
+namespace dri {
+
+constexpr int kMaxLevels = DRI_MAX_LEVELS;
+constexpr int kSums = 29;             // per term: 21 (upper J J^T) + 6 (J e) + e^2 + count
+constexpr int kSumsAll = 2 * kSums;   // ICP then photometric
+constexpr int kTrackThreadsX = 32;
+constexpr int kTrackThreadsY = 8;
+
+struct DState {                       // Eq. 1
+  double r[3];
+  double q[4];
+  double v[3];
+  double bg[3];
+  double ba[3];
+  double qg[4];
+};
+
+struct Ctrl {
+  DState x;                           // state after the last tracked frame
+  DState x0, x1;                      // Gauss-Newton iterates of the current frame
+  DState xbar;                        // prior mean
+  DState xstart;                      // state at frame start (restored on DRI_ELOST)
+  double Hs[17 * 17];                 // prior information H* (Eq. 8a)
+  double bs[17];                      // prior vector b* (Eq. 8b)
+  double Wimu[18 * 18];               // IMU weight
+  double Rref[9], rref[3];            // pose T_ref the reference maps were made at
+  double sums[64];                    // folded pixel sums of the current iteration
+  double H[34 * 34], b[34], d[34];    // last joint system and step (marginalisation)
+  double cost;
+  double t_state;                     // time of x
+  float xf_icp[12];                   // R_ref^T R_1 - I (row-major), R_ref^T (r_1 - r_ref)
+  float xf_rgb[12];                   // R_0^T R_1 - I, R_0^T (r_1 - r_0)
+  int32_t n_icp[kMaxLevels], n_rgb[kMaxLevels];
+  int32_t status;                     // DRI_OK or the frame's error
+  int32_t ref_index;                  // map set holding the reference
+  int32_t initialised;                // reference exists
+  int32_t iterations;
+  uint32_t block_counter;             // last-block detection of the pixel kernel
+  uint32_t pad1[3];
+};
+
+struct ImuHeader {
+  double t0, t1;
+  int32_t n;
+  int32_t pad;
+};
+
+struct LevelGeom {
+  int32_t w, h;
+  float fx, fy, cx, cy, ifx, ify;
+};
+
+// Pointers of one pyramid level in both map sets.
+struct LevelMaps {
+  float* depth[2];
+  void* normal[2];                    // 3 planes (x, y, z) of `plane` elements, FP32 or FP16
+  float* inten[2];
+  void* grad[2];                      // 2 planes (gx, gy)
+  int64_t plane;                      // elements per plane (>= w * h, padded)
+};
+
+struct StreamLayout {
+  size_t ctrl, imu, in_depth, in_inten, partials, flags, lin_out, total;
+  size_t level_off[kMaxLevels][2][4];  // per level, per set: depth, normal, inten, grad
+  int64_t plane[kMaxLevels];
+  int max_blocks;
+  int imu_cap;
+  int map_elem_bytes;                 // 4 (FP32) or 2 (FP16) for normal / gradient
+};
+
+struct TrackParams {
+  LevelGeom g;
+  LevelMaps m;
+  Ctrl* ctrl;
+  void* partials;
+  uint8_t* flags;
+  int32_t nblocks;
+  int32_t ppt;                        // pixel rows per thread
+  float depth_min, depth_max;
+  float icp_dist2, icp_cos;
+};
+
+struct SolveParams {
+  Ctrl* ctrl;
+  const ImuHeader* imu;               // followed by the samples
+  int32_t level;
+  int32_t last;                       // 1 on the frame's last iteration
+  // configuration (copied from dri_stream_config)
+  double R_CS[9], r_CS[3];
+  double W_icp, W_rgb;
+  double gyr_nd, acc_nd, gyr_rw, acc_rw, g, sigma_grav;
+  double prior_sigma[5];
+  int32_t min_valid;
+  int32_t imu_cap;
+};
+
+StreamLayout make_layout(const dri_stream_config& cfg);
+LevelGeom level_geom(const dri_stream_config& cfg, int level);
+
+// ---- kernel launchers (return cudaGetLastError()) ------------------------
+cudaError_t launch_copy_input(const float* in_d, const float* in_i, const LevelMaps& m0,
+                              const Ctrl* ctrl, int w, int h, cudaStream_t s);
+cudaError_t launch_pyr_down(const LevelMaps& fine, const LevelMaps& coarse, const Ctrl* ctrl,
+                            int wf, int hf, int wc, int hc, cudaStream_t s);
+cudaError_t launch_normals(const LevelMaps& m, const Ctrl* ctrl, const LevelGeom& g,
+                           float dmin, float dmax, bool fp16, int which_set, cudaStream_t s);
+cudaError_t launch_gradient(const LevelMaps& m, const Ctrl* ctrl, int w, int h, bool fp16,
+                            cudaStream_t s);
+cudaError_t launch_track(const TrackParams& p, bool fp16, bool fp32_partials, cudaStream_t s);
+int track_grid_blocks(int w, int h, int ppt);
+
+cudaError_t launch_frame_begin(const SolveParams& p, cudaStream_t s);
+cudaError_t launch_gn_step(const SolveParams& p, cudaStream_t s);
+cudaError_t launch_frame_end(const SolveParams& p, cudaStream_t s);
+cudaError_t launch_frame_init(const SolveParams& p, cudaStream_t s);
+cudaError_t launch_linearise_begin(const SolveParams& p, const DState& x0, const DState& x1,
+                                   cudaStream_t s);
+cudaError_t launch_linearise_end(const SolveParams& p, dri_linearisation* out, cudaStream_t s);
+
+}  // namespace dri

@@ -1,0 +1,333 @@
+"""Python binding of the C ABI in include/dri.h (argument marshalling only).
+
+Every function keeps the C name and argument order; a negative status raises
+DriError (dri_track returns the frame status in its result instead).  Device
+memory for a stream's workspace and the CUDA stream come from PyTorch: pass a
+torch.cuda.Stream and let dri_create_stream allocate the workspace as a torch
+uint8 tensor, or pass your own device pointer.  The compute path is libdri.so
+only: if the library is missing this module raises on import of the library,
+it never falls back to another implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DRI_OK = 0
+DRI_EINVAL = -1
+DRI_ENOMEM = -2
+DRI_EADMIT = -3
+DRI_ENOTREADY = -4
+DRI_ELOST = -5
+DRI_ETIMEDOUT = -6
+DRI_ECUDA = -7
+DRI_HOST = 0
+DRI_DEVICE = 1
+DRI_FP16_MAPS = 1
+DRI_FP32_PARTIALS = 2
+DRI_MAX_LEVELS = 4
+
+c_double_p = ctypes.POINTER(ctypes.c_double)
+
+
+class dri_stream_config(ctypes.Structure):
+    _fields_ = [
+        ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double),
+        ("cy", ctypes.c_double),
+        ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("levels", ctypes.c_int32),
+        ("iters", ctypes.c_int32 * DRI_MAX_LEVELS),
+        ("T_CS", ctypes.c_double * 7),
+        ("sigma_I", ctypes.c_double), ("sigma_d", ctypes.c_double),
+        ("gyr_nd", ctypes.c_double), ("acc_nd", ctypes.c_double),
+        ("gyr_rw", ctypes.c_double), ("acc_rw", ctypes.c_double),
+        ("g", ctypes.c_double), ("sigma_grav_rw", ctypes.c_double),
+        ("prior_sigma", ctypes.c_double * 5),
+        ("icp_dist_thr", ctypes.c_double), ("icp_angle_thr_deg", ctypes.c_double),
+        ("depth_min", ctypes.c_double), ("depth_max", ctypes.c_double),
+        ("min_valid", ctypes.c_int32), ("precision_flags", ctypes.c_int32),
+        ("max_imu", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class dri_imu_sample(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("gyr", ctypes.c_double * 3), ("acc", ctypes.c_double * 3)]
+
+
+class dri_state(ctypes.Structure):
+    _fields_ = [
+        ("r_WC", ctypes.c_double * 3), ("q_WC", ctypes.c_double * 4), ("v_I", ctypes.c_double * 3),
+        ("bg", ctypes.c_double * 3), ("ba", ctypes.c_double * 3), ("q_IW", ctypes.c_double * 4),
+        ("t", ctypes.c_double),
+    ]
+
+
+class dri_track_result(ctypes.Structure):
+    _fields_ = [
+        ("x1", dri_state), ("x0", dri_state),
+        ("n_icp", ctypes.c_int32 * DRI_MAX_LEVELS), ("n_rgb", ctypes.c_int32 * DRI_MAX_LEVELS),
+        ("cost", ctypes.c_double), ("status", ctypes.c_int32), ("initialised", ctypes.c_int32),
+    ]
+
+
+class dri_linearisation(ctypes.Structure):
+    _fields_ = [
+        ("H", ctypes.c_double * (34 * 34)), ("b", ctypes.c_double * 34),
+        ("H_icp", ctypes.c_double * 36), ("b_icp", ctypes.c_double * 6),
+        ("H_rgb", ctypes.c_double * 36), ("b_rgb", ctypes.c_double * 6),
+        ("cost_icp", ctypes.c_double), ("cost_rgb", ctypes.c_double), ("cost_imu", ctypes.c_double),
+        ("e_imu", ctypes.c_double * 18),
+        ("n_icp", ctypes.c_int64), ("n_rgb", ctypes.c_int64),
+    ]
+
+
+class DriError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load_library():
+    """Loads libdri.so (built in-tree by build.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2207_10940_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    sig = {
+        "dri_config_default": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, P(dri_stream_config)]),
+        "dri_stream_workspace_bytes": (ctypes.c_int, [P(dri_stream_config), P(ctypes.c_size_t)]),
+        "dri_create_stream": (ctypes.c_int, [P(dri_stream_config), P(dri_state), ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_size_t, P(ctypes.c_void_p)]),
+        "dri_destroy_stream": (ctypes.c_int, [ctypes.c_void_p]),
+        "dri_upload_frame": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32]),
+        "dri_push_imu": (ctypes.c_int, [ctypes.c_void_p, P(dri_imu_sample), ctypes.c_size_t]),
+        "dri_track": (ctypes.c_int, [ctypes.c_void_p, P(dri_track_result)]),
+        "dri_get_state": (ctypes.c_int, [ctypes.c_void_p, P(dri_state), c_double_p, c_double_p]),
+        "dri_set_state": (ctypes.c_int, [ctypes.c_void_p, P(dri_state), c_double_p, c_double_p]),
+        "dri_linearise": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, P(dri_state), P(dri_state),
+                                         P(dri_linearisation), ctypes.c_void_p]),
+        "dri_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "dri_launch_count": (ctypes.c_int, [ctypes.c_void_p, P(ctypes.c_int64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(code):
+    return load_library().dri_status_string(int(code)).decode()
+
+
+def _check(code, where):
+    if code < 0:
+        raise DriError(code, where)
+    return code
+
+
+# ---------------------------------------------------------------------------
+# the C entry points, same names
+# ---------------------------------------------------------------------------
+
+def dri_config_default(width, height):
+    cfg = dri_stream_config()
+    _check(load_library().dri_config_default(int(width), int(height), ctypes.byref(cfg)),
+           "dri_config_default")
+    return cfg
+
+
+def dri_stream_workspace_bytes(cfg):
+    n = ctypes.c_size_t()
+    _check(load_library().dri_stream_workspace_bytes(ctypes.byref(cfg), ctypes.byref(n)),
+           "dri_stream_workspace_bytes")
+    return n.value
+
+
+def dri_create_stream(cfg, x_init, cuda_stream=None, workspace=None, workspace_bytes=0):
+    """cuda_stream: a torch.cuda.Stream, a raw cudaStream_t int, or None (legacy default).
+    workspace: a device pointer (int) or a torch tensor; None lets the library allocate."""
+    h = ctypes.c_void_p()
+    cs = getattr(cuda_stream, "cuda_stream", cuda_stream)
+    ws = workspace
+    if ws is not None and hasattr(ws, "data_ptr"):
+        workspace_bytes = ws.numel() * ws.element_size()
+        ws = ws.data_ptr()
+    _check(load_library().dri_create_stream(ctypes.byref(cfg), ctypes.byref(x_init),
+                                            ctypes.c_void_p(cs or 0), ctypes.c_void_p(ws or 0),
+                                            ctypes.c_size_t(workspace_bytes), ctypes.byref(h)),
+           "dri_create_stream")
+    return h
+
+
+def dri_destroy_stream(s):
+    return _check(load_library().dri_destroy_stream(s), "dri_destroy_stream")
+
+
+def _ptr(a):
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def dri_upload_frame(s, t, depth, intensity, pitch_bytes=0, mem_kind=None):
+    """depth / intensity: float32 numpy arrays (host) or torch tensors (host or device)."""
+    if mem_kind is None:
+        mem_kind = DRI_DEVICE if (hasattr(depth, "is_cuda") and depth.is_cuda) else DRI_HOST
+    for a in (depth, intensity):
+        dt = getattr(a, "dtype", None)
+        if str(dt) not in ("float32", "torch.float32"):
+            raise TypeError("depth and intensity must be float32")
+    if isinstance(depth, np.ndarray) and not (depth.flags.c_contiguous and intensity.flags.c_contiguous):
+        raise ValueError("host arrays must be C-contiguous")
+    return _check(load_library().dri_upload_frame(s, float(t), ctypes.c_void_p(_ptr(depth)),
+                                                  ctypes.c_void_p(_ptr(intensity)), pitch_bytes,
+                                                  mem_kind), "dri_upload_frame")
+
+
+def imu_array(samples):
+    """(N, 7) array [t, gyr(3), acc(3)] -> ctypes array of dri_imu_sample."""
+    samples = np.ascontiguousarray(samples, dtype=np.float64).reshape(-1, 7)
+    arr = (dri_imu_sample * len(samples))()
+    ctypes.memmove(arr, samples.ctypes.data, samples.nbytes)
+    return arr
+
+
+def dri_push_imu(s, samples):
+    arr = samples if isinstance(samples, ctypes.Array) else imu_array(samples)
+    return _check(load_library().dri_push_imu(s, arr, len(arr)), "dri_push_imu")
+
+
+def dri_track(s, wait=True):
+    """Returns the dri_track_result (wait=True; its status is DRI_OK or DRI_ELOST) or
+    None (asynchronous).  Other errors raise DriError."""
+    if not wait:
+        _check(load_library().dri_track(s, None), "dri_track")
+        return None
+    res = dri_track_result()
+    code = load_library().dri_track(s, ctypes.byref(res))
+    if code < 0 and code != DRI_ELOST:
+        raise DriError(code, "dri_track")
+    return res
+
+
+def dri_get_state(s, with_prior=False):
+    x = dri_state()
+    if with_prior:
+        H = np.zeros((17, 17))
+        b = np.zeros(17)
+        _check(load_library().dri_get_state(s, ctypes.byref(x), H.ctypes.data_as(c_double_p),
+                                            b.ctypes.data_as(c_double_p)), "dri_get_state")
+        return x, H, b
+    _check(load_library().dri_get_state(s, ctypes.byref(x), None, None), "dri_get_state")
+    return x
+
+
+def dri_set_state(s, x1, H_prior=None, b_prior=None):
+    Hp = None if H_prior is None else np.ascontiguousarray(H_prior, dtype=np.float64)
+    bp = None if b_prior is None else np.ascontiguousarray(b_prior, dtype=np.float64)
+    return _check(load_library().dri_set_state(
+        s, ctypes.byref(x1), None if Hp is None else Hp.ctypes.data_as(c_double_p),
+        None if bp is None else bp.ctypes.data_as(c_double_p)), "dri_set_state")
+
+
+def dri_linearise(s, level, x0, x1, want_flags=False, shape=None):
+    out = dri_linearisation()
+    flags = None
+    fptr = None
+    if want_flags:
+        flags = np.zeros(shape, dtype=np.uint8)
+        fptr = ctypes.c_void_p(flags.ctypes.data)
+    code = load_library().dri_linearise(s, int(level), ctypes.byref(x0), ctypes.byref(x1),
+                                        ctypes.byref(out), fptr)
+    _check(code, "dri_linearise")
+    return out, flags
+
+
+def dri_launch_count(s):
+    n = ctypes.c_int64()
+    _check(load_library().dri_launch_count(s, ctypes.byref(n)), "dri_launch_count")
+    return n.value
+
+
+# ---------------------------------------------------------------------------
+# conversions (marshalling only)
+# ---------------------------------------------------------------------------
+
+def state_from_dict(d, t=0.0):
+    x = dri_state()
+    x.r_WC[:] = [float(v) for v in d["r_WC"]]
+    x.q_WC[:] = [float(v) for v in d["q_WC"]]
+    x.v_I[:] = [float(v) for v in d["v_I"]]
+    x.bg[:] = [float(v) for v in d["bg"]]
+    x.ba[:] = [float(v) for v in d["ba"]]
+    x.q_IW[:] = [float(v) for v in d["q_IW"]]
+    x.t = float(d.get("t", t))
+    return x
+
+
+def state_to_dict(x):
+    return dict(r_WC=np.array(x.r_WC[:]), q_WC=np.array(x.q_WC[:]), v_I=np.array(x.v_I[:]),
+                bg=np.array(x.bg[:]), ba=np.array(x.ba[:]), q_IW=np.array(x.q_IW[:]), t=x.t)
+
+
+def config_for(width, height, fx, fy, cx, cy, levels, iters, q_CS=None, r_CS=None, **overrides):
+    """Stream configuration from intrinsics, schedule and extrinsic T_CS; other
+    fields keep dri_config_default's values."""
+    cfg = dri_config_default(width, height)
+    cfg.fx, cfg.fy, cfg.cx, cfg.cy = float(fx), float(fy), float(cx), float(cy)
+    cfg.levels = int(levels)
+    for i in range(DRI_MAX_LEVELS):
+        cfg.iters[i] = int(iters[i]) if i < len(iters) else 0
+    if q_CS is not None:
+        cfg.T_CS[3:7] = [float(v) for v in q_CS]
+    if r_CS is not None:
+        cfg.T_CS[0:3] = [float(v) for v in r_CS]
+    for k, v in overrides.items():
+        if k == "prior_sigma":
+            cfg.prior_sigma[:] = list(v)
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+class Stream:
+    """A tracking stream whose workspace is a torch uint8 device tensor and whose
+    work is ordered on a torch CUDA stream."""
+
+    def __init__(self, cfg, x_init, torch_stream=None, device="cuda"):
+        import torch
+        self.cfg = cfg
+        self.torch_stream = torch_stream if torch_stream is not None else torch.cuda.Stream(device)
+        nbytes = dri_stream_workspace_bytes(cfg)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        ptr = self.workspace.data_ptr()
+        aligned = (ptr + 255) // 256 * 256
+        self.handle = dri_create_stream(cfg, x_init, self.torch_stream, aligned, nbytes)
+
+    def close(self):
+        if self.handle is not None:
+            dri_destroy_stream(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,63 @@
+"""Shared helpers of the GPU parity tests: matching oracle / library configurations,
+state conversions and the tolerance checks of the parity bar.
+
+Tolerances (stated once here, used by every parity test):
+* valid-correspondence counts: bit-exact per pixel outside the oracle's margin
+  pixels (1e-4 px of a bound or rounding boundary, relative 1e-5 of a threshold);
+* J^T J and J^T r entries: |dH_ij| <= 1e-5 sqrt(H_ii H_jj) and
+  |db_i| <= 1e-5 sqrt(H_ii C) with C the cost of the terms in the system;
+* final pose: 1e-6 rad and 1e-6 m.
+"""
+import numpy as np
+
+from conftest import oracle_config
+from oracle.so3 import State, log_so3
+from paper_2207_10940_gb300 import dri, synth
+
+REL = 1e-5
+POSE_RAD = 1e-6
+POSE_M = 1e-6
+
+
+def configs(seq, levels, iters, precision_flags=0, **kw):
+    ocfg = oracle_config(seq, levels=levels, iters=iters, **kw)
+    cam = seq.cam
+    dcfg = dri.config_for(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, levels, iters,
+                          q_CS=synth.matrix_to_quat(seq.R_CS), r_CS=seq.r_CS,
+                          precision_flags=precision_flags, **kw)
+    return ocfg, dcfg
+
+
+def to_dri(x, t=0.0):
+    return dri.state_from_dict(x.to_dict() if isinstance(x, State) else x, t)
+
+
+def to_oracle(x):
+    return State.from_dict(dri.state_to_dict(x))
+
+
+def check_system(H_g, b_g, H_o, b_o, cost, rel=REL, what=""):
+    H_g, b_g, H_o, b_o = map(np.asarray, (H_g, b_g, H_o, b_o))
+    d = np.sqrt(np.maximum(np.diag(H_o), 0.0))
+    tolH = rel * np.outer(d, d)
+    errH = np.abs(H_g - H_o)
+    worst = np.max(errH / np.maximum(tolH, 1e-300))
+    assert np.all(errH <= tolH), f"{what} H: worst err/tol {worst:.3g}"
+    tolb = rel * np.sqrt(np.maximum(np.diag(H_o), 0.0) * max(cost, 0.0))
+    errb = np.abs(b_g - b_o)
+    worstb = np.max(errb / np.maximum(tolb, 1e-300))
+    assert np.all(errb <= tolb), f"{what} b: worst err/tol {worstb:.3g}"
+    return worst, worstb
+
+
+def pose_error(xa, xb):
+    """(rotation angle between the two camera orientations, position distance)."""
+    a = xa if isinstance(xa, State) else to_oracle(xa)
+    b = xb if isinstance(xb, State) else to_oracle(xb)
+    return float(np.linalg.norm(log_so3(a.R @ b.R.T))), float(np.linalg.norm(a.r - b.r))
+
+
+def new_stream(dcfg, x_init):
+    import torch
+    return dri.Stream(dcfg, to_dri(x_init, x_init.get("t", 0.0) if isinstance(x_init, dict) else 0.0),
+                      torch.cuda.Stream())
