@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Benchmark of the tracking hot path: tracked frames/s at 640x480.
+
+Workload (one step = one tracked frame, i.e. one pass of every step of the
+hot path: pyramid, normal and gradient maps, 19 Gauss-Newton iterations of the
+fused photometric + ICP kernel with the FP64 IMU / solver step, marginalisation
+and the reference swap): a single camera stream of the seeded synthetic
+640x480 RGB-D + 400 Hz IMU sequence (sinusoidal path, peak 1.5 m/s and
+90 deg/s, 100-frame period rendered once and looped), 3 pyramid levels with
+10/5/4 iterations.  Frames live on the device before timing starts; the 100
+distinct frames (245 MB) exceed the 129 MB L2, so every step reads a frame
+that is not cache resident.
+
+Output: one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W, H = 640, 480
+LEVELS, ITERS = 3, (10, 5, 4)
+FPS = 30.0
+N_UNIQUE = 100
+SEQ_SEED = 2
+BYTES_PER_PIXEL_ITER = 48     # FP32 maps: see the design doc (live 20 B + reference 28 B)
+PIXEL_ITERS_PER_FRAME = sum((W >> l) * (H >> l) * ITERS[l] for l in range(LEVELS))
+
+
+def _render_one(args):
+    from paper_2207_10940_gb300 import synth
+    seed, i = args
+    seq = synth.sinusoid_sequence(seed=seed, cam=synth.CAM_640, n_frames=N_UNIQUE, rate=400.0,
+                                  render_frames=False)
+    return synth.render_frame(seq, i, seed=seed)
+
+
+def make_inputs(n_frames_total, workers):
+    """Sequence metadata, the N_UNIQUE rendered frames and IMU samples up to the
+    last timed frame (the path is periodic, so frame k shows frame k % 100)."""
+    from paper_2207_10940_gb300 import synth
+    seq = synth.sinusoid_sequence(seed=SEQ_SEED, cam=synth.CAM_640, n_frames=N_UNIQUE, rate=400.0,
+                                  render_frames=False)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        frames = pool.map(_render_one, [(SEQ_SEED, i) for i in range(N_UNIQUE)])
+    imu = synth.sequence_imu(seq, (n_frames_total + 1) / FPS, seed=SEQ_SEED)
+    return seq, frames, imu
+
+
+def dri_config(seq, flags=0):
+    from paper_2207_10940_gb300 import dri, synth
+    cam = seq.cam
+    return dri.config_for(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, LEVELS, ITERS,
+                          q_CS=synth.matrix_to_quat(seq.R_CS), r_CS=seq.r_CS, precision_flags=flags)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def track_traffic():
+    """DRAM bytes per pixel-iteration of the track kernel from the committed ncu
+    summary, or None if the kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "track_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_2207_10940_gb300", "csrc", "track.cu")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    h = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    if d.get("track_cu_sha1") != h:
+        return None
+    return float(d["dram_bytes_per_pixel_iter"])
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl) if v == "Active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded samples)
+# ---------------------------------------------------------------------------
+
+def oracle_frames_per_s(seq, frames, imu, budget_s):
+    """Whole frames tracked by the FP64 oracle until the time budget is spent."""
+    from oracle import gn
+    from oracle.params import TrackerConfig
+    from paper_2207_10940_gb300 import synth
+    cam = seq.cam
+    cfg = TrackerConfig(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, levels=LEVELS,
+                        iters=ITERS, R_CS=seq.R_CS, r_CS=seq.r_CS)
+    tr = gn.Tracker(cfg, synth.initial_state(seq))
+    tr.push_imu(imu)
+    tr.track(frames[0][0], frames[0][1], 0.0)
+    n, t_total = 0, 0.0
+    while t_total < budget_s or n == 0:
+        i = n + 1
+        t = time.perf_counter()
+        tr.track(frames[i % N_UNIQUE][0], frames[i % N_UNIQUE][1], i / FPS)
+        t_total += time.perf_counter() - t
+        n += 1
+    return n / t_total, n, t_total
+
+
+def oracle_band_steps(seq, frames, imu, steps, warmup, budget_s):
+    """Reference arm: each step is one oracle Gauss-Newton iteration (linearise
+    all terms, assemble, solve) on a band of level-0 rows of the second frame;
+    frames/s = processed pixel-iterations / time / pixel-iterations per frame."""
+    from oracle import gn, imu as imu_mod, maps
+    from oracle.gn import cholesky_solve
+    from oracle.params import TrackerConfig
+    from paper_2207_10940_gb300 import synth
+    cam = seq.cam
+    cfg = TrackerConfig(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, levels=LEVELS,
+                        iters=ITERS, R_CS=seq.R_CS, r_CS=seq.r_CS)
+    tr = gn.Tracker(cfg, synth.initial_state(seq))
+    tr.push_imu(imu)
+    tr.track(frames[0][0], frames[0][1], 0.0)
+    lv = maps.frame_levels(frames[1][0], frames[1][1], cfg)
+    x0 = tr.x.copy()
+    x1 = tr.x.copy()
+    t0, t1 = 0.0, 1.0 / FPS
+    Wimu, _ = imu_mod.weight(x0, tr.imu, t0, t1, cfg)
+
+    def band(rows, r0):
+        import copy
+        b = copy.copy(lv[0])
+        sl = slice(r0, r0 + rows)
+        b.depth, b.V, b.V_valid, b.N, b.N_valid, b.I = (b.depth[sl], b.V[sl], b.V_valid[sl],
+                                                         b.N[sl], b.N_valid[sl], b.I[sl])
+        return [b] + lv[1:]
+
+    def one(rows, r0):
+        Hs, bs, _ = tr.linearise_all(band(rows, r0), 0, x0, x1, t0, t1, Wimu)
+        cholesky_solve(Hs, bs)
+
+    t = time.perf_counter()
+    one(8, 0)
+    per_row = (time.perf_counter() - t) / 8
+    rows = int(max(1, min(H, budget_s / max(1, steps + warmup) / per_row)))
+    r0 = 0
+    for _ in range(warmup):
+        one(rows, r0)
+        r0 = (r0 + rows) % max(1, H - rows + 1)
+    px = 0
+    t = time.perf_counter()
+    for _ in range(steps):
+        one(rows, r0)
+        px += rows * W
+        r0 = (r0 + rows) % max(1, H - rows + 1)
+    el = time.perf_counter() - t
+    return px / PIXEL_ITERS_PER_FRAME / el, rows, el
+
+
+# ---------------------------------------------------------------------------
+# main
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    seq, frames, imu = make_inputs(4, min(16, os.cpu_count() or 4))
+    value, rows, el = oracle_band_steps(seq, frames, imu, args.steps, args.warmup, budget_s=120.0)
+    line = {
+        "impl": "reference", "metric": "tracked frames/s at 640x480 (plain single stream)",
+        "value": value, "unit": "frames/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * el / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_json(),
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step one oracle Gauss-Newton iteration on {rows} level-0 rows "
+                                   f"of a 640x480 frame; frames/s = pixel-iterations/s / "
+                                   f"{PIXEL_ITERS_PER_FRAME}"},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_json():
+    return {"workload": "single stream, 640x480 RGB-D + 400 Hz IMU, 3 levels 10/5/4 GN iterations",
+            "model": "dense RGB-D-inertial tracking (photometric + ICP + IMU, 34-D joint GN)",
+            "global_batch": 1, "seq_len": 1, "parallelism": "replicas (one stream per GPU)",
+            "width": W, "height": H, "levels": LEVELS, "iters": list(ITERS),
+            "l2": "inputs larger than L2 (100 distinct frames, 245 MB, cycled)"}
+
+
+def run_ours(args):
+    rank, local, world = dist_env()
+    seq, frames, imu = make_inputs(1 + args.warmup + 2 * args.steps + args.profile_frames + 2,
+                                   min(16, os.cpu_count() or 4))
+    import torch
+    from paper_2207_10940_gb300 import build, dri
+    build.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    d_dev = torch.stack([torch.from_numpy(f[0]) for f in frames]).to(dev)
+    i_dev = torch.stack([torch.from_numpy(f[1]) for f in frames]).to(dev)
+    d_pin = torch.stack([torch.from_numpy(f[0]) for f in frames]).pin_memory()
+    i_pin = torch.stack([torch.from_numpy(f[1]) for f in frames]).pin_memory()
+    torch.cuda.synchronize(dev)      # the library reads these on its own stream
+    from paper_2207_10940_gb300 import synth
+    cfg = dri_config(seq)
+    st = dri.Stream(cfg, dri.state_from_dict(synth.initial_state(seq)), torch.cuda.Stream(dev))
+    h = st.handle
+    ts = st.torch_stream
+    dri.dri_push_imu(h, imu)
+    k = 0
+
+    def step(device_inputs=True, wait=False):
+        nonlocal k
+        j = k % N_UNIQUE
+        if device_inputs:
+            dri.dri_upload_frame(h, k / FPS, d_dev[j], i_dev[j], mem_kind=dri.DRI_DEVICE)
+        else:
+            dri.dri_upload_frame(h, k / FPS, d_pin[j], i_pin[j], mem_kind=dri.DRI_HOST)
+        r = dri.dri_track(h, wait=wait)
+        k += 1
+        return r
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+
+    r0 = step(wait=True)
+    assert r0.initialised == 1
+    for _ in range(args.warmup):
+        step()
+    # ---- timed region: K frames, inputs resident on the device ----
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    n0 = dri.dri_launch_count(h)
+    barrier()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(ts):
+            evs[0].record(ts)
+        for i in range(args.steps):
+            step()
+            with torch.cuda.stream(ts):
+                evs[i + 1].record(ts)
+        barrier()
+    launches = dri.dri_launch_count(h) - n0
+    ok_frames, failed_frames = dri.dri_frame_counts(h)
+    per = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)])
+    total_ms = evs[0].elapsed_time(evs[-1])
+    state = dri.dri_get_state(h)
+    t_max = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # ---- kernel timing pass (same frames, events around every launch) ----
+    dri.dri_profile_enable(h, True)
+    for _ in range(args.profile_frames):
+        step()
+    prof = dri.dri_profile_read(h)
+    dri.dri_profile_enable(h, False)
+    t_track_ms = prof.ms[dri.DRI_KC_TRACK]
+    px_track = prof.pixels[dri.DRI_KC_TRACK]
+    n_track = prof.launches[dri.DRI_KC_TRACK]
+    achieved = BYTES_PER_PIXEL_ITER * px_track / (t_track_ms / 1000.0) / 1e9
+    peak, peak_kind = measured_peaks()
+    tr_bpp = track_traffic()
+
+    # ---- end to end: host (pinned) inputs, result read back every frame ----
+    barrier()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        res = step(device_inputs=False, wait=True)
+    barrier()
+    e2e_s = time.perf_counter() - t
+    h2d, d2h = dri.dri_io_bytes(h)
+    e2e = world * args.steps / e2e_s
+    if world > 1:
+        torch.distributed.barrier()
+    st.close()
+    if rank != 0:
+        return 0
+
+    budget = float(os.environ.get("DRI_BENCH_ORACLE_SECONDS", "15"))
+    o_fps, o_n, o_t = oracle_frames_per_s(seq, frames, imu, budget)
+    kc = {name: {"launches": int(prof.launches[c]), "ms": round(prof.ms[c], 4)}
+          for name, c in (("maps", dri.DRI_KC_MAPS), ("track", dri.DRI_KC_TRACK),
+                          ("solve", dri.DRI_KC_SOLVE), ("frame", dri.DRI_KC_FRAME),
+                          ("grad", dri.DRI_KC_GRAD))}
+    line = {
+        "metric": "tracked frames/s at 640x480 (plain single stream)",
+        "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 per-pixel, f64 reduction and solve",
+        "data": "synthetic", "config": config_json(),
+        "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+        "gpu_launches": int(launches),
+        "frames_failed": int(failed_frames), "frames_ok": int(ok_frames),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "kernel": "k_track (fused photometric + ICP linearisation)",
+                     "bytes_per_pixel_iter": BYTES_PER_PIXEL_ITER,
+                     "avg_launch_us": 1000.0 * t_track_ms / max(1, n_track),
+                     "traffic": None if tr_bpp is None else tr_bpp * px_track / max(1, n_track)},
+        "kernel_classes": kc,
+        "e2e": {"value": e2e, "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "cpu_baseline": {"value": o_fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{o_n} whole frames of the same sequence tracked by the FP64 "
+                                   f"numpy oracle in {o_t:.1f} s"},
+        "clocks": clk.summary(),
+        "final_state_t": state.t,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--profile-frames", type=int, default=60)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

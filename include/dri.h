@@ -148,7 +148,9 @@ int dri_destroy_stream(dri_stream s);
 /* Uploads the live frame at time t (seconds, strictly increasing): depth and
  * intensity, height rows of width floats, rows pitch_bytes apart (0 = packed),
  * on the host (DRI_HOST, copied before the call returns its staging) or on the
- * device (DRI_DEVICE, copied stream-ordered).  The caller keeps ownership. */
+ * device (DRI_DEVICE, copied stream-ordered on the stream's cuda_stream: work
+ * that produces the images on another stream must be ordered before it, e.g.
+ * with an event).  The caller keeps ownership. */
 int dri_upload_frame(dri_stream s, double t, const float* depth, const float* intensity,
                      size_t pitch_bytes, int32_t mem_kind);
 
@@ -187,6 +189,38 @@ const char* dri_status_string(int code);
 /* Kernel launches this stream has issued since creation (all kernels of the
  * library, counted on the host at launch). */
 int dri_launch_count(dri_stream s, int64_t* count);
+
+/* Waits for the stream's frames and returns how many tracked frames (the
+ * initialising one included) finished with DRI_OK and how many failed
+ * (DRI_ELOST, or DRI_ENOTREADY for a frame queued behind a failed one). */
+int dri_frame_counts(dri_stream s, int64_t* ok, int64_t* failed);
+
+/* Host<->device bytes the library copied for the last frame: the uploaded
+ * images (host uploads only) plus the staged IMU samples, and the result block
+ * copied back by dri_track. */
+int dri_io_bytes(dri_stream s, int64_t* h2d, int64_t* d2h);
+
+/* Per-kernel-class device time, measured with CUDA events recorded on the
+ * stream around each launch while profiling is enabled (tracing aid; adds two
+ * event records per launch).  Classes: */
+#define DRI_KC_MAPS     0   /* level-0 copy, pyramid downsample, normal maps      */
+#define DRI_KC_TRACK    1   /* fused photometric + ICP linearisation and reduction */
+#define DRI_KC_SOLVE    2   /* Gauss-Newton step (IMU, assembly, Cholesky, update) */
+#define DRI_KC_FRAME    3   /* frame begin / end / init (IMU weight, Schur)        */
+#define DRI_KC_GRAD     4   /* reference intensity-gradient maps                   */
+#define DRI_KC_COUNT    8
+typedef struct {
+    int64_t launches[DRI_KC_COUNT];
+    double ms[DRI_KC_COUNT];       /* summed device time per class                     */
+    double pixels[DRI_KC_COUNT];   /* pixels processed per class (track: pixel-iterations) */
+} dri_profile;
+
+/* Starts (enable = 1) or stops (0) recording; starting clears the counters. */
+int dri_profile_enable(dri_stream s, int32_t enable);
+
+/* Waits for the stream and returns the counters recorded since profiling was
+ * enabled (up to 65536 launches are timed; later ones are counted only). */
+int dri_profile_read(dri_stream s, dri_profile* out);
 
 #ifdef __cplusplus
 }

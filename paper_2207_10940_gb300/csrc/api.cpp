@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <new>
 #include <vector>
 
@@ -189,15 +190,63 @@ struct dri_stream_s {
   double t_prev = 0.0;             // time of the state the next frame starts from
   double t_frame = 0.0;
   bool frame_pending = false;
-  char* pin_imu = nullptr;         // pinned staging for header + samples
-  Ctrl* pin_ctrl = nullptr;        // pinned copy of the control block
-  cudaEvent_t done = nullptr;      // recorded after each frame's result copy
-  bool done_pending = false;
+  char* pin_imu = nullptr;         // pinned staging, one slot per frame in flight (+1)
+  size_t imu_slot_bytes = 0;
+  Ctrl* pin_ctrl = nullptr;        // pinned copy of the whole control block
+  // frames in flight: each copies its result head into a pinned ring slot and
+  // records an event; completed frames are settled in order on the host
+  static constexpr int kRing = 64;
+  char* pin_ring = nullptr;        // kRing result heads
+  cudaEvent_t ring_ev[kRing] = {};
+  struct InFlight { int slot; };
+  std::deque<InFlight> inflight;
+  int ring_next = 0;
+  double t_confirmed = 0.0;        // time of the last state known to be good
+  int64_t frames_ok = 0, frames_failed = 0;
   double t_prev_before = 0.0;      // t_prev before the last optimistic advance
   int64_t launches = 0;
+  int64_t h2d_last = 0, d2h_last = 0;   // bytes copied for the last frame
+  // profiling: event pairs around launches
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  struct Rec { int cls; size_t e0, e1; double pixels; };
+  std::vector<Rec> recs;
+  dri_profile counted;
 };
 
 namespace {
+
+constexpr size_t kMaxTimed = 65536;
+
+cudaEvent_t prof_event(dri_stream_s* s, size_t* idx) {
+  if (s->ev_used == s->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    s->ev_pool.push_back(e);
+  }
+  *idx = s->ev_used;
+  return s->ev_pool[s->ev_used++];
+}
+
+// Runs one kernel launcher; counts it and, while profiling, brackets it with events.
+template <class F>
+cudaError_t launch(dri_stream_s* s, int cls, double pixels, F&& f) {
+  s->launches++;
+  if (!s->profiling) return f();
+  s->counted.launches[cls]++;
+  s->counted.pixels[cls] += pixels;
+  if (s->recs.size() >= kMaxTimed) return f();
+  size_t i0 = 0, i1 = 0;
+  cudaEvent_t e0 = prof_event(s, &i0);
+  cudaEvent_t e1 = e0 ? prof_event(s, &i1) : nullptr;
+  if (!e0 || !e1) return f();
+  cudaEventRecord(e0, s->stream);
+  cudaError_t r = f();
+  cudaEventRecord(e1, s->stream);
+  s->recs.push_back({cls, i0, i1, pixels});
+  return r;
+}
 
 SolveParams solve_params(const dri_stream_s* s, int level, int last) {
   SolveParams p;
@@ -251,18 +300,22 @@ TrackParams track_params(const dri_stream_s* s, int level, uint8_t* flags) {
 // Level maps of the uploaded frame in the live map set.
 int enqueue_maps(dri_stream_s* s) {
   const bool fp16 = (s->cfg.precision_flags & DRI_FP16_MAPS) != 0;
-  CK(launch_copy_input(s->in_depth, s->in_inten, s->maps[0], s->ctrl, s->cfg.width, s->cfg.height,
-                       s->stream));
-  s->launches++;
+  const double npx = (double)s->cfg.width * s->cfg.height;
+  CK(launch(s, DRI_KC_MAPS, npx, [&] {
+    return launch_copy_input(s->in_depth, s->in_inten, s->maps[0], s->ctrl, s->cfg.width,
+                             s->cfg.height, s->stream);
+  }));
   for (int l = 1; l < s->cfg.levels; ++l) {
-    CK(launch_pyr_down(s->maps[l - 1], s->maps[l], s->ctrl, s->geom[l - 1].w, s->geom[l - 1].h,
-                       s->geom[l].w, s->geom[l].h, s->stream));
-    s->launches++;
+    CK(launch(s, DRI_KC_MAPS, (double)s->geom[l].w * s->geom[l].h, [&] {
+      return launch_pyr_down(s->maps[l - 1], s->maps[l], s->ctrl, s->geom[l - 1].w,
+                             s->geom[l - 1].h, s->geom[l].w, s->geom[l].h, s->stream);
+    }));
   }
   for (int l = 0; l < s->cfg.levels; ++l) {
-    CK(launch_normals(s->maps[l], s->ctrl, s->geom[l], (float)s->cfg.depth_min,
-                      (float)s->cfg.depth_max, fp16, -1, s->stream));
-    s->launches++;
+    CK(launch(s, DRI_KC_MAPS, (double)s->geom[l].w * s->geom[l].h, [&] {
+      return launch_normals(s->maps[l], s->ctrl, s->geom[l], (float)s->cfg.depth_min,
+                            (float)s->cfg.depth_max, fp16, -1, s->stream);
+    }));
   }
   return DRI_OK;
 }
@@ -270,14 +323,15 @@ int enqueue_maps(dri_stream_s* s) {
 int enqueue_gradients(dri_stream_s* s) {
   const bool fp16 = (s->cfg.precision_flags & DRI_FP16_MAPS) != 0;
   for (int l = 0; l < s->cfg.levels; ++l) {
-    CK(launch_gradient(s->maps[l], s->ctrl, s->geom[l].w, s->geom[l].h, fp16, s->stream));
-    s->launches++;
+    CK(launch(s, DRI_KC_GRAD, (double)s->geom[l].w * s->geom[l].h, [&] {
+      return launch_gradient(s->maps[l], s->ctrl, s->geom[l].w, s->geom[l].h, fp16, s->stream);
+    }));
   }
   return DRI_OK;
 }
 
 // Stage header + samples covering [t0, t1] and copy them to the device.
-int stage_imu(dri_stream_s* s, double t0, double t1, bool need_cover) {
+int stage_imu(dri_stream_s* s, int slot, double t0, double t1, bool need_cover) {
   ImuHeader h;
   std::memset(&h, 0, sizeof(h));
   h.t0 = t0;
@@ -296,21 +350,40 @@ int stage_imu(dri_stream_s* s, double t0, double t1, bool need_cover) {
     if ((int64_t)(k1 - k0) > s->L.imu_cap) return DRI_ENOMEM;
     h.n = (int32_t)(k1 - k0);
   }
-  std::memcpy(s->pin_imu, &h, sizeof(h));
-  if (h.n)
-    std::memcpy(s->pin_imu + sizeof(h), s->imu.data() + k0, (size_t)h.n * sizeof(dri_imu_sample));
-  CK(cudaMemcpyAsync(s->imu_dev, s->pin_imu, sizeof(h) + (size_t)h.n * sizeof(dri_imu_sample),
+  // a slot is rewritten only after the frame that last used it has completed
+  char* stage = s->pin_imu + (size_t)slot * s->imu_slot_bytes;
+  std::memcpy(stage, &h, sizeof(h));
+  if (h.n) std::memcpy(stage + sizeof(h), s->imu.data() + k0, (size_t)h.n * sizeof(dri_imu_sample));
+  CK(cudaMemcpyAsync(s->imu_dev, stage, sizeof(h) + (size_t)h.n * sizeof(dri_imu_sample),
                      cudaMemcpyHostToDevice, s->stream));
+  s->h2d_last += (int64_t)(sizeof(h) + (size_t)h.n * sizeof(dri_imu_sample));
   return DRI_OK;
 }
 
-// Learn the outcome of the previous asynchronous frame if it has finished.
-void settle_previous(dri_stream_s* s, bool wait) {
-  if (!s->done_pending) return;
-  cudaError_t q = wait ? cudaEventSynchronize(s->done) : cudaEventQuery(s->done);
-  if (q != cudaSuccess) return;
-  s->done_pending = false;
-  if (s->pin_ctrl->status != DRI_OK) s->t_prev = s->pin_ctrl->t_state;
+const Ctrl* ring_head(const dri_stream_s* s, int slot) {
+  return reinterpret_cast<const Ctrl*>(s->pin_ring + (size_t)slot * kCtrlHeadBytes);
+}
+
+// Settles, in order, the frames whose result copy has completed (all of them
+// when wait is set): a failed frame rolls the host's start time back to the
+// state the device kept.
+int settle(dri_stream_s* s, bool wait) {
+  while (!s->inflight.empty()) {
+    const int slot = s->inflight.front().slot;
+    cudaError_t q = wait ? cudaEventSynchronize(s->ring_ev[slot]) : cudaEventQuery(s->ring_ev[slot]);
+    if (q == cudaErrorNotReady) return DRI_OK;
+    if (q != cudaSuccess) return DRI_ECUDA;
+    const Ctrl* h = ring_head(s, slot);
+    s->t_confirmed = h->t_state;
+    if (h->status != DRI_OK) {
+      s->t_prev = h->t_state;
+      s->frames_failed++;
+    } else {
+      s->frames_ok++;
+    }
+    s->inflight.pop_front();
+  }
+  return DRI_OK;
 }
 
 }  // namespace
@@ -399,12 +472,18 @@ int dri_create_stream(const dri_stream_config* cfg, const dri_state* x_init, voi
     }
     s->own_ws = true;
   }
-  if (cudaMallocHost(&s->pin_imu, sizeof(ImuHeader) + (size_t)L.imu_cap * sizeof(dri_imu_sample)) !=
-          cudaSuccess ||
+  s->imu_slot_bytes = align_up(sizeof(ImuHeader) + (size_t)L.imu_cap * sizeof(dri_imu_sample), 64);
+  if (cudaMallocHost(&s->pin_imu, (size_t)(dri_stream_s::kRing + 1) * s->imu_slot_bytes) != cudaSuccess ||
       cudaMallocHost(&s->pin_ctrl, sizeof(Ctrl)) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaMallocHost(&s->pin_ring, (size_t)dri_stream_s::kRing * kCtrlHeadBytes) != cudaSuccess) {
     dri_destroy_stream(s);
     return DRI_ENOMEM;
+  }
+  for (int i = 0; i < dri_stream_s::kRing; ++i) {
+    if (cudaEventCreateWithFlags(&s->ring_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+      dri_destroy_stream(s);
+      return DRI_ENOMEM;
+    }
   }
   s->ctrl = (Ctrl*)(s->ws + L.ctrl);
   s->imu_dev = (ImuHeader*)(s->ws + L.imu);
@@ -450,7 +529,10 @@ int dri_destroy_stream(dri_stream s) {
   if (s->own_ws && s->ws) cudaFree(s->ws);
   if (s->pin_imu) cudaFreeHost(s->pin_imu);
   if (s->pin_ctrl) cudaFreeHost(s->pin_ctrl);
-  if (s->done) cudaEventDestroy(s->done);
+  if (s->pin_ring) cudaFreeHost(s->pin_ring);
+  for (int i = 0; i < dri_stream_s::kRing; ++i)
+    if (s->ring_ev[i]) cudaEventDestroy(s->ring_ev[i]);
+  for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   delete s;
   return DRI_OK;
 }
@@ -464,6 +546,7 @@ int dri_upload_frame(dri_stream s, double t, const float* depth, const float* in
   if (pitch < row) return DRI_EINVAL;
   if (s->initialised && !(t > s->t_prev)) return DRI_EINVAL;
   const cudaMemcpyKind kind = mem_kind == DRI_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  s->h2d_last = mem_kind == DRI_HOST ? (int64_t)(2 * row * s->cfg.height) : 0;
   CK(cudaMemcpy2DAsync(s->in_depth, row, depth, pitch, row, s->cfg.height, kind, s->stream));
   CK(cudaMemcpy2DAsync(s->in_inten, row, intensity, pitch, row, s->cfg.height, kind, s->stream));
   s->t_frame = t;
@@ -485,8 +568,7 @@ int dri_push_imu(dri_stream s, const dri_imu_sample* samples, size_t n) {
   return DRI_OK;
 }
 
-static int fill_result(dri_stream s, dri_track_result* out, bool init) {
-  const Ctrl* h = s->pin_ctrl;
+static int fill_result(dri_stream s, const Ctrl* h, dri_track_result* out, bool init) {
   std::memset(out, 0, sizeof(*out));
   out->x1 = from_dstate(h->x, h->t_state);
   out->x0 = from_dstate(h->x0, s->t_prev_before);
@@ -503,24 +585,29 @@ static int fill_result(dri_stream s, dri_track_result* out, bool init) {
 int dri_track(dri_stream s, dri_track_result* out) {
   if (!s) return DRI_EINVAL;
   if (!s->frame_pending) return DRI_ENOTREADY;
-  settle_previous(s, false);
+  if (settle(s, false) != DRI_OK) return DRI_ECUDA;
+  if ((int)s->inflight.size() >= dri_stream_s::kRing) {
+    // ring full: wait for the oldest frame only, so its slots can be reused
+    CK(cudaEventSynchronize(s->ring_ev[s->inflight.front().slot]));
+    if (settle(s, false) != DRI_OK) return DRI_ECUDA;
+  }
   const bool init = !s->initialised;
+  const int slot = s->ring_next;   // staging + result slot of this frame
   if (init) {
-    int r = stage_imu(s, s->t_frame, s->t_frame, false);
+    int r = stage_imu(s, slot, s->t_frame, s->t_frame, false);
     if (r != DRI_OK) return r;
     if ((r = enqueue_maps(s)) != DRI_OK) return r;
-    CK(launch_frame_init(solve_params(s, 0, 0), s->stream));
-    s->launches++;
+    CK(launch(s, DRI_KC_FRAME, 0.0, [&] { return launch_frame_init(solve_params(s, 0, 0), s->stream); }));
     if ((r = enqueue_gradients(s)) != DRI_OK) return r;
     s->initialised = true;
     s->t_prev_before = s->t_frame;
     s->t_prev = s->t_frame;
+    s->t_confirmed = s->t_frame;
   } else {
-    int r = stage_imu(s, s->t_prev, s->t_frame, true);
+    int r = stage_imu(s, slot, s->t_prev, s->t_frame, true);
     if (r != DRI_OK) return r;
     if ((r = enqueue_maps(s)) != DRI_OK) return r;
-    CK(launch_frame_begin(solve_params(s, 0, 0), s->stream));
-    s->launches++;
+    CK(launch(s, DRI_KC_FRAME, 0.0, [&] { return launch_frame_begin(solve_params(s, 0, 0), s->stream); }));
     int remaining = 0;
     for (int l = 0; l < s->cfg.levels; ++l) remaining += s->cfg.iters[l];
     for (int l = s->cfg.levels - 1; l >= 0; --l) {
@@ -529,37 +616,42 @@ int dri_track(dri_stream s, dri_track_result* out) {
       const bool fp32p = (s->cfg.precision_flags & DRI_FP32_PARTIALS) != 0;
       for (int it = 0; it < s->cfg.iters[l]; ++it) {
         --remaining;
-        CK(launch_track(tp, fp16, fp32p, s->stream));
-        CK(launch_gn_step(solve_params(s, l, remaining == 0), s->stream));
-        s->launches += 2;
+        CK(launch(s, DRI_KC_TRACK, (double)tp.g.w * tp.g.h,
+                  [&] { return launch_track(tp, fp16, fp32p, s->stream); }));
+        CK(launch(s, DRI_KC_SOLVE, 0.0,
+                  [&] { return launch_gn_step(solve_params(s, l, remaining == 0), s->stream); }));
       }
     }
-    CK(launch_frame_end(solve_params(s, 0, 0), s->stream));
-    s->launches++;
+    CK(launch(s, DRI_KC_FRAME, 0.0, [&] { return launch_frame_end(solve_params(s, 0, 0), s->stream); }));
     if ((r = enqueue_gradients(s)) != DRI_OK) return r;
-    // drop samples no later frame can need (all before the one covering t_prev)
+    // drop samples no later frame can need: all before the one covering the
+    // earliest time a frame may still start from (a failed frame in flight
+    // rolls the start back to t_confirmed)
+    const double keep_from = std::min(s->t_prev, s->t_confirmed);
     size_t a = 0;
-    while (a + 1 < s->imu.size() && s->imu[a + 1].t <= s->t_prev) ++a;
+    while (a + 1 < s->imu.size() && s->imu[a + 1].t <= keep_from) ++a;
     if (a) s->imu.erase(s->imu.begin(), s->imu.begin() + a);
     s->t_prev_before = s->t_prev;
     s->t_prev = s->t_frame;   // optimistic; rolled back when the frame is known to fail
   }
   s->frame_pending = false;
-  CK(cudaMemcpyAsync(s->pin_ctrl, s->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s->stream));
-  CK(cudaEventRecord(s->done, s->stream));
-  s->done_pending = true;
+  s->ring_next = (s->ring_next + 1) % dri_stream_s::kRing;
+  CK(cudaMemcpyAsync(s->pin_ring + (size_t)slot * kCtrlHeadBytes, s->ctrl, kCtrlHeadBytes,
+                     cudaMemcpyDeviceToHost, s->stream));
+  s->d2h_last = (int64_t)kCtrlHeadBytes;
+  CK(cudaEventRecord(s->ring_ev[slot], s->stream));
+  s->inflight.push_back({slot});
   if (!out) return DRI_OK;
-  settle_previous(s, true);
-  return fill_result(s, out, init);
+  if (settle(s, true) != DRI_OK) return DRI_ECUDA;
+  return fill_result(s, ring_head(s, slot), out, init);
 }
 
 int dri_get_state(dri_stream s, dri_state* x1, double* H_prior, double* b_prior) {
   if (!s || !x1) return DRI_EINVAL;
   CK(cudaMemcpyAsync(s->pin_ctrl, s->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
-  s->done_pending = false;
+  if (settle(s, true) != DRI_OK) return DRI_ECUDA;
   const Ctrl* h = s->pin_ctrl;
-  if (h->status != DRI_OK && s->initialised) s->t_prev = h->t_state;
   *x1 = from_dstate(h->x, h->t_state);
   if (H_prior) std::memcpy(H_prior, h->Hs, sizeof(h->Hs));
   if (b_prior) std::memcpy(b_prior, h->bs, sizeof(h->bs));
@@ -579,8 +671,9 @@ int dri_set_state(dri_stream s, const dri_state* x1, const double* H_prior, cons
   h->status = DRI_OK;
   CK(cudaMemcpyAsync(s->ctrl, h, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream));
   CK(cudaStreamSynchronize(s->stream));
+  if (settle(s, true) != DRI_OK) return DRI_ECUDA;
   s->t_prev = x1->t;
-  s->done_pending = false;
+  s->t_confirmed = x1->t;
   return DRI_OK;
 }
 
@@ -589,17 +682,18 @@ int dri_linearise(dri_stream s, int32_t level, const dri_state* x0, const dri_st
   if (!s || !x0 || !x1 || !out || level < 0 || level >= s->cfg.levels) return DRI_EINVAL;
   if (!finite_state(*x0) || !finite_state(*x1)) return DRI_EINVAL;
   if (!s->initialised || !s->frame_pending) return DRI_ENOTREADY;
-  settle_previous(s, true);
-  int r = stage_imu(s, s->t_prev, s->t_frame, true);
+  if (settle(s, true) != DRI_OK) return DRI_ECUDA;
+  int r = stage_imu(s, dri_stream_s::kRing, s->t_prev, s->t_frame, true);
   if (r != DRI_OK) return r;
   if ((r = enqueue_maps(s)) != DRI_OK) return r;
   const SolveParams sp = solve_params(s, level, 0);
-  CK(launch_linearise_begin(sp, to_dstate(*x0), to_dstate(*x1), s->stream));
   const bool fp16 = (s->cfg.precision_flags & DRI_FP16_MAPS) != 0;
   const bool fp32p = (s->cfg.precision_flags & DRI_FP32_PARTIALS) != 0;
-  CK(launch_track(track_params(s, level, flags ? s->flags : nullptr), fp16, fp32p, s->stream));
-  CK(launch_linearise_end(sp, s->lin_dev, s->stream));
-  s->launches += 3;
+  const TrackParams tp = track_params(s, level, flags ? s->flags : nullptr);
+  CK(launch(s, DRI_KC_FRAME, 0.0,
+            [&] { return launch_linearise_begin(sp, to_dstate(*x0), to_dstate(*x1), s->stream); }));
+  CK(launch(s, DRI_KC_TRACK, (double)tp.g.w * tp.g.h, [&] { return launch_track(tp, fp16, fp32p, s->stream); }));
+  CK(launch(s, DRI_KC_SOLVE, 0.0, [&] { return launch_linearise_end(sp, s->lin_dev, s->stream); }));
   CK(cudaMemcpyAsync(out, s->lin_dev, sizeof(*out), cudaMemcpyDeviceToHost, s->stream));
   if (flags) {
     const size_t n = (size_t)s->geom[level].w * s->geom[level].h;
@@ -608,6 +702,46 @@ int dri_linearise(dri_stream s, int32_t level, const dri_state* x0, const dri_st
   CK(cudaMemcpyAsync(s->pin_ctrl, s->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   return s->pin_ctrl->status;
+}
+
+int dri_profile_enable(dri_stream s, int32_t enable) {
+  if (!s) return DRI_EINVAL;
+  if (enable) {
+    CK(cudaStreamSynchronize(s->stream));
+    s->recs.clear();
+    s->ev_used = 0;
+    std::memset(&s->counted, 0, sizeof(s->counted));
+  }
+  s->profiling = enable != 0;
+  return DRI_OK;
+}
+
+int dri_profile_read(dri_stream s, dri_profile* out) {
+  if (!s || !out) return DRI_EINVAL;
+  CK(cudaStreamSynchronize(s->stream));
+  *out = s->counted;
+  for (int k = 0; k < DRI_KC_COUNT; ++k) out->ms[k] = 0.0;
+  for (const auto& r : s->recs) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, s->ev_pool[r.e0], s->ev_pool[r.e1]));
+    out->ms[r.cls] += ms;
+  }
+  return DRI_OK;
+}
+
+int dri_frame_counts(dri_stream s, int64_t* ok, int64_t* failed) {
+  if (!s || !ok || !failed) return DRI_EINVAL;
+  if (settle(s, true) != DRI_OK) return DRI_ECUDA;
+  *ok = s->frames_ok;
+  *failed = s->frames_failed;
+  return DRI_OK;
+}
+
+int dri_io_bytes(dri_stream s, int64_t* h2d, int64_t* d2h) {
+  if (!s || !h2d || !d2h) return DRI_EINVAL;
+  *h2d = s->h2d_last;
+  *d2h = s->d2h_last;
+  return DRI_OK;
 }
 
 int dri_launch_count(dri_stream s, int64_t* count) {

@@ -16,6 +16,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cstdint>
 
 #include <cuda_runtime.h>
 
@@ -39,8 +40,19 @@ struct DState {                       // Eq. 1
 };
 
 struct Ctrl {
+  // ---- result head: copied to the host after every frame ----
   DState x;                           // state after the last tracked frame
   DState x0, x1;                      // Gauss-Newton iterates of the current frame
+  double cost;
+  double t_state;                     // time of x
+  int32_t n_icp[kMaxLevels], n_rgb[kMaxLevels];
+  int32_t status;                     // DRI_OK or the frame's error
+  int32_t ref_index;                  // map set holding the reference
+  int32_t initialised;                // reference exists
+  int32_t iterations;
+  uint32_t block_counter;             // last-block detection of the pixel kernel
+  uint32_t pad1[3];
+  // ---- solver state ----
   DState xbar;                        // prior mean
   DState xstart;                      // state at frame start (restored on DRI_ELOST)
   double Hs[17 * 17];                 // prior information H* (Eq. 8a)
@@ -49,18 +61,12 @@ struct Ctrl {
   double Rref[9], rref[3];            // pose T_ref the reference maps were made at
   double sums[64];                    // folded pixel sums of the current iteration
   double H[34 * 34], b[34], d[34];    // last joint system and step (marginalisation)
-  double cost;
-  double t_state;                     // time of x
   float xf_icp[12];                   // R_ref^T R_1 - I (row-major), R_ref^T (r_1 - r_ref)
   float xf_rgb[12];                   // R_0^T R_1 - I, R_0^T (r_1 - r_0)
-  int32_t n_icp[kMaxLevels], n_rgb[kMaxLevels];
-  int32_t status;                     // DRI_OK or the frame's error
-  int32_t ref_index;                  // map set holding the reference
-  int32_t initialised;                // reference exists
-  int32_t iterations;
-  uint32_t block_counter;             // last-block detection of the pixel kernel
-  uint32_t pad1[3];
 };
+
+// Bytes of the result head (x .. pad1) copied back after each frame.
+constexpr size_t kCtrlHeadBytes = offsetof(Ctrl, xbar);
 
 struct ImuHeader {
   double t0, t1;

@@ -84,6 +84,15 @@ class dri_linearisation(ctypes.Structure):
     ]
 
 
+DRI_KC_MAPS, DRI_KC_TRACK, DRI_KC_SOLVE, DRI_KC_FRAME, DRI_KC_GRAD = 0, 1, 2, 3, 4
+DRI_KC_COUNT = 8
+
+
+class dri_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * DRI_KC_COUNT), ("ms", ctypes.c_double * DRI_KC_COUNT),
+                ("pixels", ctypes.c_double * DRI_KC_COUNT)]
+
+
 class DriError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -123,6 +132,10 @@ def load_library():
                                          P(dri_linearisation), ctypes.c_void_p]),
         "dri_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "dri_launch_count": (ctypes.c_int, [ctypes.c_void_p, P(ctypes.c_int64)]),
+        "dri_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+        "dri_io_bytes": (ctypes.c_int, [ctypes.c_void_p, P(ctypes.c_int64), P(ctypes.c_int64)]),
+        "dri_frame_counts": (ctypes.c_int, [ctypes.c_void_p, P(ctypes.c_int64), P(ctypes.c_int64)]),
+        "dri_profile_read": (ctypes.c_int, [ctypes.c_void_p, P(dri_profile)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -264,6 +277,28 @@ def dri_launch_count(s):
     n = ctypes.c_int64()
     _check(load_library().dri_launch_count(s, ctypes.byref(n)), "dri_launch_count")
     return n.value
+
+
+def dri_frame_counts(s):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().dri_frame_counts(s, ctypes.byref(a), ctypes.byref(b)), "dri_frame_counts")
+    return a.value, b.value
+
+
+def dri_io_bytes(s):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().dri_io_bytes(s, ctypes.byref(a), ctypes.byref(b)), "dri_io_bytes")
+    return a.value, b.value
+
+
+def dri_profile_enable(s, enable=True):
+    return _check(load_library().dri_profile_enable(s, 1 if enable else 0), "dri_profile_enable")
+
+
+def dri_profile_read(s):
+    out = dri_profile()
+    _check(load_library().dri_profile_read(s, ctypes.byref(out)), "dri_profile_read")
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -332,6 +332,7 @@ class Sequence:
     bg: np.ndarray
     ba: np.ndarray
     meta: dict = field(default_factory=dict)
+    traj: object = None
 
 
 def _camera_pose_I(traj, t, R_CS, r_CS):
@@ -387,7 +388,8 @@ def _make_sequence(traj, cam, scene, R_CS, r_CS, frame_times, rate, bg, ba, rng,
                       rng if imu_noise else None)
     return Sequence(cam=cam, scene=scene, R_CS=R_CS, r_CS=r_CS, R_IW=R_IW,
                     frame_times=np.asarray(frame_times, dtype=np.float64), depth=depth,
-                    intensity=inten, gt=gt, imu=imu, bg=np.asarray(bg), ba=np.asarray(ba))
+                    intensity=inten, gt=gt, imu=imu, bg=np.asarray(bg), ba=np.asarray(ba),
+                    traj=traj)
 
 
 def _random_unit(rng):
@@ -471,3 +473,20 @@ def initial_state(seq, rng=None, v_sigma=0.0, grav_sigma=0.0):
             R_IW = _rotvec_to_matrix(np.array([ax[0], ax[1], 0.0]) * grav_sigma) @ R_IW
     return dict(t=float(seq.frame_times[0]), r_WC=np.zeros(3), q_WC=np.array([1.0, 0, 0, 0]),
                 v_I=v, bg=np.zeros(3), ba=np.zeros(3), q_IW=matrix_to_quat(R_IW))
+
+
+def render_frame(seq, i, seed=0, sigma_d=0.002, sigma_I=0.01, dropout=0.0):
+    """Renders frame i of a sequence made with render_frames=False, with its own
+    noise stream (seeded by (seed, i)), so frames can be rendered in parallel."""
+    g = seq.gt[i]
+    R_IC = seq.R_IW @ g["R_WC"]
+    r_IC = seq.R_IW @ g["r_WC"]
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), int(i), 0xF7A3]))
+    return render(seq.scene, R_IC, r_IC, seq.cam, rng, sigma_d, sigma_I, dropout)
+
+
+def sequence_imu(seq, t_end, seed=0):
+    """IMU samples of the sequence's trajectory from its first frame to t_end
+    (periodic trajectories can be extended beyond the rendered frames)."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), 0x1A0]))
+    return imu_samples(seq.traj, seq.meta["rate"], seq.frame_times[0], t_end, seq.bg, seq.ba, rng)

@@ -187,3 +187,34 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(dri.DriError):
         dri.dri_track(h)                                          # no frame uploaded
     dri.dri_destroy_stream(h)
+
+
+def test_pipelined_frames_match_synchronous_tracking():
+    """Frames queued back to back (device uploads, no waits, many frames in
+    flight) give bit-identical states to tracking them one at a time."""
+    torch = _torch()
+    seq = synth.sinusoid_sequence(seed=5, cam=synth.scaled_camera(160, 120), n_frames=12)
+    _, dcfg = configs(seq, 3, (4, 3, 2))
+    x_init = synth.initial_state(seq)
+    dev = torch.device("cuda")
+    D = torch.stack([torch.from_numpy(d) for d in seq.depth]).to(dev)
+    I = torch.stack([torch.from_numpy(i) for i in seq.intensity]).to(dev)
+    torch.cuda.synchronize()
+    states = []
+    for pipelined in (False, True):
+        st = new_stream(dcfg, x_init)
+        dri.dri_push_imu(st.handle, seq.imu)
+        for i in range(12):
+            dri.dri_upload_frame(st.handle, seq.frame_times[i], D[i], I[i])
+            r = dri.dri_track(st.handle, wait=not pipelined)
+            if not pipelined:
+                assert r.status == 0
+        x, Hs, bs = dri.dri_get_state(st.handle, with_prior=True)
+        ok, failed = dri.dri_frame_counts(st.handle)
+        assert (ok, failed) == (12, 0)
+        states.append((dri.state_to_dict(x), Hs, bs))
+        st.close()
+    (a, Ha, ba), (b, Hb, bb) = states
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
+    np.testing.assert_array_equal(Ha, Hb)
