@@ -222,6 +222,40 @@ int dri_profile_enable(dri_stream s, int32_t enable);
  * enabled (up to 65536 launches are timed; later ones are counted only). */
 int dri_profile_read(dri_stream s, dri_profile* out);
 
+/* Linearisation of one image pair without any allocation.  The paper has no
+ * counterpart: this entry exists for callers that may not allocate device
+ * memory when they call the library (a host framework that owns all device
+ * memory and forbids allocation in its per-frame callback, a real-time thread
+ * that must not block in the allocator, work recorded during CUDA stream
+ * capture).  Creating a stream allocates, so such code cannot use the stream
+ * API on the fly; this call needs only the caller's buffers.
+ *
+ * Inputs: cfg (intrinsics of the images, sigma_I, sigma_d, ICP thresholds and
+ * the depth range; levels, iterations and IMU fields are ignored); the
+ * reference and live depth / intensity images, width * height FP32 each,
+ * row-major, packed, in device memory; the pose the reference images were taken
+ * at (x_ref) and the states x0, x1 to linearise at.  Output (device memory):
+ * *out receives the ICP and photometric fields of dri_linearisation exactly as
+ * dri_linearise fills them for a one-level stream (H_icp, b_icp, H_rgb, b_rgb,
+ * cost_icp, cost_rgb, n_icp, n_rgb; H, b, e_imu and cost_imu are zeroed);
+ * flags (nullable, device, width * height bytes) the per-pixel validity bits.
+ * Work is enqueued on cuda_stream; the call does not wait.
+ *
+ * Every intermediate (normal and gradient maps, per-block partial sums, the
+ * block counter and per-call transforms) lives in one static device array that
+ * the library reserves when it is loaded (about 2.6 MB per GPU, held until the
+ * process exits), sized for at most 320 x 240 pixels: larger images return
+ * DRI_EINVAL.  The array is shared by all calls on a device and keeps the last
+ * call's contents; each call clears what must start at zero.  Calls whose GPU
+ * work overlaps race on it: order them on one stream.  The first call made with
+ * a device current looks up the array's device address for that device
+ * (cudaGetSymbolAddress); make that first call before any stream capture. */
+int dri_linearise_pair_noalloc(const dri_stream_config* cfg, const float* ref_depth,
+                               const float* ref_intensity, const float* live_depth,
+                               const float* live_intensity, const dri_state* x_ref,
+                               const dri_state* x0, const dri_state* x1,
+                               dri_linearisation* out, uint8_t* flags, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -135,6 +135,11 @@ def load_library():
         "dri_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
         "dri_io_bytes": (ctypes.c_int, [ctypes.c_void_p, P(ctypes.c_int64), P(ctypes.c_int64)]),
         "dri_frame_counts": (ctypes.c_int, [ctypes.c_void_p, P(ctypes.c_int64), P(ctypes.c_int64)]),
+        "dri_linearise_pair_noalloc": (ctypes.c_int, [P(dri_stream_config), ctypes.c_void_p,
+                                                      ctypes.c_void_p, ctypes.c_void_p,
+                                                      ctypes.c_void_p, P(dri_state), P(dri_state),
+                                                      P(dri_state), ctypes.c_void_p, ctypes.c_void_p,
+                                                      ctypes.c_void_p]),
         "dri_profile_read": (ctypes.c_int, [ctypes.c_void_p, P(dri_profile)]),
     }
     for name, (res, args) in sig.items():
@@ -277,6 +282,23 @@ def dri_launch_count(s):
     n = ctypes.c_int64()
     _check(load_library().dri_launch_count(s, ctypes.byref(n)), "dri_launch_count")
     return n.value
+
+
+def dri_linearise_pair_noalloc(cfg, ref_depth, ref_intensity, live_depth, live_intensity, x_ref,
+                               x0, x1, out_ptr, flags_ptr=None, cuda_stream=None):
+    """All image and output arguments are device pointers (ints) or CUDA tensors;
+    out_ptr points to device memory of sizeof(dri_linearisation) bytes."""
+    cs = getattr(cuda_stream, "cuda_stream", cuda_stream)
+    return _check(load_library().dri_linearise_pair_noalloc(
+        ctypes.byref(cfg), ctypes.c_void_p(_dev_ptr(ref_depth)), ctypes.c_void_p(_dev_ptr(ref_intensity)),
+        ctypes.c_void_p(_dev_ptr(live_depth)), ctypes.c_void_p(_dev_ptr(live_intensity)),
+        ctypes.byref(x_ref), ctypes.byref(x0), ctypes.byref(x1), ctypes.c_void_p(_dev_ptr(out_ptr)),
+        ctypes.c_void_p(_dev_ptr(flags_ptr) if flags_ptr is not None else 0),
+        ctypes.c_void_p(cs or 0)), "dri_linearise_pair_noalloc")
+
+
+def _dev_ptr(a):
+    return a.data_ptr() if hasattr(a, "data_ptr") else int(a)
 
 
 def dri_frame_counts(s):
