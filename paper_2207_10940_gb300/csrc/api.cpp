@@ -348,6 +348,7 @@ int stage_imu(dri_stream_s* s, int slot, double t0, double t1, bool need_cover) 
     k0 = a;
     k1 = b + 1;
     if ((int64_t)(k1 - k0) > s->L.imu_cap) return DRI_ENOMEM;
+    if ((int64_t)(k1 - k0) - 1 > solver_max_imu_pieces()) return DRI_ENOMEM;
     h.n = (int32_t)(k1 - k0);
   }
   // a slot is rewritten only after the frame that last used it has completed
@@ -456,6 +457,7 @@ int dri_create_stream(const dri_stream_config* cfg, const dri_state* x_init, voi
   if (v != DRI_OK) return v;
   if (!finite_state(*x_init)) return DRI_EINVAL;
   StreamLayout L = make_layout(*cfg);
+  if (prepare_solver_kernels() != cudaSuccess) return DRI_ECUDA;
   if (workspace && (workspace_bytes < L.total || ((uintptr_t)workspace % kAlign) != 0))
     return DRI_EINVAL;
   dri_stream_s* s = new (std::nothrow) dri_stream_s();

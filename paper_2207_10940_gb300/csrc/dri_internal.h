@@ -138,6 +138,8 @@ cudaError_t launch_gradient(const LevelMaps& m, const Ctrl* ctrl, int w, int h, 
 cudaError_t launch_track(const TrackParams& p, bool fp16, bool fp32_partials, cudaStream_t s);
 int track_grid_blocks(int w, int h, int ppt);
 
+cudaError_t prepare_solver_kernels();   // opt-in shared memory sizes (current device)
+int solver_max_imu_pieces();
 cudaError_t launch_frame_begin(const SolveParams& p, cudaStream_t s);
 cudaError_t launch_gn_step(const SolveParams& p, cudaStream_t s);
 cudaError_t launch_frame_end(const SolveParams& p, cudaStream_t s);

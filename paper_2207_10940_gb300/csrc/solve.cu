@@ -6,7 +6,7 @@
 //                 biases, IMU error (Eq. 5) and its analytic 18x34 Jacobian; rotate
 //                 the pixel kernel's photometric / ICP systems into W and map the
 //                 photometric one onto both poses; add the prior (Eq. 6/9); solve the
-//                 34x34 system of Eq. 7 by Cholesky; x0, x1 boxplus= dx (Eq. 2)
+//                 34x34 system of Eq. 7; x0, x1 boxplus= dx (Eq. 2)
 //   frame_end     marginalise x0 by the Schur complement (Eq. 8) at the updated point,
 //                 make the frame the reference (flip of the map sets)
 //   frame_init    first frame: first-frame prior, the frame becomes the reference
@@ -17,6 +17,21 @@
 // (propagated (r, a, v) block, bias random walks, gravity noise) and fixed per
 // frame; the prior adds H* to H_00 and b* - H* (x0 boxminus xbar) to b_0; after the
 // last update b <- b - H dx before the Schur complement.
+//
+// GB300 design.  FP64 issue rate per SM is low, so the serial recursions are
+// restated as data-parallel sums.  With dR_k the pre-integrated rotation before
+// piece k (a prefix product, the only serial chain), u_k = dR_k (a_k - b_a),
+// w_k = dt_k s_k + dt_k^2 / 2 (s_k = time left after piece k) and
+// Y_k = dR_{k+1} Jr(theta_k):
+//   dv = sum u_k dt_k,  dp = sum u_k w_k,
+//   Psi_k = -sum_{i<k} Y_i dt_i,  d(dR)/d(b_g) = dR_N^T Psi_N,
+//   d(dv, dp)/d(b_g) = -sum [u_k]x Psi_k (dt_k, w_k),  d(dv, dp)/d(b_a) = -sum dR_k (dt_k, w_k),
+// and the noise covariance is the sum over pieces of each piece's noise carried
+// to the end of the interval (state-transition blocks from suffix sums of u_k dt_k
+// and u_k w_k).  These equal the sequential recursion exactly (same algebra,
+// other rounding order).  W_IMU's block structure (a 9x9 block and a diagonal)
+// is used in the assembly; the 34x34 system is Jacobi scaled and solved by an
+// LDL^T factorisation whose trailing updates run over all threads.
 //
 // All arithmetic here is FP64.  One block of kSolveThreads threads runs each kernel.
 #include <cmath>
@@ -29,28 +44,18 @@ namespace dri {
 namespace {
 
 constexpr int kSolveThreads = 256;
-constexpr int kMaxPieces = 256;
+constexpr int kMaxPieces = 128;
 
-struct Preint {
-  double dR[9], dv[3], dp[3];
-  double Phig[9], Vg[9], Pg[9], Va[9], Pa[9];
-  double Sig[81];
-  double T;
-};
-
-struct Pred {
-  double r[3], R[9], v[3], c[3];
-  double RWS1[9];       // R_WC0 R_CS dR
-  double A0[9];         // R_WC0 R_CS
-  double R0[9], Q0[9];
-};
+// ---------------------------------------------------------------------------
+// IMU pieces and parallel pre-integration
+// ---------------------------------------------------------------------------
 
 __device__ __forceinline__ const dri_imu_sample* imu_samples(const ImuHeader* h) {
   return reinterpret_cast<const dri_imu_sample*>(h + 1);
 }
 
-// Zero-order-hold pieces of [t0, t1]: sample index and duration.  -1 if the
-// samples do not cover the interval.
+// Zero-order-hold pieces of [t0, t1]: sample index and duration; -1 if the samples
+// do not cover the interval or there are more than kMaxPieces pieces.
 __device__ int imu_pieces(const ImuHeader* h, int* pk, double* pdt) {
   const dri_imu_sample* s = imu_samples(h);
   const int n = h->n;
@@ -74,223 +79,315 @@ __device__ int imu_pieces(const ImuHeader* h, int* pk, double* pdt) {
   return np;
 }
 
-// Sequential pre-integration with bias Jacobians (and noise covariance if cov).
-__device__ void preintegrate(const ImuHeader* h, const int* pk, const double* pdt, int np,
-                             const double* bg, const double* ba, bool cov, double gnd, double and_,
-                             Preint& P) {
+struct Preint {
+  double dR[9], dv[3], dp[3];
+  double Phig[9], Vg[9], Pg[9], Va[9], Pa[9];
+  double Sig[81];                     // covariance of (dphi, dv, dp)
+  double T;
+};
+
+struct ImuWork {
+  double dR[kMaxPieces + 1][9];       // rotation before piece k
+  double EP[kMaxPieces + 1][9];       // Exp(theta_k), then Psi_k
+  double Y[kMaxPieces][9];            // Jr(theta_k), then dR_{k+1} Jr(theta_k)
+  double u[kMaxPieces][3];            // a_k - b_a, then dR_k (a_k - b_a)
+  double dt[kMaxPieces];
+  double tau[kMaxPieces + 1];         // start of piece k relative to t0
+  double w[kMaxPieces];
+  double Cv[kMaxPieces + 1][3];       // suffix sums of u_k dt_k
+  double Dv[kMaxPieces + 1][3];       // suffix sums of u_k w_k
+  int pk[kMaxPieces];
+  int np;
+};
+
+// Row r (0..8, order phi, v, p) of piece k's gyro-noise gain to the end of the
+// interval, divided by dt_k.
+__device__ __forceinline__ void gyro_gain_row(const ImuWork& W, int np, int k, int r, double* o) {
+  const double* Yp = W.Y[k];
+  if (r < 3) {
+    const double* R = W.dR[np];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) o[m] = R[r] * Yp[m] + R[3 + r] * Yp[3 + m] + R[6 + r] * Yp[6 + m];
+  } else {
+    const double* v = (r < 6 ? W.Cv : W.Dv)[k + 1];
+    const int rr = r % 3;
+    double h0, h1, h2;   // row rr of [v]x
+    if (rr == 0) { h0 = 0.0; h1 = -v[2]; h2 = v[1]; }
+    else if (rr == 1) { h0 = v[2]; h1 = 0.0; h2 = -v[0]; }
+    else { h0 = -v[1]; h1 = v[0]; h2 = 0.0; }
+#pragma unroll
+    for (int m = 0; m < 3; ++m) o[m] = -(h0 * Yp[m] + h1 * Yp[3 + m] + h2 * Yp[6 + m]);
+  }
+}
+
+// Whole block.  Pre-integration at biases (bg, ba) into P (and the noise
+// covariance when cov).  Returns false (for all threads) if the samples do not
+// cover the interval.
+__device__ bool preintegrate_block(const ImuHeader* h, const double* bg, const double* ba, bool cov,
+                                   double gnd, double and_, ImuWork& W, Preint& P) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) W.np = imu_pieces(h, W.pk, W.dt);
+  __syncthreads();
+  const int np = W.np;
+  if (np <= 0) return false;
   const dri_imu_sample* s = imu_samples(h);
-  for (int i = 0; i < 9; ++i) {
-    P.dR[i] = (i % 4 == 0) ? 1.0 : 0.0;
-    P.Phig[i] = P.Vg[i] = P.Pg[i] = P.Va[i] = P.Pa[i] = 0.0;
+  for (int k = tid; k < np; k += nt) {
+    const dri_imu_sample& m = s[W.pk[k]];
+    const double dt = W.dt[k];
+    const double th[3] = {(m.gyr[0] - bg[0]) * dt, (m.gyr[1] - bg[1]) * dt, (m.gyr[2] - bg[2]) * dt};
+    so3_exp(th, W.EP[k]);
+    so3_jr(th, W.Y[k]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) W.u[k][i] = m.acc[i] - ba[i];
   }
-  for (int i = 0; i < 3; ++i) P.dv[i] = P.dp[i] = 0.0;
-  if (cov)
-    for (int i = 0; i < 81; ++i) P.Sig[i] = 0.0;
-  double T = 0.0;
-  for (int j = 0; j < np; ++j) {
-    const dri_imu_sample& m = s[pk[j]];
-    const double dt = pdt[j];
-    T += dt;
-    const double w[3] = {m.gyr[0] - bg[0], m.gyr[1] - bg[1], m.gyr[2] - bg[2]};
-    const double a[3] = {m.acc[0] - ba[0], m.acc[1] - ba[1], m.acc[2] - ba[2]};
-    const double th[3] = {w[0] * dt, w[1] * dt, w[2] * dt};
-    double E[9], Jr[9], K[9], Ah[9], t1[9], t2[9];
-    so3_exp(th, E);
-    so3_jr(th, Jr);
-    hat3(a, K);
-    m3_mul(P.dR, K, Ah);  // dR [a]x
-    // bias Jacobians of the recursion (old values on the right-hand side)
-    m3_mul(Ah, P.Phig, t1);  // dR [a]x Phi_g
-    for (int i = 0; i < 9; ++i) {
-      P.Pg[i] += P.Vg[i] * dt - 0.5 * t1[i] * dt * dt;
-      P.Pa[i] += P.Va[i] * dt - 0.5 * P.dR[i] * dt * dt;
-      P.Vg[i] -= t1[i] * dt;
-      P.Va[i] -= P.dR[i] * dt;
-    }
-    m3_tmul(E, P.Phig, t2);  // E^T Phi_g
-    for (int i = 0; i < 9; ++i) P.Phig[i] = t2[i] - Jr[i] * dt;
-    if (cov) {
-      // Sigma <- A Sigma A^T + Bg (gnd^2/dt) Bg^T + Ba (and^2/dt) Ba^T, order (phi, v, p)
-      double A[81];
-      for (int i = 0; i < 81; ++i) A[i] = 0.0;
-      for (int i = 0; i < 9; ++i) A[i * 9 + i] = 1.0;
-      for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) {
-          A[r * 9 + c] = E[c * 3 + r];                              // E^T
-          A[(3 + r) * 9 + c] = -Ah[r * 3 + c] * dt;
-          A[(6 + r) * 9 + c] = -0.5 * Ah[r * 3 + c] * dt * dt;
-        }
-      for (int r = 0; r < 3; ++r) A[(6 + r) * 9 + 3 + r] = dt;
-      double AS[81];
-      for (int r = 0; r < 9; ++r)
-        for (int c = 0; c < 9; ++c) {
-          double acc = 0.0;
-          for (int k = 0; k < 9; ++k) acc += A[r * 9 + k] * P.Sig[k * 9 + c];
-          AS[r * 9 + c] = acc;
-        }
-      double B[27];   // Bg columns 0..2 scaled, Ba columns in a second pass
-      const double qg = gnd * gnd / dt, qa = and_ * and_ / dt;
-      for (int r = 0; r < 9; ++r)
-        for (int c = r; c < 9; ++c) {
-          double acc = 0.0;
-          for (int k = 0; k < 9; ++k) acc += AS[r * 9 + k] * A[c * 9 + k];
-          P.Sig[r * 9 + c] = acc;
-        }
-      // Bg = [Jr dt; 0; 0]
-      for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) B[r * 3 + c] = Jr[r * 3 + c] * dt;
-      for (int r = 0; r < 3; ++r)
-        for (int c = r; c < 3; ++c) {
-          double acc = 0.0;
-          for (int k = 0; k < 3; ++k) acc += B[r * 3 + k] * B[c * 3 + k];
-          P.Sig[r * 9 + c] += qg * acc;
-        }
-      // Ba = [0; dR dt; 0.5 dR dt^2]
-      double Bv[9], Bp[9];
-      for (int i = 0; i < 9; ++i) {
-        Bv[i] = P.dR[i] * dt;
-        Bp[i] = 0.5 * P.dR[i] * dt * dt;
+  __syncthreads();
+  if (tid < 32) {                      // prefix products dR_{k+1} = dR_k Exp(theta_k)
+    const int r = tid / 3, c = tid % 3;
+    if (tid < 9) W.dR[0][tid] = (r == c) ? 1.0 : 0.0;
+    if (tid == 9) W.tau[0] = 0.0;
+    __syncwarp();
+    for (int k = 0; k < np; ++k) {
+      if (tid < 9) {
+        const double* A = W.dR[k];
+        const double* E = W.EP[k];
+        W.dR[k + 1][tid] = A[3 * r] * E[c] + A[3 * r + 1] * E[3 + c] + A[3 * r + 2] * E[6 + c];
+      } else if (tid == 9) {
+        W.tau[k + 1] = W.tau[k] + W.dt[k];
       }
-      for (int r = 0; r < 6; ++r)
-        for (int c = r; c < 6; ++c) {
-          const double* Br = r < 3 ? Bv + 3 * r : Bp + 3 * (r - 3);
-          const double* Bc = c < 3 ? Bv + 3 * c : Bp + 3 * (c - 3);
-          P.Sig[(3 + r) * 9 + 3 + c] += qa * (Br[0] * Bc[0] + Br[1] * Bc[1] + Br[2] * Bc[2]);
-        }
-      for (int r = 0; r < 9; ++r)
-        for (int c = 0; c < r; ++c) P.Sig[r * 9 + c] = P.Sig[c * 9 + r];
+      __syncwarp();
     }
-    // state recursion: p, then v, then R
-    double Ra[3];
-    m3_vec(P.dR, a, Ra);
+  }
+  __syncthreads();
+  const double T = W.tau[np];
+  for (int k = tid; k < np; k += nt) {
+    const double dt = W.dt[k];
+    double u[3], Yp[9];
+    m3_vec(W.dR[k], W.u[k], u);
+    m3_mul(W.dR[k + 1], W.Y[k], Yp);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) W.u[k][i] = u[i];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) W.Y[k][i] = Yp[i];
+    W.w[k] = dt * (T - W.tau[k + 1]) + 0.5 * dt * dt;
+  }
+  __syncthreads();
+  if (tid < 9) {                       // Psi_k = -sum_{i<k} Y_i dt_i
+    double acc = 0.0;
+    W.EP[0][tid] = 0.0;
+    for (int k = 0; k < np; ++k) {
+      acc -= W.Y[k][tid] * W.dt[k];
+      W.EP[k + 1][tid] = acc;
+    }
+  } else if (cov && tid >= 32 && tid < 38) {   // suffix sums for the noise transition
+    const int i = (tid - 32) % 3;
+    const bool isD = tid >= 35;
+    double(*S)[3] = isD ? W.Dv : W.Cv;
+    double acc = 0.0;
+    S[np][i] = 0.0;
+    for (int k = np - 1; k >= 0; --k) {
+      acc += W.u[k][i] * (isD ? W.w[k] : W.dt[k]);
+      S[k][i] = acc;
+    }
+  }
+  __syncthreads();
+  if (tid < 42) {                      // sums over pieces, one thread per value
+    double acc = 0.0;
+    for (int k = 0; k < np; ++k) {
+      const double* u = W.u[k];
+      const double dt = W.dt[k], wk = W.w[k];
+      if (tid < 3) {
+        acc += u[tid] * dt;
+      } else if (tid < 6) {
+        acc += u[tid - 3] * wk;
+      } else if (tid < 24) {           // -[u]x Psi_k (dt | w)
+        const int e = (tid - 6) % 9, r = e / 3, c = e % 3;
+        const double* Ps = W.EP[k];
+        double hv;
+        if (r == 0) hv = -u[2] * Ps[3 + c] + u[1] * Ps[6 + c];
+        else if (r == 1) hv = u[2] * Ps[c] - u[0] * Ps[6 + c];
+        else hv = -u[1] * Ps[c] + u[0] * Ps[3 + c];
+        acc -= hv * (tid < 15 ? dt : wk);
+      } else {                         // -dR_k (dt | w)
+        const int e = (tid - 24) % 9;
+        acc -= W.dR[k][e] * (tid < 33 ? dt : wk);
+      }
+    }
+    if (tid < 3) P.dv[tid] = acc;
+    else if (tid < 6) P.dp[tid - 3] = acc;
+    else if (tid < 15) P.Vg[tid - 6] = acc;
+    else if (tid < 24) P.Pg[tid - 15] = acc;
+    else if (tid < 33) P.Va[tid - 24] = acc;
+    else P.Pa[tid - 33] = acc;
+  } else if (tid >= 64 && tid < 73) {  // d(dR)/d(b_g) = dR_N^T Psi_N
+    const int e = tid - 64, r = e / 3, c = e % 3;
+    const double* R = W.dR[np];
+    const double* Ps = W.EP[np];
+    P.Phig[e] = R[r] * Ps[c] + R[3 + r] * Ps[3 + c] + R[6 + r] * Ps[6 + c];
+  } else if (tid >= 96 && tid < 105) {
+    P.dR[tid - 96] = W.dR[np][tid - 96];
+  } else if (cov && tid >= 128 && tid < 128 + 45) {
+    // covariance entry (r, c), r <= c, of (dphi, dv, dp)
+    int e = tid - 128, r = 0;
+    while (e >= 9 - r) { e -= 9 - r; ++r; }
+    const int c = r + e;
+    double acc = 0.0;
+    const double q_g = gnd * gnd, q_a = and_ * and_;
+    for (int k = 0; k < np; ++k) {
+      const double dt = W.dt[k];
+      double gr[3], gc[3];
+      gyro_gain_row(W, np, k, r, gr);
+      gyro_gain_row(W, np, k, c, gc);
+      acc += q_g * dt * (gr[0] * gc[0] + gr[1] * gc[1] + gr[2] * gc[2]);
+      if (r >= 3 && (r % 3) == (c % 3)) {   // accelerometer noise: v and p blocks
+        const double ck = (T - W.tau[k + 1]) + 0.5 * dt;
+        const double fr = r < 6 ? 1.0 : ck, fc = c < 6 ? 1.0 : ck;
+        acc += q_a * dt * fr * fc;
+      }
+    }
+    P.Sig[r * 9 + c] = acc;
+    P.Sig[c * 9 + r] = acc;
+  }
+  if (tid == 0) P.T = T;
+  __syncthreads();
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// prediction, IMU error and Jacobian
+// ---------------------------------------------------------------------------
+
+struct ImuLin {
+  double R0[9], Q0[9], R1[9], Q1[9];
+  double A0[9], RWS1[9], Rh[9], QA[9];
+  double r[3], v[3], c[3];
+  double e[18];
+  double Jla[9], Jlg[9], Jra[9], Jrg[9];
+};
+
+// Whole block: prediction x^1(x0), error e = x^1 boxminus x1 and (when J) the
+// 18 x 34 Jacobian (row-major).  cols: x0 tangent 0..16, x1 tangent 17..33.
+__device__ void imu_linearise(const DState& x0, const DState& x1, const Preint& P,
+                              const SolveParams& sp, ImuLin& L, double* J) {
+  const int tid = threadIdx.x;
+  if (tid == 0) quat_to_rot(x0.q, L.R0);
+  else if (tid == 1) quat_to_rot(x0.qg, L.Q0);
+  else if (tid == 2) quat_to_rot(x1.q, L.R1);
+  else if (tid == 3) quat_to_rot(x1.qg, L.Q1);
+  __syncthreads();
+  if (tid == 0) {
+    const double T = P.T;
+    const double gI[3] = {0.0, 0.0, -sp.g};
+    m3_mul(L.R0, sp.R_CS, L.A0);
+    m3_mul(L.A0, P.dR, L.RWS1);
+    m3_mult(L.RWS1, sp.R_CS, L.Rh);                 // R^ = R0 Rc dR Rc^T
+    m3_mul(L.Q0, L.A0, L.QA);
+    for (int i = 0; i < 3; ++i) L.c[i] = x0.v[i] * T + 0.5 * gI[i] * T * T;
+    double t1[3], t2[3], t3[3], t4[3], t5[3], M[9];
+    m3_vec(L.R0, sp.r_CS, t1);
+    m3_tvec(L.Q0, L.c, t2);
+    m3_vec(L.A0, P.dp, t3);
+    m3_vec(L.Rh, sp.r_CS, t4);
+    m3_vec(L.QA, P.dv, t5);
     for (int i = 0; i < 3; ++i) {
-      P.dp[i] += P.dv[i] * dt + 0.5 * Ra[i] * dt * dt;
-      P.dv[i] += Ra[i] * dt;
+      L.r[i] = x0.r[i] + t1[i] + t2[i] + t3[i] - t4[i];
+      L.v[i] = x0.v[i] + gI[i] * T + t5[i];
+      L.e[i] = L.r[i] - x1.r[i];
+      L.e[6 + i] = L.v[i] - x1.v[i];
     }
-    m3_mul(P.dR, E, t1);
-    for (int i = 0; i < 9; ++i) P.dR[i] = t1[i];
+    m3_mult(L.Rh, L.R1, M);
+    so3_log(M, L.e + 3);
+  } else if (tid == 32) {
+    double M[9];
+    for (int i = 0; i < 3; ++i) {
+      L.e[9 + i] = x0.bg[i] - x1.bg[i];
+      L.e[12 + i] = x0.ba[i] - x1.ba[i];
+    }
+    m3_mult(L.Q0, L.Q1, M);
+    so3_log(M, L.e + 15);
   }
-  P.T = T;
-}
-
-__device__ void predict(const DState& x0, const Preint& P, const SolveParams& sp, Pred& o) {
-  quat_to_rot(x0.q, o.R0);
-  quat_to_rot(x0.qg, o.Q0);
-  m3_mul(o.R0, sp.R_CS, o.A0);
-  m3_mul(o.A0, P.dR, o.RWS1);
-  m3_mult(o.RWS1, sp.R_CS, o.R);                 // R^ = R0 Rc dR Rc^T
-  const double T = P.T;
-  const double gI[3] = {0.0, 0.0, -sp.g};
-  for (int i = 0; i < 3; ++i) o.c[i] = x0.v[i] * T + 0.5 * gI[i] * T * T;
-  double t1[3], t2[3], t3[3], t4[3];
-  m3_vec(o.R0, sp.r_CS, t1);
-  m3_tvec(o.Q0, o.c, t2);
-  m3_vec(o.A0, P.dp, t3);
-  m3_vec(o.R, sp.r_CS, t4);
-  for (int i = 0; i < 3; ++i) o.r[i] = x0.r[i] + t1[i] + t2[i] + t3[i] - t4[i];
-  double QA[9], t5[3];
-  m3_mul(o.Q0, o.A0, QA);
-  m3_vec(QA, P.dv, t5);
-  for (int i = 0; i < 3; ++i) o.v[i] = x0.v[i] + gI[i] * T + t5[i];
-}
-
-// e = x^1(x0) boxminus x1 (18) and de/d(dx0, dx1) (18 x 34, row-major).
-__device__ void imu_error_jacobian(const DState& x0, const DState& x1, const Preint& P,
-                                   const Pred& pr, const SolveParams& sp, double* e, double* J) {
-  double R1[9], Q1[9], M[9], t[9];
-  quat_to_rot(x1.q, R1);
-  quat_to_rot(x1.qg, Q1);
-  for (int i = 0; i < 3; ++i) e[i] = pr.r[i] - x1.r[i];
-  m3_mult(pr.R, R1, M);
-  so3_log(M, e + 3);
-  for (int i = 0; i < 3; ++i) {
-    e[6 + i] = pr.v[i] - x1.v[i];
-    e[9 + i] = x0.bg[i] - x1.bg[i];
-    e[12 + i] = x0.ba[i] - x1.ba[i];
+  __syncthreads();
+  if (tid == 0) so3_jl_inv(L.e + 3, L.Jla);
+  else if (tid == 1) so3_jl_inv(L.e + 15, L.Jlg);
+  else if (tid == 2) so3_jr_inv(L.e + 3, L.Jra);
+  else if (tid == 3) so3_jr_inv(L.e + 15, L.Jrg);
+  if (J == nullptr) {
+    __syncthreads();
+    return;
   }
-  m3_mult(pr.Q0, Q1, M);
-  so3_log(M, e + 15);
-  if (J == nullptr) return;
-  for (int i = 0; i < 18 * 34; ++i) J[i] = 0.0;
-  auto put3 = [&](int r0, int c0, const double* B) {
+  for (int i = tid; i < 18 * 34; i += blockDim.x) J[i] = 0.0;
+  __syncthreads();
+  auto put3 = [&](int r0, int c0, const double* B, double s) {
     for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c) J[(r0 + r) * 34 + c0 + c] = B[r * 3 + c];
+      for (int c = 0; c < 3; ++c) J[(r0 + r) * 34 + c0 + c] = s * B[r * 3 + c];
   };
-  auto put32 = [&](int r0, int c0, const double* B) {   // B (3x3) times P2 = first two columns
+  auto put32 = [&](int r0, int c0, const double* B, double s) {   // B P2: first two columns
     for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 2; ++c) J[(r0 + r) * 34 + c0 + c] = B[r * 3 + c];
+      for (int c = 0; c < 2; ++c) J[(r0 + r) * 34 + c0 + c] = s * B[r * 3 + c];
   };
   auto ident = [&](int r0, int c0, double s) {
     for (int r = 0; r < 3; ++r) J[(r0 + r) * 34 + c0 + r] = s;
   };
-  double Jla[9], Jlg[9], Jra[9], Jrg[9];
-  so3_jl_inv(e + 3, Jla);
-  so3_jl_inv(e + 15, Jlg);
-  so3_jr_inv(e + 3, Jra);
-  so3_jr_inv(e + 15, Jrg);
-  // x1 columns 17..33
-  ident(0, 17, -1.0);
-  for (int i = 0; i < 9; ++i) t[i] = -Jra[i];
-  put3(3, 20, t);
-  ident(6, 23, -1.0);
-  ident(9, 26, -1.0);
-  ident(12, 29, -1.0);
-  for (int i = 0; i < 9; ++i) t[i] = -Jrg[i];
-  put32(15, 32, t);
-  // x0 columns 0..16
-  ident(0, 0, 1.0);
-  {
-    double u[3], QTc[3];
-    m3_tvec(pr.Q0, pr.c, QTc);
-    for (int i = 0; i < 3; ++i) u[i] = -(pr.r[i] - x0.r[i] - QTc[i]);
-    hat3(u, t);
-    put3(0, 3, t);                                   // -[r^ - r0 - Q0^T c]x
+  double t[9], K[9], u[3];
+  switch (tid) {
+    // x1 columns 17..33
+    case 0: ident(0, 17, -1.0); break;
+    case 1: put3(3, 20, L.Jra, -1.0); break;
+    case 2: ident(6, 23, -1.0); break;
+    case 3: ident(9, 26, -1.0); break;
+    case 4: ident(12, 29, -1.0); break;
+    case 5: put32(15, 32, L.Jrg, -1.0); break;
+    // x0 columns 0..16
+    case 6: ident(0, 0, 1.0); break;
+    case 7: {                                          // -[r^ - r0 - Q0^T c]x
+      m3_tvec(L.Q0, L.c, u);
+      for (int i = 0; i < 3; ++i) u[i] = L.r[i] - x0.r[i] - u[i];
+      hat3(u, K);
+      put3(0, 3, K, -1.0);
+    } break;
+    case 8: put3(3, 3, L.Jla, 1.0); break;
+    case 9: {                                          // -Q0 [A0 dv]x
+      m3_vec(L.A0, P.dv, u);
+      hat3(u, K);
+      m3_mul(L.Q0, K, t);
+      put3(6, 3, t, -1.0);
+    } break;
+    case 10: {                                         // Q0^T T
+      for (int i = 0; i < 9; ++i) t[i] = L.Q0[(i % 3) * 3 + i / 3];
+      put3(0, 6, t, P.T);
+    } break;
+    case 11: ident(6, 6, 1.0); break;
+    case 12: {                                         // A0 Pg + [R^ rc]x RWS1 Phig
+      double KR[9], KRP[9], AP[9];
+      m3_vec(L.Rh, sp.r_CS, u);
+      hat3(u, K);
+      m3_mul(K, L.RWS1, KR);
+      m3_mul(KR, P.Phig, KRP);
+      m3_mul(L.A0, P.Pg, AP);
+      for (int i = 0; i < 9; ++i) t[i] = AP[i] + KRP[i];
+      put3(0, 9, t, 1.0);
+    } break;
+    case 13: {                                         // Jl^-1(e_a) RWS1 Phig
+      double RP[9];
+      m3_mul(L.RWS1, P.Phig, RP);
+      m3_mul(L.Jla, RP, t);
+      put3(3, 9, t, 1.0);
+    } break;
+    case 14: m3_mul(L.QA, P.Vg, t); put3(6, 9, t, 1.0); break;
+    case 15: ident(9, 9, 1.0); break;
+    case 16: m3_mul(L.A0, P.Pa, t); put3(0, 12, t, 1.0); break;
+    case 17: m3_mul(L.QA, P.Va, t); put3(6, 12, t, 1.0); break;
+    case 18: ident(12, 12, 1.0); break;
+    case 19: hat3(L.c, K); m3_tmul(L.Q0, K, t); put32(0, 15, t, 1.0); break;   // Q0^T [c]x P2
+    case 20: m3_vec(L.QA, P.dv, u); hat3(u, K); put32(6, 15, K, -1.0); break;  // -[Q0 A0 dv]x P2
+    case 21: put32(15, 15, L.Jlg, 1.0); break;                                  // Jl^-1(e_g) P2
+    default: break;
   }
-  put3(3, 3, Jla);
-  double Adv[3], K[9], QK[9];
-  m3_vec(pr.A0, P.dv, Adv);
-  hat3(Adv, K);
-  m3_mul(pr.Q0, K, QK);
-  for (int i = 0; i < 9; ++i) t[i] = -QK[i];
-  put3(6, 3, t);                                     // -Q0 [A0 dv]x
-  for (int i = 0; i < 9; ++i) t[i] = pr.Q0[(i % 3) * 3 + i / 3] * P.T;
-  put3(0, 6, t);                                     // Q0^T T
-  ident(6, 6, 1.0);
-  {
-    double Rrc[3], Kr[9], KR[9], KRP[9], AP[9];
-    m3_vec(pr.R, sp.r_CS, Rrc);
-    hat3(Rrc, Kr);
-    m3_mul(Kr, pr.RWS1, KR);
-    m3_mul(KR, P.Phig, KRP);
-    m3_mul(pr.A0, P.Pg, AP);
-    for (int i = 0; i < 9; ++i) t[i] = AP[i] + KRP[i];
-    put3(0, 9, t);                                   // A0 Pg + [R^ rc]x RWS1 Phig
-    double RP[9];
-    m3_mul(pr.RWS1, P.Phig, RP);
-    m3_mul(Jla, RP, t);
-    put3(3, 9, t);                                   // Jl^-1(e_a) RWS1 Phig
-    double QA[9];
-    m3_mul(pr.Q0, pr.A0, QA);
-    m3_mul(QA, P.Vg, t);
-    put3(6, 9, t);                                   // Q0 A0 Vg
-    ident(9, 9, 1.0);
-    m3_mul(pr.A0, P.Pa, t);
-    put3(0, 12, t);                                  // A0 Pa
-    m3_mul(QA, P.Va, t);
-    put3(6, 12, t);                                  // Q0 A0 Va
-    ident(12, 12, 1.0);
-    double Kc[9];
-    hat3(pr.c, Kc);
-    m3_tmul(pr.Q0, Kc, t);
-    put32(0, 15, t);                                 // Q0^T [c]x P2
-    double QAdv[3];
-    m3_vec(QA, P.dv, QAdv);
-    hat3(QAdv, Kc);
-    for (int i = 0; i < 9; ++i) t[i] = -Kc[i];
-    put32(6, 15, t);                                 // -[Q0 A0 dv]x P2
-    put32(15, 15, Jlg);                              // Jl^-1(e_g) P2
-  }
+  __syncthreads();
 }
+
+// ---------------------------------------------------------------------------
+// state algebra
+// ---------------------------------------------------------------------------
 
 // x boxminus y (17): vector parts subtract, orientations log(p q^-1), gravity x, y of its log.
 __device__ void state_boxminus(const DState& x, const DState& y, double* d) {
@@ -342,81 +439,109 @@ __device__ void write_transforms(Ctrl* c) {
   for (int i = 0; i < 3; ++i) c->xf_rgb[9 + i] = (float)t[i];
 }
 
-// In-place Cholesky A = L L^T (lower triangle), whole block; false if not positive definite.
-__device__ bool block_cholesky(double* A, int n, int ld) {
-  __shared__ int s_fail;
-  if (threadIdx.x == 0) s_fail = 0;
+__device__ void load_pose_ref(Ctrl* c) {
+  quat_to_rot(c->x.q, c->Rref);
+  for (int i = 0; i < 3; ++i) c->rref[i] = c->x.r[i];
+}
+
+// ---------------------------------------------------------------------------
+// dense symmetric factorisation
+// ---------------------------------------------------------------------------
+
+// In-place LDL^T of the symmetric n x n matrix in A (lower triangle read): the
+// strict lower triangle becomes the unit-lower L, the diagonal D.  Whole block;
+// col is shared scratch of 2 n doubles, fail a shared int.  False (for all
+// threads) if a pivot is not positive.
+__device__ bool block_ldlt(double* A, int n, int ld, double* col, int* fail) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) *fail = 0;
   __syncthreads();
   for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
-      double a = A[k * ld + k];
-      if (!(a > 0.0) || !isfinite(a)) {
-        s_fail = 1;
-        a = 1.0;
-      }
-      A[k * ld + k] = sqrt(a);
-    }
-    __syncthreads();
-    const double piv = A[k * ld + k];
-    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[i * ld + k] /= piv;
+    const double d = A[k * ld + k];
+    if (tid == 0 && !(d > 0.0 && d < INFINITY)) *fail = 1;
+    double* ck = col + (k & 1) * n;
+    const double* cp = col + ((k + 1) & 1) * n;
+    for (int i = k + 1 + tid; i < n; i += nt) ck[i] = A[i * ld + k] / d;
+    if (k > 0)
+      for (int i = k + tid; i < n; i += nt) A[i * ld + (k - 1)] = cp[i];
     __syncthreads();
     const int m = n - k - 1;
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-      const int i = k + 1 + idx / m, j = k + 1 + idx % m;
-      if (j <= i) A[i * ld + j] -= A[i * ld + k] * A[j * ld + k];
+    for (int p = tid; p < m * m; p += nt) {
+      const int i = k + 1 + p / m, j = k + 1 + p % m;
+      if (j <= i) A[i * ld + j] -= A[i * ld + k] * ck[j];
     }
     __syncthreads();
   }
-  return s_fail == 0;
+  return *fail == 0;
 }
 
-// Solve L L^T x = b in place on b (thread 0; n <= 64).
-__device__ void chol_subst(const double* L, int n, int ld, double* b) {
+// Solve L D L^T x = b in place (b becomes x).  Warp 0 only, n <= 64.
+__device__ void ldlt_solve_warp(const double* A, int n, int ld, double* b) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < n; ++k) {
+    const double z = b[k];
+    __syncwarp();
+    for (int i = k + 1 + lane; i < n; i += 32) b[i] -= A[i * ld + k] * z;
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) b[i] /= A[i * ld + i];
+  __syncwarp();
+  for (int k = n - 1; k > 0; --k) {
+    const double x = b[k];
+    __syncwarp();
+    for (int i = lane; i < k; i += 32) b[i] -= A[k * ld + i] * x;
+    __syncwarp();
+  }
+}
+
+// The same for one right-hand side in one thread.
+__device__ void ldlt_solve_thread(const double* A, int n, int ld, double* b) {
   for (int i = 0; i < n; ++i) {
     double s = b[i];
-    for (int k = 0; k < i; ++k) s -= L[i * ld + k] * b[k];
-    b[i] = s / L[i * ld + i];
+    for (int k = 0; k < i; ++k) s -= A[i * ld + k] * b[k];
+    b[i] = s;
   }
+  for (int i = 0; i < n; ++i) b[i] /= A[i * ld + i];
   for (int i = n - 1; i >= 0; --i) {
     double s = b[i];
-    for (int k = i + 1; k < n; ++k) s -= L[k * ld + i] * b[k];
-    b[i] = s / L[i * ld + i];
+    for (int k = i + 1; k < n; ++k) s -= A[k * ld + i] * b[k];
+    b[i] = s;
   }
 }
 
-struct StepShared {
-  double H[34 * 34];
-  double b[34];
+// ---------------------------------------------------------------------------
+// joint system (Eq. 6-7)
+// ---------------------------------------------------------------------------
+
+struct GnSmem {
+  ImuWork W;
+  Preint P;
+  ImuLin L;
+  DState x0, x1;
   double J[18 * 34];
-  double WJ[18 * 34];
-  double e[18];
-  double Hl[2][36];          // world-frame 6x6 of ICP, photometric (weighted)
-  double gl[2][6];           // weighted b of each term (x1 pose)
-  double M6[36];             // [[I,0],[[r1-r0]x, I]]
-  double scale[34];
+  double WJa[9 * 26];                 // W_9 J rows 0..8, columns 0..25 (the non-zero ones)
+  double We[9];
+  double H[34 * 34];
+  double A[34 * 34];
+  double b[34], x[34], scale[34];
+  double Hl[2][36];                   // world-frame 6x6 of ICP, photometric (weighted)
+  double gl[2][6];
+  double M6[36], MH6[36];
+  double dprior[17];
+  double col[2 * 34];
   double cost_imu;
-  int pk[kMaxPieces];
-  double pdt[kMaxPieces];
-  int np;
-  int ok;
+  int ok, fail;
 };
 
-// Assemble the joint system of Eq. 7 at (ctrl->x0, ctrl->x1) in shared memory.
-__device__ void assemble(const SolveParams& sp, StepShared& S) {
+// Assemble the joint system at (ctrl->x0, ctrl->x1) into S.H (full), S.b.
+__device__ void assemble(const SolveParams& sp, GnSmem& S) {
   Ctrl* c = sp.ctrl;
-  const int tid = threadIdx.x;
-  __shared__ Preint s_pre;
-  __shared__ Pred s_pred;
+  const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) {
-    S.np = imu_pieces(sp.imu, S.pk, S.pdt);
-    S.ok = S.np > 0;
-    if (S.ok) {
-      preintegrate(sp.imu, S.pk, S.pdt, S.np, c->x0.bg, c->x0.ba, false, 0.0, 0.0, s_pre);
-      predict(c->x0, s_pre, sp, s_pred);
-      imu_error_jacobian(c->x0, c->x1, s_pre, s_pred, sp, S.e, S.J);
-    }
+    S.x0 = c->x0;
+    S.x1 = c->x1;
   }
-  // meanwhile: pixel systems into W (term 0 ICP with R_ref, term 1 photometric with R_0)
+  // pixel systems into W (term 0 ICP with R_ref, term 1 photometric with R_0)
   if (tid >= 32 && tid < 32 + 2 * 36) {
     const int term = (tid - 32) / 36, idx = (tid - 32) % 36;
     const int i = idx / 6, j = idx % 6;
@@ -431,7 +556,7 @@ __device__ void assemble(const SolveParams& sp, StepShared& S) {
       const int lo = a < b ? a : b, hi = a < b ? b : a;
       return s[lo * 6 - lo * (lo - 1) / 2 + (hi - lo)];
     };
-    // Hw = Q Hloc Q^T with Q = diag(R, R): Hw_ij = sum_kl Q_ik Hloc_kl Q_jl
+    // Hw = Q Hloc Q^T with Q = diag(R, R)
     double acc = 0.0;
     const int bi = i / 3, ri = i % 3, bj = j / 3, rj = j % 3;
     for (int k = 0; k < 3; ++k)
@@ -443,17 +568,9 @@ __device__ void assemble(const SolveParams& sp, StepShared& S) {
       for (int k = 0; k < 3; ++k) g += R[ri * 3 + k] * s[21 + bi * 3 + k];
       S.gl[term][i] = -w * g;
     }
-  }
-  __syncthreads();
-  if (!S.ok) return;
-  // WJ = W_imu J
-  for (int idx = tid; idx < 18 * 34; idx += blockDim.x) {
-    const int r = idx / 34, col = idx % 34;
-    double acc = 0.0;
-    for (int k = 0; k < 18; ++k) acc += c->Wimu[r * 18 + k] * S.J[k * 34 + col];
-    S.WJ[idx] = acc;
-  }
-  if (tid == 0) {
+  } else if (tid == 128) {
+    state_boxminus(c->x0, c->xbar, S.dprior);
+  } else if (tid == 160) {
     for (int i = 0; i < 36; ++i) S.M6[i] = (i % 7 == 0) ? 1.0 : 0.0;
     const double d[3] = {c->x1.r[0] - c->x0.r[0], c->x1.r[1] - c->x0.r[1], c->x1.r[2] - c->x0.r[2]};
     double K[9];
@@ -462,75 +579,119 @@ __device__ void assemble(const SolveParams& sp, StepShared& S) {
       for (int q = 0; q < 3; ++q) S.M6[(3 + r) * 6 + q] = K[r * 3 + q];
   }
   __syncthreads();
-  // H = J^T W J, b = -J^T W e
-  for (int idx = tid; idx < 34 * 34; idx += blockDim.x) {
+  S.ok = preintegrate_block(sp.imu, S.x0.bg, S.x0.ba, false, 0.0, 0.0, S.W, S.P);
+  if (!S.ok) return;
+  imu_linearise(S.x0, S.x1, S.P, sp, S.L, S.J);
+  // W_IMU = blockdiag(W_9, diag): W_9 J_a (columns 0..25) and W_9 e_a
+  for (int idx = tid; idx < 9 * 26; idx += nt) {
+    const int r = idx / 26, col = idx % 26;
+    double acc = 0.0;
+    for (int m = 0; m < 9; ++m) acc += c->Wimu[r * 18 + m] * S.J[m * 34 + col];
+    S.WJa[idx] = acc;
+  }
+  if (tid >= 240 && tid < 249) {
+    const int r = tid - 240;
+    double acc = 0.0;
+    for (int m = 0; m < 9; ++m) acc += c->Wimu[r * 18 + m] * S.L.e[m];
+    S.We[r] = acc;
+  }
+  if (tid < 36) {                       // MH6 = M H6 (photometric term)
+    const int i = tid / 6, j = tid % 6;
+    double acc = 0.0;
+    for (int k = 0; k < 6; ++k) acc += S.M6[i * 6 + k] * S.Hl[1][k * 6 + j];
+    S.MH6[tid] = acc;
+  }
+  __syncthreads();
+  // H upper from J_a^T W_9 J_a, b from -J_a^T W_9 e_a
+  for (int idx = tid; idx < 34 * 34; idx += nt) {
     const int i = idx / 34, j = idx % 34;
     if (j < i) continue;
-    double acc = 0.0;
-    for (int k = 0; k < 18; ++k) acc += S.J[k * 34 + i] * S.WJ[k * 34 + j];
-    S.H[i * 34 + j] = acc;
+    double v = 0.0;
+    if (j < 26)
+      for (int m = 0; m < 9; ++m) v += S.J[m * 34 + i] * S.WJa[m * 26 + j];
+    S.H[idx] = v;
   }
-  if (tid < 34) {
-    double acc = 0.0;
-    for (int k = 0; k < 18; ++k) acc += S.WJ[k * 34 + tid] * S.e[k];
-    S.b[tid] = -acc;
+  if (tid >= 200 && tid < 200 + 34) {
+    const int i = tid - 200;
+    double v = 0.0;
+    if (i < 26)
+      for (int m = 0; m < 9; ++m) v -= S.J[m * 34 + i] * S.We[m];
+    S.b[i] = v;
   }
-  if (tid == 64) {
+  if (tid == 0) {
     double ce = 0.0;
-    for (int r = 0; r < 18; ++r) {
-      double wr = 0.0;
-      for (int k = 0; k < 18; ++k) wr += c->Wimu[r * 18 + k] * S.e[k];
-      ce += S.e[r] * wr;
-    }
+    for (int m = 0; m < 9; ++m) ce += S.L.e[m] * S.We[m];
+    for (int m = 9; m < 18; ++m) ce += S.L.e[m] * c->Wimu[m * 18 + m] * S.L.e[m];
     S.cost_imu = ce;
   }
   __syncthreads();
-  // + pixel terms: ICP on x1 pose; photometric: H12 = B H6 B^T, b12 = B g6, B = [-M; I]
-  for (int idx = tid; idx < 12 * 12; idx += blockDim.x) {
+  // diagonal part of W_IMU (bias and gravity rows), pixel terms, prior: disjoint entries
+  if (tid < 6) {                        // bias rows 9..14: +I at x0, -I at x1
+    const int i = tid;
+    const double w = c->Wimu[(9 + i) * 18 + 9 + i];
+    S.H[(9 + i) * 34 + 9 + i] += w;
+    S.H[(26 + i) * 34 + 26 + i] += w;
+    S.H[(9 + i) * 34 + 26 + i] -= w;
+    S.b[9 + i] -= w * S.L.e[9 + i];
+    S.b[26 + i] += w * S.L.e[9 + i];
+  } else if (tid < 16) {                // gravity rows 15..17, columns {15, 16, 32, 33}
+    const int G[4] = {15, 16, 32, 33};
+    int e = tid - 6, a = 0;
+    while (e >= 4 - a) { e -= 4 - a; ++a; }
+    const int ci = G[a], cj = G[a + e];
+    double v = 0.0;
+    for (int k = 0; k < 3; ++k)
+      v += S.J[(15 + k) * 34 + ci] * c->Wimu[(15 + k) * 18 + 15 + k] * S.J[(15 + k) * 34 + cj];
+    S.H[ci * 34 + cj] += v;
+  } else if (tid < 20) {
+    const int G[4] = {15, 16, 32, 33};
+    const int ci = G[tid - 16];
+    double v = 0.0;
+    for (int k = 0; k < 3; ++k)
+      v -= S.J[(15 + k) * 34 + ci] * c->Wimu[(15 + k) * 18 + 15 + k] * S.L.e[15 + k];
+    S.b[ci] += v;
+  }
+  __syncthreads();
+  // photometric on both poses (H12 = B H6 B^T, B = [-M; I]) and ICP on x1's pose
+  for (int idx = tid; idx < 12 * 12; idx += nt) {
     const int i = idx / 12, j = idx % 12;
     if (j < i) continue;
     const int a = i / 6, bb = j / 6, ii = i % 6, jj = j % 6;
     double v;
     if (a == 1 && bb == 1) {
-      v = S.Hl[1][ii * 6 + jj];
-    } else if (a == 0 && bb == 1) {      // -(M H6)_{ii jj}
+      v = S.Hl[1][ii * 6 + jj] + S.Hl[0][ii * 6 + jj];
+    } else if (a == 0 && bb == 1) {
+      v = -S.MH6[ii * 6 + jj];
+    } else {
       v = 0.0;
-      for (int k = 0; k < 6; ++k) v -= S.M6[ii * 6 + k] * S.Hl[1][k * 6 + jj];
-    } else {                              // (M H6 M^T)_{ii jj}
-      v = 0.0;
-      for (int k = 0; k < 6; ++k)
-        for (int l = 0; l < 6; ++l) v += S.M6[ii * 6 + k] * S.Hl[1][k * 6 + l] * S.M6[jj * 6 + l];
+      for (int k = 0; k < 6; ++k) v += S.MH6[ii * 6 + k] * S.M6[jj * 6 + k];
     }
     const int gi = a == 0 ? ii : 17 + ii, gj = bb == 0 ? jj : 17 + jj;
-    double add = v;
-    if (a == 1 && bb == 1) add += S.Hl[0][ii * 6 + jj];
-    S.H[gi * 34 + gj] += add;
+    S.H[gi * 34 + gj] += v;
   }
-  if (tid < 6) {
+  if (tid >= 160 && tid < 166) {
+    const int i = tid - 160;
     double g0 = 0.0;
-    for (int k = 0; k < 6; ++k) g0 -= S.M6[tid * 6 + k] * S.gl[1][k];
-    S.b[tid] += g0;
-    S.b[17 + tid] += S.gl[1][tid] + S.gl[0][tid];
+    for (int k = 0; k < 6; ++k) g0 -= S.M6[i * 6 + k] * S.gl[1][k];
+    S.b[i] += g0;
+    S.b[17 + i] += S.gl[1][i] + S.gl[0][i];
   }
   __syncthreads();
-  // + prior on x0: H00 += H*, b0 += b* - H* (x0 boxminus xbar)
-  __shared__ double s_dprior[17];
-  if (tid == 0) state_boxminus(c->x0, c->xbar, s_dprior);
-  __syncthreads();
-  for (int idx = tid; idx < 17 * 17; idx += blockDim.x) {
+  // prior on x0: H00 += H*, b0 += b* - H* (x0 boxminus xbar)
+  for (int idx = tid; idx < 17 * 17; idx += nt) {
     const int i = idx / 17, j = idx % 17;
-    if (j >= i) S.H[i * 34 + j] += c->Hs[i * 17 + j];
+    if (j >= i) S.H[i * 34 + j] += c->Hs[idx];
   }
-  if (tid < 17) {
-    double acc = c->bs[tid];
-    for (int k = 0; k < 17; ++k) acc -= c->Hs[tid * 17 + k] * s_dprior[k];
-    S.b[tid] += acc;
+  if (tid >= 192 && tid < 192 + 17) {
+    const int i = tid - 192;
+    double acc = c->bs[i];
+    for (int k = 0; k < 17; ++k) acc -= c->Hs[i * 17 + k] * S.dprior[k];
+    S.b[i] += acc;
   }
   __syncthreads();
-  // mirror the upper triangle
-  for (int idx = tid; idx < 34 * 34; idx += blockDim.x) {
+  for (int idx = tid; idx < 34 * 34; idx += nt) {
     const int i = idx / 34, j = idx % 34;
-    if (j < i) S.H[i * 34 + j] = S.H[j * 34 + i];
+    if (j < i) S.H[idx] = S.H[j * 34 + i];
   }
   __syncthreads();
 }
@@ -538,136 +699,140 @@ __device__ void assemble(const SolveParams& sp, StepShared& S) {
 __global__ void __launch_bounds__(kSolveThreads) k_gn_step(SolveParams sp) {
   Ctrl* c = sp.ctrl;
   if (c->status != 0) return;
-  __shared__ StepShared S;
-  __shared__ double A[34 * 34];
-  __shared__ double x[34];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  GnSmem& S = *reinterpret_cast<GnSmem*>(smem_raw);
+  const int tid = threadIdx.x, nt = blockDim.x;
   assemble(sp, S);
-  const int tid = threadIdx.x;
   if (!S.ok) {
     if (tid == 0) c->status = DRI_ENOTREADY;
     return;
   }
-  // Jacobi-scaled Cholesky solve of H dx = b
-  if (tid < 34) S.scale[tid] = 1.0 / sqrt(fmax(S.H[tid * 34 + tid], 1e-300));
-  __syncthreads();
-  for (int idx = tid; idx < 34 * 34; idx += blockDim.x) {
-    const int i = idx / 34, j = idx % 34;
-    A[idx] = S.H[idx] * S.scale[i] * S.scale[j];
+  // Jacobi-scaled LDL^T solve of H dx = b
+  if (tid < 34) {
+    S.scale[tid] = 1.0 / sqrt(fmax(S.H[tid * 34 + tid], 1e-300));
   }
-  if (tid < 34) x[tid] = S.b[tid] * S.scale[tid];
   __syncthreads();
-  const bool pd = block_cholesky(A, 34, 34);
+  for (int idx = tid; idx < 34 * 34; idx += nt) S.A[idx] = S.H[idx] * S.scale[idx / 34] * S.scale[idx % 34];
+  if (tid < 34) S.x[tid] = S.b[tid] * S.scale[tid];
+  __syncthreads();
+  const bool pd = block_ldlt(S.A, 34, 34, S.col, &S.fail);
+  if (tid < 32) ldlt_solve_warp(S.A, 34, 34, S.x);
+  __syncthreads();
+  if (tid < 34) S.x[tid] *= S.scale[tid];
+  __syncthreads();
+  bool good = pd;
+  for (int i = 0; i < 34; ++i) good = good && isfinite(S.x[i]);
+  if (!good) {
+    if (tid == 0) c->status = DRI_ELOST;
+    return;
+  }
   if (tid == 0) {
-    bool good = pd;
-    if (good) {
-      chol_subst(A, 34, 34, x);
-      for (int i = 0; i < 34; ++i) {
-        x[i] *= S.scale[i];
-        good = good && isfinite(x[i]);
-      }
-    }
-    if (!good) {
-      c->status = DRI_ELOST;
-    } else {
-      state_boxplus(c->x0, x);
-      state_boxplus(c->x1, x + 17);
-      const double* s = c->sums;
-      c->n_icp[sp.level] = (int32_t)s[28];
-      c->n_rgb[sp.level] = (int32_t)s[kSums + 28];
-      c->cost = sp.W_icp * s[27] + sp.W_rgb * s[kSums + 27] + S.cost_imu;
-      c->iterations += 1;
-      write_transforms(c);
-    }
+    state_boxplus(S.x0, S.x);
+  } else if (tid == 32) {
+    state_boxplus(S.x1, S.x + 17);
+  } else if (tid == 64) {
+    const double* s = c->sums;
+    c->n_icp[sp.level] = (int32_t)s[28];
+    c->n_rgb[sp.level] = (int32_t)s[kSums + 28];
+    c->cost = sp.W_icp * s[27] + sp.W_rgb * s[kSums + 27] + S.cost_imu;
+    c->iterations += 1;
   }
   __syncthreads();
-  if (sp.last && c->status == 0) {
-    for (int idx = tid; idx < 34 * 34; idx += blockDim.x) c->H[idx] = S.H[idx];
-    if (tid < 34) {
-      c->b[tid] = S.b[tid];
-      c->d[tid] = x[tid];
+  if (tid == 0) {
+    c->x0 = S.x0;
+    c->x1 = S.x1;
+    write_transforms(c);
+  }
+  if (sp.last) {
+    for (int idx = tid; idx < 34 * 34; idx += nt) c->H[idx] = S.H[idx];
+    if (tid >= 64 && tid < 98) {
+      c->b[tid - 64] = S.b[tid - 64];
+      c->d[tid - 64] = S.x[tid - 64];
     }
   }
-}
-
-__device__ void load_pose_ref(Ctrl* c) {
-  quat_to_rot(c->x.q, c->Rref);
-  for (int i = 0; i < 3; ++i) c->rref[i] = c->x.r[i];
 }
 
 // W_IMU at c->x0 (noise propagated through the recursion, Sigma^-1), and the
-// IMU prediction x^1(x0).  Whole block; returns false (status set) on failure.
-__device__ bool imu_weight_and_prediction(const SolveParams& sp, Ctrl* c, DState* x1_pred) {
+// IMU prediction x^1(x0).  Whole block; false (status set) on failure.
+struct BeginSmem {
+  ImuWork W;
+  Preint P;
+  ImuLin L;
+  double G[81], GS[81], Sg[81], Winv[81];
+  double col[18];
+  int ok, fail;
+};
+
+__device__ bool imu_weight_and_prediction(const SolveParams& sp, Ctrl* c, BeginSmem& B,
+                                          DState* x1_pred) {
   const int tid = threadIdx.x;
-  __shared__ Preint P;
-  __shared__ Pred pr;
-  __shared__ int s_np, s_ok;
-  __shared__ int pk[kMaxPieces];
-  __shared__ double pdt[kMaxPieces];
-  __shared__ double G[81], GS[81], L[81], Winv[81];
   if (tid == 0) {
-    s_ok = 1;
-    if (!c->initialised || fabs(sp.imu->t0 - c->t_state) > 1e-9) s_ok = 0;
-    s_np = s_ok ? imu_pieces(sp.imu, pk, pdt) : -1;
-    if (s_np <= 0) s_ok = 0;
-    if (s_ok) {
-      preintegrate(sp.imu, pk, pdt, s_np, c->x0.bg, c->x0.ba, true, sp.gyr_nd, sp.acc_nd, P);
-      predict(c->x0, P, sp, pr);
-      // G = d(r^, a^, v^) / d(dphi, dv, dp)
-      for (int i = 0; i < 81; ++i) G[i] = 0.0;
-      double Rrc[3], K[9], KR[9], QA[9];
-      m3_vec(pr.R, sp.r_CS, Rrc);
-      hat3(Rrc, K);
-      m3_mul(K, pr.RWS1, KR);
-      m3_mul(pr.Q0, pr.A0, QA);
-      for (int r = 0; r < 3; ++r)
-        for (int q = 0; q < 3; ++q) {
-          G[r * 9 + q] = KR[r * 3 + q];
-          G[r * 9 + 6 + q] = pr.A0[r * 3 + q];
-          G[(3 + r) * 9 + q] = pr.RWS1[r * 3 + q];
-          G[(6 + r) * 9 + 3 + q] = QA[r * 3 + q];
-        }
-    } else {
-      c->status = DRI_ENOTREADY;
+    B.ok = c->initialised && !(fabs(sp.imu->t0 - c->t_state) > 1e-9);
+    if (!B.ok) c->status = DRI_ENOTREADY;
+  }
+  __syncthreads();
+  if (!B.ok) return false;
+  const DState x0 = c->x0;
+  if (!preintegrate_block(sp.imu, x0.bg, x0.ba, true, sp.gyr_nd, sp.acc_nd, B.W, B.P)) {
+    if (tid == 0) c->status = DRI_ENOTREADY;
+    return false;
+  }
+  imu_linearise(x0, x0, B.P, sp, B.L, nullptr);   // prediction only (x1 unused)
+  // G = d(r^, a^, v^) / d(dphi, dv, dp)
+  if (tid < 81) {
+    const int r = tid / 9, q = tid % 9;
+    double v = 0.0;
+    if (r < 3 && q < 3) {              // [R^ rc]x RWS1
+      double u[3];
+      m3_vec(B.L.Rh, sp.r_CS, u);
+      double K[9];
+      hat3(u, K);
+      v = K[r * 3] * B.L.RWS1[q] + K[r * 3 + 1] * B.L.RWS1[3 + q] + K[r * 3 + 2] * B.L.RWS1[6 + q];
+    } else if (r < 3 && q >= 6) {
+      v = B.L.A0[r * 3 + q - 6];
+    } else if (r >= 3 && r < 6 && q < 3) {
+      v = B.L.RWS1[(r - 3) * 3 + q];
+    } else if (r >= 6 && q >= 3 && q < 6) {
+      v = B.L.QA[(r - 6) * 3 + q - 3];
     }
-  }
-  __syncthreads();
-  if (!s_ok) return false;
-  // G Sigma_pre G^T, symmetrised
-  if (tid < 81) {
-    const int r = tid / 9, q = tid % 9;
-    double acc = 0.0;
-    for (int k = 0; k < 9; ++k) acc += G[r * 9 + k] * P.Sig[k * 9 + q];
-    GS[tid] = acc;
+    B.G[tid] = v;
   }
   __syncthreads();
   if (tid < 81) {
     const int r = tid / 9, q = tid % 9;
     double acc = 0.0;
-    for (int k = 0; k < 9; ++k) acc += GS[r * 9 + k] * G[q * 9 + k];
-    L[tid] = acc;
+    for (int k = 0; k < 9; ++k) acc += B.G[r * 9 + k] * B.P.Sig[k * 9 + q];
+    B.GS[tid] = acc;
+  }
+  __syncthreads();
+  if (tid < 81) {
+    const int r = tid / 9, q = tid % 9;
+    double acc = 0.0;
+    for (int k = 0; k < 9; ++k) acc += B.GS[r * 9 + k] * B.G[q * 9 + k];
+    B.Sg[tid] = acc;
   }
   __syncthreads();
   double sym = 0.0;
-  if (tid < 81) sym = 0.5 * (L[tid] + L[(tid % 9) * 9 + tid / 9]);
+  if (tid < 81) sym = 0.5 * (B.Sg[tid] + B.Sg[(tid % 9) * 9 + tid / 9]);
   __syncthreads();
-  if (tid < 81) L[tid] = sym;
+  if (tid < 81) B.Sg[tid] = sym;
   __syncthreads();
-  const bool pd = block_cholesky(L, 9, 9);
+  const bool pd = block_ldlt(B.Sg, 9, 9, B.col, &B.fail);
   if (tid < 9) {
-    double col[9];
-    for (int i = 0; i < 9; ++i) col[i] = (i == tid) ? 1.0 : 0.0;
-    chol_subst(L, 9, 9, col);
-    for (int i = 0; i < 9; ++i) Winv[i * 9 + tid] = col[i];
+    double colv[9];
+    for (int i = 0; i < 9; ++i) colv[i] = (i == tid) ? 1.0 : 0.0;
+    ldlt_solve_thread(B.Sg, 9, 9, colv);
+    for (int i = 0; i < 9; ++i) B.Winv[i * 9 + tid] = colv[i];
   }
   __syncthreads();
   for (int idx = tid; idx < 18 * 18; idx += blockDim.x) {
     const int r = idx / 18, q = idx % 18;
     double w = 0.0;
     if (r < 9 && q < 9) {
-      w = 0.5 * (Winv[r * 9 + q] + Winv[q * 9 + r]);
+      w = 0.5 * (B.Winv[r * 9 + q] + B.Winv[q * 9 + r]);
     } else if (r == q) {
-      if (r < 12) w = 1.0 / (sp.gyr_rw * sp.gyr_rw * P.T);
-      else if (r < 15) w = 1.0 / (sp.acc_rw * sp.acc_rw * P.T);
+      if (r < 12) w = 1.0 / (sp.gyr_rw * sp.gyr_rw * B.P.T);
+      else if (r < 15) w = 1.0 / (sp.acc_rw * sp.acc_rw * B.P.T);
       else w = 1.0 / (sp.sigma_grav * sp.sigma_grav);
     }
     c->Wimu[idx] = w;
@@ -676,12 +841,12 @@ __device__ bool imu_weight_and_prediction(const SolveParams& sp, Ctrl* c, DState
     if (!pd) c->status = DRI_ELOST;
     if (x1_pred) {
       // x1 := x^1(x0): biases and q_IW carried over
-      DState x1 = c->x0;
+      DState x1 = x0;
       for (int i = 0; i < 3; ++i) {
-        x1.r[i] = pr.r[i];
-        x1.v[i] = pr.v[i];
+        x1.r[i] = B.L.r[i];
+        x1.v[i] = B.L.v[i];
       }
-      rot_to_quat(pr.R, x1.q);
+      rot_to_quat(B.L.Rh, x1.q);
       *x1_pred = x1;
     }
   }
@@ -691,6 +856,8 @@ __device__ bool imu_weight_and_prediction(const SolveParams& sp, Ctrl* c, DState
 
 __global__ void __launch_bounds__(kSolveThreads) k_frame_begin(SolveParams sp) {
   Ctrl* c = sp.ctrl;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BeginSmem& B = *reinterpret_cast<BeginSmem*>(smem_raw);
   const int tid = threadIdx.x;
   if (tid == 0) {
     c->status = 0;
@@ -701,13 +868,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_frame_begin(SolveParams sp) {
     for (int l = 0; l < kMaxLevels; ++l) c->n_icp[l] = c->n_rgb[l] = 0;
   }
   __syncthreads();
-  if (imu_weight_and_prediction(sp, c, &c->x1) && tid == 0) write_transforms(c);
+  if (imu_weight_and_prediction(sp, c, B, &c->x1) && tid == 0) write_transforms(c);
 }
 
 __global__ void __launch_bounds__(kSolveThreads) k_frame_end(SolveParams sp) {
   Ctrl* c = sp.ctrl;
   const int tid = threadIdx.x;
-  __shared__ int s_ok;
+  __shared__ int s_ok, s_fail;
   if (tid == 0) {
     if (c->status == 0 && c->n_icp[0] + c->n_rgb[0] < sp.min_valid) c->status = DRI_ELOST;
     s_ok = c->status == 0;
@@ -722,6 +889,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_frame_end(SolveParams sp) {
   __shared__ double bp[34];
   __shared__ double L[17 * 17];
   __shared__ double X[17 * 18];
+  __shared__ double colbuf[34];
+  __shared__ double Hs[17 * 17], bs[17];
   for (int idx = tid; idx < 34 * 34; idx += blockDim.x) H[idx] = c->H[idx];
   __syncthreads();
   if (tid < 34) {
@@ -731,15 +900,14 @@ __global__ void __launch_bounds__(kSolveThreads) k_frame_end(SolveParams sp) {
   }
   for (int idx = tid; idx < 17 * 17; idx += blockDim.x) L[idx] = H[(idx / 17) * 34 + idx % 17];
   __syncthreads();
-  const bool pd = block_cholesky(L, 17, 17);
+  const bool pd = block_ldlt(L, 17, 17, colbuf, &s_fail);
   if (tid < 18) {
-    double col[17];
-    for (int i = 0; i < 17; ++i) col[i] = tid < 17 ? H[i * 34 + 17 + tid] : bp[i];
-    chol_subst(L, 17, 17, col);
-    for (int i = 0; i < 17; ++i) X[i * 18 + tid] = col[i];
+    double colv[17];
+    for (int i = 0; i < 17; ++i) colv[i] = tid < 17 ? H[i * 34 + 17 + tid] : bp[i];
+    ldlt_solve_thread(L, 17, 17, colv);
+    for (int i = 0; i < 17; ++i) X[i * 18 + tid] = colv[i];
   }
   __syncthreads();
-  __shared__ double Hs[17 * 17], bs[17];
   for (int idx = tid; idx < 17 * 17; idx += blockDim.x) {
     const int i = idx / 17, j = idx % 17;
     double acc = H[(17 + i) * 34 + 17 + j];
@@ -808,6 +976,8 @@ __global__ void k_frame_init(SolveParams sp) {
 
 __global__ void __launch_bounds__(kSolveThreads) k_linearise_begin(SolveParams sp, DState x0, DState x1) {
   Ctrl* c = sp.ctrl;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BeginSmem& B = *reinterpret_cast<BeginSmem*>(smem_raw);
   const int tid = threadIdx.x;
   if (tid == 0) {
     c->status = 0;
@@ -815,12 +985,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_linearise_begin(SolveParams s
     c->x1 = x1;
   }
   __syncthreads();
-  if (imu_weight_and_prediction(sp, c, nullptr) && tid == 0) write_transforms(c);
+  if (imu_weight_and_prediction(sp, c, B, nullptr) && tid == 0) write_transforms(c);
 }
 
 __global__ void __launch_bounds__(kSolveThreads) k_linearise_end(SolveParams sp, dri_linearisation* out) {
   Ctrl* c = sp.ctrl;
-  __shared__ StepShared S;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  GnSmem& S = *reinterpret_cast<GnSmem*>(smem_raw);
   assemble(sp, S);
   const int tid = threadIdx.x;
   for (int idx = tid; idx < 34 * 34; idx += blockDim.x) out->H[idx] = S.ok ? S.H[idx] : 0.0;
@@ -833,7 +1004,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_linearise_end(SolveParams sp,
     out->b_icp[tid] = S.gl[0][tid];
     out->b_rgb[tid] = S.gl[1][tid];
   }
-  if (tid < 18) out->e_imu[tid] = S.ok ? S.e[tid] : 0.0;
+  if (tid < 18) out->e_imu[tid] = S.ok ? S.L.e[tid] : 0.0;
   if (tid == 0) {
     const double* s = c->sums;
     out->cost_icp = sp.W_icp * s[27];
@@ -847,12 +1018,29 @@ __global__ void __launch_bounds__(kSolveThreads) k_linearise_end(SolveParams sp,
 
 }  // namespace
 
+cudaError_t prepare_solver_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(k_gn_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(GnSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_linearise_end, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(GnSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_frame_begin, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(BeginSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_linearise_begin, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(BeginSmem));
+  return e;
+}
+
+int solver_max_imu_pieces() { return kMaxPieces; }
+
 cudaError_t launch_frame_begin(const SolveParams& p, cudaStream_t s) {
-  k_frame_begin<<<1, kSolveThreads, 0, s>>>(p);
+  k_frame_begin<<<1, kSolveThreads, sizeof(BeginSmem), s>>>(p);
   return cudaGetLastError();
 }
 cudaError_t launch_gn_step(const SolveParams& p, cudaStream_t s) {
-  k_gn_step<<<1, kSolveThreads, 0, s>>>(p);
+  k_gn_step<<<1, kSolveThreads, sizeof(GnSmem), s>>>(p);
   return cudaGetLastError();
 }
 cudaError_t launch_frame_end(const SolveParams& p, cudaStream_t s) {
@@ -865,11 +1053,11 @@ cudaError_t launch_frame_init(const SolveParams& p, cudaStream_t s) {
 }
 cudaError_t launch_linearise_begin(const SolveParams& p, const DState& x0, const DState& x1,
                                    cudaStream_t s) {
-  k_linearise_begin<<<1, kSolveThreads, 0, s>>>(p, x0, x1);
+  k_linearise_begin<<<1, kSolveThreads, sizeof(BeginSmem), s>>>(p, x0, x1);
   return cudaGetLastError();
 }
 cudaError_t launch_linearise_end(const SolveParams& p, dri_linearisation* out, cudaStream_t s) {
-  k_linearise_end<<<1, kSolveThreads, 0, s>>>(p, out);
+  k_linearise_end<<<1, kSolveThreads, sizeof(GnSmem), s>>>(p, out);
   return cudaGetLastError();
 }
 
