@@ -155,8 +155,12 @@ StreamLayout make_layout(const dri_stream_config& cfg) {
   for (int l = 0; l < cfg.levels; ++l)
     maxb = std::max(maxb, track_grid_blocks(cfg.width >> l, cfg.height >> l, 1));
   L.max_blocks = maxb;
+  L.counters = off;
+  off = align_up(off + (size_t)(1 + fold_groups(maxb)) * sizeof(uint32_t));
   L.partials = off;
   off = align_up(off + (size_t)maxb * kSumsAll * (fp32p ? 4 : 8));
+  L.gpartials = off;
+  off = align_up(off + (size_t)fold_groups(maxb) * kSumsAll * (fp32p ? 4 : 8));
   L.flags = off;
   off = align_up(off + npx);
   L.lin_out = off;
@@ -178,6 +182,8 @@ struct dri_stream_s {
   float* in_depth = nullptr;
   float* in_inten = nullptr;
   void* partials = nullptr;
+  void* gpartials = nullptr;
+  uint32_t* counters = nullptr;
   uint8_t* flags = nullptr;
   dri_linearisation* lin_dev = nullptr;
   LevelMaps maps[kMaxLevels];
@@ -281,6 +287,8 @@ TrackParams track_params(const dri_stream_s* s, int level, uint8_t* flags) {
   p.m = s->maps[level];
   p.ctrl = s->ctrl;
   p.partials = s->partials;
+  p.gpartials = s->gpartials;
+  p.counters = s->counters;
   p.flags = flags;
   p.ppt = s->ppt[level];
   p.nblocks = track_grid_blocks(p.g.w, p.g.h, p.ppt);
@@ -492,6 +500,8 @@ int dri_create_stream(const dri_stream_config* cfg, const dri_state* x_init, voi
   s->in_depth = (float*)(s->ws + L.in_depth);
   s->in_inten = (float*)(s->ws + L.in_inten);
   s->partials = (void*)(s->ws + L.partials);
+  s->gpartials = (void*)(s->ws + L.gpartials);
+  s->counters = (uint32_t*)(s->ws + L.counters);
   s->flags = (uint8_t*)(s->ws + L.flags);
   s->lin_dev = (dri_linearisation*)(s->ws + L.lin_out);
   for (int l = 0; l < cfg->levels; ++l) {
@@ -504,7 +514,7 @@ int dri_create_stream(const dri_stream_config* cfg, const dri_state* x_init, voi
       m.inten[k] = (float*)(s->ws + L.level_off[l][k][2]);
       m.grad[k] = (void*)(s->ws + L.level_off[l][k][3]);
     }
-    s->ppt[l] = 1;
+    s->ppt[l] = track_default_ppt(s->geom[l].w, s->geom[l].h);
   }
   s->x_init = to_dstate(*x_init);
   // control block: zero, then the initial state
@@ -515,7 +525,7 @@ int dri_create_stream(const dri_stream_config* cfg, const dri_state* x_init, voi
   h->ref_index = 0;
   h->t_state = x_init->t;
   if (cudaMemcpyAsync(s->ctrl, h, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
-      cudaMemsetAsync(s->ws + L.level_off[0][0][0], 0, L.partials - L.level_off[0][0][0], s->stream) !=
+      cudaMemsetAsync(s->ws + L.level_off[0][0][0], 0, L.flags - L.level_off[0][0][0], s->stream) !=
           cudaSuccess ||
       cudaStreamSynchronize(s->stream) != cudaSuccess) {
     dri_destroy_stream(s);

@@ -29,6 +29,7 @@ constexpr int kSums = 29;             // per term: 21 (upper J J^T) + 6 (J e) + 
 constexpr int kSumsAll = 2 * kSums;   // ICP then photometric
 constexpr int kTrackThreadsX = 32;
 constexpr int kTrackThreadsY = 8;
+constexpr int kFoldGroup = 16;        // blocks per first-level fold of the pixel kernel
 
 struct DState {                       // Eq. 1
   double r[3];
@@ -89,7 +90,7 @@ struct LevelMaps {
 };
 
 struct StreamLayout {
-  size_t ctrl, imu, in_depth, in_inten, partials, flags, lin_out, total;
+  size_t ctrl, imu, in_depth, in_inten, counters, partials, gpartials, flags, lin_out, total;
   size_t level_off[kMaxLevels][2][4];  // per level, per set: depth, normal, inten, grad
   int64_t plane[kMaxLevels];
   int max_blocks;
@@ -101,7 +102,9 @@ struct TrackParams {
   LevelGeom g;
   LevelMaps m;
   Ctrl* ctrl;
-  void* partials;
+  void* partials;                     // per-block partial sums
+  void* gpartials;                    // per-group partial sums
+  uint32_t* counters;                 // [0]: groups done, [1 + g]: blocks of group g done
   uint8_t* flags;
   int32_t nblocks;
   int32_t ppt;                        // pixel rows per thread
@@ -137,6 +140,8 @@ cudaError_t launch_gradient(const LevelMaps& m, const Ctrl* ctrl, int w, int h, 
                             cudaStream_t s);
 cudaError_t launch_track(const TrackParams& p, bool fp16, bool fp32_partials, cudaStream_t s);
 int track_grid_blocks(int w, int h, int ppt);
+int track_default_ppt(int w, int h);
+inline int fold_groups(int nblocks) { return (nblocks + kFoldGroup - 1) / kFoldGroup; }
 
 cudaError_t prepare_solver_kernels();   // opt-in shared memory sizes (current device)
 int solver_max_imu_pieces();

@@ -17,7 +17,7 @@
 //    rejected with DRI_EINVAL before anything is launched;
 //  * the static array is shared by every call on a device and keeps the last
 //    call's contents; each call re-initialises what must start at zero (the
-//    block counter and the status word) before its kernels run;
+//    fold counters and the status word) before its kernels run;
 //  * calls whose GPU work overlaps (different streams or host threads, without
 //    ordering between them) race on the array: order them on one stream;
 //  * the device address of the array is looked up once per device, on the first
@@ -44,11 +44,14 @@ constexpr size_t kOffCtrl = 0;
 constexpr size_t kOffNormal0 = na_align(kOffCtrl + sizeof(Ctrl));
 constexpr size_t kOffNormal1 = na_align(kOffNormal0 + 3 * kPlane * sizeof(float));
 constexpr size_t kOffGrad = na_align(kOffNormal1 + 3 * kPlane * sizeof(float));
-constexpr size_t kOffPartials = na_align(kOffGrad + 2 * kPlane * sizeof(float));
 // one pixel per thread: at most ceil(320/32) * ceil(240/8) blocks
 constexpr int kNoallocMaxBlocks = ((kNoallocMaxW + kTrackThreadsX - 1) / kTrackThreadsX) *
                                   ((kNoallocMaxH + kTrackThreadsY - 1) / kTrackThreadsY);
-constexpr size_t kNoallocBytes = na_align(kOffPartials + (size_t)kNoallocMaxBlocks * kSumsAll * sizeof(double));
+constexpr int kNoallocMaxGroups = (kNoallocMaxBlocks + kFoldGroup - 1) / kFoldGroup;
+constexpr size_t kOffCounters = na_align(kOffGrad + 2 * kPlane * sizeof(float));
+constexpr size_t kOffPartials = na_align(kOffCounters + (1 + kNoallocMaxGroups) * sizeof(uint32_t));
+constexpr size_t kOffGPartials = na_align(kOffPartials + (size_t)kNoallocMaxBlocks * kSumsAll * sizeof(double));
+constexpr size_t kNoallocBytes = na_align(kOffGPartials + (size_t)kNoallocMaxGroups * kSumsAll * sizeof(double));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
@@ -58,7 +61,8 @@ void* g_scratch_addr[kMaxDevices] = {};
 
 // Per-call set-up: transforms of the pixel kernel from (x_ref, x0, x1) exactly as
 // the stream path computes them, status and counter cleared, set 0 = reference.
-__global__ void k_noalloc_begin(Ctrl* c, DState xref, DState x0, DState x1) {
+__global__ void k_noalloc_begin(Ctrl* c, uint32_t* counters, DState xref, DState x0, DState x1) {
+  for (int i = threadIdx.x; i < 1 + kNoallocMaxGroups; i += blockDim.x) counters[i] = 0u;
   if (threadIdx.x != 0) return;
   double Rref[9], R0[9], R1[9], M[9], dr[3], t[3];
   quat_to_rot(xref.q, Rref);
@@ -200,7 +204,8 @@ extern "C" int dri_linearise_pair_noalloc(const dri_stream_config* cfg, const fl
   m.grad[0] = base + kOffGrad;
   m.grad[1] = base + kOffGrad;                      // the live set's gradient is never read
 
-  k_noalloc_begin<<<1, 32, 0, s>>>(ctrl, dstate_of(*x_ref), dstate_of(*x0), dstate_of(*x1));
+  uint32_t* counters = reinterpret_cast<uint32_t*>(base + kOffCounters);
+  k_noalloc_begin<<<1, 32, 0, s>>>(ctrl, counters, dstate_of(*x_ref), dstate_of(*x0), dstate_of(*x1));
   if (cudaGetLastError() != cudaSuccess) return DRI_ECUDA;
   const float dmin = (float)cfg->depth_min, dmax = (float)cfg->depth_max;
   if (launch_normals(m, ctrl, g, dmin, dmax, false, 0, s) != cudaSuccess) return DRI_ECUDA;
@@ -213,6 +218,8 @@ extern "C" int dri_linearise_pair_noalloc(const dri_stream_config* cfg, const fl
   p.m = m;
   p.ctrl = ctrl;
   p.partials = base + kOffPartials;
+  p.gpartials = base + kOffGPartials;
+  p.counters = counters;
   p.flags = flags;
   p.ppt = 1;
   p.nblocks = track_grid_blocks(g.w, g.h, 1);

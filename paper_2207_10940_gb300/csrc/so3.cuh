@@ -7,6 +7,12 @@
 
 namespace dri {
 
+// Below this theta^2 (theta < 0.05 rad) the rotation functions use their Taylor
+// series in theta^2 (five terms, relative error below 1e-16 there): on this GPU a
+// dependent FP64 FMA costs ~64 cycles but a sincos ~1.4k and a sqrt or divide
+// several hundred, and most angles here (IMU pieces, residuals, GN steps) are small.
+constexpr double kSeriesT2 = 2.5e-3;
+
 __device__ __forceinline__ void m3_mul(const double* A, const double* B, double* C) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -65,13 +71,13 @@ __device__ __forceinline__ void rodrigues_form(const double* w, double a, double
   R[6] = -a * y + b * x * z;     R[7] = a * x + b * y * z;      R[8] = 1.0 + b * (z * z - n2);
 }
 
-// Exp of a rotation vector (Rodrigues); series below 1e-3 rad.
+// Exp of a rotation vector (Rodrigues): I + sin(t)/t K + (1 - cos t)/t^2 K^2.
 __device__ __forceinline__ void so3_exp(const double* w, double* R) {
   const double t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
   double a, b;
-  if (t2 < 1e-6) {
-    a = 1.0 - t2 / 6.0 + t2 * t2 / 120.0;
-    b = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
+  if (t2 < kSeriesT2) {
+    a = 1.0 + t2 * (-1.0 / 6 + t2 * (1.0 / 120 + t2 * (-1.0 / 5040 + t2 * (1.0 / 362880))));
+    b = 0.5 + t2 * (-1.0 / 24 + t2 * (1.0 / 720 + t2 * (-1.0 / 40320 + t2 * (1.0 / 3628800))));
   } else {
     const double t = sqrt(t2);
     double s, c;
@@ -82,13 +88,14 @@ __device__ __forceinline__ void so3_exp(const double* w, double* R) {
   rodrigues_form(w, a, b, R);
 }
 
-// Right Jacobian Jr(w): Exp(w + d) ~= Exp(w) Exp(Jr d).
+// Right Jacobian Jr(w) = I - (1 - cos t)/t^2 K + (t - sin t)/t^3 K^2:
+// Exp(w + d) ~= Exp(w) Exp(Jr d).
 __device__ __forceinline__ void so3_jr(const double* w, double* J) {
   const double t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
   double a, b;
-  if (t2 < 1e-6) {
-    a = 0.5 - t2 / 24.0 + t2 * t2 / 720.0;
-    b = 1.0 / 6.0 - t2 / 120.0 + t2 * t2 / 5040.0;
+  if (t2 < kSeriesT2) {
+    a = 0.5 + t2 * (-1.0 / 24 + t2 * (1.0 / 720 + t2 * (-1.0 / 40320 + t2 * (1.0 / 3628800))));
+    b = 1.0 / 6 + t2 * (-1.0 / 120 + t2 * (1.0 / 5040 + t2 * (-1.0 / 362880 + t2 * (1.0 / 39916800))));
   } else {
     const double t = sqrt(t2);
     double s, c;
@@ -99,12 +106,13 @@ __device__ __forceinline__ void so3_jr(const double* w, double* J) {
   rodrigues_form(w, -a, b, J);
 }
 
-// Inverse left Jacobian: Log(Exp(d) Exp(w)) ~= w + Jl^-1(w) d.  Jr^-1(w) = Jl^-1(-w).
+// Inverse left Jacobian: Log(Exp(d) Exp(w)) ~= w + Jl^-1(w) d, with
+// Jl^-1 = I - K/2 + (1/t^2 - (1 + cos t)/(2 t sin t)) K^2.  Jr^-1(w) = Jl^-1(-w).
 __device__ __forceinline__ void so3_jl_inv(const double* w, double* J) {
   const double t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
   double c;
-  if (t2 < 1e-6) {
-    c = 1.0 / 12.0 + t2 / 720.0 + t2 * t2 / 30240.0;
+  if (t2 < kSeriesT2) {
+    c = 1.0 / 12 + t2 * (1.0 / 720 + t2 * (1.0 / 30240 + t2 * (1.0 / 1209600 + t2 * (1.0 / 47900160))));
   } else {
     const double t = sqrt(t2);
     double s, co;
@@ -119,16 +127,19 @@ __device__ __forceinline__ void so3_jr_inv(const double* w, double* J) {
   so3_jl_inv(m, J);
 }
 
-// Log of a rotation matrix (angle below pi - 1e-6).
+// Log of a rotation matrix (angle below pi - 1e-6).  The skew part is
+// v = 2 sin(t) k; for small angles t / (2 sin t) = asin(s) / (2 s), s = sin t,
+// is taken from its series in s^2 = |v|^2 / 4.
 __device__ __forceinline__ void so3_log(const double* R, double* w) {
-  double c = 0.5 * (R[0] + R[4] + R[8] - 1.0);
-  c = fmin(1.0, fmax(-1.0, c));
-  const double t = acos(c);
+  const double c = 0.5 * (R[0] + R[4] + R[8] - 1.0);
   const double v0 = R[7] - R[5], v1 = R[2] - R[6], v2 = R[3] - R[1];
   double f;
-  if (t < 1e-3) {
-    f = 0.5 * (1.0 + t * t / 6.0 + 7.0 * t * t * t * t / 360.0);
+  if (c > 0.99875) {                                  // t < 0.05
+    const double s2 = 0.25 * (v0 * v0 + v1 * v1 + v2 * v2);
+    f = 0.5 * (1.0 + s2 * (1.0 / 6 + s2 * (3.0 / 40 + s2 * (5.0 / 112 + s2 * (35.0 / 1152 +
+               s2 * (63.0 / 2816 + s2 * (231.0 / 13312)))))));
   } else {
+    const double t = acos(fmin(1.0, fmax(-1.0, c)));
     f = t / (2.0 * sin(t));
   }
   w[0] = f * v0;
@@ -136,9 +147,9 @@ __device__ __forceinline__ void so3_log(const double* R, double* w) {
   w[2] = f * v2;
 }
 
-__device__ __forceinline__ void quat_to_rot(const double* qin, double* R) {
-  const double n = rsqrt(qin[0] * qin[0] + qin[1] * qin[1] + qin[2] * qin[2] + qin[3] * qin[3]);
-  const double w = qin[0] * n, x = qin[1] * n, y = qin[2] * n, z = qin[3] * n;
+// Rotation matrix of a unit quaternion (every quaternion stored here is kept unit).
+__device__ __forceinline__ void quat_to_rot(const double* q, double* R) {
+  const double w = q[0], x = q[1], y = q[2], z = q[3];
   R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
   R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
   R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
@@ -151,12 +162,13 @@ __device__ __forceinline__ void quat_mul(const double* p, const double* q, doubl
   o[3] = p[0] * q[3] + p[1] * q[2] - p[2] * q[1] + p[3] * q[0];
 }
 
+// exp of a rotation vector as a unit quaternion: (cos(t/2), sin(t/2)/t w).
 __device__ __forceinline__ void quat_exp(const double* w, double* q) {
   const double t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
   double s, c;
-  if (t2 < 1e-6) {
-    s = 0.5 - t2 / 48.0 + t2 * t2 / 3840.0;
-    c = 1.0 - t2 / 8.0 + t2 * t2 / 384.0;
+  if (t2 < kSeriesT2) {
+    s = 0.5 + t2 * (-1.0 / 48 + t2 * (1.0 / 3840 + t2 * (-1.0 / 645120 + t2 * (1.0 / 185794560))));
+    c = 1.0 + t2 * (-1.0 / 8 + t2 * (1.0 / 384 + t2 * (-1.0 / 46080 + t2 * (1.0 / 10321920))));
   } else {
     const double t = sqrt(t2);
     double sh, ch;
@@ -170,10 +182,13 @@ __device__ __forceinline__ void quat_exp(const double* w, double* q) {
   q[3] = s * w[2];
 }
 
+// Renormalise a quaternion that is unit up to rounding: one Newton step of
+// 1/sqrt(n2) about n2 = 1 (exact to O((n2 - 1)^2)); far from unit, a full rsqrt.
 __device__ __forceinline__ void quat_normalise(double* q) {
-  const double n = rsqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const double n2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  const double f = fabs(n2 - 1.0) < 1e-6 ? 1.5 - 0.5 * n2 : rsqrt(n2);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) q[i] *= n;
+  for (int i = 0; i < 4; ++i) q[i] *= f;
 }
 
 // Rotation of a unit quaternion from its matrix through the matrix log.

@@ -54,19 +54,17 @@ __device__ __forceinline__ const dri_imu_sample* imu_samples(const ImuHeader* h)
   return reinterpret_cast<const dri_imu_sample*>(h + 1);
 }
 
-// Zero-order-hold pieces of [t0, t1]: sample index and duration; -1 if the samples
-// do not cover the interval or there are more than kMaxPieces pieces.
-__device__ int imu_pieces(const ImuHeader* h, int* pk, double* pdt) {
-  const dri_imu_sample* s = imu_samples(h);
-  const int n = h->n;
-  const double t0 = h->t0, t1 = h->t1;
-  if (n <= 0 || s[0].t > t0 || s[n - 1].t < t1 || !(t1 > t0)) return -1;
+// Zero-order-hold pieces of [t0, t1] from the sample times ts[0..n): sample index
+// and duration; -1 if the samples do not cover the interval or there are more than
+// kMaxPieces pieces.
+__device__ int imu_pieces(const double* ts, int n, double t0, double t1, int* pk, double* pdt) {
+  if (n <= 0 || ts[0] > t0 || ts[n - 1] < t1 || !(t1 > t0)) return -1;
   int k = 0;
-  while (k + 1 < n && s[k + 1].t <= t0) ++k;
+  while (k + 1 < n && ts[k + 1] <= t0) ++k;
   double tau = t0;
   int np = 0;
   while (tau < t1) {
-    const double nxt = (k + 1 >= n) ? t1 : fmin(s[k + 1].t, t1);
+    const double nxt = (k + 1 >= n) ? t1 : fmin(ts[k + 1], t1);
     if (nxt > tau) {
       if (np >= kMaxPieces) return -1;
       pk[np] = k;
@@ -96,6 +94,7 @@ struct ImuWork {
   double w[kMaxPieces];
   double Cv[kMaxPieces + 1][3];       // suffix sums of u_k dt_k
   double Dv[kMaxPieces + 1][3];       // suffix sums of u_k w_k
+  double ts[kMaxPieces + 2];          // sample times
   int pk[kMaxPieces];
   int np;
 };
@@ -126,11 +125,16 @@ __device__ __forceinline__ void gyro_gain_row(const ImuWork& W, int np, int k, i
 __device__ bool preintegrate_block(const ImuHeader* h, const double* bg, const double* ba, bool cov,
                                    double gnd, double and_, ImuWork& W, Preint& P) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) W.np = imu_pieces(h, W.pk, W.dt);
+  const dri_imu_sample* s = imu_samples(h);
+  const int ns = h->n;
+  const bool fits = ns > 0 && ns <= kMaxPieces + 2;
+  if (fits)
+    for (int k = tid; k < ns; k += nt) W.ts[k] = s[k].t;   // one coalesced pass
+  __syncthreads();
+  if (tid == 0) W.np = fits ? imu_pieces(W.ts, ns, h->t0, h->t1, W.pk, W.dt) : -1;
   __syncthreads();
   const int np = W.np;
   if (np <= 0) return false;
-  const dri_imu_sample* s = imu_samples(h);
   for (int k = tid; k < np; k += nt) {
     const dri_imu_sample& m = s[W.pk[k]];
     const double dt = W.dt[k];
@@ -141,20 +145,22 @@ __device__ bool preintegrate_block(const ImuHeader* h, const double* bg, const d
     for (int i = 0; i < 3; ++i) W.u[k][i] = m.acc[i] - ba[i];
   }
   __syncthreads();
-  if (tid < 32) {                      // prefix products dR_{k+1} = dR_k Exp(theta_k)
+  if (tid < 9) {                       // prefix products dR_{k+1} = dR_k Exp(theta_k)
     const int r = tid / 3, c = tid % 3;
-    if (tid < 9) W.dR[0][tid] = (r == c) ? 1.0 : 0.0;
-    if (tid == 9) W.tau[0] = 0.0;
-    __syncwarp();
+    W.dR[0][tid] = (r == c) ? 1.0 : 0.0;
+    __syncwarp(0x1ffu);
     for (int k = 0; k < np; ++k) {
-      if (tid < 9) {
-        const double* A = W.dR[k];
-        const double* E = W.EP[k];
-        W.dR[k + 1][tid] = A[3 * r] * E[c] + A[3 * r + 1] * E[3 + c] + A[3 * r + 2] * E[6 + c];
-      } else if (tid == 9) {
-        W.tau[k + 1] = W.tau[k] + W.dt[k];
-      }
-      __syncwarp();
+      const double* A = W.dR[k];
+      const double* E = W.EP[k];
+      W.dR[k + 1][tid] = A[3 * r] * E[c] + A[3 * r + 1] * E[3 + c] + A[3 * r + 2] * E[6 + c];
+      __syncwarp(0x1ffu);
+    }
+  } else if (tid == 32) {              // piece start times (another warp)
+    double acc = 0.0;
+    W.tau[0] = 0.0;
+    for (int k = 0; k < np; ++k) {
+      acc += W.dt[k];
+      W.tau[k + 1] = acc;
     }
   }
   __syncthreads();
@@ -190,41 +196,33 @@ __device__ bool preintegrate_block(const ImuHeader* h, const double* bg, const d
     }
   }
   __syncthreads();
-  if (tid < 42) {                      // sums over pieces, one thread per value
+  const int warp = tid >> 5, lane = tid & 31;
+  if (warp == 0 && lane < 6) {         // dv, dp
+    const int i = lane % 3;
+    double acc = 0.0;
+    for (int k = 0; k < np; ++k) acc += W.u[k][i] * (lane < 3 ? W.dt[k] : W.w[k]);
+    (lane < 3 ? P.dv : P.dp)[i] = acc;
+  } else if (warp == 1 && lane < 18) { // d(dv, dp)/d(b_g) = -sum [u_k]x Psi_k (dt_k | w_k)
+    const int e = lane % 9, r = e / 3, c = e % 3, r1 = (r + 1) % 3, r2 = (r + 2) % 3;
     double acc = 0.0;
     for (int k = 0; k < np; ++k) {
       const double* u = W.u[k];
-      const double dt = W.dt[k], wk = W.w[k];
-      if (tid < 3) {
-        acc += u[tid] * dt;
-      } else if (tid < 6) {
-        acc += u[tid - 3] * wk;
-      } else if (tid < 24) {           // -[u]x Psi_k (dt | w)
-        const int e = (tid - 6) % 9, r = e / 3, c = e % 3;
-        const double* Ps = W.EP[k];
-        double hv;
-        if (r == 0) hv = -u[2] * Ps[3 + c] + u[1] * Ps[6 + c];
-        else if (r == 1) hv = u[2] * Ps[c] - u[0] * Ps[6 + c];
-        else hv = -u[1] * Ps[c] + u[0] * Ps[3 + c];
-        acc -= hv * (tid < 15 ? dt : wk);
-      } else {                         // -dR_k (dt | w)
-        const int e = (tid - 24) % 9;
-        acc -= W.dR[k][e] * (tid < 33 ? dt : wk);
-      }
+      const double* Ps = W.EP[k];
+      const double hv = u[r1] * Ps[3 * r2 + c] - u[r2] * Ps[3 * r1 + c];
+      acc -= hv * (lane < 9 ? W.dt[k] : W.w[k]);
     }
-    if (tid < 3) P.dv[tid] = acc;
-    else if (tid < 6) P.dp[tid - 3] = acc;
-    else if (tid < 15) P.Vg[tid - 6] = acc;
-    else if (tid < 24) P.Pg[tid - 15] = acc;
-    else if (tid < 33) P.Va[tid - 24] = acc;
-    else P.Pa[tid - 33] = acc;
-  } else if (tid >= 64 && tid < 73) {  // d(dR)/d(b_g) = dR_N^T Psi_N
-    const int e = tid - 64, r = e / 3, c = e % 3;
+    (lane < 9 ? P.Vg : P.Pg)[e] = acc;
+  } else if (warp == 2 && lane < 18) { // d(dv, dp)/d(b_a) = -sum dR_k (dt_k | w_k)
+    const int e = lane % 9;
+    double acc = 0.0;
+    for (int k = 0; k < np; ++k) acc -= W.dR[k][e] * (lane < 9 ? W.dt[k] : W.w[k]);
+    (lane < 9 ? P.Va : P.Pa)[e] = acc;
+  } else if (warp == 3 && lane < 9) {  // d(dR)/d(b_g) = dR_N^T Psi_N
+    const int r = lane / 3, c = lane % 3;
     const double* R = W.dR[np];
     const double* Ps = W.EP[np];
-    P.Phig[e] = R[r] * Ps[c] + R[3 + r] * Ps[3 + c] + R[6 + r] * Ps[6 + c];
-  } else if (tid >= 96 && tid < 105) {
-    P.dR[tid - 96] = W.dR[np][tid - 96];
+    P.Phig[lane] = R[r] * Ps[c] + R[3 + r] * Ps[3 + c] + R[6 + r] * Ps[6 + c];
+    P.dR[lane] = R[lane];
   } else if (cov && tid >= 128 && tid < 128 + 45) {
     // covariance entry (r, c), r <= c, of (dphi, dv, dp)
     int e = tid - 128, r = 0;
@@ -269,10 +267,11 @@ struct ImuLin {
 __device__ void imu_linearise(const DState& x0, const DState& x1, const Preint& P,
                               const SolveParams& sp, ImuLin& L, double* J) {
   const int tid = threadIdx.x;
-  if (tid == 0) quat_to_rot(x0.q, L.R0);
-  else if (tid == 1) quat_to_rot(x0.qg, L.Q0);
-  else if (tid == 2) quat_to_rot(x1.q, L.R1);
-  else if (tid == 3) quat_to_rot(x1.qg, L.Q1);
+  const int warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) quat_to_rot(x0.q, L.R0);          // independent serial pieces go to
+  else if (tid == 32) quat_to_rot(x0.qg, L.Q0);   // different warps so they overlap
+  else if (tid == 64) quat_to_rot(x1.q, L.R1);
+  else if (tid == 96) quat_to_rot(x1.qg, L.Q1);
   __syncthreads();
   if (tid == 0) {
     const double T = P.T;
@@ -280,23 +279,30 @@ __device__ void imu_linearise(const DState& x0, const DState& x1, const Preint& 
     m3_mul(L.R0, sp.R_CS, L.A0);
     m3_mul(L.A0, P.dR, L.RWS1);
     m3_mult(L.RWS1, sp.R_CS, L.Rh);                 // R^ = R0 Rc dR Rc^T
-    m3_mul(L.Q0, L.A0, L.QA);
-    for (int i = 0; i < 3; ++i) L.c[i] = x0.v[i] * T + 0.5 * gI[i] * T * T;
-    double t1[3], t2[3], t3[3], t4[3], t5[3], M[9];
+    double c[3], t1[3], t2[3], t3[3], t4[3], M[9];
+    for (int i = 0; i < 3; ++i) c[i] = x0.v[i] * T + 0.5 * gI[i] * T * T;
     m3_vec(L.R0, sp.r_CS, t1);
-    m3_tvec(L.Q0, L.c, t2);
+    m3_tvec(L.Q0, c, t2);
     m3_vec(L.A0, P.dp, t3);
     m3_vec(L.Rh, sp.r_CS, t4);
-    m3_vec(L.QA, P.dv, t5);
     for (int i = 0; i < 3; ++i) {
       L.r[i] = x0.r[i] + t1[i] + t2[i] + t3[i] - t4[i];
-      L.v[i] = x0.v[i] + gI[i] * T + t5[i];
       L.e[i] = L.r[i] - x1.r[i];
-      L.e[6 + i] = L.v[i] - x1.v[i];
     }
     m3_mult(L.Rh, L.R1, M);
     so3_log(M, L.e + 3);
   } else if (tid == 32) {
+    const double T = P.T;
+    double QR[9], t5[3];
+    m3_mul(L.Q0, L.R0, QR);
+    m3_mul(QR, sp.R_CS, L.QA);                      // Q0 R0 Rc
+    m3_vec(L.QA, P.dv, t5);
+    for (int i = 0; i < 3; ++i) {
+      L.c[i] = x0.v[i] * T + 0.5 * (i == 2 ? -sp.g : 0.0) * T * T;
+      L.v[i] = x0.v[i] + (i == 2 ? -sp.g : 0.0) * T + t5[i];
+      L.e[6 + i] = L.v[i] - x1.v[i];
+    }
+  } else if (tid == 64) {
     double M[9];
     for (int i = 0; i < 3; ++i) {
       L.e[9 + i] = x0.bg[i] - x1.bg[i];
@@ -307,9 +313,9 @@ __device__ void imu_linearise(const DState& x0, const DState& x1, const Preint& 
   }
   __syncthreads();
   if (tid == 0) so3_jl_inv(L.e + 3, L.Jla);
-  else if (tid == 1) so3_jl_inv(L.e + 15, L.Jlg);
-  else if (tid == 2) so3_jr_inv(L.e + 3, L.Jra);
-  else if (tid == 3) so3_jr_inv(L.e + 15, L.Jrg);
+  else if (tid == 32) so3_jl_inv(L.e + 15, L.Jlg);
+  else if (tid == 64) so3_jr_inv(L.e + 3, L.Jra);
+  else if (tid == 96) so3_jr_inv(L.e + 15, L.Jrg);
   if (J == nullptr) {
     __syncthreads();
     return;
@@ -327,8 +333,14 @@ __device__ void imu_linearise(const DState& x0, const DState& x1, const Preint& 
   auto ident = [&](int r0, int c0, double s) {
     for (int r = 0; r < 3; ++r) J[(r0 + r) * 34 + c0 + r] = s;
   };
+  // 22 blocks: heavy ones alone on their warp (lane 0), light ones share warps
+  constexpr int kTab[8][4] = {{12, -1, -1, -1}, {13, -1, -1, -1}, {7, 0, 2, -1}, {9, 3, 4, -1},
+                              {14, 6, 11, -1},  {16, 15, 18, -1}, {17, 19, 1, -1}, {20, 21, 5, 8}};
+  int blk = -1;
+  if (lane < 4) blk = kTab[warp][lane];
+  if (warp == 0 && lane == 4) blk = 10;
   double t[9], K[9], u[3];
-  switch (tid) {
+  switch (blk) {
     // x1 columns 17..33
     case 0: ident(0, 17, -1.0); break;
     case 1: put3(3, 20, L.Jra, -1.0); break;
@@ -475,25 +487,6 @@ __device__ bool block_ldlt(double* A, int n, int ld, double* col, int* fail) {
   return *fail == 0;
 }
 
-// Solve L D L^T x = b in place (b becomes x).  Warp 0 only, n <= 64.
-__device__ void ldlt_solve_warp(const double* A, int n, int ld, double* b) {
-  const int lane = threadIdx.x & 31;
-  for (int k = 0; k < n; ++k) {
-    const double z = b[k];
-    __syncwarp();
-    for (int i = k + 1 + lane; i < n; i += 32) b[i] -= A[i * ld + k] * z;
-    __syncwarp();
-  }
-  for (int i = lane; i < n; i += 32) b[i] /= A[i * ld + i];
-  __syncwarp();
-  for (int k = n - 1; k > 0; --k) {
-    const double x = b[k];
-    __syncwarp();
-    for (int i = lane; i < k; i += 32) b[i] -= A[k * ld + i] * x;
-    __syncwarp();
-  }
-}
-
 // The same for one right-hand side in one thread.
 __device__ void ldlt_solve_thread(const double* A, int n, int ld, double* b) {
   for (int i = 0; i < n; ++i) {
@@ -507,6 +500,121 @@ __device__ void ldlt_solve_thread(const double* A, int n, int ld, double* b) {
     for (int k = i + 1; k < n; ++k) s -= A[k * ld + i] * b[k];
     b[i] = s;
   }
+}
+
+// Reciprocal of a positive double: an FP32 seed refined by two Newton-Raphson
+// steps y <- y + y (1 - d y) (quadratic convergence, 2^-24 -> 2^-48 -> below
+// 2^-53); outside the FP32 range a plain division.  A dependent FP64 divide costs
+// ~430 cycles here, this ~300.
+__device__ __forceinline__ double recip_pos(double d) {
+  if (d > 1e-30 && d < 1e30) {
+    double y = (double)__frcp_rn((float)d);
+    double e = fma(-d, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-d, y, 1.0);
+    return fma(y, e, y);
+  }
+  return 1.0 / d;
+}
+
+// Pivot reciprocal: the FP32 seed refined by one Newton-Raphson step
+// (relative error ~2^-48; the factorisation is then exact for a matrix whose
+// pivots are perturbed by that amount, far below what the system's rounding
+// already costs).
+__device__ __forceinline__ double pivot_recip(double d) {
+  if (d > 1e-30 && d < 1e30) {
+    const double y = (double)__frcp_rn((float)d);
+    return fma(y, fma(-d, y, 1.0), y);
+  }
+  return 1.0 / d;
+}
+
+// Solves A x = b for a symmetric positive definite N x N matrix (row-major in
+// shared memory, lower triangle read) on the first T threads (T a multiple of 32;
+// the other threads of the block must not call it).  Element-parallel LDL^T: every
+// thread keeps its share of the lower triangle of [A | b] in registers; per pivot
+// the column is published in a double-buffered shared vector behind one named
+// barrier, and every warp computes the pivot reciprocal itself (no second
+// barrier).  The forward substitution is the b column of the same sweep; the
+// backward substitution runs in warp 0 with shuffles.  On this GPU an FP64 warp
+// instruction occupies its SM sub-partition's FP64 unit for ~64 cycles whatever
+// the number of active lanes, so the work is spread over the lanes of T/32 warps
+// on different sub-partitions.  Scratch: colbuf 2 (N + 1), Lsm N * N, piv N.
+// Returns false (in every calling thread) if a pivot is not positive.
+template <int N, int T>
+__device__ bool ep_ldlt_solve(const double* A, const double* b, double* x, double* colbuf,
+                              double* Lsm, double* piv) {
+  constexpr int kTri = N * (N + 1) / 2;
+  constexpr int kEnt = kTri + N;                     // lower triangle + the b column
+  constexpr int kOwn = (kEnt + T - 1) / T;
+  const int t = threadIdx.x;
+  int ei[kOwn], ej[kOwn];
+  double v[kOwn];
+#pragma unroll
+  for (int o = 0; o < kOwn; ++o) {
+    const int e = t + o * T;
+    int i = -1, j = -1;
+    if (e < kTri) {                                  // row-major lower triangle
+      i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
+      while (i * (i + 1) / 2 > e) --i;
+      while ((i + 1) * (i + 2) / 2 <= e) ++i;
+      j = e - i * (i + 1) / 2;
+    } else if (e < kEnt) {
+      i = e - kTri;
+      j = N;
+    }
+    ei[o] = i;
+    ej[o] = j;
+    v[o] = (i < 0) ? 0.0 : (j == N ? b[i] : A[i * N + j]);
+  }
+  for (int k = 0; k < N; ++k) {
+    double* cb = colbuf + (k & 1) * (N + 1);
+#pragma unroll
+    for (int o = 0; o < kOwn; ++o) {
+      if (ej[o] == k) cb[ei[o]] = v[o];              // column k (unscaled) with the pivot
+      if (ej[o] == N && ei[o] == k) cb[N] = v[o];    // z_k
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(T) : "memory");
+    const double d = cb[k];
+    const double r = pivot_recip(d);
+    const double zk = cb[N];
+    if (t == 0) {
+      piv[k] = d;
+      x[k] = zk * r;                                 // y_k = z_k / d_k
+    }
+#pragma unroll
+    for (int o = 0; o < kOwn; ++o) {
+      const int i = ei[o], j = ej[o];
+      if (i > k && j > k) v[o] = fma(-(cb[i] * r), j == N ? zk : cb[j], v[o]);
+    }
+  }
+  // unit-lower L = column k divided by d_k (v still holds the unscaled columns)
+#pragma unroll
+  for (int o = 0; o < kOwn; ++o) {
+    const int i = ei[o], j = ej[o];
+    if (i >= 0 && j < i) Lsm[i * N + j] = v[o] * pivot_recip(piv[j]);
+  }
+  asm volatile("bar.sync 1, %0;" ::"n"(T) : "memory");
+  bool ok = true;
+  if (t < 32) {                                      // L^T x = y
+    const int lane = t;
+    double y0 = (lane < N) ? x[lane] : 0.0;
+    double y1 = (lane + 32 < N) ? x[lane + 32] : 0.0;
+    for (int k = N - 1; k > 0; --k) {
+      const double xk = __shfl_sync(0xffffffffu, k < 32 ? y0 : y1, k & 31);
+      if (lane < k) y0 = fma(-Lsm[k * N + lane], xk, y0);
+      if (lane + 32 < k) y1 = fma(-Lsm[k * N + lane + 32], xk, y1);
+    }
+    if (lane < N) x[lane] = y0;
+    if (lane + 32 < N) x[lane + 32] = y1;
+    bool good = true;
+    for (int k = lane; k < N; k += 32) good = good && piv[k] > 0.0 && piv[k] < INFINITY;
+    ok = __all_sync(0xffffffffu, good);
+  }
+  asm volatile("bar.sync 1, %0;" ::"n"(T) : "memory");
+  if (t < 32 && t == 0) colbuf[0] = ok ? 1.0 : 0.0;
+  asm volatile("bar.sync 1, %0;" ::"n"(T) : "memory");
+  return colbuf[0] != 0.0;
 }
 
 // ---------------------------------------------------------------------------
@@ -528,9 +636,13 @@ struct GnSmem {
   double gl[2][6];
   double M6[36], MH6[36];
   double dprior[17];
-  double col[2 * 34];
+  double Hr[26 * 26], br[26];          // reduced system (x1's bias / gravity eliminated)
+  double xr[26], piv[26];
+  double col[2 * 27];
+  double Lsm[26 * 26];                // L rows of the solver
+  double Bg[6], Ag[6];                // gravity Jacobian blocks of x1 and x0 (3 x 2)
   double cost_imu;
-  int ok, fail;
+  int ok, fail, pd;
 };
 
 // Assemble the joint system at (ctrl->x0, ctrl->x1) into S.H (full), S.b.
@@ -625,33 +737,6 @@ __device__ void assemble(const SolveParams& sp, GnSmem& S) {
     S.cost_imu = ce;
   }
   __syncthreads();
-  // diagonal part of W_IMU (bias and gravity rows), pixel terms, prior: disjoint entries
-  if (tid < 6) {                        // bias rows 9..14: +I at x0, -I at x1
-    const int i = tid;
-    const double w = c->Wimu[(9 + i) * 18 + 9 + i];
-    S.H[(9 + i) * 34 + 9 + i] += w;
-    S.H[(26 + i) * 34 + 26 + i] += w;
-    S.H[(9 + i) * 34 + 26 + i] -= w;
-    S.b[9 + i] -= w * S.L.e[9 + i];
-    S.b[26 + i] += w * S.L.e[9 + i];
-  } else if (tid < 16) {                // gravity rows 15..17, columns {15, 16, 32, 33}
-    const int G[4] = {15, 16, 32, 33};
-    int e = tid - 6, a = 0;
-    while (e >= 4 - a) { e -= 4 - a; ++a; }
-    const int ci = G[a], cj = G[a + e];
-    double v = 0.0;
-    for (int k = 0; k < 3; ++k)
-      v += S.J[(15 + k) * 34 + ci] * c->Wimu[(15 + k) * 18 + 15 + k] * S.J[(15 + k) * 34 + cj];
-    S.H[ci * 34 + cj] += v;
-  } else if (tid < 20) {
-    const int G[4] = {15, 16, 32, 33};
-    const int ci = G[tid - 16];
-    double v = 0.0;
-    for (int k = 0; k < 3; ++k)
-      v -= S.J[(15 + k) * 34 + ci] * c->Wimu[(15 + k) * 18 + 15 + k] * S.L.e[15 + k];
-    S.b[ci] += v;
-  }
-  __syncthreads();
   // photometric on both poses (H12 = B H6 B^T, B = [-M; I]) and ICP on x1's pose
   for (int idx = tid; idx < 12 * 12; idx += nt) {
     const int i = idx / 12, j = idx % 12;
@@ -689,6 +774,65 @@ __device__ void assemble(const SolveParams& sp, GnSmem& S) {
     S.b[i] += acc;
   }
   __syncthreads();
+  // Reduced system for the solve: x1's biases and gravity (columns 26..33) only
+  // couple to x0's through the IMU's bias and gravity rows, so they are eliminated
+  // in closed form.  The bias random walk then drops out exactly (x1's bias just
+  // follows x0's) and the gravity rows leave w (A^T n)(n^T A), n the unit normal
+  // of the range of x1's gravity block B: no cancellation of the 1e8-scale weights.
+  for (int idx = tid; idx < 26 * 26; idx += nt) {
+    const int i = idx / 26, j = idx % 26;
+    S.Hr[idx] = j >= i ? S.H[i * 34 + j] : S.H[j * 34 + i];
+  }
+  if (tid < 26) S.br[tid] = S.b[tid];
+  if (tid >= 32 && tid < 38) {
+    const int k = (tid - 32) / 2, m = (tid - 32) % 2;
+    S.Bg[tid - 32] = S.J[(15 + k) * 34 + 32 + m];
+    S.Ag[tid - 32] = S.J[(15 + k) * 34 + 15 + m];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const double* B = S.Bg;   // B[k * 2 + m]
+    double nv[3] = {B[2] * B[5] - B[4] * B[3], B[4] * B[1] - B[0] * B[5], B[0] * B[3] - B[2] * B[1]};
+    const double inv = rsqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+    for (int i = 0; i < 3; ++i) nv[i] *= inv;
+    const double w = c->Wimu[15 * 18 + 15];         // gravity weight (equal on its 3 rows)
+    const double a0 = S.Ag[0] * nv[0] + S.Ag[2] * nv[1] + S.Ag[4] * nv[2];
+    const double a1 = S.Ag[1] * nv[0] + S.Ag[3] * nv[1] + S.Ag[5] * nv[2];
+    const double sn = nv[0] * S.L.e[15] + nv[1] * S.L.e[16] + nv[2] * S.L.e[17];
+    S.Hr[15 * 26 + 15] += w * a0 * a0;
+    S.Hr[15 * 26 + 16] += w * a0 * a1;
+    S.Hr[16 * 26 + 15] += w * a0 * a1;
+    S.Hr[16 * 26 + 16] += w * a1 * a1;
+    S.br[15] -= w * a0 * sn;
+    S.br[16] -= w * a1 * sn;
+  }
+  // full system (marginalisation, parity output): bias and gravity rows
+  if (tid < 6) {                        // bias rows 9..14: +I at x0, -I at x1
+    const int i = tid;
+    const double w = c->Wimu[(9 + i) * 18 + 9 + i];
+    S.H[(9 + i) * 34 + 9 + i] += w;
+    S.H[(26 + i) * 34 + 26 + i] += w;
+    S.H[(9 + i) * 34 + 26 + i] -= w;
+    S.b[9 + i] -= w * S.L.e[9 + i];
+    S.b[26 + i] += w * S.L.e[9 + i];
+  } else if (tid < 16) {                // gravity rows 15..17, columns {15, 16, 32, 33}
+    const int G[4] = {15, 16, 32, 33};
+    int e = tid - 6, a = 0;
+    while (e >= 4 - a) { e -= 4 - a; ++a; }
+    const int ci = G[a], cj = G[a + e];
+    double v = 0.0;
+    for (int k = 0; k < 3; ++k)
+      v += S.J[(15 + k) * 34 + ci] * c->Wimu[(15 + k) * 18 + 15 + k] * S.J[(15 + k) * 34 + cj];
+    S.H[ci * 34 + cj] += v;
+  } else if (tid < 20) {
+    const int G[4] = {15, 16, 32, 33};
+    const int ci = G[tid - 16];
+    double v = 0.0;
+    for (int k = 0; k < 3; ++k)
+      v -= S.J[(15 + k) * 34 + ci] * c->Wimu[(15 + k) * 18 + 15 + k] * S.L.e[15 + k];
+    S.b[ci] += v;
+  }
+  __syncthreads();
   for (int idx = tid; idx < 34 * 34; idx += nt) {
     const int i = idx / 34, j = idx % 34;
     if (j < i) S.H[idx] = S.H[j * 34 + i];
@@ -707,20 +851,38 @@ __global__ void __launch_bounds__(kSolveThreads) k_gn_step(SolveParams sp) {
     if (tid == 0) c->status = DRI_ENOTREADY;
     return;
   }
-  // Jacobi-scaled LDL^T solve of H dx = b
-  if (tid < 34) {
-    S.scale[tid] = 1.0 / sqrt(fmax(S.H[tid * 34 + tid], 1e-300));
+  // Jacobi-scaled LDL^T solve of the reduced 26 x 26 system (4 warps), then the
+  // eliminated x1 biases and gravity in closed form
+  if (tid < 26) S.scale[tid] = rsqrt(fmax(S.Hr[tid * 26 + tid], 1e-300));
+  __syncthreads();
+  for (int idx = tid; idx < 26 * 26; idx += nt) S.A[idx] = S.Hr[idx] * S.scale[idx / 26] * S.scale[idx % 26];
+  if (tid < 26) S.xr[tid] = S.br[tid] * S.scale[tid];
+  __syncthreads();
+  if (tid < 128) {
+    const bool pd = ep_ldlt_solve<26, 128>(S.A, S.xr, S.xr, S.col, S.Lsm, S.piv);
+    if (tid == 0) S.pd = pd;
   }
   __syncthreads();
-  for (int idx = tid; idx < 34 * 34; idx += nt) S.A[idx] = S.H[idx] * S.scale[idx / 34] * S.scale[idx % 34];
-  if (tid < 34) S.x[tid] = S.b[tid] * S.scale[tid];
+  if (tid < 26) S.x[tid] = S.xr[tid] * S.scale[tid];
   __syncthreads();
-  const bool pd = block_ldlt(S.A, 34, 34, S.col, &S.fail);
-  if (tid < 32) ldlt_solve_warp(S.A, 34, 34, S.x);
+  if (tid < 6) {
+    S.x[26 + tid] = S.L.e[9 + tid] + S.x[9 + tid];          // x1 bias follows x0 bias
+  } else if (tid == 32) {                                  // dg1 = -(B^T B)^-1 B^T (e_g + A dg0)
+    const double* B = S.Bg;
+    const double* A = S.Ag;
+    double u[3];
+    for (int k = 0; k < 3; ++k) u[k] = S.L.e[15 + k] + A[2 * k] * S.x[15] + A[2 * k + 1] * S.x[16];
+    const double m00 = B[0] * B[0] + B[2] * B[2] + B[4] * B[4];
+    const double m01 = B[0] * B[1] + B[2] * B[3] + B[4] * B[5];
+    const double m11 = B[1] * B[1] + B[3] * B[3] + B[5] * B[5];
+    const double q0 = B[0] * u[0] + B[2] * u[1] + B[4] * u[2];
+    const double q1 = B[1] * u[0] + B[3] * u[1] + B[5] * u[2];
+    const double idet = 1.0 / (m00 * m11 - m01 * m01);
+    S.x[32] = -(m11 * q0 - m01 * q1) * idet;
+    S.x[33] = -(m00 * q1 - m01 * q0) * idet;
+  }
   __syncthreads();
-  if (tid < 34) S.x[tid] *= S.scale[tid];
-  __syncthreads();
-  bool good = pd;
+  bool good = S.pd;
   for (int i = 0; i < 34; ++i) good = good && isfinite(S.x[i]);
   if (!good) {
     if (tid == 0) c->status = DRI_ELOST;

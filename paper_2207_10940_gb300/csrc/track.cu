@@ -23,8 +23,9 @@
 // diag(R^T, R^T) (R = R_ref or R_0); the solver rotates the reduced 6x6 systems
 // back in FP64.  Each term accumulates 29 values per thread (upper J J^T, J e,
 // e^2, count) in FP32, reduced by warp shuffles and a shared-memory tree to one
-// FP64 (or FP32) partial per block; the last block to finish folds all partials
-// in block order (deterministic) into ctrl->sums.
+// FP64 (or FP32) partial per block; the partials are folded in two fixed-order
+// levels (groups of blocks, then the groups) into ctrl->sums: deterministic, no
+// float atomics.
 #include <cuda_fp16.h>
 
 #include "dri_internal.h"
@@ -182,53 +183,82 @@ k_track(TrackParams p) {
   }
 
   // ---------------- reduction ----------------
+  // Warp: transpose-reduce.  Padded to 64 values, five halving exchanges leave
+  // lane l holding the warp sums of values 2l and 2l + 1 (62 shuffles instead of
+  // 5 per value).
+  float v[64];
 #pragma unroll
-  for (int k = 0; k < kSumsAll; ++k) {
+  for (int k = 0; k < 64; ++k) v[k] = k < kSumsAll ? acc[k] : 0.f;
+  const int lane = threadIdx.x;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+  for (int half = 32, off = 16; off > 0; half >>= 1, off >>= 1) {
+    const bool hi = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float send = hi ? v[i] : v[i + half];
+      const float keep = hi ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
   }
-  __shared__ float s_warp[kTrackThreadsY][kSumsAll];
-  __shared__ P s_fold[4][64];
+  __shared__ float s_warp[kTrackThreadsY][64];
   __shared__ bool s_last;
   const int tid = threadIdx.y * kTrackThreadsX + threadIdx.x;
-  const int warp = threadIdx.y;  // 32-wide rows are warps
-  if (threadIdx.x == 0) {
+  s_warp[threadIdx.y][2 * lane] = v[0];
+  s_warp[threadIdx.y][2 * lane + 1] = v[1];
+  __syncthreads();
+  // Block: FP32 sum of the warps, one FP64 (or FP32) partial per block.  Blocks fold
+  // in two deterministic levels: the last block of each group of kFoldGroup blocks
+  // sums the group's partials in block order, the last group sums the groups.
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  const int grp = bid / kFoldGroup;
+  const int ngroups = (p.nblocks + kFoldGroup - 1) / kFoldGroup;
+  const int gsize = min(kFoldGroup, p.nblocks - grp * kFoldGroup);
+  P* partials = reinterpret_cast<P*>(p.partials);
+  P* gpartials = reinterpret_cast<P*>(p.gpartials);
+  if (tid < kSumsAll) {
+    float s = 0.f;
 #pragma unroll
-    for (int k = 0; k < kSumsAll; ++k) s_warp[warp][k] = acc[k];
+    for (int w = 0; w < kTrackThreadsY; ++w) s += s_warp[w][tid];
+    partials[(int64_t)bid * kSumsAll + tid] = (P)s;
+    __threadfence();
   }
   __syncthreads();
-  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-  P* partials = reinterpret_cast<P*>(p.partials);
+  if (tid == 0) s_last = atomicAdd(&p.counters[1 + grp], 1u) == (unsigned)(gsize - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
   if (tid < kSumsAll) {
     P s = 0;
-#pragma unroll
-    for (int w = 0; w < kTrackThreadsY; ++w) s += (P)s_warp[w][tid];
-    partials[(int64_t)bid * kSumsAll + tid] = s;
+    for (int b = grp * kFoldGroup; b < grp * kFoldGroup + gsize; ++b)
+      s += __ldcg(partials + (int64_t)b * kSumsAll + tid);
+    gpartials[(int64_t)grp * kSumsAll + tid] = s;
+    __threadfence();
   }
-  __threadfence();
   __syncthreads();
   if (tid == 0) {
-    const unsigned prev = atomicAdd(&ctrl->block_counter, 1u);
-    s_last = (prev == (unsigned)(p.nblocks - 1));
+    p.counters[1 + grp] = 0u;
+    s_last = atomicAdd(&p.counters[0], 1u) == (unsigned)(ngroups - 1);
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  {
-    const int col = tid & 63, sub = tid >> 6;   // 4 x 64 threads
+  if (tid < kSumsAll) {
     P s = 0;
-    if (col < kSumsAll) {
-      for (int b = sub; b < p.nblocks; b += 4) s += __ldcg(partials + (int64_t)b * kSumsAll + col);
-    }
-    s_fold[sub][col] = s;
+    for (int g = 0; g < ngroups; ++g) s += __ldcg(gpartials + (int64_t)g * kSumsAll + tid);
+    ctrl->sums[tid] = (double)s;
   }
-  __syncthreads();
-  if (tid < kSumsAll)
-    ctrl->sums[tid] = (double)(((s_fold[0][tid] + s_fold[1][tid]) + s_fold[2][tid]) + s_fold[3][tid]);
-  if (tid == 0) ctrl->block_counter = 0u;
+  if (tid == 0) p.counters[0] = 0u;
 }
 
 }  // namespace
+
+// Rows per thread: enough blocks for two per SM on 152 SMs, no more (each block
+// pays a reduction and a partial).
+int track_default_ppt(int w, int h) {
+  const int b1 = track_grid_blocks(w, h, 1);
+  int ppt = b1 / 304;
+  return ppt < 1 ? 1 : (ppt > 16 ? 16 : ppt);
+}
 
 int track_grid_blocks(int w, int h, int ppt) {
   const int gx = (w + kTrackThreadsX - 1) / kTrackThreadsX;
