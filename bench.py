@@ -1,18 +1,22 @@
 #!/usr/bin/env python3
-"""Benchmark of the tracking hot path: tracked frames/s at 640x480.
+"""Benchmark of the tracking hot path: tracked frames/s at 640x480, batched
+and plain.
 
-Workload (one step = one tracked frame, i.e. one pass of every step of the
-hot path: pyramid, normal and gradient maps, 19 Gauss-Newton iterations of the
-fused photometric + ICP kernel with the FP64 IMU / solver step, marginalisation
-and the reference swap): a single camera stream of the seeded synthetic
-640x480 RGB-D + 400 Hz IMU sequence (sinusoidal path, peak 1.5 m/s and
-90 deg/s, 100-frame period rendered once and looped), 3 pyramid levels with
-10/5/4 iterations.  Frames live on the device before timing starts; the 100
-distinct frames (245 MB) exceed the 129 MB L2, so every step reads a frame
-that is not cache resident.
+A tracked frame is one pass of every step of the hot path: pyramid, normal and
+gradient maps, 19 Gauss-Newton iterations of the fused photometric + ICP kernel
+with the FP64 IMU / solver step, marginalisation and the reference swap, on the
+seeded synthetic 640x480 RGB-D + 400 Hz IMU sequence (sinusoidal path, peak
+1.5 m/s and 90 deg/s, 100-frame period rendered once and looped), 3 pyramid
+levels with 10/5/4 iterations.
 
-Output: one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-on a bounded sample of the same workload instead.
+* batched (the headline, one step = one frame of each of 64 independent
+  streams in one dri_track_batch call): stream i starts at frame 37 i mod 100
+  of the loop, so a step reads 64 different frames;
+* plain (one step = one frame of a single stream, dri_track).
+
+Frames live on the device before timing starts; the 100 distinct frames
+(245 MB) exceed the 129 MB L2.  Output: one JSON line (rank 0).
+`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
 """
 import os
 
@@ -39,6 +43,8 @@ N_UNIQUE = 100
 SEQ_SEED = 2
 BYTES_PER_PIXEL_ITER = 48     # FP32 maps: see the design doc (live 20 B + reference 28 B)
 PIXEL_ITERS_PER_FRAME = sum((W >> l) * (H >> l) * ITERS[l] for l in range(LEVELS))
+BATCH = 64
+BATCH_OFFSET = 37             # stream i starts at frame (37 i) mod 100 of the loop
 
 
 def _render_one(args):
@@ -229,7 +235,7 @@ def run_reference(args):
     seq, frames, imu = make_inputs(4, min(16, os.cpu_count() or 4))
     value, rows, el = oracle_band_steps(seq, frames, imu, args.steps, args.warmup, budget_s=120.0)
     line = {
-        "impl": "reference", "metric": "tracked frames/s at 640x480 (plain single stream)",
+        "impl": "reference", "metric": "tracked frames/s at 640x480 (batched vs plain)",
         "value": value, "unit": "frames/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * el / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -245,17 +251,159 @@ def run_reference(args):
 
 
 def config_json():
-    return {"workload": "single stream, 640x480 RGB-D + 400 Hz IMU, 3 levels 10/5/4 GN iterations",
+    return {"workload": f"{BATCH} independent streams of 640x480 RGB-D + 400 Hz IMU per step "
+                        f"(one dri_track_batch call), 3 levels 10/5/4 GN iterations; plain: one "
+                        f"stream, one frame per step",
             "model": "dense RGB-D-inertial tracking (photometric + ICP + IMU, 34-D joint GN)",
-            "global_batch": 1, "seq_len": 1, "parallelism": "replicas (one stream per GPU)",
+            "global_batch": BATCH, "seq_len": 1, "parallelism": "replicas (independent streams per GPU)",
             "width": W, "height": H, "levels": LEVELS, "iters": list(ITERS),
-            "l2": "inputs larger than L2 (100 distinct frames, 245 MB, cycled)"}
+            "l2": "inputs larger than L2 (100 distinct frames, 245 MB, cycled; a batched step "
+                  "reads 64 of them)"}
+
+
+def initial_state_at(seq, i):
+    """State at loop frame i for a stream whose world frame is that camera frame."""
+    from paper_2207_10940_gb300 import synth
+    g = seq.gt[i % N_UNIQUE]
+    return dict(t=i / FPS, r_WC=np.zeros(3), q_WC=np.array([1.0, 0, 0, 0]), v_I=g["v_I"].copy(),
+                bg=np.zeros(3), ba=np.zeros(3), q_IW=synth.matrix_to_quat(g["R_IW"]))
+
+
+def kernel_classes(prof, dri):
+    return {name: {"launches": int(prof.launches[c]), "ms": round(prof.ms[c], 4)}
+            for name, c in (("maps", dri.DRI_KC_MAPS), ("track", dri.DRI_KC_TRACK),
+                            ("solve", dri.DRI_KC_SOLVE), ("frame", dri.DRI_KC_FRAME),
+                            ("grad", dri.DRI_KC_GRAD))}
+
+
+def roofline(prof, dri, traffic_bpp):
+    t_ms = prof.ms[dri.DRI_KC_TRACK]
+    px = prof.pixels[dri.DRI_KC_TRACK]
+    n = max(1, prof.launches[dri.DRI_KC_TRACK])
+    achieved = BYTES_PER_PIXEL_ITER * px / (t_ms / 1000.0) / 1e9
+    peak, peak_kind = measured_peaks()
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind,
+            "kernel": "k_track_batch (fused photometric + ICP linearisation)",
+            "bytes_per_pixel_iter": BYTES_PER_PIXEL_ITER, "avg_launch_us": 1000.0 * t_ms / n,
+            "pixel_iters_per_launch": px / n,
+            "traffic": None if traffic_bpp is None else traffic_bpp * px / n}
+
+
+class Runner:
+    """Streams of the benchmark on one device: frame k of stream i shows loop
+    frame (offset_i + k) mod 100 at time (offset_i + k) / 30 s."""
+
+    def __init__(self, seq, imu, d_dev, i_dev, d_pin, i_pin, offsets, dev):
+        import torch
+        from paper_2207_10940_gb300 import dri
+        self.dri, self.torch = dri, torch
+        self.dev = dev
+        self.d_dev, self.i_dev, self.d_pin, self.i_pin = d_dev, i_dev, d_pin, i_pin
+        self.ts = torch.cuda.Stream(dev)
+        cfg = dri_config(seq)
+        self.offsets = list(offsets)
+        self.streams = [dri.Stream(cfg, dri.state_from_dict(initial_state_at(seq, o), o / FPS), self.ts)
+                        for o in self.offsets]
+        arr = dri.imu_array(imu)
+        for st in self.streams:
+            dri.dri_push_imu(st.handle, arr)
+        self.k = 0
+
+    def upload(self, device_inputs=True):
+        dri = self.dri
+        for st, o in zip(self.streams, self.offsets):
+            j = (o + self.k) % N_UNIQUE
+            t = (o + self.k) / FPS
+            if device_inputs:
+                dri.dri_upload_frame(st.handle, t, self.d_dev[j], self.i_dev[j], mem_kind=dri.DRI_DEVICE)
+            else:
+                dri.dri_upload_frame(st.handle, t, self.d_pin[j], self.i_pin[j], mem_kind=dri.DRI_HOST)
+        self.k += 1
+
+    def step(self, device_inputs=True, wait=False):
+        self.upload(device_inputs)
+        if len(self.streams) == 1:
+            return self.dri.dri_track(self.streams[0].handle, wait=wait)
+        return self.dri.dri_track_batch(self.streams, wait=wait)
+
+    def close(self):
+        for st in self.streams:
+            st.close()
+
+
+def timed_pass(run, steps, world, local):
+    """Device time of `steps` steps (CUDA events on the library's stream)."""
+    torch, dri = run.torch, run.dri
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    h0 = run.streams[0].handle
+    n0 = dri.dri_launch_count(h0)
+    barrier(run.dev, world)
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(run.ts):
+            evs[0].record(run.ts)
+        for i in range(steps):
+            run.step()
+            with torch.cuda.stream(run.ts):
+                evs[i + 1].record(run.ts)
+        barrier(run.dev, world)
+    launches = dri.dri_launch_count(h0) - n0
+    per = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(steps)])
+    total_ms = evs[0].elapsed_time(evs[-1])
+    t_max = torch.tensor([total_ms], device=run.dev, dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
+    return float(t_max.item()), per, launches, clk.summary()
+
+
+def profiled_pass(run, steps):
+    dri = run.dri
+    h0 = run.streams[0].handle
+    dri.dri_profile_enable(h0, True)
+    for _ in range(steps):
+        run.step()
+    prof = dri.dri_profile_read(h0)
+    dri.dri_profile_enable(h0, False)
+    return prof
+
+
+def e2e_pass(run, steps, world):
+    barrier(run.dev, world)
+    t = time.perf_counter()
+    for _ in range(steps):
+        run.step(device_inputs=False, wait=True)
+    barrier(run.dev, world)
+    el = time.perf_counter() - t
+    h2d = d2h = 0
+    for st in run.streams:
+        a, b = run.dri.dri_io_bytes(st.handle)
+        h2d += a
+        d2h += b
+    return el, h2d, d2h
+
+
+def frame_counts(run):
+    ok = failed = 0
+    for st in run.streams:
+        a, b = run.dri.dri_frame_counts(st.handle)
+        ok += a
+        failed += b
+    return ok, failed
+
+
+def barrier(dev, world):
+    import torch
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
 
 
 def run_ours(args):
     rank, local, world = dist_env()
-    seq, frames, imu = make_inputs(1 + args.warmup + 2 * args.steps + args.profile_frames + 2,
-                                   min(16, os.cpu_count() or 4))
+    plain_steps = args.plain_steps
+    n_frames = max(BATCH_OFFSET * (BATCH - 1) % N_UNIQUE, N_UNIQUE) + 2 * (
+        args.warmup + 2 * max(args.steps, plain_steps) + args.profile_frames + 8)
+    seq, frames, imu = make_inputs(n_frames, min(16, os.cpu_count() or 4))
     import torch
     from paper_2207_10940_gb300 import build, dri
     build.build()
@@ -269,114 +417,60 @@ def run_ours(args):
     d_pin = torch.stack([torch.from_numpy(f[0]) for f in frames]).pin_memory()
     i_pin = torch.stack([torch.from_numpy(f[1]) for f in frames]).pin_memory()
     torch.cuda.synchronize(dev)      # the library reads these on its own stream
-    from paper_2207_10940_gb300 import synth
-    cfg = dri_config(seq)
-    st = dri.Stream(cfg, dri.state_from_dict(synth.initial_state(seq)), torch.cuda.Stream(dev))
-    h = st.handle
-    ts = st.torch_stream
-    dri.dri_push_imu(h, imu)
-    k = 0
-
-    def step(device_inputs=True, wait=False):
-        nonlocal k
-        j = k % N_UNIQUE
-        if device_inputs:
-            dri.dri_upload_frame(h, k / FPS, d_dev[j], i_dev[j], mem_kind=dri.DRI_DEVICE)
-        else:
-            dri.dri_upload_frame(h, k / FPS, d_pin[j], i_pin[j], mem_kind=dri.DRI_HOST)
-        r = dri.dri_track(h, wait=wait)
-        k += 1
-        return r
-
-    def barrier():
+    out = {}
+    for mode, n_streams, steps in (("batched", BATCH, args.steps), ("plain", 1, plain_steps)):
+        offsets = [(BATCH_OFFSET * i) % N_UNIQUE for i in range(n_streams)]
+        run = Runner(seq, imu, d_dev, i_dev, d_pin, i_pin, offsets, dev)
+        res = run.step(wait=True)
+        for _ in range(args.warmup):
+            run.step()
+        total_ms, per, launches, clocks = timed_pass(run, steps, world, local)
+        ok, failed = frame_counts(run)
+        prof = profiled_pass(run, max(3, args.profile_frames // (8 if n_streams > 1 else 1)))
+        e2e_steps = max(3, steps // 4)
+        e2e_s, h2d, d2h = e2e_pass(run, e2e_steps, world)
+        tiles = dri.dri_batch_tiles([s.handle for s in run.streams])
+        out[mode] = {
+            "value": world * n_streams * steps / (total_ms / 1000.0), "steps": steps,
+            "streams": n_streams, "ms_per_step": total_ms / steps,
+            "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+            "gpu_launches": int(launches), "frames_ok": int(ok), "frames_failed": int(failed),
+            "roofline": roofline(prof, dri, track_traffic()), "kernel_classes": kernel_classes(prof, dri),
+            "e2e": {"value": world * n_streams * e2e_steps / e2e_s, "unit": "frames/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "clocks": clocks, "rows_per_thread": tiles[:LEVELS],
+        }
+        run.close()
+        del run
         torch.cuda.synchronize(dev)
-        if world > 1:
-            torch.distributed.barrier()
-
-    r0 = step(wait=True)
-    assert r0.initialised == 1
-    for _ in range(args.warmup):
-        step()
-    # ---- timed region: K frames, inputs resident on the device ----
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    n0 = dri.dri_launch_count(h)
-    barrier()
-    with ClockSampler(local) as clk:
-        with torch.cuda.stream(ts):
-            evs[0].record(ts)
-        for i in range(args.steps):
-            step()
-            with torch.cuda.stream(ts):
-                evs[i + 1].record(ts)
-        barrier()
-    launches = dri.dri_launch_count(h) - n0
-    ok_frames, failed_frames = dri.dri_frame_counts(h)
-    per = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)])
-    total_ms = evs[0].elapsed_time(evs[-1])
-    state = dri.dri_get_state(h)
-    t_max = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t_max.item())
-    value = world * args.steps / (total_ms / 1000.0)
-
-    # ---- kernel timing pass (same frames, events around every launch) ----
-    dri.dri_profile_enable(h, True)
-    for _ in range(args.profile_frames):
-        step()
-    prof = dri.dri_profile_read(h)
-    dri.dri_profile_enable(h, False)
-    t_track_ms = prof.ms[dri.DRI_KC_TRACK]
-    px_track = prof.pixels[dri.DRI_KC_TRACK]
-    n_track = prof.launches[dri.DRI_KC_TRACK]
-    achieved = BYTES_PER_PIXEL_ITER * px_track / (t_track_ms / 1000.0) / 1e9
-    peak, peak_kind = measured_peaks()
-    tr_bpp = track_traffic()
-
-    # ---- end to end: host (pinned) inputs, result read back every frame ----
-    barrier()
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        res = step(device_inputs=False, wait=True)
-    barrier()
-    e2e_s = time.perf_counter() - t
-    h2d, d2h = dri.dri_io_bytes(h)
-    e2e = world * args.steps / e2e_s
     if world > 1:
         torch.distributed.barrier()
-    st.close()
     if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return 0
-
     budget = float(os.environ.get("DRI_BENCH_ORACLE_SECONDS", "15"))
     o_fps, o_n, o_t = oracle_frames_per_s(seq, frames, imu, budget)
-    kc = {name: {"launches": int(prof.launches[c]), "ms": round(prof.ms[c], 4)}
-          for name, c in (("maps", dri.DRI_KC_MAPS), ("track", dri.DRI_KC_TRACK),
-                          ("solve", dri.DRI_KC_SOLVE), ("frame", dri.DRI_KC_FRAME),
-                          ("grad", dri.DRI_KC_GRAD))}
+    b, p = out["batched"], out["plain"]
     line = {
-        "metric": "tracked frames/s at 640x480 (plain single stream)",
-        "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "metric": "tracked frames/s at 640x480 (batched vs plain)",
+        "value": b["value"], "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 per-pixel, f64 reduction and solve",
         "data": "synthetic", "config": config_json(),
-        "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
-        "gpu_launches": int(launches),
-        "frames_failed": int(failed_frames), "frames_ok": int(ok_frames),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind,
-                     "kernel": "k_track (fused photometric + ICP linearisation)",
-                     "bytes_per_pixel_iter": BYTES_PER_PIXEL_ITER,
-                     "avg_launch_us": 1000.0 * t_track_ms / max(1, n_track),
-                     "traffic": None if tr_bpp is None else tr_bpp * px_track / max(1, n_track)},
-        "kernel_classes": kc,
-        "e2e": {"value": e2e, "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+        "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"],
+        "gpu_launches": b["gpu_launches"],
+        "frames_failed": b["frames_failed"], "frames_ok": b["frames_ok"],
+        "roofline": b["roofline"], "kernel_classes": b["kernel_classes"], "e2e": b["e2e"],
+        "rows_per_thread": b["rows_per_thread"],
+        "plain": {k: p[k] for k in ("value", "steps", "ms_per_step", "p50_ms", "p99_ms",
+                                     "gpu_launches", "frames_ok", "frames_failed", "roofline",
+                                     "kernel_classes", "e2e", "rows_per_thread")},
+        "batched_over_plain": b["value"] / p["value"],
         "cpu_baseline": {"value": o_fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
                          "sample": f"{o_n} whole frames of the same sequence tracked by the FP64 "
                                    f"numpy oracle in {o_t:.1f} s"},
-        "clocks": clk.summary(),
-        "final_state_t": state.t,
+        "clocks": b["clocks"], "clocks_plain": p["clocks"],
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -387,7 +481,8 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--plain-steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--profile-frames", type=int, default=60)

@@ -146,10 +146,13 @@ int dri_create_stream(const dri_stream_config* cfg, const dri_state* x_init, voi
 int dri_destroy_stream(dri_stream s);
 
 /* Uploads the live frame at time t (seconds, strictly increasing): depth and
- * intensity, height rows of width floats, rows pitch_bytes apart (0 = packed),
- * on the host (DRI_HOST, copied before the call returns its staging) or on the
- * device (DRI_DEVICE, copied stream-ordered on the stream's cuda_stream: work
- * that produces the images on another stream must be ordered before it, e.g.
+ * intensity, height rows of width floats, rows pitch_bytes apart (0 = packed,
+ * a multiple of 4).  DRI_HOST: host memory, copied into the stream's workspace
+ * stream-ordered on the stream's cuda_stream (pinned memory makes the copy
+ * asynchronous).  DRI_DEVICE: device memory, not copied here: the first kernel
+ * of the next dri_track / dri_track_batch of this stream reads it, so the
+ * caller keeps it unchanged until that work has run on cuda_stream, and work
+ * that produces it on another stream is ordered before the track call (e.g.
  * with an event).  The caller keeps ownership. */
 int dri_upload_frame(dri_stream s, double t, const float* depth, const float* intensity,
                      size_t pitch_bytes, int32_t mem_kind);
@@ -166,6 +169,35 @@ int dri_push_imu(dri_stream s, const dri_imu_sample* samples, size_t n);
  * DRI_ENOTREADY when no new frame is uploaded or the IMU samples do not cover
  * [t_previous_frame, t_frame]. */
 int dri_track(dri_stream s, dri_track_result* out);
+
+/* Tracks the uploaded frame of each of n streams (Sec. IV, as dri_track) in
+ * one batched launch sequence: every kernel of a frame (maps, frame start, each
+ * Gauss-Newton iteration's pixel kernel and solve, marginalisation, gradients)
+ * is one launch over the pixels or states of all n streams.  The paper tracks
+ * one camera; batching independent streams is this library's throughput mode.
+ *
+ * streams: n (1..4096) distinct handles created on the same cuda_stream with
+ * the same levels, iterations and precision flags (sizes and intrinsics may
+ * differ), otherwise DRI_EINVAL.  The first call with a given list (same
+ * handles, same order) builds a plan: device tables, a staging ring and
+ * buffers for the n result blocks (allocated; freed when one of the streams
+ * is destroyed).  On the first call that tracks a frame the plan times the
+ * pixel kernel at rows-per-thread 1, 2, 3, 4, 6, 8 on each level and keeps the
+ * fastest (this call waits); later calls replay the sequence as one CUDA graph
+ * (launched directly on the legacy default stream or while profiling).
+ *
+ * A stream without an uploaded frame, or whose IMU samples do not yet cover
+ * [t_previous_frame, t_frame], sits the call out (its frame stays pending).
+ * out == NULL: returns after enqueuing; out != NULL: waits and fills out[i]
+ * for every stream (status DRI_ENOTREADY for one that sat out).  Returns
+ * DRI_OK when the batch ran, DRI_ENOTREADY when no stream had work. */
+int dri_track_batch(const dri_stream* streams, int32_t n, dri_track_result* out);
+
+/* Rows per thread of the pixel kernel on each level (ppt[DRI_MAX_LEVELS], 0
+ * past the last level) of the plan for this stream list: the autotuned values
+ * of dri_track_batch's plan, or for n = 1 and no batch plan the stream's own
+ * (fixed by a size heuristic).  DRI_ENOTREADY if no such plan exists. */
+int dri_batch_tiles(const dri_stream* streams, int32_t n, int32_t* ppt);
 
 /* Waits for the stream and copies out x1 and, when non-NULL, the prior
  * H* (17 x 17, row-major) and b* (17) that the next frame will use. */

@@ -1,12 +1,15 @@
 // C ABI of the tracking library (include/dri.h): argument checks, the stream's
 // device workspace, IMU bookkeeping on the host and the per-frame launch
-// sequence.  All arithmetic of a frame runs in the kernels of maps.cu,
-// track.cu and solve.cu.
+// sequence ("plan") over one stream (dri_track) or many (dri_track_batch),
+// captured once as a CUDA graph and replayed per frame.  All arithmetic of a
+// frame runs in the kernels of maps.cu, track.cu and solve.cu.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -19,6 +22,9 @@ using namespace dri;
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kStreamRing = 64;   // frames of one stream in flight (dri_track, out = NULL)
+constexpr int kBatchRing = 8;     // launches of one batch plan in flight
+constexpr int kMaxBatch = 4096;
 inline size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
 
 int valid_config(const dri_stream_config* c) {
@@ -119,6 +125,37 @@ LevelGeom level_geom(const dri_stream_config& cfg, int level) {
   return g;
 }
 
+TableView table_view(int nslots, int levels) {
+  TableView v;
+  std::memset(&v, 0, sizeof(v));
+  size_t off = align_up((size_t)nslots * sizeof(SlotStatic), 16);
+  const size_t pre = (size_t)(nslots + 1) * sizeof(int32_t);
+  v.copy_off = off;
+  off = align_up(off + pre, 16);
+  for (int l = 0; l < levels; ++l) {
+    v.map_off[l] = off;
+    off = align_up(off + pre, 16);
+    v.track_off[l] = off;
+    off = align_up(off + pre, 16);
+  }
+  v.bytes = align_up(off);
+  return v;
+}
+
+}  // namespace dri
+
+namespace {
+
+// Staged bytes of one launch: SlotDyn[nslots], then one IMU block per slot.
+size_t dyn_header_bytes(int nslots) { return align_up((size_t)nslots * sizeof(SlotDyn), 64); }
+size_t imu_block_bytes(int imu_cap) {
+  return align_up(sizeof(ImuHeader) + (size_t)imu_cap * sizeof(dri_imu_sample), 16);
+}
+
+}  // namespace
+
+namespace dri {
+
 StreamLayout make_layout(const dri_stream_config& cfg) {
   StreamLayout L;
   std::memset(&L, 0, sizeof(L));
@@ -129,8 +166,11 @@ StreamLayout make_layout(const dri_stream_config& cfg) {
   size_t off = 0;
   L.ctrl = off;
   off = align_up(off + sizeof(Ctrl));
-  L.imu = off;
-  off = align_up(off + sizeof(ImuHeader) + (size_t)L.imu_cap * sizeof(dri_imu_sample));
+  L.dyn = off;
+  L.dyn_bytes = dyn_header_bytes(1) + imu_block_bytes(L.imu_cap);
+  off = align_up(off + L.dyn_bytes);
+  L.table = off;
+  off = align_up(off + table_view(1, cfg.levels).bytes);
   const size_t npx = (size_t)cfg.width * cfg.height;
   L.in_depth = off;
   off = align_up(off + npx * 4);
@@ -171,6 +211,8 @@ StreamLayout make_layout(const dri_stream_config& cfg) {
 
 }  // namespace dri
 
+struct Plan;
+
 struct dri_stream_s {
   dri_stream_config cfg;
   StreamLayout L;
@@ -178,7 +220,6 @@ struct dri_stream_s {
   char* ws = nullptr;
   bool own_ws = false;
   Ctrl* ctrl = nullptr;
-  ImuHeader* imu_dev = nullptr;
   float* in_depth = nullptr;
   float* in_inten = nullptr;
   void* partials = nullptr;
@@ -190,26 +231,25 @@ struct dri_stream_s {
   LevelGeom geom[kMaxLevels];
   int ppt[kMaxLevels];
   DState x_init;
+  Plan* own = nullptr;              // one-slot plan of dri_track (in the workspace)
+  std::vector<Plan*> batches;       // batch plans this stream is a slot of
   // host bookkeeping
   std::vector<dri_imu_sample> imu;
-  bool initialised = false;        // host view: the init frame was enqueued
-  double t_prev = 0.0;             // time of the state the next frame starts from
+  bool initialised = false;         // host view: the init frame was enqueued
+  double t_prev = 0.0;              // time of the state the next frame starts from
   double t_frame = 0.0;
   bool frame_pending = false;
-  char* pin_imu = nullptr;         // pinned staging, one slot per frame in flight (+1)
-  size_t imu_slot_bytes = 0;
-  Ctrl* pin_ctrl = nullptr;        // pinned copy of the whole control block
-  // frames in flight: each copies its result head into a pinned ring slot and
-  // records an event; completed frames are settled in order on the host
-  static constexpr int kRing = 64;
-  char* pin_ring = nullptr;        // kRing result heads
-  cudaEvent_t ring_ev[kRing] = {};
-  struct InFlight { int slot; };
+  const float* src_depth = nullptr; // the pending frame's level-0 images on the device
+  const float* src_inten = nullptr;
+  int32_t src_pitch = 0;            // floats
+  int64_t h2d_frame = 0;            // bytes of the pending frame's host upload
+  Ctrl* pin_ctrl = nullptr;         // pinned copy of the whole control block
+  // frames in flight, settled in order once their result copy has completed
+  struct InFlight { cudaEvent_t ev; const Ctrl* head; };
   std::deque<InFlight> inflight;
-  int ring_next = 0;
-  double t_confirmed = 0.0;        // time of the last state known to be good
+  double t_confirmed = 0.0;         // time of the last state known to be good
   int64_t frames_ok = 0, frames_failed = 0;
-  double t_prev_before = 0.0;      // t_prev before the last optimistic advance
+  double t_prev_before = 0.0;       // t_prev before the last optimistic advance
   int64_t launches = 0;
   int64_t h2d_last = 0, d2h_last = 0;   // bytes copied for the last frame
   // profiling: event pairs around launches
@@ -219,6 +259,36 @@ struct dri_stream_s {
   struct Rec { int cls; size_t e0, e1; double pixels; };
   std::vector<Rec> recs;
   dri_profile counted;
+};
+
+// The launch sequence of one frame over nslots streams: the device table of
+// the slots' static parameters, the staging ring, the captured graph.
+struct Plan {
+  std::vector<dri_stream_s*> slots;
+  cudaStream_t stream = nullptr;
+  int S = 0, levels = 0;
+  int iters[kMaxLevels] = {};
+  bool fp16 = false, fp32p = false;
+  bool owns_device = false;         // table / dyn / heads allocated by the plan
+  char* table = nullptr;
+  TableView tv;
+  unsigned char* dyn = nullptr;
+  size_t dyn_cap = 0;
+  unsigned char* heads = nullptr;   // S result heads (batch plans)
+  std::vector<SlotStatic> host_slots;
+  std::vector<int32_t> pre_copy, pre_map[kMaxLevels], pre_track[kMaxLevels];
+  int R = 0;                        // staging ring
+  char* pin_dyn = nullptr;
+  char* pin_heads = nullptr;
+  std::vector<cudaEvent_t> ev;
+  std::vector<char> ring_used;
+  int next = 0;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_failed = false;
+  bool autotune = false;            // choose rows per thread by timing, on the first tracked frame
+  bool tuned = false;
+  std::vector<std::array<int, kMaxLevels>> ppt;   // rows per thread of each slot's pixel kernel
+  int64_t kernels_per_frame = 0;
 };
 
 namespace {
@@ -235,11 +305,11 @@ cudaEvent_t prof_event(dri_stream_s* s, size_t* idx) {
   return s->ev_pool[s->ev_used++];
 }
 
-// Runs one kernel launcher; counts it and, while profiling, brackets it with events.
+// Runs one kernel launcher; while profiling, brackets it with events recorded
+// into stream s's counters.
 template <class F>
 cudaError_t launch(dri_stream_s* s, int cls, double pixels, F&& f) {
-  s->launches++;
-  if (!s->profiling) return f();
+  if (!s || !s->profiling) return f();
   s->counted.launches[cls]++;
   s->counted.pixels[cls] += pixels;
   if (s->recs.size() >= kMaxTimed) return f();
@@ -258,7 +328,7 @@ SolveParams solve_params(const dri_stream_s* s, int level, int last) {
   SolveParams p;
   std::memset(&p, 0, sizeof(p));
   p.ctrl = s->ctrl;
-  p.imu = s->imu_dev;
+  p.imu = reinterpret_cast<const ImuHeader*>(s->ws + s->L.dyn + dyn_header_bytes(1));
   p.level = level;
   p.last = last;
   const dri_stream_config& c = s->cfg;
@@ -280,7 +350,7 @@ SolveParams solve_params(const dri_stream_s* s, int level, int last) {
   return p;
 }
 
-TrackParams track_params(const dri_stream_s* s, int level, uint8_t* flags) {
+TrackParams track_params(const dri_stream_s* s, int level, int ppt, uint8_t* flags) {
   TrackParams p;
   std::memset(&p, 0, sizeof(p));
   p.g = s->geom[level];
@@ -290,7 +360,7 @@ TrackParams track_params(const dri_stream_s* s, int level, uint8_t* flags) {
   p.gpartials = s->gpartials;
   p.counters = s->counters;
   p.flags = flags;
-  p.ppt = s->ppt[level];
+  p.ppt = ppt;
   p.nblocks = track_grid_blocks(p.g.w, p.g.h, p.ppt);
   p.depth_min = (float)s->cfg.depth_min;
   p.depth_max = (float)s->cfg.depth_max;
@@ -305,72 +375,123 @@ TrackParams track_params(const dri_stream_s* s, int level, uint8_t* flags) {
     if (e_ != cudaSuccess) return DRI_ECUDA;       \
   } while (0)
 
-// Level maps of the uploaded frame in the live map set.
-int enqueue_maps(dri_stream_s* s) {
-  const bool fp16 = (s->cfg.precision_flags & DRI_FP16_MAPS) != 0;
-  const double npx = (double)s->cfg.width * s->cfg.height;
-  CK(launch(s, DRI_KC_MAPS, npx, [&] {
-    return launch_copy_input(s->in_depth, s->in_inten, s->maps[0], s->ctrl, s->cfg.width,
-                             s->cfg.height, s->stream);
-  }));
-  for (int l = 1; l < s->cfg.levels; ++l) {
-    CK(launch(s, DRI_KC_MAPS, (double)s->geom[l].w * s->geom[l].h, [&] {
-      return launch_pyr_down(s->maps[l - 1], s->maps[l], s->ctrl, s->geom[l - 1].w,
-                             s->geom[l - 1].h, s->geom[l].w, s->geom[l].h, s->stream);
-    }));
+// ---- plans ------------------------------------------------------------------
+
+// Block prefixes and static slot records from the slots' configurations and
+// the chosen rows per thread.
+void plan_fill_tables(Plan* p) {
+  p->host_slots.assign(p->S, SlotStatic());
+  p->pre_copy.assign(p->S + 1, 0);
+  for (int l = 0; l < p->levels; ++l) {
+    p->pre_map[l].assign(p->S + 1, 0);
+    p->pre_track[l].assign(p->S + 1, 0);
   }
-  for (int l = 0; l < s->cfg.levels; ++l) {
-    CK(launch(s, DRI_KC_MAPS, (double)s->geom[l].w * s->geom[l].h, [&] {
-      return launch_normals(s->maps[l], s->ctrl, s->geom[l], (float)s->cfg.depth_min,
-                            (float)s->cfg.depth_max, fp16, -1, s->stream);
-    }));
+  for (int i = 0; i < p->S; ++i) {
+    const dri_stream_s* s = p->slots[i];
+    SlotStatic& st = p->host_slots[i];
+    std::memset(&st, 0, sizeof(st));
+    for (int l = 0; l < p->levels; ++l) st.tp[l] = track_params(s, l, p->ppt[i][l], nullptr);
+    st.sp = solve_params(s, 0, 0);
+    st.sp.imu = nullptr;
+    st.in_depth = s->in_depth;
+    st.in_inten = s->in_inten;
+    st.levels = p->levels;
+    p->pre_copy[i + 1] = p->pre_copy[i] + copy_tiles(s->cfg.width, s->cfg.height);
+    for (int l = 0; l < p->levels; ++l) {
+      p->pre_map[l][i + 1] = p->pre_map[l][i] + map_tiles(s->geom[l].w, s->geom[l].h);
+      p->pre_track[l][i + 1] = p->pre_track[l][i] + st.tp[l].nblocks;
+    }
   }
+}
+
+int plan_upload_tables(Plan* p) {
+  std::vector<char> img(p->tv.bytes, 0);
+  std::memcpy(img.data(), p->host_slots.data(), (size_t)p->S * sizeof(SlotStatic));
+  const size_t pre = (size_t)(p->S + 1) * sizeof(int32_t);
+  std::memcpy(img.data() + p->tv.copy_off, p->pre_copy.data(), pre);
+  for (int l = 0; l < p->levels; ++l) {
+    std::memcpy(img.data() + p->tv.map_off[l], p->pre_map[l].data(), pre);
+    std::memcpy(img.data() + p->tv.track_off[l], p->pre_track[l].data(), pre);
+  }
+  CK(cudaMemcpyAsync(p->table, img.data(), img.size(), cudaMemcpyHostToDevice, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
   return DRI_OK;
 }
 
-int enqueue_gradients(dri_stream_s* s) {
-  const bool fp16 = (s->cfg.precision_flags & DRI_FP16_MAPS) != 0;
-  for (int l = 0; l < s->cfg.levels; ++l) {
-    CK(launch(s, DRI_KC_GRAD, (double)s->geom[l].w * s->geom[l].h, [&] {
-      return launch_gradient(s->maps[l], s->ctrl, s->geom[l].w, s->geom[l].h, fp16, s->stream);
-    }));
+void plan_free(Plan* p) {
+  if (!p) return;
+  if (p->graph) cudaGraphExecDestroy(p->graph);
+  for (cudaEvent_t e : p->ev)
+    if (e) cudaEventDestroy(e);
+  if (p->pin_dyn) cudaFreeHost(p->pin_dyn);
+  if (p->pin_heads) cudaFreeHost(p->pin_heads);
+  if (p->owns_device) {
+    if (p->table) cudaFree(p->table);
+    if (p->dyn) cudaFree(p->dyn);
+    if (p->heads) cudaFree(p->heads);
   }
+  delete p;
+}
+
+// Creates a plan over the given streams.  Single-slot plans use the stream's
+// workspace; batch plans allocate their own table, staging and head buffers.
+int plan_create(dri_stream_s* const* streams, int n, int ring, bool in_workspace, Plan** out) {
+  *out = nullptr;
+  Plan* p = new (std::nothrow) Plan();
+  if (!p) return DRI_ENOMEM;
+  p->slots.assign(streams, streams + n);
+  p->S = n;
+  p->stream = streams[0]->stream;
+  p->levels = streams[0]->cfg.levels;
+  for (int l = 0; l < kMaxLevels; ++l) p->iters[l] = l < p->levels ? streams[0]->cfg.iters[l] : 0;
+  p->fp16 = (streams[0]->cfg.precision_flags & DRI_FP16_MAPS) != 0;
+  p->fp32p = (streams[0]->cfg.precision_flags & DRI_FP32_PARTIALS) != 0;
+  p->tv = table_view(n, p->levels);
+  p->R = ring;
+  p->ppt.resize(n);
+  for (int i = 0; i < n; ++i)
+    for (int l = 0; l < kMaxLevels; ++l) p->ppt[i][l] = streams[i]->ppt[l];
+  int imu_cap = 0;
+  for (int i = 0; i < n; ++i) imu_cap = std::max(imu_cap, streams[i]->L.imu_cap);
+  p->dyn_cap = dyn_header_bytes(n) + (size_t)n * imu_block_bytes(imu_cap);
+  if (in_workspace) {             // the one-slot plan of dri_track
+    dri_stream_s* s = streams[0];
+    p->table = s->ws + s->L.table;
+    p->dyn = reinterpret_cast<unsigned char*>(s->ws + s->L.dyn);
+  } else {
+    p->owns_device = true;
+    if (cudaMalloc(&p->table, p->tv.bytes) != cudaSuccess ||
+        cudaMalloc(&p->dyn, p->dyn_cap) != cudaSuccess ||
+        cudaMalloc(&p->heads, (size_t)n * kCtrlHeadBytes) != cudaSuccess) {
+      plan_free(p);
+      return DRI_ENOMEM;
+    }
+  }
+  if (cudaMallocHost(&p->pin_dyn, (size_t)ring * p->dyn_cap) != cudaSuccess ||
+      cudaMallocHost(&p->pin_heads, (size_t)ring * n * kCtrlHeadBytes) != cudaSuccess) {
+    plan_free(p);
+    return DRI_ENOMEM;
+  }
+  p->ev.assign(ring, nullptr);
+  p->ring_used.assign(ring, 0);
+  for (int i = 0; i < ring; ++i) {
+    if (cudaEventCreateWithFlags(&p->ev[i], cudaEventDisableTiming) != cudaSuccess) {
+      plan_free(p);
+      return DRI_ENOMEM;
+    }
+  }
+  plan_fill_tables(p);
+  const int r = plan_upload_tables(p);
+  if (r != DRI_OK) {
+    plan_free(p);
+    return r;
+  }
+  *out = p;
   return DRI_OK;
 }
 
-// Stage header + samples covering [t0, t1] and copy them to the device.
-int stage_imu(dri_stream_s* s, int slot, double t0, double t1, bool need_cover) {
-  ImuHeader h;
-  std::memset(&h, 0, sizeof(h));
-  h.t0 = t0;
-  h.t1 = t1;
-  size_t k0 = 0, k1 = 0;
-  if (need_cover) {
-    const auto& v = s->imu;
-    if (v.empty() || v.front().t > t0 || v.back().t < t1) return DRI_ENOTREADY;
-    size_t a = 0;
-    while (a + 1 < v.size() && v[a + 1].t <= t0) ++a;
-    size_t b = a;
-    while (b < v.size() && v[b].t < t1) ++b;
-    if (b >= v.size()) return DRI_ENOTREADY;
-    k0 = a;
-    k1 = b + 1;
-    if ((int64_t)(k1 - k0) > s->L.imu_cap) return DRI_ENOMEM;
-    if ((int64_t)(k1 - k0) - 1 > solver_max_imu_pieces()) return DRI_ENOMEM;
-    h.n = (int32_t)(k1 - k0);
-  }
-  // a slot is rewritten only after the frame that last used it has completed
-  char* stage = s->pin_imu + (size_t)slot * s->imu_slot_bytes;
-  std::memcpy(stage, &h, sizeof(h));
-  if (h.n) std::memcpy(stage + sizeof(h), s->imu.data() + k0, (size_t)h.n * sizeof(dri_imu_sample));
-  CK(cudaMemcpyAsync(s->imu_dev, stage, sizeof(h) + (size_t)h.n * sizeof(dri_imu_sample),
-                     cudaMemcpyHostToDevice, s->stream));
-  s->h2d_last += (int64_t)(sizeof(h) + (size_t)h.n * sizeof(dri_imu_sample));
-  return DRI_OK;
-}
-
-const Ctrl* ring_head(const dri_stream_s* s, int slot) {
-  return reinterpret_cast<const Ctrl*>(s->pin_ring + (size_t)slot * kCtrlHeadBytes);
+const Ctrl* ring_head(const Plan* p, int slot, int i) {
+  return reinterpret_cast<const Ctrl*>(p->pin_heads + ((size_t)slot * p->S + i) * kCtrlHeadBytes);
 }
 
 // Settles, in order, the frames whose result copy has completed (all of them
@@ -378,14 +499,13 @@ const Ctrl* ring_head(const dri_stream_s* s, int slot) {
 // state the device kept.
 int settle(dri_stream_s* s, bool wait) {
   while (!s->inflight.empty()) {
-    const int slot = s->inflight.front().slot;
-    cudaError_t q = wait ? cudaEventSynchronize(s->ring_ev[slot]) : cudaEventQuery(s->ring_ev[slot]);
+    const dri_stream_s::InFlight f = s->inflight.front();
+    cudaError_t q = wait ? cudaEventSynchronize(f.ev) : cudaEventQuery(f.ev);
     if (q == cudaErrorNotReady) return DRI_OK;
     if (q != cudaSuccess) return DRI_ECUDA;
-    const Ctrl* h = ring_head(s, slot);
-    s->t_confirmed = h->t_state;
-    if (h->status != DRI_OK) {
-      s->t_prev = h->t_state;
+    s->t_confirmed = f.head->t_state;
+    if (f.head->status != DRI_OK) {
+      s->t_prev = f.head->t_state;
       s->frames_failed++;
     } else {
       s->frames_ok++;
@@ -393,6 +513,320 @@ int settle(dri_stream_s* s, bool wait) {
     s->inflight.pop_front();
   }
   return DRI_OK;
+}
+
+// Next staging slot of the plan; waits for the launch that last used it and
+// settles the streams whose results it held.
+int plan_acquire(Plan* p, int* slot) {
+  const int r = p->next;
+  if (p->ring_used[r]) {
+    CK(cudaEventSynchronize(p->ev[r]));
+    for (dri_stream_s* s : p->slots)
+      if (settle(s, false) != DRI_OK) return DRI_ECUDA;
+    p->ring_used[r] = 0;
+  }
+  *slot = r;
+  return DRI_OK;
+}
+
+// Samples covering [t0, t1] (the last one at or before t0 through the first at
+// or after t1): [k0, k1).
+int select_imu(const dri_stream_s* s, double t0, double t1, size_t* k0, size_t* k1) {
+  const auto& v = s->imu;
+  if (v.empty() || v.front().t > t0 || v.back().t < t1) return DRI_ENOTREADY;
+  size_t a = 0;
+  while (a + 1 < v.size() && v[a + 1].t <= t0) ++a;
+  size_t b = a;
+  while (b < v.size() && v[b].t < t1) ++b;
+  if (b >= v.size()) return DRI_ENOTREADY;
+  *k0 = a;
+  *k1 = b + 1;
+  if ((int64_t)(*k1 - *k0) > s->L.imu_cap) return DRI_ENOMEM;
+  if ((int64_t)(*k1 - *k0) - 1 > solver_max_imu_pieces()) return DRI_ENOMEM;
+  return DRI_OK;
+}
+
+// One slot's staged record: mode, image pointers and the IMU block of
+// [t0, t1] at byte `off` of the staging image.  Returns the block's size.
+size_t stage_slot(const dri_stream_s* s, char* img, int i, int mode, double t0, double t1, size_t k0,
+                  size_t k1, size_t off) {
+  SlotDyn d;
+  std::memset(&d, 0, sizeof(d));
+  d.mode = mode;
+  d.pitch = s->src_pitch;
+  d.imu_off = (int64_t)off;
+  d.src_depth = s->src_depth;
+  d.src_inten = s->src_inten;
+  std::memcpy(img + (size_t)i * sizeof(SlotDyn), &d, sizeof(d));
+  ImuHeader h;
+  std::memset(&h, 0, sizeof(h));
+  h.t0 = t0;
+  h.t1 = t1;
+  h.n = (int32_t)(k1 - k0);
+  std::memcpy(img + off, &h, sizeof(h));
+  if (h.n) std::memcpy(img + off + sizeof(h), s->imu.data() + k0, (size_t)h.n * sizeof(dri_imu_sample));
+  return align_up(sizeof(h) + (size_t)h.n * sizeof(dri_imu_sample), 16);
+}
+
+BatchArgs plan_args(const Plan* p, size_t start_off, int level, int last) {
+  BatchArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.slots = reinterpret_cast<const SlotStatic*>(p->table);
+  a.dyn = p->dyn;
+  a.start = reinterpret_cast<const int32_t*>(p->table + start_off);
+  a.nslots = p->S;
+  a.level = level;
+  a.last = last;
+  return a;
+}
+
+double plan_pixels(const Plan* p, int level) {
+  double n = 0;
+  for (const dri_stream_s* s : p->slots) n += (double)s->geom[level].w * s->geom[level].h;
+  return n;
+}
+
+// Kernel launches of one frame, in order.  phase 1: maps and frame begin;
+// phase 2: the Gauss-Newton loop, frame end, gradients and the head gather.
+int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
+  dri_stream_s* prof = p->slots[0];
+  cudaStream_t st = p->stream;
+  const int L = p->levels;
+  int64_t k = 0;
+  if (phases & 1) {
+    const BatchArgs a0 = plan_args(p, p->tv.copy_off, 0, 0);
+    CK(launch(prof, DRI_KC_MAPS, plan_pixels(p, 0),
+              [&] { return launch_copy_batch(a0, p->pre_copy[p->S], st); }));
+    ++k;
+    for (int l = 1; l < L; ++l) {
+      const BatchArgs a = plan_args(p, p->tv.map_off[l], l, 0);
+      CK(launch(prof, DRI_KC_MAPS, plan_pixels(p, l),
+                [&] { return launch_pyr_down_batch(a, p->pre_map[l][p->S], st); }));
+      ++k;
+    }
+    for (int l = 0; l < L; ++l) {
+      const BatchArgs a = plan_args(p, p->tv.map_off[l], l, 0);
+      CK(launch(prof, DRI_KC_MAPS, plan_pixels(p, l),
+                [&] { return launch_normals_batch(a, p->pre_map[l][p->S], p->fp16, st); }));
+      ++k;
+    }
+    const BatchArgs ab = plan_args(p, p->tv.copy_off, 0, 0);
+    CK(launch(prof, DRI_KC_FRAME, 0.0, [&] { return launch_frame_begin_batch(ab, st); }));
+    ++k;
+  }
+  if (phases & 2) {
+    int remaining = 0;
+    for (int l = 0; l < L; ++l) remaining += p->iters[l];
+    for (int l = L - 1; l >= 0; --l) {
+      for (int it = 0; it < p->iters[l]; ++it) {
+        --remaining;
+        const BatchArgs at = plan_args(p, p->tv.track_off[l], l, 0);
+        CK(launch(prof, DRI_KC_TRACK, plan_pixels(p, l),
+                  [&] { return launch_track_batch(at, p->pre_track[l][p->S], p->fp16, p->fp32p, st); }));
+        const BatchArgs as = plan_args(p, p->tv.copy_off, l, remaining == 0);
+        CK(launch(prof, DRI_KC_SOLVE, 0.0, [&] { return launch_gn_step_batch(as, st); }));
+        k += 2;
+      }
+    }
+    const BatchArgs ae = plan_args(p, p->tv.copy_off, 0, 0);
+    CK(launch(prof, DRI_KC_FRAME, 0.0, [&] { return launch_frame_end_batch(ae, st); }));
+    ++k;
+    for (int l = 0; l < L; ++l) {
+      const BatchArgs a = plan_args(p, p->tv.map_off[l], l, 0);
+      CK(launch(prof, DRI_KC_GRAD, plan_pixels(p, l),
+                [&] { return launch_gradient_batch(a, p->pre_map[l][p->S], p->fp16, st); }));
+      ++k;
+    }
+    if (p->heads) {
+      CK(launch_gather_heads(ae, p->heads, st));
+      ++k;
+    }
+  }
+  if (kernels) *kernels += k;
+  return DRI_OK;
+}
+
+// Chooses each level's rows per thread by timing the pixel kernel on the
+// frames just staged (their maps and frame start are already enqueued):
+// candidates 1, 2, 3, 4, 6 and 8, three launches each, the fastest mean wins.
+int plan_autotune(Plan* p, int64_t* kernels) {
+  static const int cand[] = {1, 2, 3, 4, 6, 8};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int rc = DRI_OK;
+  for (int l = 0; l < p->levels && rc == DRI_OK; ++l) {
+    float best = 1e30f;
+    int best_ppt = p->ppt[0][l];
+    for (int c : cand) {
+      for (auto& v : p->ppt) v[l] = c;
+      plan_fill_tables(p);
+      if ((rc = plan_upload_tables(p)) != DRI_OK) break;
+      const BatchArgs at = plan_args(p, p->tv.track_off[l], l, 0);
+      if (launch_track_batch(at, p->pre_track[l][p->S], p->fp16, p->fp32p, p->stream) != cudaSuccess ||
+          cudaEventRecord(e0, p->stream) != cudaSuccess) {
+        rc = DRI_ECUDA;
+        break;
+      }
+      for (int rep = 0; rep < 3; ++rep)
+        if (launch_track_batch(at, p->pre_track[l][p->S], p->fp16, p->fp32p, p->stream) != cudaSuccess)
+          rc = DRI_ECUDA;
+      float ms = 0.f;
+      if (rc != DRI_OK || cudaEventRecord(e1, p->stream) != cudaSuccess ||
+          cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = DRI_ECUDA;
+        break;
+      }
+      *kernels += 4;
+      if (ms < best) {
+        best = ms;
+        best_ppt = c;
+      }
+    }
+    for (auto& v : p->ppt) v[l] = best_ppt;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != DRI_OK) return rc;
+  plan_fill_tables(p);
+  return plan_upload_tables(p);
+}
+
+// Captures the per-frame launch sequence once as a CUDA graph; a stream that
+// cannot be captured (the legacy default stream) keeps launching directly.
+int plan_run(Plan* p, int64_t* kernels) {
+  const bool profiling = p->slots[0]->profiling;
+  if (!profiling && !p->graph && !p->graph_failed && p->stream != nullptr &&
+      (!p->autotune || p->tuned)) {
+    cudaGraph_t g = nullptr;
+    int64_t k = 0;
+    if (cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int r = plan_enqueue(p, 3, &k);
+      const cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+      if (r == DRI_OK && e == cudaSuccess && g &&
+          cudaGraphInstantiate(&p->graph, g, 0) == cudaSuccess) {
+        p->kernels_per_frame = k;
+      } else {
+        p->graph = nullptr;
+        p->graph_failed = true;
+      }
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+    } else {
+      cudaGetLastError();
+      p->graph_failed = true;
+    }
+  }
+  if (p->graph && !profiling) {
+    CK(cudaGraphLaunch(p->graph, p->stream));
+    *kernels += p->kernels_per_frame;
+    return DRI_OK;
+  }
+  return plan_enqueue(p, 3, kernels);
+}
+
+// Per-slot decision for one launch of plan p.
+struct SlotWork {
+  int mode = kSlotIdle;
+  int status = DRI_ENOTREADY;       // result for a slot that does not run
+  size_t k0 = 0, k1 = 0;
+};
+
+SlotWork plan_slot_work(const dri_stream_s* s) {
+  SlotWork w;
+  if (!s->frame_pending) return w;
+  if (!s->initialised) {
+    w.mode = kSlotInit;
+    w.status = DRI_OK;
+    return w;
+  }
+  const int r = select_imu(s, s->t_prev, s->t_frame, &w.k0, &w.k1);
+  if (r != DRI_OK) {
+    w.status = r;
+    return w;
+  }
+  w.mode = kSlotTrack;
+  w.status = DRI_OK;
+  return w;
+}
+
+// Stages and launches one frame of every slot with work; records the result
+// copies and the streams' bookkeeping.  *ring_slot receives the staging slot
+// (-1 if nothing ran).
+int plan_launch(Plan* p, const std::vector<SlotWork>& work, int* ring_slot) {
+  *ring_slot = -1;
+  int r = settle(p->slots[0], false);
+  if (r != DRI_OK) return r;
+  int rs = 0;
+  if ((r = plan_acquire(p, &rs)) != DRI_OK) return r;
+  char* img = p->pin_dyn + (size_t)rs * p->dyn_cap;
+  std::memset(img, 0, dyn_header_bytes(p->S));
+  size_t off = dyn_header_bytes(p->S);
+  bool any_track = false;
+  for (int i = 0; i < p->S; ++i) {
+    const dri_stream_s* s = p->slots[i];
+    const SlotWork& w = work[i];
+    if (w.mode == kSlotIdle) continue;
+    const double t0 = w.mode == kSlotInit ? s->t_frame : s->t_prev;
+    off += stage_slot(s, img, i, w.mode, t0, s->t_frame, w.k0, w.k1, off);
+    any_track = any_track || w.mode == kSlotTrack;
+  }
+  CK(cudaMemcpyAsync(p->dyn, img, off, cudaMemcpyHostToDevice, p->stream));
+  int64_t kernels = 0;
+  if (p->autotune && !p->tuned && any_track && !p->slots[0]->profiling) {
+    if ((r = plan_enqueue(p, 1, &kernels)) != DRI_OK) return r;
+    if ((r = plan_autotune(p, &kernels)) != DRI_OK) return r;
+    p->tuned = true;
+    if ((r = plan_enqueue(p, 2, &kernels)) != DRI_OK) return r;
+  } else if ((r = plan_run(p, &kernels)) != DRI_OK) {
+    return r;
+  }
+  const void* src = p->heads ? (const void*)p->heads : (const void*)p->slots[0]->ctrl;
+  CK(cudaMemcpyAsync(p->pin_heads + (size_t)rs * p->S * kCtrlHeadBytes, src,
+                     (size_t)p->S * kCtrlHeadBytes, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaEventRecord(p->ev[rs], p->stream));
+  p->ring_used[rs] = 1;
+  p->next = (p->next + 1) % p->R;
+  for (int i = 0; i < p->S; ++i) {
+    dri_stream_s* s = p->slots[i];
+    s->launches += kernels;
+    const SlotWork& w = work[i];
+    if (w.mode == kSlotIdle) continue;
+    s->h2d_last = s->h2d_frame + (int64_t)(sizeof(SlotDyn) + sizeof(ImuHeader) +
+                                           (w.k1 - w.k0) * sizeof(dri_imu_sample));
+    s->d2h_last = (int64_t)kCtrlHeadBytes;
+    if (w.mode == kSlotInit) {
+      s->initialised = true;
+      s->t_prev_before = s->t_frame;
+      s->t_prev = s->t_frame;
+      s->t_confirmed = s->t_frame;
+    } else {
+      // drop samples no later frame can need: all before the one covering the
+      // earliest time a frame may still start from (a failed frame in flight
+      // rolls the start back to t_confirmed)
+      const double keep_from = std::min(s->t_prev, s->t_confirmed);
+      size_t a = 0;
+      while (a + 1 < s->imu.size() && s->imu[a + 1].t <= keep_from) ++a;
+      if (a) s->imu.erase(s->imu.begin(), s->imu.begin() + a);
+      s->t_prev_before = s->t_prev;
+      s->t_prev = s->t_frame;   // optimistic; rolled back when the frame is known to fail
+    }
+    s->frame_pending = false;
+    s->inflight.push_back({p->ev[rs], ring_head(p, rs, i)});
+  }
+  *ring_slot = rs;
+  return DRI_OK;
+}
+
+std::mutex g_batch_mu;   // guards every stream's batch-plan list and the plan cache
+std::vector<Plan*> g_batch_plans;
+
+void forget_plan_locked(Plan* p) {
+  for (dri_stream_s* s : p->slots) {
+    auto& v = s->batches;
+    v.erase(std::remove(v.begin(), v.end(), p), v.end());
+  }
+  g_batch_plans.erase(std::remove(g_batch_plans.begin(), g_batch_plans.end(), p), g_batch_plans.end());
 }
 
 }  // namespace
@@ -482,21 +916,11 @@ int dri_create_stream(const dri_stream_config* cfg, const dri_state* x_init, voi
     }
     s->own_ws = true;
   }
-  s->imu_slot_bytes = align_up(sizeof(ImuHeader) + (size_t)L.imu_cap * sizeof(dri_imu_sample), 64);
-  if (cudaMallocHost(&s->pin_imu, (size_t)(dri_stream_s::kRing + 1) * s->imu_slot_bytes) != cudaSuccess ||
-      cudaMallocHost(&s->pin_ctrl, sizeof(Ctrl)) != cudaSuccess ||
-      cudaMallocHost(&s->pin_ring, (size_t)dri_stream_s::kRing * kCtrlHeadBytes) != cudaSuccess) {
+  if (cudaMallocHost(&s->pin_ctrl, sizeof(Ctrl)) != cudaSuccess) {
     dri_destroy_stream(s);
     return DRI_ENOMEM;
   }
-  for (int i = 0; i < dri_stream_s::kRing; ++i) {
-    if (cudaEventCreateWithFlags(&s->ring_ev[i], cudaEventDisableTiming) != cudaSuccess) {
-      dri_destroy_stream(s);
-      return DRI_ENOMEM;
-    }
-  }
   s->ctrl = (Ctrl*)(s->ws + L.ctrl);
-  s->imu_dev = (ImuHeader*)(s->ws + L.imu);
   s->in_depth = (float*)(s->ws + L.in_depth);
   s->in_inten = (float*)(s->ws + L.in_inten);
   s->partials = (void*)(s->ws + L.partials);
@@ -531,6 +955,12 @@ int dri_create_stream(const dri_stream_config* cfg, const dri_state* x_init, voi
     dri_destroy_stream(s);
     return DRI_ECUDA;
   }
+  dri_stream_s* one[1] = {s};
+  const int r = plan_create(one, 1, kStreamRing, true, &s->own);
+  if (r != DRI_OK) {
+    dri_destroy_stream(s);
+    return r;
+  }
   *out = s;
   return DRI_OK;
 }
@@ -538,12 +968,20 @@ int dri_create_stream(const dri_stream_config* cfg, const dri_state* x_init, voi
 int dri_destroy_stream(dri_stream s) {
   if (!s) return DRI_EINVAL;
   if (s->stream || s->ws) cudaStreamSynchronize(s->stream);
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    while (!s->batches.empty()) {
+      Plan* p = s->batches.back();
+      cudaStreamSynchronize(p->stream);
+      for (dri_stream_s* o : p->slots) settle(o, true);
+      forget_plan_locked(p);
+      plan_free(p);
+    }
+  }
+  settle(s, true);
+  plan_free(s->own);
   if (s->own_ws && s->ws) cudaFree(s->ws);
-  if (s->pin_imu) cudaFreeHost(s->pin_imu);
   if (s->pin_ctrl) cudaFreeHost(s->pin_ctrl);
-  if (s->pin_ring) cudaFreeHost(s->pin_ring);
-  for (int i = 0; i < dri_stream_s::kRing; ++i)
-    if (s->ring_ev[i]) cudaEventDestroy(s->ring_ev[i]);
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
   delete s;
   return DRI_OK;
@@ -555,12 +993,24 @@ int dri_upload_frame(dri_stream s, double t, const float* depth, const float* in
   if (mem_kind != DRI_HOST && mem_kind != DRI_DEVICE) return DRI_EINVAL;
   const size_t row = (size_t)s->cfg.width * sizeof(float);
   const size_t pitch = pitch_bytes ? pitch_bytes : row;
-  if (pitch < row) return DRI_EINVAL;
+  if (pitch < row || pitch % sizeof(float) != 0 || pitch / sizeof(float) > (size_t)INT32_MAX)
+    return DRI_EINVAL;
   if (s->initialised && !(t > s->t_prev)) return DRI_EINVAL;
-  const cudaMemcpyKind kind = mem_kind == DRI_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  s->h2d_last = mem_kind == DRI_HOST ? (int64_t)(2 * row * s->cfg.height) : 0;
-  CK(cudaMemcpy2DAsync(s->in_depth, row, depth, pitch, row, s->cfg.height, kind, s->stream));
-  CK(cudaMemcpy2DAsync(s->in_inten, row, intensity, pitch, row, s->cfg.height, kind, s->stream));
+  if (mem_kind == DRI_HOST) {
+    CK(cudaMemcpy2DAsync(s->in_depth, row, depth, pitch, row, s->cfg.height, cudaMemcpyHostToDevice,
+                         s->stream));
+    CK(cudaMemcpy2DAsync(s->in_inten, row, intensity, pitch, row, s->cfg.height,
+                         cudaMemcpyHostToDevice, s->stream));
+    s->src_depth = s->in_depth;
+    s->src_inten = s->in_inten;
+    s->src_pitch = s->cfg.width;
+    s->h2d_frame = (int64_t)(2 * row * s->cfg.height);
+  } else {
+    s->src_depth = depth;
+    s->src_inten = intensity;
+    s->src_pitch = (int32_t)(pitch / sizeof(float));
+    s->h2d_frame = 0;
+  }
   s->t_frame = t;
   s->frame_pending = true;
   return DRI_OK;
@@ -580,10 +1030,11 @@ int dri_push_imu(dri_stream s, const dri_imu_sample* samples, size_t n) {
   return DRI_OK;
 }
 
-static int fill_result(dri_stream s, const Ctrl* h, dri_track_result* out, bool init) {
+static void fill_result(const dri_stream_s* s, const Ctrl* h, dri_track_result* out, bool init,
+                        double t0) {
   std::memset(out, 0, sizeof(*out));
   out->x1 = from_dstate(h->x, h->t_state);
-  out->x0 = from_dstate(h->x0, s->t_prev_before);
+  out->x0 = from_dstate(h->x0, t0);
   for (int l = 0; l < kMaxLevels; ++l) {
     out->n_icp[l] = h->n_icp[l];
     out->n_rgb[l] = h->n_rgb[l];
@@ -591,71 +1042,78 @@ static int fill_result(dri_stream s, const Ctrl* h, dri_track_result* out, bool 
   out->cost = h->cost;
   out->status = h->status;
   out->initialised = init ? 1 : 0;
-  return h->status;
+  (void)s;
 }
 
 int dri_track(dri_stream s, dri_track_result* out) {
   if (!s) return DRI_EINVAL;
   if (!s->frame_pending) return DRI_ENOTREADY;
-  if (settle(s, false) != DRI_OK) return DRI_ECUDA;
-  if ((int)s->inflight.size() >= dri_stream_s::kRing) {
-    // ring full: wait for the oldest frame only, so its slots can be reused
-    CK(cudaEventSynchronize(s->ring_ev[s->inflight.front().slot]));
-    if (settle(s, false) != DRI_OK) return DRI_ECUDA;
-  }
-  const bool init = !s->initialised;
-  const int slot = s->ring_next;   // staging + result slot of this frame
-  if (init) {
-    int r = stage_imu(s, slot, s->t_frame, s->t_frame, false);
-    if (r != DRI_OK) return r;
-    if ((r = enqueue_maps(s)) != DRI_OK) return r;
-    CK(launch(s, DRI_KC_FRAME, 0.0, [&] { return launch_frame_init(solve_params(s, 0, 0), s->stream); }));
-    if ((r = enqueue_gradients(s)) != DRI_OK) return r;
-    s->initialised = true;
-    s->t_prev_before = s->t_frame;
-    s->t_prev = s->t_frame;
-    s->t_confirmed = s->t_frame;
-  } else {
-    int r = stage_imu(s, slot, s->t_prev, s->t_frame, true);
-    if (r != DRI_OK) return r;
-    if ((r = enqueue_maps(s)) != DRI_OK) return r;
-    CK(launch(s, DRI_KC_FRAME, 0.0, [&] { return launch_frame_begin(solve_params(s, 0, 0), s->stream); }));
-    int remaining = 0;
-    for (int l = 0; l < s->cfg.levels; ++l) remaining += s->cfg.iters[l];
-    for (int l = s->cfg.levels - 1; l >= 0; --l) {
-      const TrackParams tp = track_params(s, l, nullptr);
-      const bool fp16 = (s->cfg.precision_flags & DRI_FP16_MAPS) != 0;
-      const bool fp32p = (s->cfg.precision_flags & DRI_FP32_PARTIALS) != 0;
-      for (int it = 0; it < s->cfg.iters[l]; ++it) {
-        --remaining;
-        CK(launch(s, DRI_KC_TRACK, (double)tp.g.w * tp.g.h,
-                  [&] { return launch_track(tp, fp16, fp32p, s->stream); }));
-        CK(launch(s, DRI_KC_SOLVE, 0.0,
-                  [&] { return launch_gn_step(solve_params(s, l, remaining == 0), s->stream); }));
-      }
-    }
-    CK(launch(s, DRI_KC_FRAME, 0.0, [&] { return launch_frame_end(solve_params(s, 0, 0), s->stream); }));
-    if ((r = enqueue_gradients(s)) != DRI_OK) return r;
-    // drop samples no later frame can need: all before the one covering the
-    // earliest time a frame may still start from (a failed frame in flight
-    // rolls the start back to t_confirmed)
-    const double keep_from = std::min(s->t_prev, s->t_confirmed);
-    size_t a = 0;
-    while (a + 1 < s->imu.size() && s->imu[a + 1].t <= keep_from) ++a;
-    if (a) s->imu.erase(s->imu.begin(), s->imu.begin() + a);
-    s->t_prev_before = s->t_prev;
-    s->t_prev = s->t_frame;   // optimistic; rolled back when the frame is known to fail
-  }
-  s->frame_pending = false;
-  s->ring_next = (s->ring_next + 1) % dri_stream_s::kRing;
-  CK(cudaMemcpyAsync(s->pin_ring + (size_t)slot * kCtrlHeadBytes, s->ctrl, kCtrlHeadBytes,
-                     cudaMemcpyDeviceToHost, s->stream));
-  s->d2h_last = (int64_t)kCtrlHeadBytes;
-  CK(cudaEventRecord(s->ring_ev[slot], s->stream));
-  s->inflight.push_back({slot});
+  std::vector<SlotWork> work(1, plan_slot_work(s));
+  if (work[0].mode == kSlotIdle) return work[0].status;
+  const bool init = work[0].mode == kSlotInit;
+  int rs = -1;
+  const int r = plan_launch(s->own, work, &rs);
+  if (r != DRI_OK) return r;
   if (!out) return DRI_OK;
   if (settle(s, true) != DRI_OK) return DRI_ECUDA;
-  return fill_result(s, ring_head(s, slot), out, init);
+  const Ctrl* h = ring_head(s->own, rs, 0);
+  fill_result(s, h, out, init, s->t_prev_before);
+  return h->status;
+}
+
+int dri_track_batch(const dri_stream* streams, int32_t n, dri_track_result* out) {
+  if (!streams || n < 1 || n > kMaxBatch) return DRI_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    const dri_stream_s* s = streams[i];
+    if (!s) return DRI_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (streams[j] == s) return DRI_EINVAL;
+    const dri_stream_s* s0 = streams[0];
+    if (s->stream != s0->stream || s->cfg.levels != s0->cfg.levels ||
+        s->cfg.precision_flags != s0->cfg.precision_flags)
+      return DRI_EINVAL;
+    for (int l = 0; l < s->cfg.levels; ++l)
+      if (s->cfg.iters[l] != s0->cfg.iters[l]) return DRI_EINVAL;
+  }
+  std::vector<dri_stream_s*> key(streams, streams + n);
+  Plan* p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (Plan* q : g_batch_plans)
+      if (q->slots == key) p = q;
+    if (!p) {
+      const int r = plan_create(key.data(), n, kBatchRing, false, &p);
+      if (r != DRI_OK) return r;
+      p->autotune = true;
+      g_batch_plans.push_back(p);
+      for (dri_stream_s* s : key) s->batches.push_back(p);
+    }
+  }
+  std::vector<SlotWork> work(n);
+  bool any = false;
+  for (int i = 0; i < n; ++i) {
+    if (settle(key[i], false) != DRI_OK) return DRI_ECUDA;
+    work[i] = plan_slot_work(key[i]);
+    any = any || work[i].mode != kSlotIdle;
+  }
+  if (!any) return DRI_ENOTREADY;
+  std::vector<double> t0(n);
+  for (int i = 0; i < n; ++i) t0[i] = key[i]->t_prev;
+  int rs = -1;
+  const int r = plan_launch(p, work, &rs);
+  if (r != DRI_OK) return r;
+  if (!out) return DRI_OK;
+  CK(cudaEventSynchronize(p->ev[rs]));
+  for (int i = 0; i < n; ++i) {
+    if (settle(key[i], true) != DRI_OK) return DRI_ECUDA;
+    if (work[i].mode == kSlotIdle) {
+      std::memset(&out[i], 0, sizeof(out[i]));
+      out[i].status = work[i].status;
+      continue;
+    }
+    fill_result(key[i], ring_head(p, rs, i), &out[i], work[i].mode == kSlotInit, t0[i]);
+  }
+  return DRI_OK;
 }
 
 int dri_get_state(dri_stream s, dri_state* x1, double* H_prior, double* b_prior) {
@@ -695,16 +1153,40 @@ int dri_linearise(dri_stream s, int32_t level, const dri_state* x0, const dri_st
   if (!finite_state(*x0) || !finite_state(*x1)) return DRI_EINVAL;
   if (!s->initialised || !s->frame_pending) return DRI_ENOTREADY;
   if (settle(s, true) != DRI_OK) return DRI_ECUDA;
-  int r = stage_imu(s, dri_stream_s::kRing, s->t_prev, s->t_frame, true);
+  size_t k0 = 0, k1 = 0;
+  int r = select_imu(s, s->t_prev, s->t_frame, &k0, &k1);
   if (r != DRI_OK) return r;
-  if ((r = enqueue_maps(s)) != DRI_OK) return r;
+  Plan* p = s->own;
+  int rs = 0;
+  if ((r = plan_acquire(p, &rs)) != DRI_OK) return r;
+  char* img = p->pin_dyn + (size_t)rs * p->dyn_cap;
+  std::memset(img, 0, dyn_header_bytes(1));
+  const size_t off = dyn_header_bytes(1);
+  const size_t used = off + stage_slot(s, img, 0, kSlotTrack, s->t_prev, s->t_frame, k0, k1, off);
+  CK(cudaMemcpyAsync(p->dyn, img, used, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaEventRecord(p->ev[rs], s->stream));
+  p->ring_used[rs] = 1;
+  p->next = (p->next + 1) % p->R;
+  // the maps of the pending frame (the frame itself stays pending)
+  const int L = s->cfg.levels;
+  const BatchArgs a0 = plan_args(p, p->tv.copy_off, 0, 0);
+  CK(launch(s, DRI_KC_MAPS, 0.0, [&] { return launch_copy_batch(a0, p->pre_copy[1], s->stream); }));
+  for (int l = 1; l < L; ++l) {
+    const BatchArgs a = plan_args(p, p->tv.map_off[l], l, 0);
+    CK(launch(s, DRI_KC_MAPS, 0.0, [&] { return launch_pyr_down_batch(a, p->pre_map[l][1], s->stream); }));
+  }
+  for (int l = 0; l < L; ++l) {
+    const BatchArgs a = plan_args(p, p->tv.map_off[l], l, 0);
+    CK(launch(s, DRI_KC_MAPS, 0.0,
+              [&] { return launch_normals_batch(a, p->pre_map[l][1], p->fp16, s->stream); }));
+  }
+  s->launches += 1 + 2 * L - 1 + 3;
   const SolveParams sp = solve_params(s, level, 0);
-  const bool fp16 = (s->cfg.precision_flags & DRI_FP16_MAPS) != 0;
-  const bool fp32p = (s->cfg.precision_flags & DRI_FP32_PARTIALS) != 0;
-  const TrackParams tp = track_params(s, level, flags ? s->flags : nullptr);
+  const TrackParams tp = track_params(s, level, s->ppt[level], flags ? s->flags : nullptr);
   CK(launch(s, DRI_KC_FRAME, 0.0,
             [&] { return launch_linearise_begin(sp, to_dstate(*x0), to_dstate(*x1), s->stream); }));
-  CK(launch(s, DRI_KC_TRACK, (double)tp.g.w * tp.g.h, [&] { return launch_track(tp, fp16, fp32p, s->stream); }));
+  CK(launch(s, DRI_KC_TRACK, (double)tp.g.w * tp.g.h,
+            [&] { return launch_track(tp, p->fp16, p->fp32p, s->stream); }));
   CK(launch(s, DRI_KC_SOLVE, 0.0, [&] { return launch_linearise_end(sp, s->lin_dev, s->stream); }));
   CK(cudaMemcpyAsync(out, s->lin_dev, sizeof(*out), cudaMemcpyDeviceToHost, s->stream));
   if (flags) {
@@ -759,6 +1241,19 @@ int dri_io_bytes(dri_stream s, int64_t* h2d, int64_t* d2h) {
 int dri_launch_count(dri_stream s, int64_t* count) {
   if (!s || !count) return DRI_EINVAL;
   *count = s->launches;
+  return DRI_OK;
+}
+
+int dri_batch_tiles(const dri_stream* streams, int32_t n, int32_t* ppt) {
+  if (!streams || n < 1 || !ppt) return DRI_EINVAL;
+  std::vector<dri_stream_s*> key(streams, streams + n);
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  const Plan* p = nullptr;
+  if (n == 1 && key[0]) p = key[0]->own;
+  for (const Plan* q : g_batch_plans)
+    if (q->slots == key) p = q;
+  if (!p) return DRI_ENOTREADY;
+  for (int l = 0; l < kMaxLevels; ++l) ppt[l] = l < p->levels ? p->ppt[0][l] : 0;
   return DRI_OK;
 }
 

@@ -4,18 +4,25 @@
 //   Ctrl           FP64 state block: x, the iterates x0 / x1, the prior (H*, b*, xbar),
 //                  W_IMU, the reference pose, the per-iteration pixel transforms, the
 //                  folded sums and the last joint system (Sec. IV-D/E).
-//   ImuBuf         header (t0, t1, n) + the samples covering [t0, t1].
-//   input depth/I  level-0 upload target (fixed address, so uploads never race the
-//                  buffer-set flip decided on the device).
+//   dyn            per-frame staging of the stream's own launch sequence: SlotDyn,
+//                  then an ImuHeader and the samples covering [t0, t1].
+//   table          SlotStatic of the stream and the block-count prefixes of its
+//                  launches (the one-slot plan of dri_track).
+//   input depth/I  level-0 host-upload target.
 //   2 map sets     per level: depth, normal (3 planes), intensity, gradient (2 planes).
 //                  Set ctrl.ref_index is the reference, the other the live frame; a
 //                  tracked frame flips the index on the device (no host round trip).
 //   partials       per-block sums of the pixel kernel (FP64 or FP32).
 //   flags          per-pixel validity bytes for the parity entry point.
+//
+// Every launch of a frame is "batched": its blocks are spread over one or more
+// slots (streams) by a prefix of per-slot block counts, each slot reading its
+// static parameters (SlotStatic) from a device table and its per-frame mode,
+// image pointers and IMU block from the staged dyn buffer.  dri_track runs the
+// sequence over one slot, dri_track_batch over many.
 #pragma once
 
 #include <cstddef>
-#include <cstdint>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -28,7 +35,8 @@ constexpr int kMaxLevels = DRI_MAX_LEVELS;
 constexpr int kSums = 29;             // per term: 21 (upper J J^T) + 6 (J e) + e^2 + count
 constexpr int kSumsAll = 2 * kSums;   // ICP then photometric
 constexpr int kTrackThreadsX = 32;
-constexpr int kTrackThreadsY = 8;
+constexpr int kTrackThreadsY = 8;      // warps of the pixel kernel: 4 ICP, 4 photometric
+constexpr int kTrackRows = 4;          // tile rows per unit of rows-per-thread
 constexpr int kFoldGroup = 16;        // blocks per first-level fold of the pixel kernel
 
 struct DState {                       // Eq. 1
@@ -90,7 +98,8 @@ struct LevelMaps {
 };
 
 struct StreamLayout {
-  size_t ctrl, imu, in_depth, in_inten, counters, partials, gpartials, flags, lin_out, total;
+  size_t ctrl, dyn, dyn_bytes, table, in_depth, in_inten, counters, partials, gpartials, flags,
+      lin_out, total;
   size_t level_off[kMaxLevels][2][4];  // per level, per set: depth, normal, inten, grad
   int64_t plane[kMaxLevels];
   int max_blocks;
@@ -126,29 +135,96 @@ struct SolveParams {
   int32_t imu_cap;
 };
 
+// ---- batched launches --------------------------------------------------------
+enum SlotMode : int32_t { kSlotIdle = 0, kSlotTrack = 1, kSlotInit = 2 };
+
+constexpr int kCopyTileW = 128;       // level-0 input copy: 32 x 8 threads, 4 pixels each
+constexpr int kCopyTileH = 8;
+constexpr int kMapTileW = 32;         // pyramid, normal and gradient maps: one pixel a thread
+constexpr int kMapTileH = 8;
+
+// Per-slot parameters fixed for the life of a plan.
+struct SlotStatic {
+  TrackParams tp[kMaxLevels];         // flags = nullptr; ppt / nblocks as planned
+  SolveParams sp;                     // imu, level and last are set per launch
+  const float* in_depth;              // level-0 host-upload target
+  const float* in_inten;
+  int32_t levels;
+  int32_t pad;
+};
+
+// Per-slot record staged with every launch of a frame.
+struct SlotDyn {
+  int32_t mode;                       // SlotMode
+  int32_t pitch;                      // source row pitch, floats
+  int64_t imu_off;                    // byte offset of the slot's ImuHeader in the dyn buffer
+  const float* src_depth;             // this frame's level-0 images (device)
+  const float* src_inten;
+};
+
+// Table of one plan in device memory: SlotStatic[nslots], then the int32
+// prefixes copy[n + 1], map[levels][n + 1] and track[levels][n + 1].
+struct TableView {
+  size_t copy_off, map_off[kMaxLevels], track_off[kMaxLevels], bytes;
+};
+TableView table_view(int nslots, int levels);
+
+// Kernel argument of every batched launch.
+struct BatchArgs {
+  const SlotStatic* slots;
+  const unsigned char* dyn;           // SlotDyn[nslots], then the IMU blocks
+  const int32_t* start;               // block prefix over the slots for this launch
+  int32_t nslots;
+  int32_t level;
+  int32_t last;                       // 1 on the frame's last Gauss-Newton iteration
+  int32_t pad;
+};
+
+__device__ __forceinline__ int batch_slot(const BatchArgs& a, int block) {
+  int lo = 0, hi = a.nslots;          // start[lo] <= block < start[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(a.start + mid) <= block) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ const SlotDyn& batch_dyn(const BatchArgs& a, int slot) {
+  return reinterpret_cast<const SlotDyn*>(a.dyn)[slot];
+}
+
 StreamLayout make_layout(const dri_stream_config& cfg);
 LevelGeom level_geom(const dri_stream_config& cfg, int level);
 
 // ---- kernel launchers (return cudaGetLastError()) ------------------------
-cudaError_t launch_copy_input(const float* in_d, const float* in_i, const LevelMaps& m0,
-                              const Ctrl* ctrl, int w, int h, cudaStream_t s);
-cudaError_t launch_pyr_down(const LevelMaps& fine, const LevelMaps& coarse, const Ctrl* ctrl,
-                            int wf, int hf, int wc, int hc, cudaStream_t s);
+cudaError_t launch_copy_batch(const BatchArgs& a, int blocks, cudaStream_t s);
+cudaError_t launch_pyr_down_batch(const BatchArgs& a, int blocks, cudaStream_t s);
+cudaError_t launch_normals_batch(const BatchArgs& a, int blocks, bool fp16, cudaStream_t s);
+cudaError_t launch_gradient_batch(const BatchArgs& a, int blocks, bool fp16, cudaStream_t s);
+inline int copy_tiles(int w, int h) {
+  return ((w + kCopyTileW - 1) / kCopyTileW) * ((h + kCopyTileH - 1) / kCopyTileH);
+}
+inline int map_tiles(int w, int h) {
+  return ((w + kMapTileW - 1) / kMapTileW) * ((h + kMapTileH - 1) / kMapTileH);
+}
 cudaError_t launch_normals(const LevelMaps& m, const Ctrl* ctrl, const LevelGeom& g,
                            float dmin, float dmax, bool fp16, int which_set, cudaStream_t s);
 cudaError_t launch_gradient(const LevelMaps& m, const Ctrl* ctrl, int w, int h, bool fp16,
                             cudaStream_t s);
 cudaError_t launch_track(const TrackParams& p, bool fp16, bool fp32_partials, cudaStream_t s);
+cudaError_t launch_track_batch(const BatchArgs& a, int blocks, bool fp16, bool fp32_partials,
+                               cudaStream_t s);
 int track_grid_blocks(int w, int h, int ppt);
 int track_default_ppt(int w, int h);
 inline int fold_groups(int nblocks) { return (nblocks + kFoldGroup - 1) / kFoldGroup; }
 
 cudaError_t prepare_solver_kernels();   // opt-in shared memory sizes (current device)
 int solver_max_imu_pieces();
-cudaError_t launch_frame_begin(const SolveParams& p, cudaStream_t s);
-cudaError_t launch_gn_step(const SolveParams& p, cudaStream_t s);
-cudaError_t launch_frame_end(const SolveParams& p, cudaStream_t s);
-cudaError_t launch_frame_init(const SolveParams& p, cudaStream_t s);
+cudaError_t launch_frame_begin_batch(const BatchArgs& a, cudaStream_t s);
+cudaError_t launch_gn_step_batch(const BatchArgs& a, cudaStream_t s);
+cudaError_t launch_frame_end_batch(const BatchArgs& a, cudaStream_t s);
+cudaError_t launch_gather_heads(const BatchArgs& a, unsigned char* out, cudaStream_t s);
 cudaError_t launch_linearise_begin(const SolveParams& p, const DState& x0, const DState& x1,
                                    cudaStream_t s);
 cudaError_t launch_linearise_end(const SolveParams& p, dri_linearisation* out, cudaStream_t s);

@@ -1,7 +1,7 @@
 // Map building of the tracking pyramid (Sec. IV-D coarse-to-fine scheme; the
 // inputs of Eq. 3 and Eq. 4).
 //
-//   copy_input   level-0 depth / intensity of the live map set from the upload buffer
+//   copy         level-0 depth / intensity of the live map set from the frame's images
 //   pyr_down     level l from level l-1: depth = mean of the 2x2 samples > 0 (0 if
 //                none), intensity = 2x2 mean
 //   normals      n = normalise((v(x+1,y) - v) x (v(x,y+1) - v)), facing the camera,
@@ -11,6 +11,8 @@
 //
 // All maps are planar (one plane per component) so a warp reads 128 contiguous
 // bytes per plane; normals and gradients are FP32 or, with DRI_FP16_MAPS, FP16.
+// The batched kernels cover the images of every slot of a plan in one launch;
+// the single-image normal and gradient kernels serve the allocation-free entry.
 #include <cuda_fp16.h>
 
 #include "dri_internal.h"
@@ -28,59 +30,69 @@ __device__ __forceinline__ void store_map<__half>(__half* p, int64_t i, float v)
   p[i] = __float2half_rn(v);
 }
 
-__global__ void k_copy_input(const float* __restrict__ in_d, const float* __restrict__ in_i,
-                             LevelMaps m, const Ctrl* __restrict__ ctrl, int w, int h) {
-  const int cs = 1 - ctrl->ref_index;
-  const int64_t n = (int64_t)w * h;
-  const int64_t n4 = n / 4;
-  const float4* d4 = reinterpret_cast<const float4*>(in_d);
-  const float4* i4 = reinterpret_cast<const float4*>(in_i);
-  float4* od = reinterpret_cast<float4*>(m.depth[cs]);
-  float4* oi = reinterpret_cast<float4*>(m.inten[cs]);
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n4;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    od[k] = __ldg(d4 + k);
-    oi[k] = __ldg(i4 + k);
-  }
-  for (int64_t k = n4 * 4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    m.depth[cs][k] = in_d[k];
-    m.inten[cs][k] = in_i[k];
+// Level-0 copy of one 128 x 8 tile: each thread moves 4 pixels of a row, as one
+// 16-byte load and store when both rows allow it.
+__global__ void __launch_bounds__(256) k_copy_batch(const BatchArgs a) {
+  const int slot = batch_slot(a, blockIdx.x);
+  const SlotDyn& d = batch_dyn(a, slot);
+  if (d.mode == kSlotIdle) return;
+  const TrackParams& tp = a.slots[slot].tp[0];
+  const int w = tp.g.w, h = tp.g.h;
+  const int cs = 1 - tp.ctrl->ref_index;
+  const int t = blockIdx.x - __ldg(a.start + slot);
+  const int gx = (w + kCopyTileW - 1) / kCopyTileW;
+  const int x = (t % gx) * kCopyTileW + threadIdx.x * 4;
+  const int y = (t / gx) * kCopyTileH + threadIdx.y;
+  if (x >= w || y >= h) return;
+  const float* sd = d.src_depth + (int64_t)y * d.pitch + x;
+  const float* si = d.src_inten + (int64_t)y * d.pitch + x;
+  float* od = tp.m.depth[cs] + (int64_t)y * w + x;
+  float* oi = tp.m.inten[cs] + (int64_t)y * w + x;
+  const uintptr_t al = (uintptr_t)sd | (uintptr_t)si | (uintptr_t)od | (uintptr_t)oi;
+  if (x + 4 <= w && (al & 15) == 0) {
+    *reinterpret_cast<float4*>(od) = __ldg(reinterpret_cast<const float4*>(sd));
+    *reinterpret_cast<float4*>(oi) = __ldg(reinterpret_cast<const float4*>(si));
+  } else {
+    const int n = min(4, w - x);
+    for (int k = 0; k < n; ++k) {
+      od[k] = __ldg(sd + k);
+      oi[k] = __ldg(si + k);
+    }
   }
 }
 
-__global__ void k_pyr_down(LevelMaps fine, LevelMaps coarse, const Ctrl* __restrict__ ctrl,
-                           int wf, int hf, int wc, int hc) {
-  const int cs = 1 - ctrl->ref_index;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= wc || y >= hc) return;
+__device__ __forceinline__ void pyr_down_px(const LevelMaps& fine, const LevelMaps& coarse, int cs,
+                                            int wf, int wc, int x, int y) {
   const float* D = fine.depth[cs];
   const float* I = fine.inten[cs];
   const int64_t i0 = (int64_t)(2 * y) * wf + 2 * x;
   const int64_t i1 = i0 + wf;
-  const float2 da = __ldg(reinterpret_cast<const float2*>(D + i0));
-  const float2 db = __ldg(reinterpret_cast<const float2*>(D + i1));
-  const float2 ia = __ldg(reinterpret_cast<const float2*>(I + i0));
-  const float2 ib = __ldg(reinterpret_cast<const float2*>(I + i1));
+  float da0, da1, db0, db1, ia0, ia1, ib0, ib1;
+  if ((wf & 1) == 0) {                 // rows of even width keep the 2x2 pairs 8-byte aligned
+    const float2 da = __ldg(reinterpret_cast<const float2*>(D + i0));
+    const float2 db = __ldg(reinterpret_cast<const float2*>(D + i1));
+    const float2 ia = __ldg(reinterpret_cast<const float2*>(I + i0));
+    const float2 ib = __ldg(reinterpret_cast<const float2*>(I + i1));
+    da0 = da.x; da1 = da.y; db0 = db.x; db1 = db.y;
+    ia0 = ia.x; ia1 = ia.y; ib0 = ib.x; ib1 = ib.y;
+  } else {
+    da0 = __ldg(D + i0); da1 = __ldg(D + i0 + 1); db0 = __ldg(D + i1); db1 = __ldg(D + i1 + 1);
+    ia0 = __ldg(I + i0); ia1 = __ldg(I + i0 + 1); ib0 = __ldg(I + i1); ib1 = __ldg(I + i1 + 1);
+  }
   float s = 0.f;
   int n = 0;
-  if (da.x > 0.f) { s += da.x; ++n; }
-  if (da.y > 0.f) { s += da.y; ++n; }
-  if (db.x > 0.f) { s += db.x; ++n; }
-  if (db.y > 0.f) { s += db.y; ++n; }
+  if (da0 > 0.f) { s += da0; ++n; }
+  if (da1 > 0.f) { s += da1; ++n; }
+  if (db0 > 0.f) { s += db0; ++n; }
+  if (db1 > 0.f) { s += db1; ++n; }
   const int64_t o = (int64_t)y * wc + x;
   coarse.depth[cs][o] = n ? s / (float)n : 0.f;
-  coarse.inten[cs][o] = ((ia.x + ia.y) + (ib.x + ib.y)) * 0.25f;
+  coarse.inten[cs][o] = ((ia0 + ia1) + (ib0 + ib1)) * 0.25f;
 }
 
 template <typename T>
-__global__ void k_normals(LevelMaps m, const Ctrl* __restrict__ ctrl, LevelGeom g, float dmin,
-                          float dmax, int which) {
-  const int set = which < 0 ? 1 - ctrl->ref_index : which;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= g.w || y >= g.h) return;
+__device__ __forceinline__ void normal_px(const LevelMaps& m, int set, const LevelGeom& g,
+                                          float dmin, float dmax, int x, int y) {
   const float* D = m.depth[set];
   T* N = reinterpret_cast<T*>(m.normal[set]);
   const int64_t o = (int64_t)y * g.w + x;
@@ -95,20 +107,22 @@ __global__ void k_normals(LevelMaps m, const Ctrl* __restrict__ ctrl, LevelGeom 
       const float ry = ((float)y - g.cy) * g.ify;
       const float rx1 = ((float)(x + 1) - g.cx) * g.ifx;
       const float ry2 = ((float)(y + 1) - g.cy) * g.ify;
-      // forward differences of v = d * ray, written so no large terms cancel
+      // forward differences of v = d * ray, written so no large terms cancel; every
+      // product and sum is spelled out (fmaf / __fmul_rn) so that no kernel this is
+      // inlined into contracts it differently: all map kernels give identical bits
       const float e1 = d1 - d0, e2 = d2 - d0;
-      const float ax = fmaf(e1, rx1, d0 * g.ifx), ay = e1 * ry, az = e1;
-      const float bx = e2 * rx, by = fmaf(e2, ry2, d0 * g.ify), bz = e2;
-      float cx = ay * bz - az * by;
-      float cy = az * bx - ax * bz;
-      float cz = ax * by - ay * bx;
-      const float n2 = cx * cx + cy * cy + cz * cz;
+      const float ax = fmaf(e1, rx1, __fmul_rn(d0, g.ifx)), ay = __fmul_rn(e1, ry), az = e1;
+      const float bx = __fmul_rn(e2, rx), by = fmaf(e2, ry2, __fmul_rn(d0, g.ify)), bz = e2;
+      float cx = fmaf(ay, bz, -__fmul_rn(az, by));
+      float cy = fmaf(az, bx, -__fmul_rn(ax, bz));
+      float cz = fmaf(ax, by, -__fmul_rn(ay, bx));
+      const float n2 = fmaf(cx, cx, fmaf(cy, cy, __fmul_rn(cz, cz)));
       if (n2 > 0.f) {
         const float inv = rsqrtf(n2);
-        cx *= inv;
-        cy *= inv;
-        cz *= inv;
-        if (cx * rx + cy * ry + cz > 0.f) {   // sign of n . v (v = d0 * ray, d0 > 0)
+        cx = __fmul_rn(cx, inv);
+        cy = __fmul_rn(cy, inv);
+        cz = __fmul_rn(cz, inv);
+        if (fmaf(cx, rx, fmaf(cy, ry, cz)) > 0.f) {   // sign of n . v (v = d0 * ray, d0 > 0)
           cx = -cx;
           cy = -cy;
           cz = -cz;
@@ -125,12 +139,7 @@ __global__ void k_normals(LevelMaps m, const Ctrl* __restrict__ ctrl, LevelGeom 
 }
 
 template <typename T>
-__global__ void k_gradient(LevelMaps m, const Ctrl* __restrict__ ctrl, int w, int h) {
-  // the set that is (or just became) the reference
-  const int set = ctrl->ref_index;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  if (x >= w || y >= h) return;
+__device__ __forceinline__ void gradient_px(const LevelMaps& m, int set, int w, int h, int x, int y) {
   const float* I = m.inten[set];
   T* G = reinterpret_cast<T*>(m.grad[set]);
   const int64_t o = (int64_t)y * w + x;
@@ -143,23 +152,85 @@ __global__ void k_gradient(LevelMaps m, const Ctrl* __restrict__ ctrl, int w, in
   store_map<T>(G, o + m.plane, gy);
 }
 
+// Block -> (slot, 32 x 8 tile of the slot's level-`a.level` image); false for an
+// idle slot or a thread outside the image.
+__device__ __forceinline__ bool map_pixel(const BatchArgs& a, int* slot, int* x, int* y) {
+  *slot = batch_slot(a, blockIdx.x);
+  if (batch_dyn(a, *slot).mode == kSlotIdle) return false;
+  const LevelGeom& g = a.slots[*slot].tp[a.level].g;
+  const int t = blockIdx.x - __ldg(a.start + *slot);
+  const int gx = (g.w + kMapTileW - 1) / kMapTileW;
+  *x = (t % gx) * kMapTileW + threadIdx.x;
+  *y = (t / gx) * kMapTileH + threadIdx.y;
+  return *x < g.w && *y < g.h;
+}
+
+__global__ void __launch_bounds__(256) k_pyr_down_batch(const BatchArgs a) {
+  int slot, x, y;
+  if (!map_pixel(a, &slot, &x, &y)) return;
+  const SlotStatic& st = a.slots[slot];
+  const int cs = 1 - st.tp[0].ctrl->ref_index;
+  pyr_down_px(st.tp[a.level - 1].m, st.tp[a.level].m, cs, st.tp[a.level - 1].g.w,
+              st.tp[a.level].g.w, x, y);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_normals_batch(const BatchArgs a) {
+  int slot, x, y;
+  if (!map_pixel(a, &slot, &x, &y)) return;
+  const TrackParams& tp = a.slots[slot].tp[a.level];
+  normal_px<T>(tp.m, 1 - tp.ctrl->ref_index, tp.g, tp.depth_min, tp.depth_max, x, y);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gradient_batch(const BatchArgs a) {
+  int slot, x, y;
+  if (!map_pixel(a, &slot, &x, &y)) return;
+  const TrackParams& tp = a.slots[slot].tp[a.level];
+  // the set that is (or just became) the reference
+  gradient_px<T>(tp.m, tp.ctrl->ref_index, tp.g.w, tp.g.h, x, y);
+}
+
+template <typename T>
+__global__ void k_normals(LevelMaps m, const Ctrl* __restrict__ ctrl, LevelGeom g, float dmin,
+                          float dmax, int which) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= g.w || y >= g.h) return;
+  normal_px<T>(m, which < 0 ? 1 - ctrl->ref_index : which, g, dmin, dmax, x, y);
+}
+
+template <typename T>
+__global__ void k_gradient(LevelMaps m, const Ctrl* __restrict__ ctrl, int w, int h) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= w || y >= h) return;
+  gradient_px<T>(m, ctrl->ref_index, w, h, x, y);
+}
+
 inline dim3 grid2(int w, int h, dim3 b) { return dim3((w + b.x - 1) / b.x, (h + b.y - 1) / b.y); }
 
 }  // namespace
 
-cudaError_t launch_copy_input(const float* in_d, const float* in_i, const LevelMaps& m0,
-                              const Ctrl* ctrl, int w, int h, cudaStream_t s) {
-  const int64_t n4 = ((int64_t)w * h + 3) / 4;
-  int blocks = (int)((n4 + 255) / 256);
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  k_copy_input<<<blocks, 256, 0, s>>>(in_d, in_i, m0, ctrl, w, h);
+cudaError_t launch_copy_batch(const BatchArgs& a, int blocks, cudaStream_t s) {
+  k_copy_batch<<<blocks, dim3(kCopyTileW / 4, kCopyTileH), 0, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pyr_down(const LevelMaps& fine, const LevelMaps& coarse, const Ctrl* ctrl,
-                            int wf, int hf, int wc, int hc, cudaStream_t s) {
-  const dim3 b(32, 8);
-  k_pyr_down<<<grid2(wc, hc, b), b, 0, s>>>(fine, coarse, ctrl, wf, hf, wc, hc);
+cudaError_t launch_pyr_down_batch(const BatchArgs& a, int blocks, cudaStream_t s) {
+  k_pyr_down_batch<<<blocks, dim3(kMapTileW, kMapTileH), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normals_batch(const BatchArgs& a, int blocks, bool fp16, cudaStream_t s) {
+  if (fp16) k_normals_batch<__half><<<blocks, dim3(kMapTileW, kMapTileH), 0, s>>>(a);
+  else k_normals_batch<float><<<blocks, dim3(kMapTileW, kMapTileH), 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gradient_batch(const BatchArgs& a, int blocks, bool fp16, cudaStream_t s) {
+  if (fp16) k_gradient_batch<__half><<<blocks, dim3(kMapTileW, kMapTileH), 0, s>>>(a);
+  else k_gradient_batch<float><<<blocks, dim3(kMapTileW, kMapTileH), 0, s>>>(a);
   return cudaGetLastError();
 }
 

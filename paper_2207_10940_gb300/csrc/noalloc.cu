@@ -44,9 +44,9 @@ constexpr size_t kOffCtrl = 0;
 constexpr size_t kOffNormal0 = na_align(kOffCtrl + sizeof(Ctrl));
 constexpr size_t kOffNormal1 = na_align(kOffNormal0 + 3 * kPlane * sizeof(float));
 constexpr size_t kOffGrad = na_align(kOffNormal1 + 3 * kPlane * sizeof(float));
-// one pixel per thread: at most ceil(320/32) * ceil(240/8) blocks
+// one row per thread: at most ceil(320/32) * ceil(240/4) blocks
 constexpr int kNoallocMaxBlocks = ((kNoallocMaxW + kTrackThreadsX - 1) / kTrackThreadsX) *
-                                  ((kNoallocMaxH + kTrackThreadsY - 1) / kTrackThreadsY);
+                                  ((kNoallocMaxH + kTrackRows - 1) / kTrackRows);
 constexpr int kNoallocMaxGroups = (kNoallocMaxBlocks + kFoldGroup - 1) / kFoldGroup;
 constexpr size_t kOffCounters = na_align(kOffGrad + 2 * kPlane * sizeof(float));
 constexpr size_t kOffPartials = na_align(kOffCounters + (1 + kNoallocMaxGroups) * sizeof(uint32_t));

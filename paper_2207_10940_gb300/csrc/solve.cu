@@ -33,7 +33,8 @@
 // is used in the assembly; the 34x34 system is Jacobi scaled and solved by an
 // LDL^T factorisation whose trailing updates run over all threads.
 //
-// All arithmetic here is FP64.  One block of kSolveThreads threads runs each kernel.
+// All arithmetic here is FP64.  One block of kSolveThreads threads runs each
+// stream's kernel; a batched launch has one block per slot.
 #include <cmath>
 
 #include "dri_internal.h"
@@ -840,11 +841,9 @@ __device__ void assemble(const SolveParams& sp, GnSmem& S) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSolveThreads) k_gn_step(SolveParams sp) {
+__device__ void gn_step_body(const SolveParams& sp, GnSmem& S) {
   Ctrl* c = sp.ctrl;
   if (c->status != 0) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  GnSmem& S = *reinterpret_cast<GnSmem*>(smem_raw);
   const int tid = threadIdx.x, nt = blockDim.x;
   assemble(sp, S);
   if (!S.ok) {
@@ -1016,10 +1015,8 @@ __device__ bool imu_weight_and_prediction(const SolveParams& sp, Ctrl* c, BeginS
   return pd;
 }
 
-__global__ void __launch_bounds__(kSolveThreads) k_frame_begin(SolveParams sp) {
+__device__ void frame_begin_body(const SolveParams& sp, BeginSmem& B) {
   Ctrl* c = sp.ctrl;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  BeginSmem& B = *reinterpret_cast<BeginSmem*>(smem_raw);
   const int tid = threadIdx.x;
   if (tid == 0) {
     c->status = 0;
@@ -1033,7 +1030,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_frame_begin(SolveParams sp) {
   if (imu_weight_and_prediction(sp, c, B, &c->x1) && tid == 0) write_transforms(c);
 }
 
-__global__ void __launch_bounds__(kSolveThreads) k_frame_end(SolveParams sp) {
+__device__ void frame_end_body(const SolveParams& sp) {
   Ctrl* c = sp.ctrl;
   const int tid = threadIdx.x;
   __shared__ int s_ok, s_fail;
@@ -1103,12 +1100,12 @@ __global__ void __launch_bounds__(kSolveThreads) k_frame_end(SolveParams sp) {
   }
 }
 
-__global__ void k_frame_init(SolveParams sp) {
+__device__ void frame_init_body(const SolveParams& sp) {
   const double t_frame = sp.imu->t1;
   Ctrl* c = sp.ctrl;
   const int tid = threadIdx.x;
-  if (tid < 17 * 17) {
-    const int i = tid / 17, j = tid % 17;
+  for (int idx = tid; idx < 17 * 17; idx += blockDim.x) {
+    const int i = idx / 17, j = idx % 17;
     double v = 0.0;
     if (i == j) {
       const double s = i < 6 ? sp.prior_sigma[0]
@@ -1117,7 +1114,7 @@ __global__ void k_frame_init(SolveParams sp) {
                      : i < 15 ? sp.prior_sigma[3] : sp.prior_sigma[4];
       v = 1.0 / (s * s);
     }
-    c->Hs[tid] = v;
+    c->Hs[idx] = v;
   }
   if (tid < 17) c->bs[tid] = 0.0;
   if (tid == 0) {
@@ -1178,16 +1175,65 @@ __global__ void __launch_bounds__(kSolveThreads) k_linearise_end(SolveParams sp,
   }
 }
 
+// Slot blockIdx.x of a batched launch: its SolveParams with this launch's IMU
+// block, level and last-iteration flag, copied to shared memory; returns the
+// slot's mode (uniform over the block).
+__device__ int load_slot_params(const BatchArgs& a, SolveParams& sp) {
+  const int slot = blockIdx.x;
+  const SlotDyn& d = batch_dyn(a, slot);
+  const int mode = d.mode;
+  if (mode == kSlotIdle) return mode;
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&a.slots[slot].sp);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&sp);
+  for (int i = threadIdx.x; i < (int)(sizeof(SolveParams) / 4); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sp.imu = reinterpret_cast<const ImuHeader*>(a.dyn + d.imu_off);
+    sp.level = a.level;
+    sp.last = a.last;
+  }
+  __syncthreads();
+  return mode;
+}
+
+// One block per slot: a tracked slot starts its frame (x0 := x, IMU weight and
+// prediction), an initialising slot takes the first-frame prior.
+__global__ void __launch_bounds__(kSolveThreads) k_frame_begin_batch(const BatchArgs a) {
+  __shared__ SolveParams sp;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int mode = load_slot_params(a, sp);
+  if (mode == kSlotInit) frame_init_body(sp);
+  else if (mode == kSlotTrack) frame_begin_body(sp, *reinterpret_cast<BeginSmem*>(smem_raw));
+}
+
+__global__ void __launch_bounds__(kSolveThreads) k_gn_step_batch(const BatchArgs a) {
+  __shared__ SolveParams sp;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (load_slot_params(a, sp) == kSlotTrack) gn_step_body(sp, *reinterpret_cast<GnSmem*>(smem_raw));
+}
+
+__global__ void __launch_bounds__(kSolveThreads) k_frame_end_batch(const BatchArgs a) {
+  __shared__ SolveParams sp;
+  if (load_slot_params(a, sp) == kSlotTrack) frame_end_body(sp);
+}
+
+// Result heads of all slots into one contiguous buffer (one copy to the host).
+__global__ void k_gather_heads(const BatchArgs a, unsigned char* __restrict__ out) {
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(a.slots[blockIdx.x].sp.ctrl);
+  uint64_t* dst = reinterpret_cast<uint64_t*>(out + (size_t)blockIdx.x * kCtrlHeadBytes);
+  for (int i = threadIdx.x; i < (int)(kCtrlHeadBytes / 8); i += blockDim.x) dst[i] = src[i];
+}
+
 }  // namespace
 
 cudaError_t prepare_solver_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_gn_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_gn_step_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(GnSmem));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_linearise_end, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(GnSmem));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_frame_begin, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_frame_begin_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(BeginSmem));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_linearise_begin, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1197,20 +1243,20 @@ cudaError_t prepare_solver_kernels() {
 
 int solver_max_imu_pieces() { return kMaxPieces; }
 
-cudaError_t launch_frame_begin(const SolveParams& p, cudaStream_t s) {
-  k_frame_begin<<<1, kSolveThreads, sizeof(BeginSmem), s>>>(p);
+cudaError_t launch_frame_begin_batch(const BatchArgs& a, cudaStream_t s) {
+  k_frame_begin_batch<<<a.nslots, kSolveThreads, sizeof(BeginSmem), s>>>(a);
   return cudaGetLastError();
 }
-cudaError_t launch_gn_step(const SolveParams& p, cudaStream_t s) {
-  k_gn_step<<<1, kSolveThreads, sizeof(GnSmem), s>>>(p);
+cudaError_t launch_gn_step_batch(const BatchArgs& a, cudaStream_t s) {
+  k_gn_step_batch<<<a.nslots, kSolveThreads, sizeof(GnSmem), s>>>(a);
   return cudaGetLastError();
 }
-cudaError_t launch_frame_end(const SolveParams& p, cudaStream_t s) {
-  k_frame_end<<<1, kSolveThreads, 0, s>>>(p);
+cudaError_t launch_frame_end_batch(const BatchArgs& a, cudaStream_t s) {
+  k_frame_end_batch<<<a.nslots, kSolveThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
-cudaError_t launch_frame_init(const SolveParams& p, cudaStream_t s) {
-  k_frame_init<<<1, 320, 0, s>>>(p);
+cudaError_t launch_gather_heads(const BatchArgs& a, unsigned char* out, cudaStream_t s) {
+  k_gather_heads<<<a.nslots, 64, 0, s>>>(a, out);
   return cudaGetLastError();
 }
 cudaError_t launch_linearise_begin(const SolveParams& p, const DState& x0, const DState& x1,

@@ -2,8 +2,13 @@
 // point-to-plane ICP (Eq. 4) terms at one pyramid level, block-reduced into the
 // normal equations of Eq. 7 (Sec. IV-B, IV-D).
 //
-// One thread handles `ppt` pixels of one column of a 32-wide tile (a warp reads
-// 128 contiguous bytes per map plane).  Per pixel, in FP32:
+// Block: 8 warps over a tile of 32 columns x 4 * ppt rows.  Warps 0-3 evaluate
+// the ICP term and warps 4-7 the photometric term of the same pixels (warp w and
+// w + 4 take rows w, w + 4, w + 8, ... of the tile), so each thread carries the
+// 29 sums of one term only: half the registers of a thread that does both, twice
+// the warps resident per SM to hide the latency of the dependent gathers.  A warp
+// reads 128 contiguous bytes per map plane; each thread loads its next row's
+// live-frame samples before it works on the current one.  Per pixel, in FP32:
 //
 //   p   = d K^-1 [u, v, 1]^T                       live point, camera frame C1
 //   ICP: D = A_ref p + t_ref  with A_ref = R_ref^T R_1 - I, t_ref = R_ref^T (r_1 - r_ref),
@@ -21,11 +26,12 @@
 //
 // The local Jacobians are the world-frame ones of Eq. 3-4 rotated by
 // diag(R^T, R^T) (R = R_ref or R_0); the solver rotates the reduced 6x6 systems
-// back in FP64.  Each term accumulates 29 values per thread (upper J J^T, J e,
-// e^2, count) in FP32, reduced by warp shuffles and a shared-memory tree to one
-// FP64 (or FP32) partial per block; the partials are folded in two fixed-order
-// levels (groups of blocks, then the groups) into ctrl->sums: deterministic, no
-// float atomics.
+// back in FP64.  Each thread accumulates its term's 29 values (upper J J^T, J e,
+// e^2, count) in FP32; a warp transposes and sums them with 31 shuffles, the
+// block adds its four warps per term in fixed order into one FP64 (or FP32)
+// partial of 58 values; the partials are folded in two fixed-order levels
+// (groups of blocks, then the groups) into ctrl->sums: deterministic, no float
+// atomics.
 #include <cuda_fp16.h>
 
 #include "dri_internal.h"
@@ -58,11 +64,111 @@ __device__ __forceinline__ void accumulate(float* a, const float* J, float e) {
   a[28] += 1.f;
 }
 
+// Live-frame samples of one pixel: depth and the term's own map (the normal for
+// ICP, the intensity for the photometric term).
+struct Live {
+  float d, a, b, c;
+};
+
+// ICP term (Eq. 4) of the pixel (u, v) with live depth d and normal n1.
+template <typename T>
+__device__ __forceinline__ bool icp_pixel(const TrackParams& p, const LevelGeom& g, const float* A,
+                                          const float* t, const float* __restrict__ D0,
+                                          const T* __restrict__ N0, int u, int v, const Live& L,
+                                          float* acc) {
+  const float n1x = L.a, n1y = L.b, n1z = L.c;
+  if (n1x == 0.f && n1y == 0.f && n1z == 0.f) return false;
+  const float d = L.d;
+  const float rx = ((float)u - g.cx) * g.ifx;
+  const float ry = ((float)v - g.cy) * g.ify;
+  const float px = d * rx, py = d * ry, pz = d;
+  const float ex = fmaf(A[0], px, fmaf(A[1], py, fmaf(A[2], pz, t[0])));
+  const float ey = fmaf(A[3], px, fmaf(A[4], py, fmaf(A[5], pz, t[1])));
+  const float ez = fmaf(A[6], px, fmaf(A[7], py, fmaf(A[8], pz, t[2])));
+  const float z = d + ez;
+  if (!(z > 0.f)) return false;
+  const float iz = 1.f / z;
+  const float sxp = g.fx * (fmaf(-rx, ez, ex) * iz);
+  const float syp = g.fy * (fmaf(-ry, ez, ey) * iz);
+  const bool sane = fabsf(sxp) < 1e7f && fabsf(syp) < 1e7f;   // int conversion in range
+  const int xi = sane ? u + (int)floorf(sxp + 0.5f) : -1;
+  const int yi = sane ? v + (int)floorf(syp + 0.5f) : -1;
+  if (xi < 0 || xi >= g.w || yi < 0 || yi >= g.h) return false;
+  const int64_t q = (int64_t)yi * g.w + xi;
+  const int64_t plane = p.m.plane;
+  const float Nx = load_map(N0, q), Ny = load_map(N0, plane + q), Nz = load_map(N0, 2 * plane + q);
+  if (Nx == 0.f && Ny == 0.f && Nz == 0.f) return false;
+  const float dr = __ldg(D0 + q);
+  const float Vx = dr * (((float)xi - g.cx) * g.ifx), Vy = dr * (((float)yi - g.cy) * g.ify);
+  const float dx = (px - Vx) + ex, dy = (py - Vy) + ey, dz = (pz - dr) + ez;
+  const float dist2 = dx * dx + dy * dy + dz * dz;
+  const float mx = n1x + (A[0] * n1x + A[1] * n1y + A[2] * n1z);
+  const float my = n1y + (A[3] * n1x + A[4] * n1y + A[5] * n1z);
+  const float mz = n1z + (A[6] * n1x + A[7] * n1y + A[8] * n1z);
+  const float cosang = mx * Nx + my * Ny + mz * Nz;
+  if (!(dist2 < p.icp_dist2 && cosang > p.icp_cos)) return false;
+  const float e = Nx * dx + Ny * dy + Nz * dz;
+  const float sx = px + (ex - t[0]), sy = py + (ey - t[1]), sz = pz + (ez - t[2]);
+  const float J[6] = {Nx, Ny, Nz, sy * Nz - sz * Ny, sz * Nx - sx * Nz, sx * Ny - sy * Nx};
+  accumulate(acc, J, e);
+  return true;
+}
+
+// Photometric term (Eq. 3) of the pixel (u, v) with live depth d and intensity i1.
+template <typename T>
+__device__ __forceinline__ bool rgb_pixel(const TrackParams& p, const LevelGeom& g, const float* A,
+                                          const float* t, const float* __restrict__ I0,
+                                          const T* __restrict__ G0, int u, int v, const Live& L,
+                                          float* acc) {
+  const float d = L.d;
+  const float rx = ((float)u - g.cx) * g.ifx;
+  const float ry = ((float)v - g.cy) * g.ify;
+  const float px = d * rx, py = d * ry, pz = d;
+  const float ex = fmaf(A[0], px, fmaf(A[1], py, fmaf(A[2], pz, t[0])));
+  const float ey = fmaf(A[3], px, fmaf(A[4], py, fmaf(A[5], pz, t[1])));
+  const float ez = fmaf(A[6], px, fmaf(A[7], py, fmaf(A[8], pz, t[2])));
+  const float z = d + ez;
+  if (!(z > 0.f)) return false;
+  const float iz = 1.f / z;
+  // displacement of the projection from (u, v): small, so FP32 keeps it to
+  // ~1e-6 px, and integer parts of the position stay exact
+  const float sxp = g.fx * (fmaf(-rx, ez, ex) * iz);
+  const float syp = g.fy * (fmaf(-ry, ez, ey) * iz);
+  const float fxp = floorf(sxp), fyp = floorf(syp);
+  const bool sane = fabsf(sxp) < 1e7f && fabsf(syp) < 1e7f;   // int conversion in range
+  const int xb = sane ? u + (int)fxp : -1, yb = sane ? v + (int)fyp : -1;
+  if (xb < 0 || xb >= g.w - 1 || yb < 0 || yb >= g.h - 1) return false;
+  const float ax = sxp - fxp, ay = syp - fyp;
+  const int64_t q = (int64_t)yb * g.w + xb;
+  const int64_t plane = p.m.plane;
+  const float w00 = (1.f - ax) * (1.f - ay), w01 = ax * (1.f - ay);
+  const float w10 = (1.f - ax) * ay, w11 = ax * ay;
+  const float iv = w00 * __ldg(I0 + q) + w01 * __ldg(I0 + q + 1) + w10 * __ldg(I0 + q + g.w) +
+                   w11 * __ldg(I0 + q + g.w + 1);
+  const float gx = w00 * load_map(G0, q) + w01 * load_map(G0, q + 1) + w10 * load_map(G0, q + g.w) +
+                   w11 * load_map(G0, q + g.w + 1);
+  const float gy = w00 * load_map(G0, plane + q) + w01 * load_map(G0, plane + q + 1) +
+                   w10 * load_map(G0, plane + q + g.w) + w11 * load_map(G0, plane + q + g.w + 1);
+  const float e = iv - L.a;
+  const float a0 = g.fx * gx * iz, a1 = g.fy * gy * iz;
+  const float a2 = -(gx * (((float)u - g.cx) + sxp) + gy * (((float)v - g.cy) + syp)) * iz;
+  const float sx = px + (ex - t[0]), sy = py + (ey - t[1]), sz = pz + (ez - t[2]);
+  const float J[6] = {a0, a1, a2, sy * a2 - sz * a1, sz * a0 - sx * a2, sx * a1 - sy * a0};
+  accumulate(acc, J, e);
+  return true;
+}
+
+// One tile (32 columns x 4 * ppt rows) of one image: (bx, by) its tile
+// coordinates, bid its index in the image's fold order.
 template <typename T, typename P, bool FLAGS>
-__global__ void __launch_bounds__(kTrackThreadsX * kTrackThreadsY)
-k_track(TrackParams p) {
+__device__ __forceinline__ void track_tile(const TrackParams& p, const int bx, const int by,
+                                           const int bid) {
   Ctrl* __restrict__ ctrl = p.ctrl;
   if (ctrl->status != 0) return;
+  const int lane = threadIdx.x;
+  const int warp = threadIdx.y;
+  const bool icp = warp < kTrackRows;          // warp-uniform
+  const int wrow = warp & (kTrackRows - 1);
   const int rs = ctrl->ref_index;
   const int cs = 1 - rs;
   const LevelGeom g = p.g;
@@ -75,150 +181,92 @@ k_track(TrackParams p) {
   const T* __restrict__ N0 = reinterpret_cast<const T*>(p.m.normal[rs]);
   const T* __restrict__ G0 = reinterpret_cast<const T*>(p.m.grad[rs]);
 
-  float Ai[9], ti[3], Ar[9], tr[3];
+  float A[9], t[3];
+  const float* xf = icp ? ctrl->xf_icp : ctrl->xf_rgb;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    Ai[k] = ctrl->xf_icp[k];
-    Ar[k] = ctrl->xf_rgb[k];
-  }
+  for (int k = 0; k < 9; ++k) A[k] = xf[k];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    ti[k] = ctrl->xf_icp[9 + k];
-    tr[k] = ctrl->xf_rgb[9 + k];
-  }
+  for (int k = 0; k < 3; ++k) t[k] = xf[9 + k];
 
-  float acc[kSumsAll];
+  float acc[kSums];
 #pragma unroll
-  for (int k = 0; k < kSumsAll; ++k) acc[k] = 0.f;
+  for (int k = 0; k < kSums; ++k) acc[k] = 0.f;
 
-  const int u = blockIdx.x * kTrackThreadsX + threadIdx.x;
-  for (int r = 0; r < p.ppt; ++r) {
-    const int v = (blockIdx.y * p.ppt + r) * kTrackThreadsY + threadIdx.y;
-    if (u >= g.w || v >= g.h) continue;
-    const int64_t o = (int64_t)v * g.w + u;
-    const float d = __ldg(D1 + o);
-    uint8_t flag = 0;
-    if (d >= p.depth_min && d <= p.depth_max) {
-      const float rx = ((float)u - g.cx) * g.ifx;
-      const float ry = ((float)v - g.cy) * g.ify;
-      const float px = d * rx, py = d * ry, pz = d;
-
-      // ---------------- photometric term (Eq. 3) ----------------
-      {
-        const float ex = fmaf(Ar[0], px, fmaf(Ar[1], py, fmaf(Ar[2], pz, tr[0])));
-        const float ey = fmaf(Ar[3], px, fmaf(Ar[4], py, fmaf(Ar[5], pz, tr[1])));
-        const float ez = fmaf(Ar[6], px, fmaf(Ar[7], py, fmaf(Ar[8], pz, tr[2])));
-        const float z = d + ez;
-        if (z > 0.f) {
-          const float iz = 1.f / z;
-          // displacement of the projection from (u, v): small, so FP32 keeps it to
-          // ~1e-6 px, and integer parts of the position stay exact
-          const float sxp = g.fx * (fmaf(-rx, ez, ex) * iz);
-          const float syp = g.fy * (fmaf(-ry, ez, ey) * iz);
-          const float fxp = floorf(sxp), fyp = floorf(syp);
-          const bool sane = fabsf(sxp) < 1e7f && fabsf(syp) < 1e7f;   // int conversion in range
-          const int xb = sane ? u + (int)fxp : -1, yb = sane ? v + (int)fyp : -1;
-          if (xb >= 0 && xb < g.w - 1 && yb >= 0 && yb < g.h - 1) {
-            const float ax = sxp - fxp, ay = syp - fyp;
-            const int64_t q = (int64_t)yb * g.w + xb;
-            const float w00 = (1.f - ax) * (1.f - ay), w01 = ax * (1.f - ay);
-            const float w10 = (1.f - ax) * ay, w11 = ax * ay;
-            const float iv = w00 * __ldg(I0 + q) + w01 * __ldg(I0 + q + 1) +
-                             w10 * __ldg(I0 + q + g.w) + w11 * __ldg(I0 + q + g.w + 1);
-            const float gx = w00 * load_map(G0, q) + w01 * load_map(G0, q + 1) +
-                             w10 * load_map(G0, q + g.w) + w11 * load_map(G0, q + g.w + 1);
-            const float gy = w00 * load_map(G0, plane + q) + w01 * load_map(G0, plane + q + 1) +
-                             w10 * load_map(G0, plane + q + g.w) +
-                             w11 * load_map(G0, plane + q + g.w + 1);
-            const float e = iv - __ldg(I1 + o);
-            const float a0 = g.fx * gx * iz, a1 = g.fy * gy * iz;
-            const float a2 = -(gx * (((float)u - g.cx) + sxp) + gy * (((float)v - g.cy) + syp)) * iz;
-            const float sx = px + (ex - tr[0]), sy = py + (ey - tr[1]), sz = pz + (ez - tr[2]);
-            float J[6] = {a0, a1, a2, sy * a2 - sz * a1, sz * a0 - sx * a2, sx * a1 - sy * a0};
-            accumulate(acc + kSums, J, e);
-            flag |= 2;
-          }
-        }
-      }
-
-      // ---------------- ICP term (Eq. 4) ----------------
-      const float n1x = load_map(N1, o), n1y = load_map(N1, plane + o), n1z = load_map(N1, 2 * plane + o);
-      if (n1x != 0.f || n1y != 0.f || n1z != 0.f) {
-        const float ex = fmaf(Ai[0], px, fmaf(Ai[1], py, fmaf(Ai[2], pz, ti[0])));
-        const float ey = fmaf(Ai[3], px, fmaf(Ai[4], py, fmaf(Ai[5], pz, ti[1])));
-        const float ez = fmaf(Ai[6], px, fmaf(Ai[7], py, fmaf(Ai[8], pz, ti[2])));
-        const float z = d + ez;
-        if (z > 0.f) {
-          const float iz = 1.f / z;
-          const float sxp = g.fx * (fmaf(-rx, ez, ex) * iz);
-          const float syp = g.fy * (fmaf(-ry, ez, ey) * iz);
-          const bool sane = fabsf(sxp) < 1e7f && fabsf(syp) < 1e7f;
-          const int xi = sane ? u + (int)floorf(sxp + 0.5f) : -1;
-          const int yi = sane ? v + (int)floorf(syp + 0.5f) : -1;
-          if (xi >= 0 && xi < g.w && yi >= 0 && yi < g.h) {
-            const int64_t q = (int64_t)yi * g.w + xi;
-            const float Nx = load_map(N0, q), Ny = load_map(N0, plane + q), Nz = load_map(N0, 2 * plane + q);
-            if (Nx != 0.f || Ny != 0.f || Nz != 0.f) {
-              const float dr = __ldg(D0 + q);
-              const float Vx = dr * (((float)xi - g.cx) * g.ifx), Vy = dr * (((float)yi - g.cy) * g.ify);
-              const float dx = (px - Vx) + ex, dy = (py - Vy) + ey, dz = (pz - dr) + ez;
-              const float dist2 = dx * dx + dy * dy + dz * dz;
-              const float mx = n1x + (Ai[0] * n1x + Ai[1] * n1y + Ai[2] * n1z);
-              const float my = n1y + (Ai[3] * n1x + Ai[4] * n1y + Ai[5] * n1z);
-              const float mz = n1z + (Ai[6] * n1x + Ai[7] * n1y + Ai[8] * n1z);
-              const float cosang = mx * Nx + my * Ny + mz * Nz;
-              if (dist2 < p.icp_dist2 && cosang > p.icp_cos) {
-                const float e = Nx * dx + Ny * dy + Nz * dz;
-                const float sx = px + (ex - ti[0]), sy = py + (ey - ti[1]), sz = pz + (ez - ti[2]);
-                float J[6] = {Nx, Ny, Nz, sy * Nz - sz * Ny, sz * Nx - sx * Nz, sx * Ny - sy * Nx};
-                accumulate(acc, J, e);
-                flag |= 1;
-              }
-            }
-          }
-        }
+  const int u = bx * kTrackThreadsX + lane;
+  const bool col_ok = u < g.w;
+  const float dmin = p.depth_min, dmax = p.depth_max;
+  // live samples of the thread's row r (zero depth outside the image)
+  auto load_live = [&](int r) {
+    Live L = {0.f, 0.f, 0.f, 0.f};
+    const int v = (by * p.ppt + r) * kTrackRows + wrow;
+    if (col_ok && v < g.h) {
+      const int64_t o = (int64_t)v * g.w + u;
+      L.d = __ldg(D1 + o);
+      if (icp) {
+        L.a = load_map(N1, o);
+        L.b = load_map(N1, plane + o);
+        L.c = load_map(N1, 2 * plane + o);
+      } else {
+        L.a = __ldg(I1 + o);
       }
     }
-    if (FLAGS) p.flags[o] = flag;
+    return L;
+  };
+  __shared__ uint8_t s_flag[kTrackRows][kTrackThreadsX];
+  Live cur = load_live(0);
+  for (int r = 0; r < p.ppt; ++r) {
+    const Live nxt = r + 1 < p.ppt ? load_live(r + 1) : Live{0.f, 0.f, 0.f, 0.f};
+    const int v = (by * p.ppt + r) * kTrackRows + wrow;
+    bool ok = false;
+    if (col_ok && v < g.h && cur.d >= dmin && cur.d <= dmax) {
+      ok = icp ? icp_pixel<T>(p, g, A, t, D0, N0, u, v, cur, acc)
+               : rgb_pixel<T>(p, g, A, t, I0, G0, u, v, cur, acc);
+    }
+    if (FLAGS) {             // bit 0 ICP, bit 1 photometric, combined through shared memory
+      if (icp) s_flag[wrow][lane] = ok ? 1 : 0;
+      __syncthreads();
+      if (!icp && col_ok && v < g.h)
+        p.flags[(int64_t)v * g.w + u] = (uint8_t)(s_flag[wrow][lane] | (ok ? 2 : 0));
+      __syncthreads();
+    }
+    cur = nxt;
   }
 
   // ---------------- reduction ----------------
-  // Warp: transpose-reduce.  Padded to 64 values, five halving exchanges leave
-  // lane l holding the warp sums of values 2l and 2l + 1 (62 shuffles instead of
-  // 5 per value).
-  float v[64];
+  // Warp: transpose-reduce.  Padded to 32 values, five halving exchanges leave
+  // lane l holding the warp sum of value l (31 shuffles instead of 5 per value).
+  float w[32];
 #pragma unroll
-  for (int k = 0; k < 64; ++k) v[k] = k < kSumsAll ? acc[k] : 0.f;
-  const int lane = threadIdx.x;
+  for (int k = 0; k < 32; ++k) w[k] = k < kSums ? acc[k] : 0.f;
 #pragma unroll
-  for (int half = 32, off = 16; off > 0; half >>= 1, off >>= 1) {
+  for (int half = 16, off = 16; off > 0; half >>= 1, off >>= 1) {
     const bool hi = (lane & off) != 0;
 #pragma unroll
     for (int i = 0; i < half; ++i) {
-      const float send = hi ? v[i] : v[i + half];
-      const float keep = hi ? v[i + half] : v[i];
-      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      const float send = hi ? w[i] : w[i + half];
+      const float keep = hi ? w[i + half] : w[i];
+      w[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
     }
   }
-  __shared__ float s_warp[kTrackThreadsY][64];
+  __shared__ float s_warp[kTrackThreadsY][32];
   __shared__ bool s_last;
-  const int tid = threadIdx.y * kTrackThreadsX + threadIdx.x;
-  s_warp[threadIdx.y][2 * lane] = v[0];
-  s_warp[threadIdx.y][2 * lane + 1] = v[1];
+  const int tid = warp * kTrackThreadsX + lane;
+  s_warp[warp][lane] = w[0];
   __syncthreads();
-  // Block: FP32 sum of the warps, one FP64 (or FP32) partial per block.  Blocks fold
-  // in two deterministic levels: the last block of each group of kFoldGroup blocks
-  // sums the group's partials in block order, the last group sums the groups.
-  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  // Block: FP32 sum of each term's four warps, one FP64 (or FP32) partial per
+  // block.  Blocks fold in two deterministic levels: the last block of each group
+  // of kFoldGroup blocks sums the group's partials in block order, the last group
+  // sums the groups.
   const int grp = bid / kFoldGroup;
   const int ngroups = (p.nblocks + kFoldGroup - 1) / kFoldGroup;
   const int gsize = min(kFoldGroup, p.nblocks - grp * kFoldGroup);
   P* partials = reinterpret_cast<P*>(p.partials);
   P* gpartials = reinterpret_cast<P*>(p.gpartials);
   if (tid < kSumsAll) {
+    const int term = tid / kSums, k = tid - term * kSums;
     float s = 0.f;
 #pragma unroll
-    for (int w = 0; w < kTrackThreadsY; ++w) s += s_warp[w][tid];
+    for (int q = 0; q < kTrackRows; ++q) s += s_warp[term * kTrackRows + q][k];
     partials[(int64_t)bid * kSumsAll + tid] = (P)s;
     __threadfence();
   }
@@ -244,10 +292,35 @@ k_track(TrackParams p) {
   __threadfence();
   if (tid < kSumsAll) {
     P s = 0;
-    for (int g = 0; g < ngroups; ++g) s += __ldcg(gpartials + (int64_t)g * kSumsAll + tid);
+    for (int q = 0; q < ngroups; ++q) s += __ldcg(gpartials + (int64_t)q * kSumsAll + tid);
     ctrl->sums[tid] = (double)s;
   }
   if (tid == 0) p.counters[0] = 0u;
+}
+
+template <typename T, typename P, bool FLAGS>
+__global__ void __launch_bounds__(kTrackThreadsX * kTrackThreadsY)
+k_track(TrackParams p) {
+  track_tile<T, P, FLAGS>(p, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// Tiles of every tracking slot at one level: block -> (slot, tile) through the
+// block prefix, tile -> (column, row band) in the slot's image.
+template <typename T, typename P>
+__global__ void __launch_bounds__(kTrackThreadsX * kTrackThreadsY, 3)
+k_track_batch(const BatchArgs a) {
+  const int slot = batch_slot(a, blockIdx.x);
+  if (batch_dyn(a, slot).mode != kSlotTrack) return;
+  // the slot's parameters, staged once per block in shared memory
+  __shared__ TrackParams p;
+  const int tid = threadIdx.y * kTrackThreadsX + threadIdx.x;
+  if (tid < (int)(sizeof(TrackParams) / 4))
+    reinterpret_cast<uint32_t*>(&p)[tid] =
+        __ldg(reinterpret_cast<const uint32_t*>(&a.slots[slot].tp[a.level]) + tid);
+  __syncthreads();
+  const int t = blockIdx.x - __ldg(a.start + slot);
+  const int gx = (p.g.w + kTrackThreadsX - 1) / kTrackThreadsX;
+  track_tile<T, P, false>(p, t % gx, t / gx, t);
 }
 
 }  // namespace
@@ -262,14 +335,14 @@ int track_default_ppt(int w, int h) {
 
 int track_grid_blocks(int w, int h, int ppt) {
   const int gx = (w + kTrackThreadsX - 1) / kTrackThreadsX;
-  const int rows = kTrackThreadsY * ppt;
+  const int rows = kTrackRows * ppt;
   const int gy = (h + rows - 1) / rows;
   return gx * gy;
 }
 
 cudaError_t launch_track(const TrackParams& p, bool fp16, bool fp32_partials, cudaStream_t s) {
   const dim3 block(kTrackThreadsX, kTrackThreadsY);
-  const int rows = kTrackThreadsY * p.ppt;
+  const int rows = kTrackRows * p.ppt;
   const dim3 grid((p.g.w + kTrackThreadsX - 1) / kTrackThreadsX, (p.g.h + rows - 1) / rows);
   const bool flags = p.flags != nullptr;
 #define DRI_TRACK_LAUNCH(T, P)                                              \
@@ -285,6 +358,19 @@ cudaError_t launch_track(const TrackParams& p, bool fp16, bool fp32_partials, cu
     else DRI_TRACK_LAUNCH(float, double);
   }
 #undef DRI_TRACK_LAUNCH
+  return cudaGetLastError();
+}
+
+cudaError_t launch_track_batch(const BatchArgs& a, int blocks, bool fp16, bool fp32_partials,
+                               cudaStream_t s) {
+  const dim3 block(kTrackThreadsX, kTrackThreadsY);
+  if (fp16) {
+    if (fp32_partials) k_track_batch<__half, float><<<blocks, block, 0, s>>>(a);
+    else k_track_batch<__half, double><<<blocks, block, 0, s>>>(a);
+  } else {
+    if (fp32_partials) k_track_batch<float, float><<<blocks, block, 0, s>>>(a);
+    else k_track_batch<float, double><<<blocks, block, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

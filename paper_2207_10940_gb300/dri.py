@@ -126,6 +126,8 @@ def load_library():
                                             ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32]),
         "dri_push_imu": (ctypes.c_int, [ctypes.c_void_p, P(dri_imu_sample), ctypes.c_size_t]),
         "dri_track": (ctypes.c_int, [ctypes.c_void_p, P(dri_track_result)]),
+        "dri_track_batch": (ctypes.c_int, [P(ctypes.c_void_p), ctypes.c_int32, P(dri_track_result)]),
+        "dri_batch_tiles": (ctypes.c_int, [P(ctypes.c_void_p), ctypes.c_int32, P(ctypes.c_int32)]),
         "dri_get_state": (ctypes.c_int, [ctypes.c_void_p, P(dri_state), c_double_p, c_double_p]),
         "dri_set_state": (ctypes.c_int, [ctypes.c_void_p, P(dri_state), c_double_p, c_double_p]),
         "dri_linearise": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, P(dri_state), P(dri_state),
@@ -243,6 +245,35 @@ def dri_track(s, wait=True):
     if code < 0 and code != DRI_ELOST:
         raise DriError(code, "dri_track")
     return res
+
+
+def _handles(streams):
+    arr = (ctypes.c_void_p * len(streams))()
+    for i, h in enumerate(streams):
+        arr[i] = getattr(h, "handle", h)
+    return arr
+
+
+def dri_track_batch(streams, wait=True):
+    """Tracks the uploaded frame of every stream (handles or Stream objects) in
+    one batched launch sequence.  wait=True: returns the list of
+    dri_track_result (status DRI_OK, DRI_ELOST or DRI_ENOTREADY for a stream
+    that sat the call out); wait=False: None.  Call errors raise DriError."""
+    arr = _handles(streams)
+    if not wait:
+        _check(load_library().dri_track_batch(arr, len(streams), None), "dri_track_batch")
+        return None
+    res = (dri_track_result * len(streams))()
+    _check(load_library().dri_track_batch(arr, len(streams), res), "dri_track_batch")
+    return list(res)
+
+
+def dri_batch_tiles(streams):
+    """Rows per thread of the pixel kernel per level for this stream list's plan."""
+    arr = _handles(streams)
+    out = (ctypes.c_int32 * DRI_MAX_LEVELS)()
+    _check(load_library().dri_batch_tiles(arr, len(streams), out), "dri_batch_tiles")
+    return list(out)
 
 
 def dri_get_state(s, with_prior=False):
