@@ -250,15 +250,15 @@ def run_reference(args):
     return 0
 
 
-def config_json():
-    return {"workload": f"{BATCH} independent streams of 640x480 RGB-D + 400 Hz IMU per step "
+def config_json(batch=BATCH):
+    return {"workload": f"{batch} independent streams of 640x480 RGB-D + 400 Hz IMU per step "
                         f"(one dri_track_batch call), 3 levels 10/5/4 GN iterations; plain: one "
                         f"stream, one frame per step",
             "model": "dense RGB-D-inertial tracking (photometric + ICP + IMU, 34-D joint GN)",
-            "global_batch": BATCH, "seq_len": 1, "parallelism": "replicas (independent streams per GPU)",
+            "global_batch": batch, "seq_len": 1, "parallelism": "replicas (independent streams per GPU)",
             "width": W, "height": H, "levels": LEVELS, "iters": list(ITERS),
             "l2": "inputs larger than L2 (100 distinct frames, 245 MB, cycled; a batched step "
-                  "reads 64 of them)"}
+                  f"reads {min(batch, N_UNIQUE)} of them)"}
 
 
 def initial_state_at(seq, i):
@@ -294,7 +294,7 @@ class Runner:
     """Streams of the benchmark on one device: frame k of stream i shows loop
     frame (offset_i + k) mod 100 at time (offset_i + k) / 30 s."""
 
-    def __init__(self, seq, imu, d_dev, i_dev, d_pin, i_pin, offsets, dev):
+    def __init__(self, seq, imu, d_dev, i_dev, d_pin, i_pin, offsets, dev, tiles=None, groups=None):
         import torch
         from paper_2207_10940_gb300 import dri
         self.dri, self.torch = dri, torch
@@ -308,6 +308,9 @@ class Runner:
         arr = dri.imu_array(imu)
         for st in self.streams:
             dri.dri_push_imu(st.handle, arr)
+        if tiles or groups:
+            dri.dri_batch_set_options([st.handle for st in self.streams], rows_per_thread=tiles,
+                                      groups=groups)
         self.k = 0
 
     def upload(self, device_inputs=True):
@@ -418,9 +421,14 @@ def run_ours(args):
     i_pin = torch.stack([torch.from_numpy(f[1]) for f in frames]).pin_memory()
     torch.cuda.synchronize(dev)      # the library reads these on its own stream
     out = {}
-    for mode, n_streams, steps in (("batched", BATCH, args.steps), ("plain", 1, plain_steps)):
+    passes = [("batched", args.batch, args.steps)]
+    if plain_steps > 0:
+        passes.append(("plain", 1, plain_steps))
+    for mode, n_streams, steps in passes:
         offsets = [(BATCH_OFFSET * i) % N_UNIQUE for i in range(n_streams)]
-        run = Runner(seq, imu, d_dev, i_dev, d_pin, i_pin, offsets, dev)
+        run = Runner(seq, imu, d_dev, i_dev, d_pin, i_pin, offsets, dev,
+                     args.rows_per_thread if n_streams > 1 else None,
+                     args.groups if n_streams > 1 else None)
         res = run.step(wait=True)
         for _ in range(args.warmup):
             run.step()
@@ -429,7 +437,8 @@ def run_ours(args):
         prof = profiled_pass(run, max(3, args.profile_frames // (8 if n_streams > 1 else 1)))
         e2e_steps = max(3, steps // 4)
         e2e_s, h2d, d2h = e2e_pass(run, e2e_steps, world)
-        tiles = dri.dri_batch_tiles([s.handle for s in run.streams])
+        opts = dri.dri_batch_get_options([s.handle for s in run.streams])
+        tiles = list(opts.rows_per_thread)
         out[mode] = {
             "value": world * n_streams * steps / (total_ms / 1000.0), "steps": steps,
             "streams": n_streams, "ms_per_step": total_ms / steps,
@@ -438,7 +447,7 @@ def run_ours(args):
             "roofline": roofline(prof, dri, track_traffic()), "kernel_classes": kernel_classes(prof, dri),
             "e2e": {"value": world * n_streams * e2e_steps / e2e_s, "unit": "frames/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            "clocks": clocks, "rows_per_thread": tiles[:LEVELS],
+            "clocks": clocks, "rows_per_thread": tiles[:LEVELS], "groups": opts.groups,
         }
         run.close()
         del run
@@ -451,26 +460,27 @@ def run_ours(args):
         return 0
     budget = float(os.environ.get("DRI_BENCH_ORACLE_SECONDS", "15"))
     o_fps, o_n, o_t = oracle_frames_per_s(seq, frames, imu, budget)
-    b, p = out["batched"], out["plain"]
+    b, p = out["batched"], out.get("plain")
     line = {
         "metric": "tracked frames/s at 640x480 (batched vs plain)",
         "value": b["value"], "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 per-pixel, f64 reduction and solve",
-        "data": "synthetic", "config": config_json(),
+        "data": "synthetic", "config": config_json(args.batch),
         "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"],
         "gpu_launches": b["gpu_launches"],
         "frames_failed": b["frames_failed"], "frames_ok": b["frames_ok"],
         "roofline": b["roofline"], "kernel_classes": b["kernel_classes"], "e2e": b["e2e"],
-        "rows_per_thread": b["rows_per_thread"],
-        "plain": {k: p[k] for k in ("value", "steps", "ms_per_step", "p50_ms", "p99_ms",
-                                     "gpu_launches", "frames_ok", "frames_failed", "roofline",
-                                     "kernel_classes", "e2e", "rows_per_thread")},
-        "batched_over_plain": b["value"] / p["value"],
+        "rows_per_thread": b["rows_per_thread"], "groups": b["groups"],
+        "plain": None if p is None else {
+            k: p[k] for k in ("value", "steps", "ms_per_step", "p50_ms", "p99_ms", "gpu_launches",
+                              "frames_ok", "frames_failed", "roofline", "kernel_classes", "e2e",
+                              "rows_per_thread")},
+        "batched_over_plain": None if p is None else b["value"] / p["value"],
         "cpu_baseline": {"value": o_fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
                          "sample": f"{o_n} whole frames of the same sequence tracked by the FP64 "
                                    f"numpy oracle in {o_t:.1f} s"},
-        "clocks": b["clocks"], "clocks_plain": p["clocks"],
+        "clocks": b["clocks"], "clocks_plain": None if p is None else p["clocks"],
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -482,7 +492,14 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--plain-steps", type=int, default=600)
+    ap.add_argument("--plain-steps", type=int, default=600,
+                    help="frames of the plain single-stream pass (0: skip it)")
+    ap.add_argument("--batch", type=int, default=BATCH, help="streams of the batched pass")
+    ap.add_argument("--rows-per-thread", type=lambda v: [int(x) for x in v.split(",")], default=None,
+                    help="pixel-kernel rows per thread per level for the batched pass, e.g. 8,8,8 "
+                         "(default: the plan's autotuner)")
+    ap.add_argument("--groups", type=int, default=None,
+                    help="slot groups of the batched Gauss-Newton loop (default: the library's)")
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--profile-frames", type=int, default=60)

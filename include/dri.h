@@ -186,6 +186,7 @@ int dri_track(dri_stream s, dri_track_result* out);
  * fastest (this call waits); later calls replay the sequence as one CUDA graph
  * (launched directly on the legacy default stream or while profiling).
  *
+ * With n = 1 the call tracks through the stream's own plan, as dri_track does.
  * A stream without an uploaded frame, or whose IMU samples do not yet cover
  * [t_previous_frame, t_frame], sits the call out (its frame stays pending).
  * out == NULL: returns after enqueuing; out != NULL: waits and fills out[i]
@@ -193,11 +194,33 @@ int dri_track(dri_stream s, dri_track_result* out);
  * DRI_OK when the batch ran, DRI_ENOTREADY when no stream had work. */
 int dri_track_batch(const dri_stream* streams, int32_t n, dri_track_result* out);
 
-/* Rows per thread of the pixel kernel on each level (ppt[DRI_MAX_LEVELS], 0
- * past the last level) of the plan for this stream list: the autotuned values
- * of dri_track_batch's plan, or for n = 1 and no batch plan the stream's own
- * (fixed by a size heuristic).  DRI_ENOTREADY if no such plan exists. */
-int dri_batch_tiles(const dri_stream* streams, int32_t n, int32_t* ppt);
+/* Launch options of a plan (the stream's own for n = 1, else the batch plan of
+ * the list):
+ *   rows_per_thread  pixel-kernel rows per thread on each level (tile = 32
+ *                    columns x 4 * rows); 0 past the last level
+ *   groups           the Gauss-Newton loop runs as this many groups of slots,
+ *                    each on its own CUDA stream forked from and joined to the
+ *                    plan's stream, so one group's FP64 solves can overlap another
+ *                    group's pixel kernels (1 .. min(n, 8); default 1; a
+ *                    stream's own plan has 1)
+ *   autotune         1: the next tracked frame times rows per thread
+ *                    1, 2, 3, 4, 6, 8 per level and keeps the fastest (batch
+ *                    plans start with it on); 0: rows_per_thread as given, so
+ *                    repeated runs sum pixels in the same order (identical bits) */
+typedef struct {
+    int32_t rows_per_thread[DRI_MAX_LEVELS];
+    int32_t groups;
+    int32_t autotune;
+} dri_batch_options;
+
+/* Reads the options of the plan for this stream list; DRI_ENOTREADY if no
+ * batch plan exists for it yet. */
+int dri_batch_get_options(const dri_stream* streams, int32_t n, dri_batch_options* out);
+
+/* Sets them (creating the batch plan if needed, as dri_track_batch would).
+ * Waits for the streams' work.  rows_per_thread is ignored when autotune is 1.
+ * DRI_EINVAL for a bad list or value. */
+int dri_batch_set_options(const dri_stream* streams, int32_t n, const dri_batch_options* opt);
 
 /* Waits for the stream and copies out x1 and, when non-NULL, the prior
  * H* (17 x 17, row-major) and b* (17) that the next frame will use. */
@@ -275,7 +298,7 @@ int dri_profile_read(dri_stream s, dri_profile* out);
  *
  * Every intermediate (normal and gradient maps, per-block partial sums, the
  * block counter and per-call transforms) lives in one static device array that
- * the library reserves when it is loaded (about 2.6 MB per GPU, held until the
+ * the library reserves when it is loaded (about 4.0 MB per GPU, held until the
  * process exits), sized for at most 320 x 240 pixels: larger images return
  * DRI_EINVAL.  The array is shared by all calls on a device and keeps the last
  * call's contents; each call clears what must start at zero.  Calls whose GPU

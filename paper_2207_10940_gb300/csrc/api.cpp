@@ -25,6 +25,9 @@ constexpr size_t kAlign = 256;
 constexpr int kStreamRing = 64;   // frames of one stream in flight (dri_track, out = NULL)
 constexpr int kBatchRing = 8;     // launches of one batch plan in flight
 constexpr int kMaxBatch = 4096;
+constexpr int kMaxRowsPerThread = 64;
+constexpr int kMaxGroups = 8;     // slot groups of a batch plan's Gauss-Newton loop
+constexpr int kDefaultGroups = 1;
 inline size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
 
 int valid_config(const dri_stream_config* c) {
@@ -125,18 +128,19 @@ LevelGeom level_geom(const dri_stream_config& cfg, int level) {
   return g;
 }
 
-TableView table_view(int nslots, int levels) {
+TableView table_view(int nslots, int levels, int groups) {
   TableView v;
   std::memset(&v, 0, sizeof(v));
   size_t off = align_up((size_t)nslots * sizeof(SlotStatic), 16);
   const size_t pre = (size_t)(nslots + 1) * sizeof(int32_t);
+  const size_t pre_g = (size_t)(nslots + groups) * sizeof(int32_t);
   v.copy_off = off;
   off = align_up(off + pre, 16);
   for (int l = 0; l < levels; ++l) {
     v.map_off[l] = off;
     off = align_up(off + pre, 16);
     v.track_off[l] = off;
-    off = align_up(off + pre, 16);
+    off = align_up(off + pre_g, 16);
   }
   v.bytes = align_up(off);
   return v;
@@ -161,7 +165,7 @@ StreamLayout make_layout(const dri_stream_config& cfg) {
   std::memset(&L, 0, sizeof(L));
   const bool fp16 = (cfg.precision_flags & DRI_FP16_MAPS) != 0;
   const bool fp32p = (cfg.precision_flags & DRI_FP32_PARTIALS) != 0;
-  L.map_elem_bytes = fp16 ? 2 : 4;
+  L.pack_bytes = fp16 ? 8 : 16;
   L.imu_cap = cfg.max_imu;
   size_t off = 0;
   L.ctrl = off;
@@ -170,7 +174,7 @@ StreamLayout make_layout(const dri_stream_config& cfg) {
   L.dyn_bytes = dyn_header_bytes(1) + imu_block_bytes(L.imu_cap);
   off = align_up(off + L.dyn_bytes);
   L.table = off;
-  off = align_up(off + table_view(1, cfg.levels).bytes);
+  off = align_up(off + table_view(1, cfg.levels, 1).bytes);
   const size_t npx = (size_t)cfg.width * cfg.height;
   L.in_depth = off;
   off = align_up(off + npx * 4);
@@ -184,11 +188,11 @@ StreamLayout make_layout(const dri_stream_config& cfg) {
       L.level_off[l][s][0] = off;
       off = align_up(off + plane * 4);
       L.level_off[l][s][1] = off;
-      off = align_up(off + 3 * plane * L.map_elem_bytes);
-      L.level_off[l][s][2] = off;
       off = align_up(off + plane * 4);
+      L.level_off[l][s][2] = off;
+      off = align_up(off + plane * L.pack_bytes);
       L.level_off[l][s][3] = off;
-      off = align_up(off + 2 * plane * L.map_elem_bytes);
+      off = align_up(off + plane * L.pack_bytes);
     }
   }
   int maxb = 1;
@@ -270,6 +274,11 @@ struct Plan {
   int iters[kMaxLevels] = {};
   bool fp16 = false, fp32p = false;
   bool owns_device = false;         // table / dyn / heads allocated by the plan
+  int groups = 1;                   // slot groups of the Gauss-Newton loop, one CUDA stream each
+  std::vector<int> gfirst, gcount;
+  std::vector<cudaStream_t> aux;    // streams of groups 1 .. groups - 1
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
   char* table = nullptr;
   TableView tv;
   unsigned char* dyn = nullptr;
@@ -384,7 +393,7 @@ void plan_fill_tables(Plan* p) {
   p->pre_copy.assign(p->S + 1, 0);
   for (int l = 0; l < p->levels; ++l) {
     p->pre_map[l].assign(p->S + 1, 0);
-    p->pre_track[l].assign(p->S + 1, 0);
+    p->pre_track[l].assign(p->S + p->groups, 0);
   }
   for (int i = 0; i < p->S; ++i) {
     const dri_stream_s* s = p->slots[i];
@@ -397,11 +406,24 @@ void plan_fill_tables(Plan* p) {
     st.in_inten = s->in_inten;
     st.levels = p->levels;
     p->pre_copy[i + 1] = p->pre_copy[i] + copy_tiles(s->cfg.width, s->cfg.height);
-    for (int l = 0; l < p->levels; ++l) {
+    for (int l = 0; l < p->levels; ++l)
       p->pre_map[l][i + 1] = p->pre_map[l][i] + map_tiles(s->geom[l].w, s->geom[l].h);
-      p->pre_track[l][i + 1] = p->pre_track[l][i] + st.tp[l].nblocks;
-    }
   }
+  for (int g = 0; g < p->groups; ++g) {       // local prefix of each group's slots
+    const int base = p->gfirst[g] + g;
+    for (int l = 0; l < p->levels; ++l)
+      for (int k = 0; k < p->gcount[g]; ++k)
+        p->pre_track[l][base + k + 1] =
+            p->pre_track[l][base + k] + p->host_slots[p->gfirst[g] + k].tp[l].nblocks;
+  }
+}
+
+// Pixel-kernel blocks of group g at level l, and the byte offset of its prefix.
+int track_blocks(const Plan* p, int l, int g) {
+  return p->pre_track[l][p->gfirst[g] + g + p->gcount[g]];
+}
+size_t track_start(const Plan* p, int l, int g) {
+  return p->tv.track_off[l] + (size_t)(p->gfirst[g] + g) * sizeof(int32_t);
 }
 
 int plan_upload_tables(Plan* p) {
@@ -411,7 +433,8 @@ int plan_upload_tables(Plan* p) {
   std::memcpy(img.data() + p->tv.copy_off, p->pre_copy.data(), pre);
   for (int l = 0; l < p->levels; ++l) {
     std::memcpy(img.data() + p->tv.map_off[l], p->pre_map[l].data(), pre);
-    std::memcpy(img.data() + p->tv.track_off[l], p->pre_track[l].data(), pre);
+    std::memcpy(img.data() + p->tv.track_off[l], p->pre_track[l].data(),
+                (size_t)(p->S + p->groups) * sizeof(int32_t));
   }
   CK(cudaMemcpyAsync(p->table, img.data(), img.size(), cudaMemcpyHostToDevice, p->stream));
   CK(cudaStreamSynchronize(p->stream));
@@ -421,6 +444,11 @@ int plan_upload_tables(Plan* p) {
 void plan_free(Plan* p) {
   if (!p) return;
   if (p->graph) cudaGraphExecDestroy(p->graph);
+  for (cudaStream_t a : p->aux)
+    if (a) cudaStreamDestroy(a);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  for (cudaEvent_t e : p->ev_join)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : p->ev)
     if (e) cudaEventDestroy(e);
   if (p->pin_dyn) cudaFreeHost(p->pin_dyn);
@@ -435,7 +463,19 @@ void plan_free(Plan* p) {
 
 // Creates a plan over the given streams.  Single-slot plans use the stream's
 // workspace; batch plans allocate their own table, staging and head buffers.
-int plan_create(dri_stream_s* const* streams, int n, int ring, bool in_workspace, Plan** out) {
+// Splits the plan's slots into `groups` contiguous groups of near-equal size.
+void plan_set_groups(Plan* p, int groups) {
+  p->groups = groups;
+  p->gfirst.assign(groups, 0);
+  p->gcount.assign(groups, 0);
+  for (int g = 0; g < groups; ++g) {
+    p->gfirst[g] = (int)((int64_t)p->S * g / groups);
+    p->gcount[g] = (int)((int64_t)p->S * (g + 1) / groups) - p->gfirst[g];
+  }
+}
+
+int plan_create(dri_stream_s* const* streams, int n, int ring, bool in_workspace, int groups,
+                Plan** out) {
   *out = nullptr;
   Plan* p = new (std::nothrow) Plan();
   if (!p) return DRI_ENOMEM;
@@ -446,7 +486,10 @@ int plan_create(dri_stream_s* const* streams, int n, int ring, bool in_workspace
   for (int l = 0; l < kMaxLevels; ++l) p->iters[l] = l < p->levels ? streams[0]->cfg.iters[l] : 0;
   p->fp16 = (streams[0]->cfg.precision_flags & DRI_FP16_MAPS) != 0;
   p->fp32p = (streams[0]->cfg.precision_flags & DRI_FP32_PARTIALS) != 0;
-  p->tv = table_view(n, p->levels);
+  plan_set_groups(p, groups);
+  // a batch plan's table has room for any group count; a stream's own plan has
+  // one group and exactly the workspace's table region
+  p->tv = table_view(n, p->levels, in_workspace ? 1 : kMaxGroups);
   p->R = ring;
   p->ppt.resize(n);
   for (int i = 0; i < n; ++i)
@@ -456,6 +499,10 @@ int plan_create(dri_stream_s* const* streams, int n, int ring, bool in_workspace
   p->dyn_cap = dyn_header_bytes(n) + (size_t)n * imu_block_bytes(imu_cap);
   if (in_workspace) {             // the one-slot plan of dri_track
     dri_stream_s* s = streams[0];
+    if (n != 1 || groups != 1 || p->tv.bytes > s->L.in_depth - s->L.table) {
+      plan_free(p);
+      return DRI_EINVAL;
+    }
     p->table = s->ws + s->L.table;
     p->dyn = reinterpret_cast<unsigned char*>(s->ws + s->L.dyn);
   } else {
@@ -471,6 +518,21 @@ int plan_create(dri_stream_s* const* streams, int n, int ring, bool in_workspace
       cudaMallocHost(&p->pin_heads, (size_t)ring * n * kCtrlHeadBytes) != cudaSuccess) {
     plan_free(p);
     return DRI_ENOMEM;
+  }
+  p->aux.assign(kMaxGroups - 1, nullptr);
+  p->ev_join.assign(kMaxGroups - 1, nullptr);
+  if (!in_workspace) {
+    if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+      plan_free(p);
+      return DRI_ENOMEM;
+    }
+    for (int g = 0; g < kMaxGroups - 1; ++g) {
+      if (cudaStreamCreateWithFlags(&p->aux[g], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&p->ev_join[g], cudaEventDisableTiming) != cudaSuccess) {
+        plan_free(p);
+        return DRI_ENOMEM;
+      }
+    }
   }
   p->ev.assign(ring, nullptr);
   p->ring_used.assign(ring, 0);
@@ -568,13 +630,15 @@ size_t stage_slot(const dri_stream_s* s, char* img, int i, int mode, double t0, 
   return align_up(sizeof(h) + (size_t)h.n * sizeof(dri_imu_sample), 16);
 }
 
-BatchArgs plan_args(const Plan* p, size_t start_off, int level, int last) {
+BatchArgs plan_args(const Plan* p, size_t start_off, int level, int last, int slot0 = 0,
+                    int nslots = -1) {
   BatchArgs a;
   std::memset(&a, 0, sizeof(a));
   a.slots = reinterpret_cast<const SlotStatic*>(p->table);
   a.dyn = p->dyn;
   a.start = reinterpret_cast<const int32_t*>(p->table + start_off);
-  a.nslots = p->S;
+  a.slot0 = slot0;
+  a.nslots = nslots < 0 ? p->S : nslots;
   a.level = level;
   a.last = last;
   return a;
@@ -615,17 +679,33 @@ int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
     ++k;
   }
   if (phases & 2) {
-    int remaining = 0;
-    for (int l = 0; l < L; ++l) remaining += p->iters[l];
-    for (int l = L - 1; l >= 0; --l) {
-      for (int it = 0; it < p->iters[l]; ++it) {
-        --remaining;
-        const BatchArgs at = plan_args(p, p->tv.track_off[l], l, 0);
-        CK(launch(prof, DRI_KC_TRACK, plan_pixels(p, l),
-                  [&] { return launch_track_batch(at, p->pre_track[l][p->S], p->fp16, p->fp32p, st); }));
-        const BatchArgs as = plan_args(p, p->tv.copy_off, l, remaining == 0);
-        CK(launch(prof, DRI_KC_SOLVE, 0.0, [&] { return launch_gn_step_batch(as, st); }));
-        k += 2;
+    // Gauss-Newton loop per slot group; groups run on their own streams (forked
+    // from and joined back into the plan's stream) so that one group's FP64
+    // solves overlap another group's pixel kernels.  While profiling, the groups
+    // run one after the other on the plan's stream.
+    const bool fork = p->groups > 1 && !prof->profiling;
+    if (fork) CK(cudaEventRecord(p->ev_fork, st));
+    for (int g = 0; g < p->groups; ++g) {
+      cudaStream_t sg = (fork && g > 0) ? p->aux[g - 1] : st;
+      if (fork && g > 0) CK(cudaStreamWaitEvent(sg, p->ev_fork, 0));
+      const double px_scale = (double)p->gcount[g] / p->S;
+      int remaining = 0;
+      for (int l = 0; l < L; ++l) remaining += p->iters[l];
+      for (int l = L - 1; l >= 0; --l) {
+        for (int it = 0; it < p->iters[l]; ++it) {
+          --remaining;
+          const BatchArgs at = plan_args(p, track_start(p, l, g), l, 0, p->gfirst[g], p->gcount[g]);
+          const int nb = track_blocks(p, l, g);
+          CK(launch(prof, DRI_KC_TRACK, plan_pixels(p, l) * px_scale,
+                    [&] { return launch_track_batch(at, nb, p->fp16, p->fp32p, sg); }));
+          const BatchArgs as = plan_args(p, p->tv.copy_off, l, remaining == 0, p->gfirst[g], p->gcount[g]);
+          CK(launch(prof, DRI_KC_SOLVE, 0.0, [&] { return launch_gn_step_batch(as, sg); }));
+          k += 2;
+        }
+      }
+      if (fork && g > 0) {
+        CK(cudaEventRecord(p->ev_join[g - 1], sg));
+        CK(cudaStreamWaitEvent(st, p->ev_join[g - 1], 0));
       }
     }
     const BatchArgs ae = plan_args(p, p->tv.copy_off, 0, 0);
@@ -662,22 +742,27 @@ int plan_autotune(Plan* p, int64_t* kernels) {
       for (auto& v : p->ppt) v[l] = c;
       plan_fill_tables(p);
       if ((rc = plan_upload_tables(p)) != DRI_OK) break;
-      const BatchArgs at = plan_args(p, p->tv.track_off[l], l, 0);
-      if (launch_track_batch(at, p->pre_track[l][p->S], p->fp16, p->fp32p, p->stream) != cudaSuccess ||
-          cudaEventRecord(e0, p->stream) != cudaSuccess) {
+      auto all_groups = [&] {
+        for (int g = 0; g < p->groups; ++g) {
+          const BatchArgs at = plan_args(p, track_start(p, l, g), l, 0, p->gfirst[g], p->gcount[g]);
+          if (launch_track_batch(at, track_blocks(p, l, g), p->fp16, p->fp32p, p->stream) != cudaSuccess)
+            return false;
+        }
+        return true;
+      };
+      if (!all_groups() || cudaEventRecord(e0, p->stream) != cudaSuccess) {
         rc = DRI_ECUDA;
         break;
       }
       for (int rep = 0; rep < 3; ++rep)
-        if (launch_track_batch(at, p->pre_track[l][p->S], p->fp16, p->fp32p, p->stream) != cudaSuccess)
-          rc = DRI_ECUDA;
+        if (!all_groups()) rc = DRI_ECUDA;
       float ms = 0.f;
       if (rc != DRI_OK || cudaEventRecord(e1, p->stream) != cudaSuccess ||
           cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
         rc = DRI_ECUDA;
         break;
       }
-      *kernels += 4;
+      *kernels += 4 * p->groups;
       if (ms < best) {
         best = ms;
         best_ppt = c;
@@ -931,12 +1016,11 @@ int dri_create_stream(const dri_stream_config* cfg, const dri_state* x_init, voi
   for (int l = 0; l < cfg->levels; ++l) {
     s->geom[l] = level_geom(*cfg, l);
     LevelMaps& m = s->maps[l];
-    m.plane = L.plane[l];
     for (int k = 0; k < 2; ++k) {
       m.depth[k] = (float*)(s->ws + L.level_off[l][k][0]);
-      m.normal[k] = (void*)(s->ws + L.level_off[l][k][1]);
-      m.inten[k] = (float*)(s->ws + L.level_off[l][k][2]);
-      m.grad[k] = (void*)(s->ws + L.level_off[l][k][3]);
+      m.inten[k] = (float*)(s->ws + L.level_off[l][k][1]);
+      m.packA[k] = (void*)(s->ws + L.level_off[l][k][2]);
+      m.packB[k] = (void*)(s->ws + L.level_off[l][k][3]);
     }
     s->ppt[l] = track_default_ppt(s->geom[l].w, s->geom[l].h);
   }
@@ -956,7 +1040,7 @@ int dri_create_stream(const dri_stream_config* cfg, const dri_state* x_init, voi
     return DRI_ECUDA;
   }
   dri_stream_s* one[1] = {s};
-  const int r = plan_create(one, 1, kStreamRing, true, &s->own);
+  const int r = plan_create(one, 1, kStreamRing, true, 1, &s->own);
   if (r != DRI_OK) {
     dri_destroy_stream(s);
     return r;
@@ -1061,7 +1145,14 @@ int dri_track(dri_stream s, dri_track_result* out) {
   return h->status;
 }
 
-int dri_track_batch(const dri_stream* streams, int32_t n, dri_track_result* out) {
+}  // extern "C"
+
+namespace {
+
+// The plan of a stream list: a stream's own plan for one stream, else the
+// cached batch plan of exactly this list (created on first use).
+int batch_plan(const dri_stream* streams, int32_t n, Plan** out) {
+  *out = nullptr;
   if (!streams || n < 1 || n > kMaxBatch) return DRI_EINVAL;
   for (int i = 0; i < n; ++i) {
     const dri_stream_s* s = streams[i];
@@ -1075,20 +1166,34 @@ int dri_track_batch(const dri_stream* streams, int32_t n, dri_track_result* out)
     for (int l = 0; l < s->cfg.levels; ++l)
       if (s->cfg.iters[l] != s0->cfg.iters[l]) return DRI_EINVAL;
   }
-  std::vector<dri_stream_s*> key(streams, streams + n);
-  Plan* p = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_batch_mu);
-    for (Plan* q : g_batch_plans)
-      if (q->slots == key) p = q;
-    if (!p) {
-      const int r = plan_create(key.data(), n, kBatchRing, false, &p);
-      if (r != DRI_OK) return r;
-      p->autotune = true;
-      g_batch_plans.push_back(p);
-      for (dri_stream_s* s : key) s->batches.push_back(p);
-    }
+  if (n == 1) {
+    *out = streams[0]->own;
+    return DRI_OK;
   }
+  std::vector<dri_stream_s*> key(streams, streams + n);
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (Plan* q : g_batch_plans)
+    if (q->slots == key) *out = q;
+  if (*out) return DRI_OK;
+  Plan* p = nullptr;
+  const int r = plan_create(key.data(), n, kBatchRing, false, std::min(n, kDefaultGroups), &p);
+  if (r != DRI_OK) return r;
+  p->autotune = true;
+  g_batch_plans.push_back(p);
+  for (dri_stream_s* s : key) s->batches.push_back(p);
+  *out = p;
+  return DRI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dri_track_batch(const dri_stream* streams, int32_t n, dri_track_result* out) {
+  Plan* p = nullptr;
+  const int rp = batch_plan(streams, n, &p);
+  if (rp != DRI_OK) return rp;
+  const std::vector<dri_stream_s*>& key = p->slots;
   std::vector<SlotWork> work(n);
   bool any = false;
   for (int i = 0; i < n; ++i) {
@@ -1244,17 +1349,49 @@ int dri_launch_count(dri_stream s, int64_t* count) {
   return DRI_OK;
 }
 
-int dri_batch_tiles(const dri_stream* streams, int32_t n, int32_t* ppt) {
-  if (!streams || n < 1 || !ppt) return DRI_EINVAL;
-  std::vector<dri_stream_s*> key(streams, streams + n);
-  std::lock_guard<std::mutex> lk(g_batch_mu);
+int dri_batch_get_options(const dri_stream* streams, int32_t n, dri_batch_options* out) {
+  if (!streams || n < 1 || !out) return DRI_EINVAL;
   const Plan* p = nullptr;
-  if (n == 1 && key[0]) p = key[0]->own;
-  for (const Plan* q : g_batch_plans)
-    if (q->slots == key) p = q;
+  if (n == 1) {
+    if (!streams[0]) return DRI_EINVAL;
+    p = streams[0]->own;
+  } else {
+    std::vector<dri_stream_s*> key(streams, streams + n);
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (const Plan* q : g_batch_plans)
+      if (q->slots == key) p = q;
+  }
   if (!p) return DRI_ENOTREADY;
-  for (int l = 0; l < kMaxLevels; ++l) ppt[l] = l < p->levels ? p->ppt[0][l] : 0;
+  std::memset(out, 0, sizeof(*out));
+  for (int l = 0; l < kMaxLevels; ++l) out->rows_per_thread[l] = l < p->levels ? p->ppt[0][l] : 0;
+  out->groups = p->groups;
+  out->autotune = p->autotune && !p->tuned ? 1 : 0;
   return DRI_OK;
+}
+
+int dri_batch_set_options(const dri_stream* streams, int32_t n, const dri_batch_options* opt) {
+  if (!opt) return DRI_EINVAL;
+  Plan* p = nullptr;
+  const int r = batch_plan(streams, n, &p);
+  if (r != DRI_OK) return r;
+  if (opt->groups < 1 || opt->groups > std::min(p->S, kMaxGroups)) return DRI_EINVAL;
+  if (!opt->autotune)
+    for (int l = 0; l < p->levels; ++l)
+      if (opt->rows_per_thread[l] < 1 || opt->rows_per_thread[l] > kMaxRowsPerThread) return DRI_EINVAL;
+  CK(cudaStreamSynchronize(p->stream));      // in-flight frames read the current tables
+  if (!opt->autotune)
+    for (auto& v : p->ppt)
+      for (int l = 0; l < p->levels; ++l) v[l] = opt->rows_per_thread[l];
+  p->autotune = opt->autotune != 0;
+  p->tuned = !p->autotune;
+  plan_set_groups(p, opt->groups);
+  if (p->graph) {
+    cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  p->graph_failed = false;
+  plan_fill_tables(p);
+  return plan_upload_tables(p);
 }
 
 }  // extern "C"

@@ -9,7 +9,8 @@
 //   table          SlotStatic of the stream and the block-count prefixes of its
 //                  launches (the one-slot plan of dri_track).
 //   input depth/I  level-0 host-upload target.
-//   2 map sets     per level: depth, normal (3 planes), intensity, gradient (2 planes).
+//   2 map sets     per level: depth and intensity planes, pack A (normal + depth) and
+//                  pack B (intensity + gradient) per pixel, FP32 or FP16 (packs.cuh).
 //                  Set ctrl.ref_index is the reference, the other the live frame; a
 //                  tracked frame flips the index on the device (no host round trip).
 //   partials       per-block sums of the pixel kernel (FP64 or FP32).
@@ -27,7 +28,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/dri.h"
+#include "dri.h"
 
 namespace dri {
 
@@ -88,23 +89,22 @@ struct LevelGeom {
   float fx, fy, cx, cy, ifx, ify;
 };
 
-// Pointers of one pyramid level in both map sets.
+// Pointers of one pyramid level in both map sets (row-major, w * h pixels).
 struct LevelMaps {
   float* depth[2];
-  void* normal[2];                    // 3 planes (x, y, z) of `plane` elements, FP32 or FP16
   float* inten[2];
-  void* grad[2];                      // 2 planes (gx, gy)
-  int64_t plane;                      // elements per plane (>= w * h, padded)
+  void* packA[2];                     // per pixel normal + depth (packs.cuh)
+  void* packB[2];                     // per pixel intensity + gradient (packs.cuh)
 };
 
 struct StreamLayout {
   size_t ctrl, dyn, dyn_bytes, table, in_depth, in_inten, counters, partials, gpartials, flags,
       lin_out, total;
-  size_t level_off[kMaxLevels][2][4];  // per level, per set: depth, normal, inten, grad
+  size_t level_off[kMaxLevels][2][4];  // per level, per set: depth, inten, pack A, pack B
   int64_t plane[kMaxLevels];
   int max_blocks;
   int imu_cap;
-  int map_elem_bytes;                 // 4 (FP32) or 2 (FP16) for normal / gradient
+  int pack_bytes;                     // 16 (FP32) or 8 (FP16) per pack element
 };
 
 struct TrackParams {
@@ -163,23 +163,28 @@ struct SlotDyn {
 };
 
 // Table of one plan in device memory: SlotStatic[nslots], then the int32
-// prefixes copy[n + 1], map[levels][n + 1] and track[levels][n + 1].
+// block prefixes copy[n + 1], map[levels][n + 1] and, per level, one prefix of
+// n_g + 1 entries for each of the G slot groups of the Gauss-Newton loop
+// (group g's at entry first_slot(g) + g).
 struct TableView {
   size_t copy_off, map_off[kMaxLevels], track_off[kMaxLevels], bytes;
 };
-TableView table_view(int nslots, int levels);
+TableView table_view(int nslots, int levels, int groups);
 
-// Kernel argument of every batched launch.
+// Kernel argument of every batched launch: it covers slots slot0 ..
+// slot0 + nslots - 1 of the plan (all of them, or one group of the
+// Gauss-Newton loop).
 struct BatchArgs {
-  const SlotStatic* slots;
-  const unsigned char* dyn;           // SlotDyn[nslots], then the IMU blocks
-  const int32_t* start;               // block prefix over the slots for this launch
+  const SlotStatic* slots;            // every slot of the plan
+  const unsigned char* dyn;           // SlotDyn[all slots], then the IMU blocks
+  const int32_t* start;               // block prefix over this launch's slots (nslots + 1)
+  int32_t slot0;
   int32_t nslots;
   int32_t level;
   int32_t last;                       // 1 on the frame's last Gauss-Newton iteration
-  int32_t pad;
 };
 
+// Index (0 .. nslots - 1, relative to slot0) of the launch slot owning `block`.
 __device__ __forceinline__ int batch_slot(const BatchArgs& a, int block) {
   int lo = 0, hi = a.nslots;          // start[lo] <= block < start[hi]
   while (hi - lo > 1) {

@@ -6,40 +6,34 @@
 //                none), intensity = 2x2 mean
 //   normals      n = normalise((v(x+1,y) - v) x (v(x,y+1) - v)), facing the camera,
 //                invalid (stored as 0) on the last row / column or next to an invalid
-//                depth; v = d K^-1 [u, v, 1]^T
-//   gradient     central-difference intensity gradient, zero on the one-pixel border
+//                depth; v = d K^-1 [u, v, 1]^T; written with the depth as pack A
+//   gradient     central-difference intensity gradient, zero on the one-pixel border;
+//                written with the intensity as pack B
 //
-// All maps are planar (one plane per component) so a warp reads 128 contiguous
-// bytes per plane; normals and gradients are FP32 or, with DRI_FP16_MAPS, FP16.
+// Depth and intensity are FP32 planes; the packs (packs.cuh) hold FP32 or, with
+// DRI_FP16_MAPS, FP16 normals and gradients.
 // The batched kernels cover the images of every slot of a plan in one launch;
 // the single-image normal and gradient kernels serve the allocation-free entry.
 #include <cuda_fp16.h>
 
 #include "dri_internal.h"
+#include "packs.cuh"
 
 namespace dri {
 
 namespace {
 
-template <typename T>
-__device__ __forceinline__ void store_map(T* p, int64_t i, float v);
-template <>
-__device__ __forceinline__ void store_map<float>(float* p, int64_t i, float v) { p[i] = v; }
-template <>
-__device__ __forceinline__ void store_map<__half>(__half* p, int64_t i, float v) {
-  p[i] = __float2half_rn(v);
-}
-
 // Level-0 copy of one 128 x 8 tile: each thread moves 4 pixels of a row, as one
 // 16-byte load and store when both rows allow it.
 __global__ void __launch_bounds__(256) k_copy_batch(const BatchArgs a) {
-  const int slot = batch_slot(a, blockIdx.x);
+  const int i = batch_slot(a, blockIdx.x);
+  const int slot = a.slot0 + i;
   const SlotDyn& d = batch_dyn(a, slot);
   if (d.mode == kSlotIdle) return;
   const TrackParams& tp = a.slots[slot].tp[0];
   const int w = tp.g.w, h = tp.g.h;
   const int cs = 1 - tp.ctrl->ref_index;
-  const int t = blockIdx.x - __ldg(a.start + slot);
+  const int t = blockIdx.x - __ldg(a.start + i);
   const int gx = (w + kCopyTileW - 1) / kCopyTileW;
   const int x = (t % gx) * kCopyTileW + threadIdx.x * 4;
   const int y = (t / gx) * kCopyTileH + threadIdx.y;
@@ -94,11 +88,10 @@ template <typename T>
 __device__ __forceinline__ void normal_px(const LevelMaps& m, int set, const LevelGeom& g,
                                           float dmin, float dmax, int x, int y) {
   const float* D = m.depth[set];
-  T* N = reinterpret_cast<T*>(m.normal[set]);
-  const int64_t o = (int64_t)y * g.w + x;
+  const int o = y * g.w + x;
+  const float d0 = __ldg(D + o);
   float nx = 0.f, ny = 0.f, nz = 0.f;
   if (x + 1 < g.w && y + 1 < g.h) {
-    const float d0 = __ldg(D + o);
     const float d1 = __ldg(D + o + 1);
     const float d2 = __ldg(D + o + g.w);
     const bool ok = d0 >= dmin && d0 <= dmax && d1 >= dmin && d1 <= dmax && d2 >= dmin && d2 <= dmax;
@@ -133,32 +126,29 @@ __device__ __forceinline__ void normal_px(const LevelMaps& m, int set, const Lev
       }
     }
   }
-  store_map<T>(N, o, nx);
-  store_map<T>(N, o + m.plane, ny);
-  store_map<T>(N, o + 2 * m.plane, nz);
+  Packs<T>::store_a(m.packA[set], o, nx, ny, nz, d0);
 }
 
 template <typename T>
 __device__ __forceinline__ void gradient_px(const LevelMaps& m, int set, int w, int h, int x, int y) {
   const float* I = m.inten[set];
-  T* G = reinterpret_cast<T*>(m.grad[set]);
-  const int64_t o = (int64_t)y * w + x;
+  const int o = y * w + x;
   float gx = 0.f, gy = 0.f;
   if (x > 0 && y > 0 && x + 1 < w && y + 1 < h) {
     gx = 0.5f * (__ldg(I + o + 1) - __ldg(I + o - 1));
     gy = 0.5f * (__ldg(I + o + w) - __ldg(I + o - w));
   }
-  store_map<T>(G, o, gx);
-  store_map<T>(G, o + m.plane, gy);
+  Packs<T>::store_b(m.packB[set], o, __ldg(I + o), gx, gy);
 }
 
 // Block -> (slot, 32 x 8 tile of the slot's level-`a.level` image); false for an
 // idle slot or a thread outside the image.
 __device__ __forceinline__ bool map_pixel(const BatchArgs& a, int* slot, int* x, int* y) {
-  *slot = batch_slot(a, blockIdx.x);
+  const int i = batch_slot(a, blockIdx.x);
+  *slot = a.slot0 + i;
   if (batch_dyn(a, *slot).mode == kSlotIdle) return false;
   const LevelGeom& g = a.slots[*slot].tp[a.level].g;
-  const int t = blockIdx.x - __ldg(a.start + *slot);
+  const int t = blockIdx.x - __ldg(a.start + i);
   const int gx = (g.w + kMapTileW - 1) / kMapTileW;
   *x = (t % gx) * kMapTileW + threadIdx.x;
   *y = (t / gx) * kMapTileH + threadIdx.y;

@@ -41,14 +41,14 @@ constexpr size_t na_align(size_t v) { return (v + kAlignNA - 1) / kAlignNA * kAl
 
 constexpr int64_t kPlane = (kNoallocMaxPixels + 63) / 64 * 64;
 constexpr size_t kOffCtrl = 0;
-constexpr size_t kOffNormal0 = na_align(kOffCtrl + sizeof(Ctrl));
-constexpr size_t kOffNormal1 = na_align(kOffNormal0 + 3 * kPlane * sizeof(float));
-constexpr size_t kOffGrad = na_align(kOffNormal1 + 3 * kPlane * sizeof(float));
+constexpr size_t kOffPackA0 = na_align(kOffCtrl + sizeof(Ctrl));       // reference normals + depth
+constexpr size_t kOffPackA1 = na_align(kOffPackA0 + kPlane * 16);         // live normals + depth
+constexpr size_t kOffPackB = na_align(kOffPackA1 + kPlane * 16);          // reference intensity + gradient
 // one row per thread: at most ceil(320/32) * ceil(240/4) blocks
 constexpr int kNoallocMaxBlocks = ((kNoallocMaxW + kTrackThreadsX - 1) / kTrackThreadsX) *
                                   ((kNoallocMaxH + kTrackRows - 1) / kTrackRows);
 constexpr int kNoallocMaxGroups = (kNoallocMaxBlocks + kFoldGroup - 1) / kFoldGroup;
-constexpr size_t kOffCounters = na_align(kOffGrad + 2 * kPlane * sizeof(float));
+constexpr size_t kOffCounters = na_align(kOffPackB + kPlane * 16);
 constexpr size_t kOffPartials = na_align(kOffCounters + (1 + kNoallocMaxGroups) * sizeof(uint32_t));
 constexpr size_t kOffGPartials = na_align(kOffPartials + (size_t)kNoallocMaxBlocks * kSumsAll * sizeof(double));
 constexpr size_t kNoallocBytes = na_align(kOffGPartials + (size_t)kNoallocMaxGroups * kSumsAll * sizeof(double));
@@ -194,15 +194,14 @@ extern "C" int dri_linearise_pair_noalloc(const dri_stream_config* cfg, const fl
   LevelGeom g = level_geom(*cfg, 0);
   LevelMaps m;
   std::memset(&m, 0, sizeof(m));
-  m.plane = kPlane;
   m.depth[0] = const_cast<float*>(ref_depth);      // set 0: reference
   m.inten[0] = const_cast<float*>(ref_intensity);
   m.depth[1] = const_cast<float*>(live_depth);     // set 1: live frame
   m.inten[1] = const_cast<float*>(live_intensity);
-  m.normal[0] = base + kOffNormal0;
-  m.normal[1] = base + kOffNormal1;
-  m.grad[0] = base + kOffGrad;
-  m.grad[1] = base + kOffGrad;                      // the live set's gradient is never read
+  m.packA[0] = base + kOffPackA0;
+  m.packA[1] = base + kOffPackA1;
+  m.packB[0] = base + kOffPackB;
+  m.packB[1] = base + kOffPackB;                    // the live set's pack B is never read
 
   uint32_t* counters = reinterpret_cast<uint32_t*>(base + kOffCounters);
   k_noalloc_begin<<<1, 32, 0, s>>>(ctrl, counters, dstate_of(*x_ref), dstate_of(*x0), dstate_of(*x1));

@@ -1179,7 +1179,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_linearise_end(SolveParams sp,
 // block, level and last-iteration flag, copied to shared memory; returns the
 // slot's mode (uniform over the block).
 __device__ int load_slot_params(const BatchArgs& a, SolveParams& sp) {
-  const int slot = blockIdx.x;
+  const int slot = a.slot0 + blockIdx.x;
   const SlotDyn& d = batch_dyn(a, slot);
   const int mode = d.mode;
   if (mode == kSlotIdle) return mode;
@@ -1219,8 +1219,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_frame_end_batch(const BatchAr
 
 // Result heads of all slots into one contiguous buffer (one copy to the host).
 __global__ void k_gather_heads(const BatchArgs a, unsigned char* __restrict__ out) {
-  const uint64_t* src = reinterpret_cast<const uint64_t*>(a.slots[blockIdx.x].sp.ctrl);
-  uint64_t* dst = reinterpret_cast<uint64_t*>(out + (size_t)blockIdx.x * kCtrlHeadBytes);
+  const int slot = a.slot0 + blockIdx.x;
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(a.slots[slot].sp.ctrl);
+  uint64_t* dst = reinterpret_cast<uint64_t*>(out + (size_t)slot * kCtrlHeadBytes);
   for (int i = threadIdx.x; i < (int)(kCtrlHeadBytes / 8); i += blockDim.x) dst[i] = src[i];
 }
 

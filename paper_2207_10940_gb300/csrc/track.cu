@@ -5,10 +5,13 @@
 // Block: 8 warps over a tile of 32 columns x 4 * ppt rows.  Warps 0-3 evaluate
 // the ICP term and warps 4-7 the photometric term of the same pixels (warp w and
 // w + 4 take rows w, w + 4, w + 8, ... of the tile), so each thread carries the
-// 29 sums of one term only: half the registers of a thread that does both, twice
-// the warps resident per SM to hide the latency of the dependent gathers.  A warp
-// reads 128 contiguous bytes per map plane; each thread loads its next row's
-// live-frame samples before it works on the current one.  Per pixel, in FP32:
+// 29 sums of one term only: half the registers of a thread that does both, more
+// warps resident per SM to hide the latency of the dependent gathers.  Each
+// gather is one vector load of a per-pixel pack (packs.cuh): the ICP term reads
+// pack A (normal + depth) of the live pixel and of the associated reference
+// pixel, the photometric term the live depth and intensity and four pack-B taps
+// (intensity + gradient) of the reference.  Each thread loads its next row's
+// live samples before it works on the current one.  Per pixel, in FP32:
 //
 //   p   = d K^-1 [u, v, 1]^T                       live point, camera frame C1
 //   ICP: D = A_ref p + t_ref  with A_ref = R_ref^T R_1 - I, t_ref = R_ref^T (r_1 - r_ref),
@@ -35,19 +38,11 @@
 #include <cuda_fp16.h>
 
 #include "dri_internal.h"
+#include "packs.cuh"
 
 namespace dri {
 
 namespace {
-
-template <typename T>
-__device__ __forceinline__ float load_map(const T* p, int64_t i);
-template <>
-__device__ __forceinline__ float load_map<float>(const float* p, int64_t i) { return __ldg(p + i); }
-template <>
-__device__ __forceinline__ float load_map<__half>(const __half* p, int64_t i) {
-  return __half2float(__ldg(p + i));
-}
 
 __device__ __forceinline__ void accumulate(float* a, const float* J, float e) {
   int k = 0;
@@ -64,6 +59,15 @@ __device__ __forceinline__ void accumulate(float* a, const float* J, float e) {
   a[28] += 1.f;
 }
 
+// Rows ahead of the current one whose live and reference samples (at the same
+// pixel) each thread asks L2 to fetch: the gathers of a later row then find
+// their lines in L2 instead of waiting on HBM (0: none).
+constexpr int kPrefetchRows = 4;
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Live-frame samples of one pixel: depth and the term's own map (the normal for
 // ICP, the intensity for the photometric term).
 struct Live {
@@ -73,8 +77,8 @@ struct Live {
 // ICP term (Eq. 4) of the pixel (u, v) with live depth d and normal n1.
 template <typename T>
 __device__ __forceinline__ bool icp_pixel(const TrackParams& p, const LevelGeom& g, const float* A,
-                                          const float* t, const float* __restrict__ D0,
-                                          const T* __restrict__ N0, int u, int v, const Live& L,
+                                          const float* t, const void* __restrict__ A0,
+                                          const float* __restrict__ D0, int u, int v, const Live& L,
                                           float* acc) {
   const float n1x = L.a, n1y = L.b, n1z = L.c;
   if (n1x == 0.f && n1y == 0.f && n1z == 0.f) return false;
@@ -87,18 +91,16 @@ __device__ __forceinline__ bool icp_pixel(const TrackParams& p, const LevelGeom&
   const float ez = fmaf(A[6], px, fmaf(A[7], py, fmaf(A[8], pz, t[2])));
   const float z = d + ez;
   if (!(z > 0.f)) return false;
-  const float iz = 1.f / z;
+  const float iz = __fdividef(1.f, z);
   const float sxp = g.fx * (fmaf(-rx, ez, ex) * iz);
   const float syp = g.fy * (fmaf(-ry, ez, ey) * iz);
   const bool sane = fabsf(sxp) < 1e7f && fabsf(syp) < 1e7f;   // int conversion in range
   const int xi = sane ? u + (int)floorf(sxp + 0.5f) : -1;
   const int yi = sane ? v + (int)floorf(syp + 0.5f) : -1;
   if (xi < 0 || xi >= g.w || yi < 0 || yi >= g.h) return false;
-  const int64_t q = (int64_t)yi * g.w + xi;
-  const int64_t plane = p.m.plane;
-  const float Nx = load_map(N0, q), Ny = load_map(N0, plane + q), Nz = load_map(N0, 2 * plane + q);
+  const float4 n0 = Packs<T>::load_a(A0, D0, yi * g.w + xi);   // N (x, y, z), reference depth
+  const float Nx = n0.x, Ny = n0.y, Nz = n0.z, dr = n0.w;
   if (Nx == 0.f && Ny == 0.f && Nz == 0.f) return false;
-  const float dr = __ldg(D0 + q);
   const float Vx = dr * (((float)xi - g.cx) * g.ifx), Vy = dr * (((float)yi - g.cy) * g.ify);
   const float dx = (px - Vx) + ex, dy = (py - Vy) + ey, dz = (pz - dr) + ez;
   const float dist2 = dx * dx + dy * dy + dz * dz;
@@ -116,9 +118,8 @@ __device__ __forceinline__ bool icp_pixel(const TrackParams& p, const LevelGeom&
 
 // Photometric term (Eq. 3) of the pixel (u, v) with live depth d and intensity i1.
 template <typename T>
-__device__ __forceinline__ bool rgb_pixel(const TrackParams& p, const LevelGeom& g, const float* A,
-                                          const float* t, const float* __restrict__ I0,
-                                          const T* __restrict__ G0, int u, int v, const Live& L,
+__device__ __forceinline__ bool rgb_pixel(const LevelGeom& g, const float* A, const float* t,
+                                          const void* __restrict__ B0, int u, int v, const Live& L,
                                           float* acc) {
   const float d = L.d;
   const float rx = ((float)u - g.cx) * g.ifx;
@@ -129,7 +130,7 @@ __device__ __forceinline__ bool rgb_pixel(const TrackParams& p, const LevelGeom&
   const float ez = fmaf(A[6], px, fmaf(A[7], py, fmaf(A[8], pz, t[2])));
   const float z = d + ez;
   if (!(z > 0.f)) return false;
-  const float iz = 1.f / z;
+  const float iz = __fdividef(1.f, z);
   // displacement of the projection from (u, v): small, so FP32 keeps it to
   // ~1e-6 px, and integer parts of the position stay exact
   const float sxp = g.fx * (fmaf(-rx, ez, ex) * iz);
@@ -139,16 +140,14 @@ __device__ __forceinline__ bool rgb_pixel(const TrackParams& p, const LevelGeom&
   const int xb = sane ? u + (int)fxp : -1, yb = sane ? v + (int)fyp : -1;
   if (xb < 0 || xb >= g.w - 1 || yb < 0 || yb >= g.h - 1) return false;
   const float ax = sxp - fxp, ay = syp - fyp;
-  const int64_t q = (int64_t)yb * g.w + xb;
-  const int64_t plane = p.m.plane;
+  const int q = yb * g.w + xb;
+  const float3 s00 = Packs<T>::load_b(B0, q), s01 = Packs<T>::load_b(B0, q + 1);
+  const float3 s10 = Packs<T>::load_b(B0, q + g.w), s11 = Packs<T>::load_b(B0, q + g.w + 1);
   const float w00 = (1.f - ax) * (1.f - ay), w01 = ax * (1.f - ay);
   const float w10 = (1.f - ax) * ay, w11 = ax * ay;
-  const float iv = w00 * __ldg(I0 + q) + w01 * __ldg(I0 + q + 1) + w10 * __ldg(I0 + q + g.w) +
-                   w11 * __ldg(I0 + q + g.w + 1);
-  const float gx = w00 * load_map(G0, q) + w01 * load_map(G0, q + 1) + w10 * load_map(G0, q + g.w) +
-                   w11 * load_map(G0, q + g.w + 1);
-  const float gy = w00 * load_map(G0, plane + q) + w01 * load_map(G0, plane + q + 1) +
-                   w10 * load_map(G0, plane + q + g.w) + w11 * load_map(G0, plane + q + g.w + 1);
+  const float iv = w00 * s00.x + w01 * s01.x + w10 * s10.x + w11 * s11.x;
+  const float gx = w00 * s00.y + w01 * s01.y + w10 * s10.y + w11 * s11.y;
+  const float gy = w00 * s00.z + w01 * s01.z + w10 * s10.z + w11 * s11.z;
   const float e = iv - L.a;
   const float a0 = g.fx * gx * iz, a1 = g.fy * gy * iz;
   const float a2 = -(gx * (((float)u - g.cx) + sxp) + gy * (((float)v - g.cy) + syp)) * iz;
@@ -172,14 +171,12 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int bx, c
   const int rs = ctrl->ref_index;
   const int cs = 1 - rs;
   const LevelGeom g = p.g;
-  const int64_t plane = p.m.plane;
   const float* __restrict__ D1 = p.m.depth[cs];
   const float* __restrict__ I1 = p.m.inten[cs];
-  const T* __restrict__ N1 = reinterpret_cast<const T*>(p.m.normal[cs]);
+  const void* __restrict__ A1 = p.m.packA[cs];
   const float* __restrict__ D0 = p.m.depth[rs];
-  const float* __restrict__ I0 = p.m.inten[rs];
-  const T* __restrict__ N0 = reinterpret_cast<const T*>(p.m.normal[rs]);
-  const T* __restrict__ G0 = reinterpret_cast<const T*>(p.m.grad[rs]);
+  const void* __restrict__ A0 = p.m.packA[rs];
+  const void* __restrict__ B0 = p.m.packB[rs];
 
   float A[9], t[3];
   const float* xf = icp ? ctrl->xf_icp : ctrl->xf_rgb;
@@ -200,13 +197,15 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int bx, c
     Live L = {0.f, 0.f, 0.f, 0.f};
     const int v = (by * p.ppt + r) * kTrackRows + wrow;
     if (col_ok && v < g.h) {
-      const int64_t o = (int64_t)v * g.w + u;
-      L.d = __ldg(D1 + o);
+      const int o = v * g.w + u;
       if (icp) {
-        L.a = load_map(N1, o);
-        L.b = load_map(N1, plane + o);
-        L.c = load_map(N1, 2 * plane + o);
+        const float4 a = Packs<T>::load_a(A1, D1, o);
+        L.d = a.w;
+        L.a = a.x;
+        L.b = a.y;
+        L.c = a.z;
       } else {
+        L.d = Packs<T>::depth(A1, D1, o);
         L.a = __ldg(I1 + o);
       }
     }
@@ -217,16 +216,28 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int bx, c
   for (int r = 0; r < p.ppt; ++r) {
     const Live nxt = r + 1 < p.ppt ? load_live(r + 1) : Live{0.f, 0.f, 0.f, 0.f};
     const int v = (by * p.ppt + r) * kTrackRows + wrow;
+    if (kPrefetchRows > 0 && r + kPrefetchRows < p.ppt) {
+      const int vf = v + kPrefetchRows * kTrackRows;
+      if (col_ok && vf < g.h) {
+        const int of = vf * g.w + u;
+        if (icp) {
+          prefetch_l2(static_cast<const char*>(A1) + (size_t)of * Packs<T>::kBytesA);
+          prefetch_l2(static_cast<const char*>(A0) + (size_t)of * Packs<T>::kBytesA);
+        } else {
+          prefetch_l2(I1 + of);
+          prefetch_l2(static_cast<const char*>(B0) + (size_t)of * Packs<T>::kBytesB);
+        }
+      }
+    }
     bool ok = false;
     if (col_ok && v < g.h && cur.d >= dmin && cur.d <= dmax) {
-      ok = icp ? icp_pixel<T>(p, g, A, t, D0, N0, u, v, cur, acc)
-               : rgb_pixel<T>(p, g, A, t, I0, G0, u, v, cur, acc);
+      ok = icp ? icp_pixel<T>(p, g, A, t, A0, D0, u, v, cur, acc)
+               : rgb_pixel<T>(g, A, t, B0, u, v, cur, acc);
     }
     if (FLAGS) {             // bit 0 ICP, bit 1 photometric, combined through shared memory
       if (icp) s_flag[wrow][lane] = ok ? 1 : 0;
       __syncthreads();
-      if (!icp && col_ok && v < g.h)
-        p.flags[(int64_t)v * g.w + u] = (uint8_t)(s_flag[wrow][lane] | (ok ? 2 : 0));
+      if (!icp && col_ok && v < g.h) p.flags[v * g.w + u] = (uint8_t)(s_flag[wrow][lane] | (ok ? 2 : 0));
       __syncthreads();
     }
     cur = nxt;
@@ -307,9 +318,10 @@ k_track(TrackParams p) {
 // Tiles of every tracking slot at one level: block -> (slot, tile) through the
 // block prefix, tile -> (column, row band) in the slot's image.
 template <typename T, typename P>
-__global__ void __launch_bounds__(kTrackThreadsX * kTrackThreadsY, 3)
+__global__ void __launch_bounds__(kTrackThreadsX * kTrackThreadsY, 4)
 k_track_batch(const BatchArgs a) {
-  const int slot = batch_slot(a, blockIdx.x);
+  const int i = batch_slot(a, blockIdx.x);
+  const int slot = a.slot0 + i;
   if (batch_dyn(a, slot).mode != kSlotTrack) return;
   // the slot's parameters, staged once per block in shared memory
   __shared__ TrackParams p;
@@ -318,7 +330,7 @@ k_track_batch(const BatchArgs a) {
     reinterpret_cast<uint32_t*>(&p)[tid] =
         __ldg(reinterpret_cast<const uint32_t*>(&a.slots[slot].tp[a.level]) + tid);
   __syncthreads();
-  const int t = blockIdx.x - __ldg(a.start + slot);
+  const int t = blockIdx.x - __ldg(a.start + i);
   const int gx = (p.g.w + kTrackThreadsX - 1) / kTrackThreadsX;
   track_tile<T, P, false>(p, t % gx, t / gx, t);
 }

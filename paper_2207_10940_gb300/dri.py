@@ -93,6 +93,11 @@ class dri_profile(ctypes.Structure):
                 ("pixels", ctypes.c_double * DRI_KC_COUNT)]
 
 
+class dri_batch_options(ctypes.Structure):
+    _fields_ = [("rows_per_thread", ctypes.c_int32 * DRI_MAX_LEVELS), ("groups", ctypes.c_int32),
+                ("autotune", ctypes.c_int32)]
+
+
 class DriError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -127,7 +132,10 @@ def load_library():
         "dri_push_imu": (ctypes.c_int, [ctypes.c_void_p, P(dri_imu_sample), ctypes.c_size_t]),
         "dri_track": (ctypes.c_int, [ctypes.c_void_p, P(dri_track_result)]),
         "dri_track_batch": (ctypes.c_int, [P(ctypes.c_void_p), ctypes.c_int32, P(dri_track_result)]),
-        "dri_batch_tiles": (ctypes.c_int, [P(ctypes.c_void_p), ctypes.c_int32, P(ctypes.c_int32)]),
+        "dri_batch_get_options": (ctypes.c_int, [P(ctypes.c_void_p), ctypes.c_int32,
+                                                 P(dri_batch_options)]),
+        "dri_batch_set_options": (ctypes.c_int, [P(ctypes.c_void_p), ctypes.c_int32,
+                                                 P(dri_batch_options)]),
         "dri_get_state": (ctypes.c_int, [ctypes.c_void_p, P(dri_state), c_double_p, c_double_p]),
         "dri_set_state": (ctypes.c_int, [ctypes.c_void_p, P(dri_state), c_double_p, c_double_p]),
         "dri_linearise": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, P(dri_state), P(dri_state),
@@ -268,12 +276,31 @@ def dri_track_batch(streams, wait=True):
     return list(res)
 
 
-def dri_batch_tiles(streams):
-    """Rows per thread of the pixel kernel per level for this stream list's plan."""
-    arr = _handles(streams)
-    out = (ctypes.c_int32 * DRI_MAX_LEVELS)()
-    _check(load_library().dri_batch_tiles(arr, len(streams), out), "dri_batch_tiles")
-    return list(out)
+def dri_batch_get_options(streams):
+    out = dri_batch_options()
+    _check(load_library().dri_batch_get_options(_handles(streams), len(streams), ctypes.byref(out)),
+           "dri_batch_get_options")
+    return out
+
+
+def dri_batch_set_options(streams, rows_per_thread=None, groups=None, autotune=None):
+    """Updates the given fields of this stream list's plan options."""
+    try:
+        opt = dri_batch_get_options(streams)
+    except DriError:
+        opt = dri_batch_options()
+        opt.groups = 1
+        opt.autotune = 0 if len(streams) == 1 else 1
+    if rows_per_thread is not None:
+        rows = list(rows_per_thread) + [1] * (DRI_MAX_LEVELS - len(rows_per_thread))
+        opt.rows_per_thread[:] = rows
+        opt.autotune = 0
+    if groups is not None:
+        opt.groups = int(groups)
+    if autotune is not None:
+        opt.autotune = int(autotune)
+    _check(load_library().dri_batch_set_options(_handles(streams), len(streams), ctypes.byref(opt)),
+           "dri_batch_set_options")
 
 
 def dri_get_state(s, with_prior=False):

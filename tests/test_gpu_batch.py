@@ -62,8 +62,9 @@ def test_batch_matches_streams_tracked_alone():
         res = dri.dri_track_batch(batch)
         assert [r.status for r in res] == [0] * len(batch)
         assert [r.initialised for r in res] == [int(i == 0)] * len(batch)
-    ppt = dri.dri_batch_tiles(batch)
-    assert all(p in (1, 2, 3, 4, 6, 8) for p in ppt[:3])
+    opts = dri.dri_batch_get_options(batch)
+    assert all(p in (1, 2, 3, 4, 6, 8) for p in opts.rows_per_thread[:3])
+    assert opts.groups == 1 and opts.autotune == 0
     for st, (xa, Ha, ba) in zip(batch, alone):
         xb, Hb, bb = dri.dri_get_state(st.handle, with_prior=True)
         da, dr = pose_error(xa, xb)
@@ -160,3 +161,47 @@ def test_batch_rejects_mismatched_streams():
     assert e.value.code == dri.DRI_EINVAL
     for s in (a, b, c, d):
         s.close()
+
+
+def test_fixed_tiles_give_identical_bits_for_any_group_count():
+    """With the rows per thread fixed, the result does not depend on how many
+    slot groups (CUDA streams) run the Gauss-Newton loop: every slot sums the
+    same pixels in the same order, so the states are bit-identical."""
+    torch = _torch()
+    seqs = _sequences(3)
+    results = []
+    for groups in (1, 2, 3):
+        batch = _streams(seqs, torch.cuda.Stream())
+        dri.dri_batch_set_options(batch, rows_per_thread=[2, 2, 1], groups=groups)
+        opts = dri.dri_batch_get_options(batch)
+        assert opts.groups == groups and opts.autotune == 0
+        assert list(opts.rows_per_thread) == [2, 2, 1, 0]
+        for i in range(3):
+            for st, seq in zip(batch, seqs):
+                dri.dri_upload_frame(st.handle, seq.frame_times[i], seq.depth[i], seq.intensity[i])
+            assert [r.status for r in dri.dri_track_batch(batch)] == [0] * len(batch)
+        results.append([dri.dri_get_state(st.handle, with_prior=True) for st in batch])
+        for st in batch:
+            st.close()
+    for other in results[1:]:
+        for (xa, Ha, ba), (xb, Hb, bb) in zip(results[0], other):
+            a, b = dri.state_to_dict(xa), dri.state_to_dict(xb)
+            for k in a:
+                np.testing.assert_array_equal(a[k], b[k])
+            np.testing.assert_array_equal(Ha, Hb)
+            np.testing.assert_array_equal(ba, bb)
+
+
+def test_batch_options_are_checked():
+    torch = _torch()
+    seqs = _sequences(2)[:2]
+    batch = _streams(seqs, torch.cuda.Stream())
+    for kw in ({"groups": 0}, {"groups": 3}, {"rows_per_thread": [0, 1, 1]},
+               {"rows_per_thread": [65, 1, 1]}):
+        with pytest.raises(dri.DriError) as e:
+            dri.dri_batch_set_options(batch, **kw)
+        assert e.value.code == dri.DRI_EINVAL
+    own = dri.dri_batch_get_options([batch[0]])        # a stream's own plan
+    assert own.groups == 1 and own.autotune == 0
+    for st in batch:
+        st.close()
