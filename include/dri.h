@@ -222,6 +222,69 @@ int dri_batch_get_options(const dri_stream* streams, int32_t n, dri_batch_option
  * DRI_EINVAL for a bad list or value. */
 int dri_batch_set_options(const dri_stream* streams, int32_t n, const dri_batch_options* opt);
 
+/* ---- serving loop --------------------------------------------------------
+ * A server tracks many independent camera streams on one GPU by continuous
+ * batching (the paper tracks one camera; this is the library's serving mode).
+ * Streams are admitted while the device bytes of all admitted streams
+ * (workspace + 64 KB of plan state each) stay within hbm_budget_bytes;
+ * all of a server's streams share levels, iterations and precision flags.
+ * Requests (a frame with the IMU samples since the stream's previous frame)
+ * are submitted from any thread; a worker thread takes the oldest request of
+ * each stream, at most max_batch streams per tick, and tracks them in one
+ * batched launch sequence (dri_track_batch's plan over all the server's
+ * streams; streams without a request sit the tick out).  Two ticks may be on
+ * the GPU at once: requests that arrive while one runs go into the next. */
+typedef struct dri_server_s* dri_server;
+
+/* Creates a server; cuda_stream orders all its work (NULL = legacy default
+ * stream: no CUDA-graph replay).  DRI_EINVAL for a zero budget or max_batch
+ * outside 1..4096. */
+int dri_server_create(size_t hbm_budget_bytes, int32_t max_batch, void* cuda_stream, dri_server* out);
+
+/* Finishes every submitted request, closes every stream, frees the server. */
+int dri_server_destroy(dri_server srv);
+
+/* Admits and creates a stream (as dri_create_stream, library-allocated
+ * workspace, the server's cuda_stream).  DRI_EADMIT if it would exceed the
+ * budget; DRI_EINVAL if its levels, iterations or precision flags differ from
+ * the server's first stream.  The handle is driven by the server only: use
+ * it with dri_server_submit / dri_server_close_stream, and for reads
+ * (dri_get_state) only while none of its requests is pending. */
+int dri_server_open_stream(dri_server srv, const dri_stream_config* cfg, const dri_state* x_init,
+                           dri_stream* out);
+
+/* Waits until the stream's submitted requests are done, then destroys it and
+ * returns its bytes to the budget. */
+int dri_server_close_stream(dri_server srv, dri_stream s);
+
+/* Queues the frame at time t of stream s (images as in dri_upload_frame; they
+ * are read when the request's tick runs, so the caller keeps them unchanged
+ * until the ticket is done) with the n_imu samples (copied here) that extend
+ * the stream's IMU record to t.  *ticket identifies the request. */
+int dri_server_submit(dri_server srv, dri_stream s, double t, const float* depth,
+                      const float* intensity, size_t pitch_bytes, int32_t mem_kind,
+                      const dri_imu_sample* imu, size_t n_imu, uint64_t* ticket);
+
+/* Waits up to timeout_ms (< 0: without limit; 0: just checks) for the
+ * request; returns DRI_ETIMEDOUT if it is not done, else fills *out (nullable)
+ * and returns the request's status (DRI_OK, DRI_ELOST, DRI_ENOTREADY when its
+ * IMU samples did not cover the frame, or the upload's error); a done ticket
+ * is released by this call. */
+int dri_server_poll(dri_server srv, uint64_t ticket, dri_track_result* out, int32_t timeout_ms);
+
+typedef struct {
+    int64_t submitted, completed, failed, ticks;
+    double mean_batch;             /* requests per tick                              */
+    double p50_ms, p99_ms, max_ms; /* submit-to-done latency of completed requests   */
+    double frames_per_s;           /* completed / (last done - first submit)         */
+    size_t hbm_used, hbm_budget;
+    int32_t streams;
+    int32_t reserved;
+} dri_server_stats;
+
+/* Counters since creation or the last reset (reset = 1 clears them). */
+int dri_server_stats_read(dri_server srv, int32_t reset, dri_server_stats* out);
+
 /* Waits for the stream and copies out x1 and, when non-NULL, the prior
  * H* (17 x 17, row-major) and b* (17) that the next frame will use. */
 int dri_get_state(dri_stream s, dri_state* x1, double* H_prior, double* b_prior);

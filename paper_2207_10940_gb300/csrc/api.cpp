@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "dri_internal.h"
+#include "host.h"
 
 using namespace dri;
 
@@ -215,92 +216,7 @@ StreamLayout make_layout(const dri_stream_config& cfg) {
 
 }  // namespace dri
 
-struct Plan;
-
-struct dri_stream_s {
-  dri_stream_config cfg;
-  StreamLayout L;
-  cudaStream_t stream = nullptr;
-  char* ws = nullptr;
-  bool own_ws = false;
-  Ctrl* ctrl = nullptr;
-  float* in_depth = nullptr;
-  float* in_inten = nullptr;
-  void* partials = nullptr;
-  void* gpartials = nullptr;
-  uint32_t* counters = nullptr;
-  uint8_t* flags = nullptr;
-  dri_linearisation* lin_dev = nullptr;
-  LevelMaps maps[kMaxLevels];
-  LevelGeom geom[kMaxLevels];
-  int ppt[kMaxLevels];
-  DState x_init;
-  Plan* own = nullptr;              // one-slot plan of dri_track (in the workspace)
-  std::vector<Plan*> batches;       // batch plans this stream is a slot of
-  // host bookkeeping
-  std::vector<dri_imu_sample> imu;
-  bool initialised = false;         // host view: the init frame was enqueued
-  double t_prev = 0.0;              // time of the state the next frame starts from
-  double t_frame = 0.0;
-  bool frame_pending = false;
-  const float* src_depth = nullptr; // the pending frame's level-0 images on the device
-  const float* src_inten = nullptr;
-  int32_t src_pitch = 0;            // floats
-  int64_t h2d_frame = 0;            // bytes of the pending frame's host upload
-  Ctrl* pin_ctrl = nullptr;         // pinned copy of the whole control block
-  // frames in flight, settled in order once their result copy has completed
-  struct InFlight { cudaEvent_t ev; const Ctrl* head; };
-  std::deque<InFlight> inflight;
-  double t_confirmed = 0.0;         // time of the last state known to be good
-  int64_t frames_ok = 0, frames_failed = 0;
-  double t_prev_before = 0.0;       // t_prev before the last optimistic advance
-  int64_t launches = 0;
-  int64_t h2d_last = 0, d2h_last = 0;   // bytes copied for the last frame
-  // profiling: event pairs around launches
-  bool profiling = false;
-  std::vector<cudaEvent_t> ev_pool;
-  size_t ev_used = 0;
-  struct Rec { int cls; size_t e0, e1; double pixels; };
-  std::vector<Rec> recs;
-  dri_profile counted;
-};
-
-// The launch sequence of one frame over nslots streams: the device table of
-// the slots' static parameters, the staging ring, the captured graph.
-struct Plan {
-  std::vector<dri_stream_s*> slots;
-  cudaStream_t stream = nullptr;
-  int S = 0, levels = 0;
-  int iters[kMaxLevels] = {};
-  bool fp16 = false, fp32p = false;
-  bool owns_device = false;         // table / dyn / heads allocated by the plan
-  int groups = 1;                   // slot groups of the Gauss-Newton loop, one CUDA stream each
-  std::vector<int> gfirst, gcount;
-  std::vector<cudaStream_t> aux;    // streams of groups 1 .. groups - 1
-  cudaEvent_t ev_fork = nullptr;
-  std::vector<cudaEvent_t> ev_join;
-  char* table = nullptr;
-  TableView tv;
-  unsigned char* dyn = nullptr;
-  size_t dyn_cap = 0;
-  unsigned char* heads = nullptr;   // S result heads (batch plans)
-  std::vector<SlotStatic> host_slots;
-  std::vector<int32_t> pre_copy, pre_map[kMaxLevels], pre_track[kMaxLevels];
-  int R = 0;                        // staging ring
-  char* pin_dyn = nullptr;
-  char* pin_heads = nullptr;
-  std::vector<cudaEvent_t> ev;
-  std::vector<char> ring_used;
-  int next = 0;
-  cudaGraphExec_t graph = nullptr;
-  bool graph_failed = false;
-  bool autotune = false;            // choose rows per thread by timing, on the first tracked frame
-  bool tuned = false;
-  std::vector<std::array<int, kMaxLevels>> ppt;   // rows per thread of each slot's pixel kernel
-  int64_t kernels_per_frame = 0;
-};
-
-namespace {
+namespace dri_host {
 
 constexpr size_t kMaxTimed = 65536;
 
@@ -810,13 +726,6 @@ int plan_run(Plan* p, int64_t* kernels) {
   return plan_enqueue(p, 3, kernels);
 }
 
-// Per-slot decision for one launch of plan p.
-struct SlotWork {
-  int mode = kSlotIdle;
-  int status = DRI_ENOTREADY;       // result for a slot that does not run
-  size_t k0 = 0, k1 = 0;
-};
-
 SlotWork plan_slot_work(const dri_stream_s* s) {
   SlotWork w;
   if (!s->frame_pending) return w;
@@ -914,7 +823,21 @@ void forget_plan_locked(Plan* p) {
   g_batch_plans.erase(std::remove(g_batch_plans.begin(), g_batch_plans.end(), p), g_batch_plans.end());
 }
 
-}  // namespace
+void release_batch_plan(const std::vector<dri_stream_s*>& key) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (Plan* q : g_batch_plans) {
+    if (q->slots != key) continue;
+    cudaStreamSynchronize(q->stream);
+    for (dri_stream_s* o : q->slots) settle(o, true);
+    forget_plan_locked(q);
+    plan_free(q);
+    return;
+  }
+}
+
+}  // namespace dri_host
+
+using namespace dri_host;
 
 extern "C" {
 
@@ -1114,20 +1037,6 @@ int dri_push_imu(dri_stream s, const dri_imu_sample* samples, size_t n) {
   return DRI_OK;
 }
 
-static void fill_result(const dri_stream_s* s, const Ctrl* h, dri_track_result* out, bool init,
-                        double t0) {
-  std::memset(out, 0, sizeof(*out));
-  out->x1 = from_dstate(h->x, h->t_state);
-  out->x0 = from_dstate(h->x0, t0);
-  for (int l = 0; l < kMaxLevels; ++l) {
-    out->n_icp[l] = h->n_icp[l];
-    out->n_rgb[l] = h->n_rgb[l];
-  }
-  out->cost = h->cost;
-  out->status = h->status;
-  out->initialised = init ? 1 : 0;
-  (void)s;
-}
 
 int dri_track(dri_stream s, dri_track_result* out) {
   if (!s) return DRI_EINVAL;
@@ -1147,7 +1056,22 @@ int dri_track(dri_stream s, dri_track_result* out) {
 
 }  // extern "C"
 
-namespace {
+namespace dri_host {
+
+void fill_result(const dri_stream_s* s, const Ctrl* h, dri_track_result* out, bool init,
+                        double t0) {
+  std::memset(out, 0, sizeof(*out));
+  out->x1 = from_dstate(h->x, h->t_state);
+  out->x0 = from_dstate(h->x0, t0);
+  for (int l = 0; l < kMaxLevels; ++l) {
+    out->n_icp[l] = h->n_icp[l];
+    out->n_rgb[l] = h->n_rgb[l];
+  }
+  out->cost = h->cost;
+  out->status = h->status;
+  out->initialised = init ? 1 : 0;
+  (void)s;
+}
 
 // The plan of a stream list: a stream's own plan for one stream, else the
 // cached batch plan of exactly this list (created on first use).
@@ -1185,7 +1109,7 @@ int batch_plan(const dri_stream* streams, int32_t n, Plan** out) {
   return DRI_OK;
 }
 
-}  // namespace
+}  // namespace dri_host
 
 extern "C" {
 

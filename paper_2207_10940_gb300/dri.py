@@ -98,6 +98,14 @@ class dri_batch_options(ctypes.Structure):
                 ("autotune", ctypes.c_int32)]
 
 
+class dri_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("ticks", ctypes.c_int64), ("mean_batch", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("frames_per_s", ctypes.c_double), ("hbm_used", ctypes.c_size_t),
+                ("hbm_budget", ctypes.c_size_t), ("streams", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class DriError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -151,6 +159,19 @@ def load_library():
                                                       P(dri_state), ctypes.c_void_p, ctypes.c_void_p,
                                                       ctypes.c_void_p]),
         "dri_profile_read": (ctypes.c_int, [ctypes.c_void_p, P(dri_profile)]),
+        "dri_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int32, ctypes.c_void_p,
+                                             P(ctypes.c_void_p)]),
+        "dri_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+        "dri_server_open_stream": (ctypes.c_int, [ctypes.c_void_p, P(dri_stream_config), P(dri_state),
+                                                  P(ctypes.c_void_p)]),
+        "dri_server_close_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+        "dri_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                             ctypes.c_int32, P(dri_imu_sample), ctypes.c_size_t,
+                                             P(ctypes.c_uint64)]),
+        "dri_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, P(dri_track_result),
+                                           ctypes.c_int32]),
+        "dri_server_stats_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, P(dri_server_stats)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -446,3 +467,63 @@ class Stream:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# serving loop
+# ---------------------------------------------------------------------------
+
+def dri_server_create(hbm_budget_bytes, max_batch, cuda_stream=None):
+    cs = getattr(cuda_stream, "cuda_stream", cuda_stream)
+    h = ctypes.c_void_p()
+    _check(load_library().dri_server_create(int(hbm_budget_bytes), int(max_batch),
+                                            ctypes.c_void_p(cs or 0), ctypes.byref(h)),
+           "dri_server_create")
+    return h
+
+
+def dri_server_destroy(srv):
+    return _check(load_library().dri_server_destroy(srv), "dri_server_destroy")
+
+
+def dri_server_open_stream(srv, cfg, x_init):
+    h = ctypes.c_void_p()
+    _check(load_library().dri_server_open_stream(srv, ctypes.byref(cfg), ctypes.byref(x_init),
+                                                 ctypes.byref(h)), "dri_server_open_stream")
+    return h
+
+
+def dri_server_close_stream(srv, s):
+    return _check(load_library().dri_server_close_stream(srv, s), "dri_server_close_stream")
+
+
+def dri_server_submit(srv, s, t, depth, intensity, imu=(), pitch_bytes=0, mem_kind=None):
+    """Queues a frame; the images must stay alive until the ticket is done."""
+    if mem_kind is None:
+        mem_kind = DRI_DEVICE if (hasattr(depth, "is_cuda") and depth.is_cuda) else DRI_HOST
+    arr = imu if isinstance(imu, ctypes.Array) else (imu_array(imu) if len(imu) else None)
+    n = 0 if arr is None else len(arr)
+    ticket = ctypes.c_uint64()
+    _check(load_library().dri_server_submit(srv, s, float(t), ctypes.c_void_p(_ptr(depth)),
+                                            ctypes.c_void_p(_ptr(intensity)), pitch_bytes, mem_kind,
+                                            arr, n, ctypes.byref(ticket)), "dri_server_submit")
+    return ticket.value
+
+
+def dri_server_poll(srv, ticket, timeout_ms=-1):
+    """(status, dri_track_result) of a done request, or (DRI_ETIMEDOUT, None)."""
+    res = dri_track_result()
+    code = load_library().dri_server_poll(srv, ctypes.c_uint64(ticket), ctypes.byref(res),
+                                          int(timeout_ms))
+    if code == DRI_ETIMEDOUT:
+        return code, None
+    if code == DRI_EINVAL:
+        raise DriError(code, "dri_server_poll")
+    return code, res
+
+
+def dri_server_stats_read(srv, reset=False):
+    out = dri_server_stats()
+    _check(load_library().dri_server_stats_read(srv, int(bool(reset)), ctypes.byref(out)),
+           "dri_server_stats_read")
+    return out
