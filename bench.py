@@ -12,7 +12,11 @@ levels with 10/5/4 iterations.
 * batched (the headline, one step = one frame of each of 64 independent
   streams in one dri_track_batch call): stream i starts at frame 37 i mod 100
   of the loop, so a step reads 64 different frames;
-* plain (one step = one frame of a single stream, dri_track).
+* plain (one step = one frame of a single stream, dri_track);
+* served: 256 streams of mixed resolution (320x240, 640x480, 1280x720 by
+  stream id mod 3) submit frames at 30 Hz each with exponential arrival jitter
+  to the library's serving loop (dri_server_*); p50 / p99 submit-to-result
+  latency and completed frames/s are reported beside the batched number.
 
 Frames live on the device before timing starts; the 100 distinct frames
 (245 MB) exceed the 129 MB L2.  Output: one JSON line (rank 0).
@@ -401,6 +405,216 @@ def barrier(dev, world):
         torch.distributed.barrier()
 
 
+SERVE_STREAMS = 256
+SERVE_CLASSES = ((320, 240), (640, 480), (1280, 720))   # stream i: class i mod 3
+SERVE_LOOP = 30                                         # frames of each class's looping sequence
+SERVE_BUDGET = 120 << 30
+
+
+def _render_class(args):
+    from paper_2207_10940_gb300 import synth
+    c, i = args
+    seq = _serve_sequence(c, render=False)
+    return c, i, synth.render_frame(seq, i, seed=SERVE_SEED + c)
+
+
+SERVE_SEED = 500
+
+
+def _serve_sequence(c, render=False):
+    from paper_2207_10940_gb300 import synth
+    w, h = SERVE_CLASSES[c]
+    cam = {320: synth.CAM_320, 640: synth.CAM_640, 1280: synth.CAM_1280}[w]
+    return synth.sinusoid_sequence(seed=SERVE_SEED + c, cam=cam, n_frames=SERVE_LOOP, rate=400.0,
+                                   period_frames=SERVE_LOOP, render_frames=render)
+
+
+def served_pass(args, dev, workers):
+    """Serving loop: SERVE_STREAMS streams (resolution by id mod 3), 30 Hz each with
+    exponential arrival jitter, for args.serve_seconds of arrivals; frames on the
+    device, one client thread submitting on schedule and one polling tickets."""
+    import threading
+    import torch
+    from paper_2207_10940_gb300 import dri, synth
+    seqs = [_serve_sequence(c) for c in range(len(SERVE_CLASSES))]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        out = pool.map(_render_class, [(c, i) for c in range(len(SERVE_CLASSES)) for i in range(SERVE_LOOP)])
+    frames = [[None] * SERVE_LOOP for _ in SERVE_CLASSES]
+    for c, i, f in out:
+        frames[c][i] = f
+    D = [torch.stack([torch.from_numpy(f[0]) for f in fc]).to(dev) for fc in frames]
+    I = [torch.stack([torch.from_numpy(f[1]) for f in fc]).to(dev) for fc in frames]
+    torch.cuda.synchronize(dev)
+    secs = float(args.serve_seconds)
+    n_per = int(secs * FPS)
+    t_end = (SERVE_LOOP + n_per + 2) / FPS
+    imu = [synth.sequence_imu(s, t_end, seed=SERVE_SEED + c) for c, s in enumerate(seqs)]
+    imu_t = [m[:, 0] for m in imu]
+    ts = torch.cuda.Stream(dev)
+    srv = dri.dri_server_create(SERVE_BUDGET, SERVE_STREAMS, ts)
+    rng = np.random.default_rng(SERVE_SEED)
+    handles, cls, off = [], [], []
+    for i in range(SERVE_STREAMS):
+        c = i % len(SERVE_CLASSES)
+        o = (7 * i) % SERVE_LOOP
+        s = seqs[c]
+        cam = s.cam
+        cfg = dri.config_for(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, LEVELS, ITERS,
+                             q_CS=synth.matrix_to_quat(s.R_CS), r_CS=s.r_CS)
+        g = s.gt[o]
+        x0 = dict(t=o / FPS, r_WC=np.zeros(3), q_WC=np.array([1.0, 0, 0, 0]), v_I=g["v_I"].copy(),
+                  bg=np.zeros(3), ba=np.zeros(3), q_IW=synth.matrix_to_quat(g["R_IW"]))
+        handles.append(dri.dri_server_open_stream(srv, cfg, dri.state_from_dict(x0, o / FPS)))
+        cls.append(c)
+        off.append(o)
+    # arrival schedule: stream i's frame k at phase_i + k / 30 s + Exp(3 ms) jitter
+    phase = rng.uniform(0.0, 1.0 / FPS, SERVE_STREAMS)
+    events = []
+    for i in range(SERVE_STREAMS):
+        jit = np.minimum(rng.exponential(0.003, n_per), 0.02)
+        for k in range(n_per):
+            events.append((phase[i] + k / FPS + jit[k], i, k))
+    events.sort()
+    covering = []   # per class: index of the first sample at or after each frame time
+    for c in range(len(SERVE_CLASSES)):
+        ft = (np.arange(SERVE_LOOP + n_per + 1)) / FPS
+        covering.append(np.searchsorted(imu_t[c], ft))
+    tickets = []
+    lock = threading.Condition()
+    done_sub = [False]
+
+    def client():
+        t0 = time.perf_counter() + 0.2
+        for (ta, i, k) in events:
+            c, o = cls[i], off[i]
+            j = o + k                                  # global frame index of the class
+            lo = 0 if k == 0 else covering[c][j - 1] + 1
+            hi = covering[c][j] + 1
+            now = time.perf_counter()
+            if t0 + ta > now:
+                time.sleep(t0 + ta - now)
+            tk = dri.dri_server_submit(srv, handles[i], j / FPS, D[c][j % SERVE_LOOP],
+                                       I[c][j % SERVE_LOOP], imu[c][lo:hi])
+            with lock:
+                tickets.append(tk)
+                lock.notify()
+        with lock:
+            done_sub[0] = True
+            lock.notify()
+
+    statuses = []
+
+    def poller():
+        n = 0
+        while True:
+            with lock:
+                while n >= len(tickets) and not done_sub[0]:
+                    lock.wait()
+                if n >= len(tickets):
+                    return
+                tk = tickets[n]
+            statuses.append(dri.dri_server_poll(srv, tk, timeout_ms=-1)[0])
+            n += 1
+
+    th = [threading.Thread(target=client), threading.Thread(target=poller)]
+    t_start = time.perf_counter()
+    for t in th:
+        t.start()
+    time.sleep(min(2.0, secs / 4))
+    dri.dri_server_stats_read(srv, reset=True)      # latency after the warm-up (first frames, tuning)
+    for t in th:
+        t.join()
+    wall = time.perf_counter() - t_start
+    st = dri.dri_server_stats_read(srv)
+    bad = sum(1 for s in statuses if s != 0)
+    dri.dri_server_destroy(srv)
+    return {
+        "streams": SERVE_STREAMS, "mix": "stream i: " + ", ".join(f"{w}x{h}" for w, h in SERVE_CLASSES)
+        + " by i mod 3", "rate_hz_per_stream": FPS, "arrival_jitter": "exponential, mean 3 ms",
+        "seconds": secs, "offered_frames_per_s": SERVE_STREAMS * FPS,
+        "requests": len(events), "wall_s": wall, "value": st.frames_per_s, "unit": "frames/s",
+        "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "max_ms": st.max_ms, "failed": int(bad),
+        "mean_batch": st.mean_batch, "ticks": int(st.ticks), "hbm_used_gb": st.hbm_used / 1e9,
+        "hbm_budget_gb": SERVE_BUDGET / 1e9, "inputs": "device-resident frames (30-frame loops per "
+        "resolution, period-30 sinusoid), IMU copied per request",
+        "latency_from": "submit to result (warm-up excluded)"}
+
+
+PRECISION_VARIANTS = (("fp32_pixel_fp64_partials", 0), ("fp32_pixel_fp32_partials", 2),
+                      ("fp16_maps_fp64_partials", 1), ("fp16_maps_fp32_partials", 3))
+
+
+def _norm_errors(H_g, b_g, H_o, b_o, cost):
+    """max |dH_ij| / sqrt(H_ii H_jj) and max |db_i| / sqrt(H_ii C) (the parity
+    tolerance's normalisation, bar 1e-5)."""
+    H_g, b_g, H_o, b_o = (np.asarray(a, dtype=np.float64) for a in (H_g, b_g, H_o, b_o))
+    d = np.sqrt(np.maximum(np.diag(H_o), 1e-300))
+    eh = float(np.max(np.abs(H_g - H_o) / np.outer(d, d)))
+    eb = float(np.max(np.abs(b_g - b_o) / (d * np.sqrt(max(cost, 1e-300)))))
+    return eh, eb
+
+
+def precision_study(seq, frames, imu, dev, n_frames):
+    """Each precision variant against the exact FP64 oracle on the 640x480
+    sequence: the level-0 systems of frame 1 against frame 0 at the ground-truth
+    states, and the pose after tracking frames 0 .. n_frames - 1."""
+    import torch
+    from oracle import gn, imu as imu_mod, maps
+    from oracle.params import TrackerConfig
+    from oracle.so3 import State, log_so3
+    from paper_2207_10940_gb300 import dri, synth
+    cam = seq.cam
+    ocfg = TrackerConfig(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, levels=LEVELS,
+                         iters=ITERS, R_CS=seq.R_CS, r_CS=seq.r_CS)
+    x_init = synth.initial_state(seq)
+    tr = gn.Tracker(ocfg, x_init)
+    tr.push_imu(imu)
+    tr.track(frames[0][0], frames[0][1], 0.0)
+    x0, x1 = State.from_dict(seq.gt[0]), State.from_dict(seq.gt[1])
+    lv = maps.frame_levels(frames[1][0], frames[1][1], ocfg)
+    W, _ = imu_mod.weight(x0, tr.imu, 0.0, 1.0 / FPS, ocfg)
+    H_o, b_o, parts = tr.linearise_all(lv, 0, x0, x1, 0.0, 1.0 / FPS, W)
+    lin = parts["lin"]
+    t = time.perf_counter()
+    for i in range(1, n_frames):
+        x_o = tr.track(frames[i][0], frames[i][1], i / FPS)["x1"]
+    t_oracle = time.perf_counter() - t
+    out = {"workload": f"640x480 sinusoid sequence, frames 0-{n_frames - 1}; systems: level 0 of "
+                       f"frame 1 against frame 0 at the ground-truth states",
+           "oracle": "exact FP64 (maps not rounded)", "solve": "FP64 on the GPU in every variant",
+           "normalisation": "max |dH_ij|/sqrt(H_ii H_jj), max |db_i|/sqrt(H_ii C); bar 1e-5",
+           "oracle_track_s": t_oracle, "variants": {}}
+    for name, flags in PRECISION_VARIANTS:
+        cfg = dri_config(seq, flags)
+        st = dri.Stream(cfg, dri.state_from_dict(x_init), torch.cuda.Stream(dev))
+        dri.dri_push_imu(st.handle, imu)
+        dri.dri_upload_frame(st.handle, 0.0, frames[0][0], frames[0][1])
+        dri.dri_track(st.handle)
+        dri.dri_upload_frame(st.handle, 1.0 / FPS, frames[1][0], frames[1][1])
+        g, _ = dri.dri_linearise(st.handle, 0, dri.state_from_dict(x0.to_dict()),
+                                 dri.state_from_dict(x1.to_dict()))
+        e_icp = _norm_errors(np.array(g.H_icp).reshape(6, 6), g.b_icp, lin["H_icp"], lin["b_icp"],
+                             lin["cost_icp"])
+        e_rgb = _norm_errors(np.array(g.H_rgb).reshape(6, 6), g.b_rgb, lin["H_rgb"][6:, 6:],
+                             lin["b_rgb"][6:], lin["cost_rgb"])
+        e_joint = _norm_errors(np.array(g.H).reshape(34, 34), g.b, H_o, b_o,
+                               lin["cost_icp"] + lin["cost_rgb"] + parts["cost_imu"])
+        for i in range(1, n_frames):
+            dri.dri_upload_frame(st.handle, i / FPS, frames[i][0], frames[i][1])
+            r = dri.dri_track(st.handle)
+        xg = State.from_dict(dri.state_to_dict(r.x1))
+        out["variants"][name] = {
+            "flags": flags, "H_icp": e_icp[0], "b_icp": e_icp[1], "H_rgb": e_rgb[0], "b_rgb": e_rgb[1],
+            "H_joint": e_joint[0], "b_joint": e_joint[1],
+            "n_icp": int(g.n_icp), "n_icp_oracle": int(lin["n_icp"]),
+            "n_rgb": int(g.n_rgb), "n_rgb_oracle": int(lin["n_rgb"]),
+            "pose_err_rad": float(np.linalg.norm(log_so3(xg.R @ x_o.R.T))),
+            "pose_err_m": float(np.linalg.norm(xg.r - x_o.r)), "status": int(r.status)}
+        st.close()
+    return out
+
+
 def run_ours(args):
     rank, local, world = dist_env()
     plain_steps = args.plain_steps
@@ -452,6 +666,12 @@ def run_ours(args):
         run.close()
         del run
         torch.cuda.synchronize(dev)
+    served = None
+    if args.serve_seconds > 0:
+        served = served_pass(args, dev, min(16, os.cpu_count() or 4))
+    precision = None
+    if args.precision_frames > 1 and rank == 0:
+        precision = precision_study(seq, frames, imu, dev, args.precision_frames)
     if world > 1:
         torch.distributed.barrier()
     if rank != 0:
@@ -477,6 +697,8 @@ def run_ours(args):
                               "frames_ok", "frames_failed", "roofline", "kernel_classes", "e2e",
                               "rows_per_thread")},
         "batched_over_plain": None if p is None else b["value"] / p["value"],
+        "served": served,
+        "precision": precision,
         "cpu_baseline": {"value": o_fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
                          "sample": f"{o_n} whole frames of the same sequence tracked by the FP64 "
                                    f"numpy oracle in {o_t:.1f} s"},
@@ -495,6 +717,10 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=600,
                     help="frames of the plain single-stream pass (0: skip it)")
     ap.add_argument("--batch", type=int, default=BATCH, help="streams of the batched pass")
+    ap.add_argument("--precision-frames", type=int, default=3,
+                    help="frames of the precision study against the FP64 oracle (< 2: skip it)")
+    ap.add_argument("--serve-seconds", type=float, default=15.0,
+                    help="seconds of arrivals in the serving pass (0: skip it)")
     ap.add_argument("--rows-per-thread", type=lambda v: [int(x) for x in v.split(",")], default=None,
                     help="pixel-kernel rows per thread per level for the batched pass, e.g. 8,8,8 "
                          "(default: the plan's autotuner)")

@@ -122,7 +122,7 @@ class Tracker:
         if self.ref is None:                       # first frame: initialise only
             self.t = t
             self.T_ref = (self.x.R, self.x.r.copy())
-            self.ref = reference_from_frame(levels, *self.T_ref)
+            self.ref = reference_from_frame(levels, *self.T_ref, fp16=self.cfg.fp16_maps)
             self.xbar = self.x.copy()
             return dict(status="init", x1=self.x.copy())
         t0, t1 = self.t, t
@@ -155,7 +155,7 @@ class Tracker:
         self.x = x1.copy()
         self.t = t1
         self.T_ref = (x1.R, x1.r.copy())
-        self.ref = reference_from_frame(levels, *self.T_ref)
+        self.ref = reference_from_frame(levels, *self.T_ref, fp16=self.cfg.fp16_maps)
         keep = np.searchsorted(self.imu[:, 0], t1, side="right") - 1
         self.imu = self.imu[max(keep, 0):]
         return dict(status="ok", x0=x0, x1=x1, counts=counts, H=H, b=b, d_last=d,

@@ -17,6 +17,11 @@ maps, without describing how they are built.  Readings used here:
 * Reference maps (the "global model" of Eq. 4, here the previous frame's maps
   moved into W with its final pose): V_W = R_ref v + r_ref, N_W = R_ref n,
   intensity and its gradient, and the pose T_ref they were made at.
+* Reduced-precision storage (cfg.fp16_maps): the camera-frame normals and the
+  intensity gradients are rounded to IEEE half precision (round to nearest
+  even) where they are stored, before any use; everything else stays FP64.
+  This is the storage format of the FP16-map variant, so that variant can be
+  compared with an oracle that sees the same maps.
 """
 from __future__ import annotations
 
@@ -116,23 +121,34 @@ class RefLevel:
     depth: np.ndarray        # kept for the margin test of the association
 
 
+def half(a):
+    """Round to IEEE half precision (nearest even) and back to FP64."""
+    return np.asarray(a, dtype=np.float64).astype(np.float16).astype(np.float64)
+
+
 def frame_levels(depth, intensity, cfg):
     ds, Is = pyramid(depth, intensity, cfg.levels)
+    fp16 = getattr(cfg, "fp16_maps", False)
     out = []
     for l in range(cfg.levels):
         cam = cfg.level_camera(l)
         V, vv = vertex_map(ds[l], cam, cfg)
         N, nv = normal_map(V, vv)
+        if fp16:
+            N = half(N)
         out.append(FrameLevel(cam=cam, depth=ds[l], V=V, V_valid=vv, N=N, N_valid=nv, I=Is[l]))
     return out
 
 
-def reference_from_frame(levels, R_ref, r_ref):
+def reference_from_frame(levels, R_ref, r_ref, fp16=False):
     """The live frame's maps become the next reference, moved into W with T_ref."""
     out = []
     for fl in levels:
         V_W = fl.V @ R_ref.T + r_ref
         N_W = fl.N @ R_ref.T
+        G = gradient_map(fl.I)
+        if fp16:
+            G = half(G)
         out.append(RefLevel(cam=fl.cam, V_W=V_W, N_W=N_W, valid=fl.V_valid & fl.N_valid,
-                            I=fl.I, G=gradient_map(fl.I), depth=fl.depth))
+                            I=fl.I, G=G, depth=fl.depth))
     return out

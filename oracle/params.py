@@ -64,6 +64,7 @@ class TrackerConfig:
     prior_sigma: dict = field(default_factory=lambda: dict(
         pose=1e-6, v=0.1, bg=GYR_BIAS_PRIOR, ba=ACC_BIAS_PRIOR, grav=0.1))
     min_valid: int = 64                 # level-0 correspondences below this: tracking lost
+    fp16_maps: bool = False             # normals and intensity gradients rounded to FP16
 
     def level_camera(self, level):
         """Intrinsics at pyramid level l: f_l = f / 2^l, c_l = (c + 0.5) / 2^l - 0.5

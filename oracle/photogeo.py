@@ -30,7 +30,10 @@ Margin pixels.  A pixel whose accept / reject decision sits within 1e-4 px of
 an image bound or rounding boundary, or within a relative 1e-5 of a metric
 threshold (depth range, z > 0, distance, normal angle, normal orientation), is
 flagged: an FP32 implementation may legitimately decide it the other way, so
-exact count comparisons exclude these pixels and count them separately.
+exact count comparisons exclude these pixels and count them separately.  With
+normals stored in FP16 (cfg.fp16_maps) the angle test's margin is 4 * 2^-11 in
+cos: the stored normal is a rounding, and rounding an FP32-computed normal may
+give the neighbouring half-precision value of the FP64-computed one.
 """
 from __future__ import annotations
 
@@ -40,6 +43,7 @@ from .maps import FrameLevel, RefLevel, depth_valid
 
 PX_MARGIN = 1e-4
 REL_MARGIN = 1e-5
+FP16_COS_MARGIN = 4.0 * 2.0 ** -11      # angle-test margin when normals are stored in FP16
 
 
 def _near_rel(a, thr):
@@ -128,6 +132,11 @@ def linearise(cur: FrameLevel, ref: RefLevel, R_ref, r_ref, x0, x1, cfg):
     ref_nm = _normal_margin(ref.depth, (ref.V_W - r_ref) @ R_ref, ref.N_W @ R_ref, cfg)
     m_icp |= cand & inb & ref_nm[yc, xc]
     m_icp |= cand & rvalid & (_near_rel(dist, cfg.icp_dist_thr) | _near_rel(cosang, cos_thr))
+    if getattr(cfg, "fp16_maps", False):
+        # normals stored in half precision: an implementation that rounds a normal
+        # computed in FP32 may land one half-precision unit (2^-11 relative) away
+        # from the rounding of the FP64 normal, which moves cos by up to ~2 * 2^-11
+        m_icp |= cand & rvalid & (np.abs(cosang - cos_thr) <= FP16_COS_MARGIN)
 
     # ---------------- photometric (Eq. 3) ----------------
     p0 = (pW - r0) @ R0                  # R_0^T (p_W - r_0)

@@ -45,7 +45,7 @@ def _oracle_system(tr, seq, ocfg, level, x0, x1):
     return H, b, parts, prior_cost
 
 
-def _compare_linearisation(st, tr, seq, ocfg, level, x0, x1):
+def _compare_linearisation(st, tr, seq, ocfg, level, x0, x1, rel=None):
     lvl_shape = (ocfg.height >> level, ocfg.width >> level)
     out, flags = dri.dri_linearise(st.handle, level, to_dri(x0), to_dri(x1), want_flags=True,
                                    shape=lvl_shape)
@@ -62,15 +62,16 @@ def _compare_linearisation(st, tr, seq, ocfg, level, x0, x1):
     assert abs(out.n_rgb - lin["n_rgb"]) <= mr.sum()
     assert out.n_icp == gi.sum() and out.n_rgb == gr.sum()
     # per term (x1 pose block, world frame)
+    kw = {} if rel is None else {"rel": rel}
     check_system(np.array(out.H_icp).reshape(6, 6), out.b_icp, lin["H_icp"], lin["b_icp"],
-                 lin["cost_icp"], what="ICP")
+                 lin["cost_icp"], what="ICP", **kw)
     check_system(np.array(out.H_rgb).reshape(6, 6), out.b_rgb, lin["H_rgb"][6:, 6:],
-                 lin["b_rgb"][6:], lin["cost_rgb"], what="RGB")
+                 lin["b_rgb"][6:], lin["cost_rgb"], what="RGB", **kw)
     np.testing.assert_allclose(out.e_imu, parts["e_imu"], rtol=1e-9, atol=1e-12)
     np.testing.assert_allclose(out.cost_imu, parts["cost_imu"], rtol=1e-8, atol=1e-9)
     # the assembled 34x34 system
     cost = lin["cost_icp"] + lin["cost_rgb"] + parts["cost_imu"] + prior_cost
-    check_system(np.array(out.H).reshape(34, 34), out.b, H, b, cost, what="joint")
+    check_system(np.array(out.H).reshape(34, 34), out.b, H, b, cost, what="joint", **kw)
     return out, lin
 
 

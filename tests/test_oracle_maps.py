@@ -106,3 +106,30 @@ def test_reference_maps_are_moved_into_world():
         np.testing.assert_allclose(rl.V_W, fl.V @ R.T + r, atol=1e-14)
         np.testing.assert_allclose(np.linalg.norm(rl.N_W[rl.valid], axis=-1), 1.0, atol=1e-14)
         np.testing.assert_allclose((rl.N_W @ R)[rl.valid], fl.N[rl.valid], atol=1e-14)
+
+
+def test_fp16_map_storage_rounds_normals_and_gradients_to_half(pair_small):
+    """With fp16_maps the stored normals and gradients are exactly the IEEE
+    half-precision roundings of the FP64 maps (relative error <= 2^-11 for
+    normal-range values, as for any round-to-nearest binary16), the depth,
+    vertices and intensities are untouched."""
+    from oracle.params import TrackerConfig
+    seq = pair_small
+    cam = seq.cam
+    exact = TrackerConfig(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, levels=2)
+    half = TrackerConfig(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, levels=2, fp16_maps=True)
+    le = maps.frame_levels(seq.depth[0], seq.intensity[0], exact)
+    lh = maps.frame_levels(seq.depth[0], seq.intensity[0], half)
+    for a, b in zip(le, lh):
+        np.testing.assert_array_equal(b.N, a.N.astype(np.float16).astype(np.float64))
+        np.testing.assert_array_equal(b.V, a.V)
+        np.testing.assert_array_equal(b.I, a.I)
+        big = np.abs(a.N) >= 2.0 ** -14
+        assert np.all(np.abs(b.N - a.N)[big] <= 2.0 ** -11 * np.abs(a.N)[big])
+        assert np.any(b.N != a.N)                      # rounding did happen
+    R, r = np.eye(3), np.zeros(3)
+    re = maps.reference_from_frame(le, R, r)
+    rh = maps.reference_from_frame(lh, R, r, fp16=True)
+    for a, b in zip(re, rh):
+        np.testing.assert_array_equal(b.G, a.G.astype(np.float16).astype(np.float64))
+        np.testing.assert_array_equal(b.I, a.I)
