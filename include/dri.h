@@ -157,6 +157,26 @@ int dri_destroy_stream(dri_stream s);
 int dri_upload_frame(dri_stream s, double t, const float* depth, const float* intensity,
                      size_t pitch_bytes, int32_t mem_kind);
 
+/* Replaces the reference the next frame is tracked against with a model
+ * prediction rendered at T_WC_ref (r_WC (3), q_WC (w, x, y, z)), as the paper
+ * tracks against its surfel model's prediction (Sec. IV-B): vertex_W and
+ * normal_W hold an (x, y, z) FP32 triple per pixel in W, intensity one float;
+ * height rows of width pixels, pitch_px pixels apart (0 = width) in all three.
+ * A pixel with a zero normal has no surface.  Level 0 keeps, for each pixel
+ * with a surface, the depth of its vertex in the reference camera (the vertex
+ * of a prediction rendered from T_WC_ref lies on its pixel's ray) and its
+ * normal where that depth is in [depth_min, depth_max]; coarser levels average
+ * the depth over samples > 0, the intensity, and the non-zero normals
+ * (renormalised).  Only the next tracked frame uses it: that frame then becomes
+ * the reference, unless another prediction is uploaded.
+ * DRI_HOST: copied through a device staging buffer that the library allocates
+ * on first use (28 bytes per pixel, freed with the stream); DRI_DEVICE: read by
+ * this call's kernels, stream-ordered on the stream's cuda_stream.
+ * DRI_ENOTREADY before the stream's first (initialising) frame. */
+int dri_upload_reference(dri_stream s, const float* vertex_W, const float* normal_W,
+                         const float* intensity, const double* T_WC_ref, size_t pitch_px,
+                         int32_t mem_kind);
+
 /* Appends IMU samples (host memory, n >= 0) with strictly increasing times,
  * later than every sample already pushed.  DRI_EINVAL otherwise. */
 int dri_push_imu(dri_stream s, const dri_imu_sample* samples, size_t n);

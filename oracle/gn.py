@@ -102,6 +102,11 @@ class Tracker:
         self.xbar = self.x.copy()
         self.imu = np.zeros((0, 7))
 
+    def set_reference(self, ref, R_ref, r_ref):
+        """Replaces the reference with uploaded levels (maps.reference_from_upload)."""
+        self.ref = ref
+        self.T_ref = (np.asarray(R_ref, dtype=np.float64), np.asarray(r_ref, dtype=np.float64).copy())
+
     def push_imu(self, samples):
         self.imu = np.concatenate([self.imu, np.asarray(samples, dtype=np.float64)])
 

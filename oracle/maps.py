@@ -17,6 +17,15 @@ maps, without describing how they are built.  Readings used here:
 * Reference maps (the "global model" of Eq. 4, here the previous frame's maps
   moved into W with its final pose): V_W = R_ref v + r_ref, N_W = R_ref n,
   intensity and its gradient, and the pose T_ref they were made at.
+* Uploaded reference (a model prediction rendered at T_ref, given as world-frame
+  vertex and normal maps and an intensity image at level 0; the paper renders
+  it from its surfel model, Sec. IV-B): a pixel has a surface where its normal
+  is non-zero; its depth is the z of its vertex in the reference camera (the
+  vertex of a prediction rendered from T_ref lies on its pixel's ray, and the
+  maps keep that depth); its normal is kept where that depth is in range.
+  Coarser levels: depth and intensity as for a live frame, the normal is the
+  2x2 mean of the non-zero normals, renormalised (zero if none), kept where the
+  level's depth is in range.
 * Reduced-precision storage (cfg.fp16_maps): the camera-frame normals and the
   intensity gradients are rounded to IEEE half precision (round to nearest
   even) where they are stored, before any use; everything else stays FP64.
@@ -151,4 +160,46 @@ def reference_from_frame(levels, R_ref, r_ref, fp16=False):
             G = half(G)
         out.append(RefLevel(cam=fl.cam, V_W=V_W, N_W=N_W, valid=fl.V_valid & fl.N_valid,
                             I=fl.I, G=G, depth=fl.depth))
+    return out
+
+
+def downsample_normals(N):
+    """2x2 mean of the non-zero normals, renormalised; zero where none is."""
+    N = np.asarray(N, dtype=np.float64)
+    h, w = N.shape[0] // 2, N.shape[1] // 2
+    blk = N[: 2 * h, : 2 * w].reshape(h, 2, w, 2, 3)
+    nz = np.linalg.norm(blk, axis=-1) > 0
+    s = np.where(nz[..., None], blk, 0.0).sum(axis=(1, 3))
+    n = np.linalg.norm(s, axis=-1)
+    return np.where((n > 0)[..., None], s / np.where(n > 0, n, 1.0)[..., None], 0.0)
+
+
+def reference_from_upload(V_W, N_W, intensity, R_ref, r_ref, cfg):
+    """Reference levels from an uploaded prediction: V_W, N_W (H x W x 3, world
+    frame), intensity (H x W) at level 0, rendered at T_ref = (R_ref, r_ref)."""
+    V_W = np.asarray(V_W, dtype=np.float64)
+    N_W = np.asarray(N_W, dtype=np.float64)
+    V_c = (V_W - r_ref) @ R_ref            # R_ref^T (V_W - r_ref), row vectors
+    N_c = N_W @ R_ref
+    surf = np.linalg.norm(N_c, axis=-1) > 0
+    d = np.where(surf, V_c[..., 2], 0.0)
+    N = np.where((surf & depth_valid(d, cfg))[..., None], N_c, 0.0)
+    I = np.asarray(intensity, dtype=np.float64)
+    fp16 = getattr(cfg, "fp16_maps", False)
+    out = []
+    for l in range(cfg.levels):
+        if l:
+            d = downsample_depth(d)
+            I = downsample_intensity(I)
+            N = downsample_normals(N)
+            N = np.where(depth_valid(d, cfg)[..., None], N, 0.0)
+        cam = cfg.level_camera(l)
+        V, vv = vertex_map(d, cam, cfg)
+        Ns = half(N) if fp16 else N
+        nv = np.linalg.norm(Ns, axis=-1) > 0
+        G = gradient_map(I)
+        if fp16:
+            G = half(G)
+        out.append(RefLevel(cam=cam, V_W=V @ R_ref.T + r_ref, N_W=Ns @ R_ref.T, valid=vv & nv,
+                            I=I, G=G, depth=d))
     return out

@@ -987,6 +987,7 @@ int dri_destroy_stream(dri_stream s) {
   }
   settle(s, true);
   plan_free(s->own);
+  if (s->ref_stage) cudaFree(s->ref_stage);
   if (s->own_ws && s->ws) cudaFree(s->ws);
   if (s->pin_ctrl) cudaFreeHost(s->pin_ctrl);
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
@@ -1020,6 +1021,59 @@ int dri_upload_frame(dri_stream s, double t, const float* depth, const float* in
   }
   s->t_frame = t;
   s->frame_pending = true;
+  return DRI_OK;
+}
+
+int dri_upload_reference(dri_stream s, const float* vertex_W, const float* normal_W,
+                         const float* intensity, const double* T_WC_ref, size_t pitch_px,
+                         int32_t mem_kind) {
+  if (!s || !vertex_W || !normal_W || !intensity || !T_WC_ref) return DRI_EINVAL;
+  if (mem_kind != DRI_HOST && mem_kind != DRI_DEVICE) return DRI_EINVAL;
+  const int w = s->cfg.width, h = s->cfg.height;
+  const size_t pitch = pitch_px ? pitch_px : (size_t)w;
+  if (pitch < (size_t)w || pitch > (size_t)INT32_MAX) return DRI_EINVAL;
+  for (int i = 0; i < 7; ++i)
+    if (!std::isfinite(T_WC_ref[i])) return DRI_EINVAL;
+  const double qn = std::sqrt(T_WC_ref[3] * T_WC_ref[3] + T_WC_ref[4] * T_WC_ref[4] +
+                              T_WC_ref[5] * T_WC_ref[5] + T_WC_ref[6] * T_WC_ref[6]);
+  if (!(qn > 1e-12)) return DRI_EINVAL;
+  if (!s->initialised) return DRI_ENOTREADY;
+  RefUpload up;
+  std::memset(&up, 0, sizeof(up));
+  quat_to_rot_h(T_WC_ref + 3, up.R);
+  for (int i = 0; i < 3; ++i) up.r[i] = T_WC_ref[i];
+  if (mem_kind == DRI_HOST) {
+    const size_t npx = (size_t)w * h;
+    if (!s->ref_stage && cudaMalloc(&s->ref_stage, npx * 7 * sizeof(float)) != cudaSuccess) {
+      s->ref_stage = nullptr;
+      return DRI_ENOMEM;
+    }
+    float* sv = s->ref_stage;
+    float* sn = sv + 3 * npx;
+    float* si = sn + 3 * npx;
+    const size_t row3 = (size_t)w * 3 * sizeof(float), row1 = (size_t)w * sizeof(float);
+    CK(cudaMemcpy2DAsync(sv, row3, vertex_W, pitch * 3 * sizeof(float), row3, h, cudaMemcpyHostToDevice,
+                         s->stream));
+    CK(cudaMemcpy2DAsync(sn, row3, normal_W, pitch * 3 * sizeof(float), row3, h, cudaMemcpyHostToDevice,
+                         s->stream));
+    CK(cudaMemcpy2DAsync(si, row1, intensity, pitch * sizeof(float), row1, h, cudaMemcpyHostToDevice,
+                         s->stream));
+    up.V = sv;
+    up.N = sn;
+    up.I = si;
+    up.pitch = w;
+  } else {
+    up.V = vertex_W;
+    up.N = normal_W;
+    up.I = intensity;
+    up.pitch = (int64_t)pitch;
+  }
+  const bool fp16 = (s->cfg.precision_flags & DRI_FP16_MAPS) != 0;
+  CK(launch(s, DRI_KC_MAPS, (double)w * h, [&] {
+    return launch_upload_reference(s->maps, s->geom, s->cfg.levels, s->ctrl, (float)s->cfg.depth_min,
+                                   (float)s->cfg.depth_max, fp16, up, s->stream);
+  }));
+  s->launches += 2 * s->cfg.levels + 1;
   return DRI_OK;
 }
 

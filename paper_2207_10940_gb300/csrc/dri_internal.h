@@ -203,6 +203,18 @@ StreamLayout make_layout(const dri_stream_config& cfg);
 LevelGeom level_geom(const dri_stream_config& cfg, int level);
 
 // ---- kernel launchers (return cudaGetLastError()) ------------------------
+// Uploaded reference: level-0 vertex / normal maps (x, y, z per pixel, W frame),
+// intensity, rows `pitch` pixels apart, and the pose T_ref they were rendered at.
+struct RefUpload {
+  const float* V;
+  const float* N;
+  const float* I;
+  int64_t pitch;
+  double R[9], r[3];
+};
+cudaError_t launch_upload_reference(const LevelMaps* m, const LevelGeom* g, int levels, Ctrl* ctrl,
+                                    float dmin, float dmax, bool fp16, const RefUpload& up,
+                                    cudaStream_t s);
 cudaError_t launch_copy_batch(const BatchArgs& a, int blocks, cudaStream_t s);
 cudaError_t launch_pyr_down_batch(const BatchArgs& a, int blocks, cudaStream_t s);
 cudaError_t launch_normals_batch(const BatchArgs& a, int blocks, bool fp16, cudaStream_t s);

@@ -72,6 +72,7 @@ struct dri_stream_s {
   struct Rec { int cls; size_t e0, e1; double pixels; };
   std::vector<Rec> recs;
   dri_profile counted;
+  float* ref_stage = nullptr;       // device staging of host reference uploads (allocated on demand)
 };
 
 // The launch sequence of one frame over nslots streams: the device table of

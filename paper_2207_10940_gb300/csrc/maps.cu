@@ -198,6 +198,76 @@ __global__ void k_gradient(LevelMaps m, const Ctrl* __restrict__ ctrl, int w, in
   gradient_px<T>(m, ctrl->ref_index, w, h, x, y);
 }
 
+
+// ---- uploaded reference (a model prediction rendered at T_ref) ----
+// Level 0: per pixel, the vertex and normal moved into the reference camera in
+// FP64 (v = R^T (V - r), n = R^T N); a zero normal means no surface (depth 0);
+// the normal is kept where the depth is in [dmin, dmax].
+template <typename T>
+__global__ void k_ref_level0(LevelMaps m, const Ctrl* __restrict__ ctrl, LevelGeom g, float dmin,
+                             float dmax, RefUpload up) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= g.w || y >= g.h) return;
+  const int set = ctrl->ref_index;
+  const int64_t src = (int64_t)y * up.pitch + x;
+  const float* V = up.V + 3 * src;
+  const float* N = up.N + 3 * src;
+  const double vx = (double)__ldg(V) - up.r[0], vy = (double)__ldg(V + 1) - up.r[1],
+               vz = (double)__ldg(V + 2) - up.r[2];
+  const double nx = __ldg(N), ny = __ldg(N + 1), nz = __ldg(N + 2);
+  const bool surf = nx != 0.0 || ny != 0.0 || nz != 0.0;
+  const double* R = up.R;
+  const float d = surf ? (float)(R[2] * vx + R[5] * vy + R[8] * vz) : 0.f;
+  const bool keep = surf && d >= dmin && d <= dmax;
+  const float cx = keep ? (float)(R[0] * nx + R[3] * ny + R[6] * nz) : 0.f;
+  const float cy = keep ? (float)(R[1] * nx + R[4] * ny + R[7] * nz) : 0.f;
+  const float cz = keep ? (float)(R[2] * nx + R[5] * ny + R[8] * nz) : 0.f;
+  const int o = y * g.w + x;
+  m.depth[set][o] = d;
+  m.inten[set][o] = __ldg(up.I + src);
+  Packs<T>::store_a(m.packA[set], o, cx, cy, cz, d);
+}
+
+// Level l from l - 1 of the reference set: depth (mean of the samples > 0) and
+// intensity as for a live frame, the normal as the mean of the non-zero normals
+// of the 2x2 block, renormalised, kept where the level's depth is in range.
+template <typename T>
+__global__ void k_ref_down(LevelMaps fine, LevelMaps coarse, const Ctrl* __restrict__ ctrl, int wf,
+                           int wc, int hc, float dmin, float dmax) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  if (x >= wc || y >= hc) return;
+  const int set = ctrl->ref_index;
+  pyr_down_px(fine, coarse, set, wf, wc, x, y);
+  const int o = y * wc + x;
+  const float d = coarse.depth[set][o];
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int f = (2 * y + (k >> 1)) * wf + 2 * x + (k & 1);
+    const float4 n = Packs<T>::load_a(fine.packA[set], fine.depth[set], f);
+    sx += n.x;                                   // zero normals add nothing
+    sy += n.y;
+    sz += n.z;
+  }
+  const float n2 = fmaf(sx, sx, fmaf(sy, sy, __fmul_rn(sz, sz)));
+  float nx = 0.f, ny = 0.f, nz = 0.f;
+  if (n2 > 0.f && d >= dmin && d <= dmax) {
+    const float inv = rsqrtf(n2);
+    nx = __fmul_rn(sx, inv);
+    ny = __fmul_rn(sy, inv);
+    nz = __fmul_rn(sz, inv);
+  }
+  Packs<T>::store_a(coarse.packA[set], o, nx, ny, nz, d);
+}
+
+__global__ void k_ref_pose(Ctrl* __restrict__ ctrl, RefUpload up) {
+  const int i = threadIdx.x;
+  if (i < 9) ctrl->Rref[i] = up.R[i];
+  if (i < 3) ctrl->rref[i] = up.r[i];
+}
+
 inline dim3 grid2(int w, int h, dim3 b) { return dim3((w + b.x - 1) / b.x, (h + b.y - 1) / b.y); }
 
 }  // namespace
@@ -241,6 +311,29 @@ cudaError_t launch_gradient(const LevelMaps& m, const Ctrl* ctrl, int w, int h, 
     k_gradient<__half><<<grid2(w, h, b), b, 0, s>>>(m, ctrl, w, h);
   else
     k_gradient<float><<<grid2(w, h, b), b, 0, s>>>(m, ctrl, w, h);
+  return cudaGetLastError();
+}
+
+}  // namespace dri
+
+namespace dri {
+
+cudaError_t launch_upload_reference(const LevelMaps* m, const LevelGeom* g, int levels, Ctrl* ctrl,
+                                    float dmin, float dmax, bool fp16, const RefUpload& up,
+                                    cudaStream_t s) {
+  const dim3 b(32, 8);
+  if (fp16) k_ref_level0<__half><<<grid2(g[0].w, g[0].h, b), b, 0, s>>>(m[0], ctrl, g[0], dmin, dmax, up);
+  else k_ref_level0<float><<<grid2(g[0].w, g[0].h, b), b, 0, s>>>(m[0], ctrl, g[0], dmin, dmax, up);
+  for (int l = 1; l < levels; ++l) {
+    const dim3 gr = grid2(g[l].w, g[l].h, b);
+    if (fp16) k_ref_down<__half><<<gr, b, 0, s>>>(m[l - 1], m[l], ctrl, g[l - 1].w, g[l].w, g[l].h, dmin, dmax);
+    else k_ref_down<float><<<gr, b, 0, s>>>(m[l - 1], m[l], ctrl, g[l - 1].w, g[l].w, g[l].h, dmin, dmax);
+  }
+  for (int l = 0; l < levels; ++l) {
+    if (fp16) k_gradient<__half><<<grid2(g[l].w, g[l].h, b), b, 0, s>>>(m[l], ctrl, g[l].w, g[l].h);
+    else k_gradient<float><<<grid2(g[l].w, g[l].h, b), b, 0, s>>>(m[l], ctrl, g[l].w, g[l].h);
+  }
+  k_ref_pose<<<1, 32, 0, s>>>(ctrl, up);
   return cudaGetLastError();
 }
 

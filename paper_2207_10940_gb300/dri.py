@@ -138,6 +138,9 @@ def load_library():
         "dri_upload_frame": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32]),
         "dri_push_imu": (ctypes.c_int, [ctypes.c_void_p, P(dri_imu_sample), ctypes.c_size_t]),
+        "dri_upload_reference": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, c_double_p, ctypes.c_size_t,
+                                                ctypes.c_int32]),
         "dri_track": (ctypes.c_int, [ctypes.c_void_p, P(dri_track_result)]),
         "dri_track_batch": (ctypes.c_int, [P(ctypes.c_void_p), ctypes.c_int32, P(dri_track_result)]),
         "dri_batch_get_options": (ctypes.c_int, [P(ctypes.c_void_p), ctypes.c_int32,
@@ -248,6 +251,23 @@ def dri_upload_frame(s, t, depth, intensity, pitch_bytes=0, mem_kind=None):
     return _check(load_library().dri_upload_frame(s, float(t), ctypes.c_void_p(_ptr(depth)),
                                                   ctypes.c_void_p(_ptr(intensity)), pitch_bytes,
                                                   mem_kind), "dri_upload_frame")
+
+
+def dri_upload_reference(s, vertex_W, normal_W, intensity, T_WC_ref, pitch_px=0, mem_kind=None):
+    """vertex_W, normal_W: (H, W, 3) float32; intensity (H, W) float32; numpy (host)
+    or CUDA tensors (device); T_WC_ref: r (3) + q (w, x, y, z)."""
+    if mem_kind is None:
+        mem_kind = DRI_DEVICE if (hasattr(vertex_W, "is_cuda") and vertex_W.is_cuda) else DRI_HOST
+    for a in (vertex_W, normal_W, intensity):
+        if str(getattr(a, "dtype", None)) not in ("float32", "torch.float32"):
+            raise TypeError("reference maps must be float32")
+        if isinstance(a, np.ndarray) and not a.flags.c_contiguous:
+            raise ValueError("host arrays must be C-contiguous")
+    T = np.ascontiguousarray(T_WC_ref, dtype=np.float64)
+    return _check(load_library().dri_upload_reference(
+        s, ctypes.c_void_p(_ptr(vertex_W)), ctypes.c_void_p(_ptr(normal_W)),
+        ctypes.c_void_p(_ptr(intensity)), T.ctypes.data_as(c_double_p), pitch_px, mem_kind),
+        "dri_upload_reference")
 
 
 def imu_array(samples):

@@ -133,3 +133,51 @@ def test_fp16_map_storage_rounds_normals_and_gradients_to_half(pair_small):
     for a, b in zip(re, rh):
         np.testing.assert_array_equal(b.G, a.G.astype(np.float16).astype(np.float64))
         np.testing.assert_array_equal(b.I, a.I)
+
+
+def _world_maps(level, R, r):
+    return level.V @ R.T + r, np.where(level.N_valid[..., None], level.N, 0.0) @ R.T
+
+
+def test_uploaded_reference_round_trip_at_level_zero(pair_small):
+    """A frame's own level-0 maps moved into W and uploaded give back its depth
+    and normals wherever it has a normal, and no surface elsewhere."""
+    from oracle.params import TrackerConfig
+    from oracle.so3 import exp_so3
+    seq = pair_small
+    cam = seq.cam
+    cfg = TrackerConfig(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, levels=3)
+    lv = maps.frame_levels(seq.depth[0], seq.intensity[0], cfg)
+    R, r = exp_so3(np.array([0.3, -0.2, 0.5])), np.array([0.4, -1.0, 2.0])
+    V_W, N_W = _world_maps(lv[0], R, r)
+    ref = maps.reference_from_upload(V_W, N_W, lv[0].I, R, r, cfg)
+    ok = lv[0].N_valid
+    np.testing.assert_allclose(ref[0].depth[ok], lv[0].depth[ok], rtol=1e-12, atol=1e-12)
+    np.testing.assert_array_equal(ref[0].depth[~ok], 0.0)
+    np.testing.assert_allclose((ref[0].N_W @ R)[ok], lv[0].N[ok], atol=1e-12)
+    np.testing.assert_array_equal(ref[0].valid, ok)
+    np.testing.assert_array_equal(ref[0].I, lv[0].I)
+    for l in (1, 2):
+        n = np.linalg.norm(ref[l].N_W, axis=-1)
+        assert np.all((np.abs(n - 1.0) < 1e-12) | (n == 0))    # unit or none
+        assert ref[l].depth.shape == lv[l].depth.shape
+
+
+def test_uploaded_plane_keeps_its_normal_on_every_level():
+    """Averaging identical unit normals gives that normal back: a fronto-parallel
+    plane uploaded at any pose has the plane's normal at every level."""
+    from oracle.params import TrackerConfig
+    from oracle.so3 import exp_so3
+    cfg = TrackerConfig(64, 48, 60.0, 60.0, 32.0, 24.0, levels=3)
+    R, r = exp_so3(np.array([-0.1, 0.4, 0.2])), np.array([1.0, 2.0, -0.5])
+    h, w = 48, 48 * 0 + 64
+    u, v = np.meshgrid(np.arange(w), np.arange(h))
+    d = np.full((h, w), 2.0)
+    Vc = np.stack([d * (u - 32.0) / 60.0, d * (v - 24.0) / 60.0, d], axis=-1)
+    Nc = np.broadcast_to(np.array([0.0, 0.0, -1.0]), (h, w, 3))
+    ref = maps.reference_from_upload(Vc @ R.T + r, Nc @ R.T, np.full((h, w), 0.5), R, r, cfg)
+    for lev in ref:
+        np.testing.assert_allclose(lev.N_W @ R, np.broadcast_to([0.0, 0.0, -1.0], lev.N_W.shape),
+                                   atol=1e-13)
+        np.testing.assert_allclose(lev.depth, 2.0, rtol=1e-13)
+        assert lev.valid.all()
