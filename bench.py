@@ -339,6 +339,22 @@ class Runner:
             st.close()
 
 
+def max_over_ranks(x, device, world):
+    """The largest value of x over the ranks (the job's time is its slowest rank's)."""
+    import torch
+    if world <= 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms_max):
+    """Whole-job units/s: every rank processes units_per_rank (replicas, weak
+    scaling) and the job takes its slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1000.0)
+
+
 def timed_pass(run, steps, world, local):
     """Device time of `steps` steps (CUDA events on the library's stream)."""
     torch, dri = run.torch, run.dri
@@ -357,10 +373,7 @@ def timed_pass(run, steps, world, local):
     launches = dri.dri_launch_count(h0) - n0
     per = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(steps)])
     total_ms = evs[0].elapsed_time(evs[-1])
-    t_max = torch.tensor([total_ms], device=run.dev, dtype=torch.float64)
-    if world > 1:
-        torch.distributed.all_reduce(t_max, op=torch.distributed.ReduceOp.MAX)
-    return float(t_max.item()), per, launches, clk.summary()
+    return max_over_ranks(total_ms, run.dev, world), per, launches, clk.summary()
 
 
 def profiled_pass(run, steps):
@@ -654,7 +667,7 @@ def run_ours(args):
         opts = dri.dri_batch_get_options([s.handle for s in run.streams])
         tiles = list(opts.rows_per_thread)
         out[mode] = {
-            "value": world * n_streams * steps / (total_ms / 1000.0), "steps": steps,
+            "value": job_throughput(n_streams * steps, world, total_ms), "steps": steps,
             "streams": n_streams, "ms_per_step": total_ms / steps,
             "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
             "gpu_launches": int(launches), "frames_ok": int(ok), "frames_failed": int(failed),
