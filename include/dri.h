@@ -202,7 +202,7 @@ int dri_track(dri_stream s, dri_track_result* out);
  * handles, same order) builds a plan: device tables, a staging ring and
  * buffers for the n result blocks (allocated; freed when one of the streams
  * is destroyed).  On the first call that tracks a frame the plan times the
- * pixel kernel at rows-per-thread 1, 2, 3, 4, 6, 8 on each level and keeps the
+ * pixel kernel at rows-per-thread 2, 4, 8, 16, 32 on each level and keeps the
  * fastest (this call waits); later calls replay the sequence as one CUDA graph
  * (launched directly on the legacy default stream or while profiling).
  *
@@ -224,7 +224,7 @@ int dri_track_batch(const dri_stream* streams, int32_t n, dri_track_result* out)
  *                    group's pixel kernels (1 .. min(n, 8); default 1; a
  *                    stream's own plan has 1)
  *   autotune         1: the next tracked frame times rows per thread
- *                    1, 2, 3, 4, 6, 8 per level and keeps the fastest (batch
+ *                    2, 4, 8, 16, 32 per level and keeps the fastest (batch
  *                    plans start with it on); 0: rows_per_thread as given, so
  *                    repeated runs sum pixels in the same order (identical bits) */
 typedef struct {

@@ -644,9 +644,9 @@ int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
 
 // Chooses each level's rows per thread by timing the pixel kernel on the
 // frames just staged (their maps and frame start are already enqueued):
-// candidates 1, 2, 3, 4, 6 and 8, three launches each, the fastest mean wins.
+// candidates 2, 4, 8, 16 and 32, three launches each, the fastest mean wins.
 int plan_autotune(Plan* p, int64_t* kernels) {
-  static const int cand[] = {1, 2, 3, 4, 6, 8};
+  static const int cand[] = {2, 4, 8, 16, 32};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));

@@ -63,7 +63,7 @@ def test_batch_matches_streams_tracked_alone():
         assert [r.status for r in res] == [0] * len(batch)
         assert [r.initialised for r in res] == [int(i == 0)] * len(batch)
     opts = dri.dri_batch_get_options(batch)
-    assert all(p in (1, 2, 3, 4, 6, 8) for p in opts.rows_per_thread[:3])
+    assert all(p in (2, 4, 8, 16, 32) for p in opts.rows_per_thread[:3])
     assert opts.groups == 1 and opts.autotune == 0
     for st, (xa, Ha, ba) in zip(batch, alone):
         xb, Hb, bb = dri.dri_get_state(st.handle, with_prior=True)
