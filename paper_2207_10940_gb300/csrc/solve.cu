@@ -402,59 +402,145 @@ __device__ void imu_linearise(const DState& x0, const DState& x1, const Preint& 
 // state algebra
 // ---------------------------------------------------------------------------
 
-// x boxminus y (17): vector parts subtract, orientations log(p q^-1), gravity x, y of its log.
-__device__ void state_boxminus(const DState& x, const DState& y, double* d) {
-  double Rx[9], Ry[9], M[9], w[3];
-  for (int i = 0; i < 3; ++i) {
-    d[i] = x.r[i] - y.r[i];
-    d[6 + i] = x.v[i] - y.v[i];
-    d[9 + i] = x.bg[i] - y.bg[i];
-    d[12 + i] = x.ba[i] - y.ba[i];
-  }
-  quat_to_rot(x.q, Rx);
-  quat_to_rot(y.q, Ry);
-  m3_mult(Rx, Ry, M);
-  so3_log(M, d + 3);
-  quat_to_rot(x.qg, Rx);
-  quat_to_rot(y.qg, Ry);
-  m3_mult(Rx, Ry, M);
-  so3_log(M, w);
-  d[15] = w[0];
-  d[16] = w[1];
-}
-
-__device__ void state_boxplus(DState& x, const double* d) {
-  for (int i = 0; i < 3; ++i) {
-    x.r[i] += d[i];
-    x.v[i] += d[6 + i];
-    x.bg[i] += d[9 + i];
-    x.ba[i] += d[12 + i];
-  }
-  quat_boxplus(x.q, d + 3);
-  const double dg[3] = {d[15], d[16], 0.0};
-  quat_boxplus(x.qg, dg);
-}
-
-// Pixel-kernel transforms for the next linearisation (FP64 -> FP32 once).
-__device__ void write_transforms(Ctrl* c) {
-  double R0[9], R1[9], M[9], dr[3], t[3];
-  quat_to_rot(c->x0.q, R0);
-  quat_to_rot(c->x1.q, R1);
-  m3_tmul(c->Rref, R1, M);
-  for (int i = 0; i < 3; ++i) dr[i] = c->x1.r[i] - c->rref[i];
-  m3_tvec(c->Rref, dr, t);
-  for (int i = 0; i < 9; ++i) c->xf_icp[i] = (float)(M[i] - ((i % 4 == 0) ? 1.0 : 0.0));
-  for (int i = 0; i < 3; ++i) c->xf_icp[9 + i] = (float)t[i];
-  m3_tmul(R0, R1, M);
-  for (int i = 0; i < 3; ++i) dr[i] = c->x1.r[i] - c->x0.r[i];
-  m3_tvec(R0, dr, t);
-  for (int i = 0; i < 9; ++i) c->xf_rgb[i] = (float)(M[i] - ((i % 4 == 0) ? 1.0 : 0.0));
-  for (int i = 0; i < 3; ++i) c->xf_rgb[9 + i] = (float)t[i];
-}
-
 __device__ void load_pose_ref(Ctrl* c) {
   quat_to_rot(c->x.q, c->Rref);
   for (int i = 0; i < 3; ++i) c->rref[i] = c->x.r[i];
+}
+
+// ---------------------------------------------------------------------------
+// warp-cooperative state algebra
+// ---------------------------------------------------------------------------
+// An FP64 warp instruction costs the same whatever its active lanes, so the
+// small vector / quaternion / 3x3 algebra of the states runs one element per
+// lane: a quaternion product is 4 FMAs on 4 lanes instead of 16 on one.
+
+// Component k (0..3) of the Hamilton product a (x) b: the b index of a_j is
+// k ^ j, and the sign pattern of the sixteen terms is the bit mask 0x428E.
+__device__ __forceinline__ double quat_mul_k(const double a[4], const double* b, int k,
+                                             bool conj_b) {
+  double o = 0.0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int m = k ^ j;
+    const double bm = (conj_b && m) ? -b[m] : b[m];
+    const double t = ((0x428E >> (4 * k + j)) & 1) ? -a[j] : a[j];
+    o = fma(t, bm, o);
+  }
+  return o;
+}
+
+// Element e (0..8, row-major) of the rotation matrix of the unit quaternion q:
+// (w^2 - |v|^2) I + 2 v v^T + 2 w [v]x.
+__device__ __forceinline__ double quat_rot_e(const double* q, int e) {
+  const int r = e / 3, c = e % 3;
+  const double w = q[0];
+  double m = 2.0 * q[1 + r] * q[1 + c];
+  if (r == c) m += w * w - (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  else m += 2.0 * w * ((((c - r + 3) % 3) == 1) ? -q[4 - r - c] : q[4 - r - c]);
+  return m;
+}
+
+// 2 asin(s) / s for s^2 below 6.25e-4 (s = sin(theta / 2), theta < 0.05): the
+// angle / |v| factor of a unit quaternion's log, from the series of asin.
+__device__ __forceinline__ double quat_log_factor(double s2, double w) {
+  if (s2 < 6.25e-4)
+    return 2.0 * (1.0 + s2 * (1.0 / 6 + s2 * (3.0 / 40 + s2 * (5.0 / 112 + s2 * (35.0 / 1152 +
+                                                                                 s2 * (63.0 / 2816))))));
+  const double s = sqrt(s2);
+  return 2.0 * atan2(s, w) / s;
+}
+
+// x <- x boxplus d (Eq. 2) by one warp; x, d in shared or global memory.  Lanes
+// 0-11 add the vector parts; lanes 0-3 update q with d[3..5], lanes 4-7 q_IW
+// with (d[15], d[16], 0): q <- exp(d) (x) q, renormalised.
+__device__ void warp_state_boxplus(DState& x, const double* d) {
+  const int lane = threadIdx.x & 31;
+  const int grp = (lane >> 2) & 1, k = lane & 3;
+  double* q = grp ? x.qg : x.q;
+  const double d0 = grp ? d[15] : d[3], d1 = grp ? d[16] : d[4], d2 = grp ? 0.0 : d[5];
+  const double t2 = d0 * d0 + d1 * d1 + d2 * d2;
+  double sh, ch;
+  if (t2 < kSeriesT2) {
+    sh = 0.5 + t2 * (-1.0 / 48 + t2 * (1.0 / 3840 + t2 * (-1.0 / 645120 + t2 * (1.0 / 185794560))));
+    ch = 1.0 + t2 * (-1.0 / 8 + t2 * (1.0 / 384 + t2 * (-1.0 / 46080 + t2 * (1.0 / 10321920))));
+  } else {
+    const double t = sqrt(t2);
+    double sn, cs;
+    sincos(0.5 * t, &sn, &cs);
+    sh = sn / t;
+    ch = cs;
+  }
+  const double e[4] = {ch, sh * d0, sh * d1, sh * d2};
+  double o = quat_mul_k(e, q, k, false);
+  double n2 = o * o;
+  n2 += __shfl_xor_sync(0xffffffffu, n2, 1);
+  n2 += __shfl_xor_sync(0xffffffffu, n2, 2);
+  o *= fabs(n2 - 1.0) < 1e-6 ? 1.5 - 0.5 * n2 : rsqrt(n2);
+  __syncwarp();
+  if (lane < 8) q[k] = o;
+  if (lane < 12) {
+    const int g = lane / 3, i = lane % 3;
+    double* v = g == 0 ? x.r : g == 1 ? x.v : g == 2 ? x.bg : x.ba;
+    v[i] += d[(g == 0 ? 0 : 3 + 3 * g) + i];
+  }
+  __syncwarp();
+}
+
+// d = x boxminus y (17) by one warp: vector parts subtract; orientations
+// log(q_x (x) q_y^-1) (lanes 0-3), gravity the x, y of log(qg_x (x) qg_y^-1)
+// (lanes 4-7) -- the rotation vector of R_x R_y^T, taken with w >= 0.
+__device__ void warp_state_boxminus(const DState& x, const DState& y, double* d) {
+  const int lane = threadIdx.x & 31;
+  const int grp = (lane >> 2) & 1, k = lane & 3;
+  const double* qx = grp ? x.qg : x.q;
+  const double* qy = grp ? y.qg : y.q;
+  const double a[4] = {qx[0], qx[1], qx[2], qx[3]};
+  double o = quat_mul_k(a, qy, k, true);
+  const int base = lane & ~3;
+  const double w = __shfl_sync(0xffffffffu, o, base);
+  if (w < 0.0) o = -o;
+  double s2 = k ? o * o : 0.0;
+  s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
+  s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
+  const double f = quat_log_factor(s2, fabs(w));
+  if (lane < 12) {
+    const int g = lane / 3, i = lane % 3;
+    const double* vx = g == 0 ? x.r : g == 1 ? x.v : g == 2 ? x.bg : x.ba;
+    const double* vy = g == 0 ? y.r : g == 1 ? y.v : g == 2 ? y.bg : y.ba;
+    d[(g == 0 ? 0 : 3 + 3 * g) + i] = vx[i] - vy[i];
+  }
+  if (grp == 0 && k > 0 && lane < 4) d[2 + k] = f * o;
+  if (grp == 1 && k > 0 && k < 3 && lane < 8) d[14 + k] = f * o;
+  __syncwarp();
+}
+
+// Pixel-kernel transforms for the next linearisation (FP64 -> FP32), one warp:
+// A = R_ref^T R_1 - I, t = R_ref^T (r_1 - r_ref) and A_0 = R_0^T R_1 - I,
+// t_0 = R_0^T (r_1 - r_0).  R_0, R_1 go through shared scratch rot[18].
+__device__ void warp_write_transforms(Ctrl* c, const DState& x0, const DState& x1, double* rot) {
+  const int lane = threadIdx.x & 31;
+  if (lane < 18) rot[lane] = quat_rot_e(lane < 9 ? x1.q : x0.q, lane % 9);
+  __syncwarp();
+  const double* R1 = rot;
+  const double* R0 = rot + 9;
+  if (lane < 18) {
+    const int e = lane % 9, r = e / 3, cc = e % 3;
+    const double* M = lane < 9 ? c->Rref : R0;
+    double v = (r == cc) ? -1.0 : 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v = fma(M[3 * k + r], R1[3 * k + cc], v);
+    (lane < 9 ? c->xf_icp : c->xf_rgb)[e] = (float)v;
+  } else if (lane < 24) {
+    const int i = (lane - 18) % 3;
+    const bool icp = lane < 21;
+    const double* M = icp ? c->Rref : R0;
+    const double* o = icp ? c->rref : x0.r;
+    double v = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v = fma(M[3 * k + i], x1.r[k] - o[k], v);
+    (icp ? c->xf_icp : c->xf_rgb)[9 + i] = (float)v;
+  }
+  __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -501,21 +587,6 @@ __device__ void ldlt_solve_thread(const double* A, int n, int ld, double* b) {
     for (int k = i + 1; k < n; ++k) s -= A[k * ld + i] * b[k];
     b[i] = s;
   }
-}
-
-// Reciprocal of a positive double: an FP32 seed refined by two Newton-Raphson
-// steps y <- y + y (1 - d y) (quadratic convergence, 2^-24 -> 2^-48 -> below
-// 2^-53); outside the FP32 range a plain division.  A dependent FP64 divide costs
-// ~430 cycles here, this ~300.
-__device__ __forceinline__ double recip_pos(double d) {
-  if (d > 1e-30 && d < 1e30) {
-    double y = (double)__frcp_rn((float)d);
-    double e = fma(-d, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-d, y, 1.0);
-    return fma(y, e, y);
-  }
-  return 1.0 / d;
 }
 
 // Pivot reciprocal: the FP32 seed refined by one Newton-Raphson step
@@ -642,6 +713,7 @@ struct GnSmem {
   double col[2 * 27];
   double Lsm[26 * 26];                // L rows of the solver
   double Bg[6], Ag[6];                // gravity Jacobian blocks of x1 and x0 (3 x 2)
+  double rot[18];                     // R_1, R_0 of the pixel transforms
   double cost_imu;
   int ok, fail, pd;
 };
@@ -681,8 +753,8 @@ __device__ void assemble(const SolveParams& sp, GnSmem& S) {
       for (int k = 0; k < 3; ++k) g += R[ri * 3 + k] * s[21 + bi * 3 + k];
       S.gl[term][i] = -w * g;
     }
-  } else if (tid == 128) {
-    state_boxminus(c->x0, c->xbar, S.dprior);
+  } else if ((tid >> 5) == 4) {
+    warp_state_boxminus(c->x0, c->xbar, S.dprior);
   } else if (tid == 160) {
     for (int i = 0; i < 36; ++i) S.M6[i] = (i % 7 == 0) ? 1.0 : 0.0;
     const double d[3] = {c->x1.r[0] - c->x0.r[0], c->x1.r[1] - c->x0.r[1], c->x1.r[2] - c->x0.r[2]};
@@ -887,10 +959,11 @@ __device__ void gn_step_body(const SolveParams& sp, GnSmem& S) {
     if (tid == 0) c->status = DRI_ELOST;
     return;
   }
-  if (tid == 0) {
-    state_boxplus(S.x0, S.x);
-  } else if (tid == 32) {
-    state_boxplus(S.x1, S.x + 17);
+  const int warp = tid >> 5;
+  if (warp == 0) {
+    warp_state_boxplus(S.x0, S.x);
+  } else if (warp == 1) {
+    warp_state_boxplus(S.x1, S.x + 17);
   } else if (tid == 64) {
     const double* s = c->sums;
     c->n_icp[sp.level] = (int32_t)s[28];
@@ -899,10 +972,11 @@ __device__ void gn_step_body(const SolveParams& sp, GnSmem& S) {
     c->iterations += 1;
   }
   __syncthreads();
-  if (tid == 0) {
+  if (warp == 0) {
+    warp_write_transforms(c, S.x0, S.x1, S.rot);
+  } else if (tid == 32) {
     c->x0 = S.x0;
     c->x1 = S.x1;
-    write_transforms(c);
   }
   if (sp.last) {
     for (int idx = tid; idx < 34 * 34; idx += nt) c->H[idx] = S.H[idx];
@@ -921,6 +995,7 @@ struct BeginSmem {
   ImuLin L;
   double G[81], GS[81], Sg[81], Winv[81];
   double col[18];
+  double rot[18];
   int ok, fail;
 };
 
@@ -1027,7 +1102,8 @@ __device__ void frame_begin_body(const SolveParams& sp, BeginSmem& B) {
     for (int l = 0; l < kMaxLevels; ++l) c->n_icp[l] = c->n_rgb[l] = 0;
   }
   __syncthreads();
-  if (imu_weight_and_prediction(sp, c, B, &c->x1) && tid == 0) write_transforms(c);
+  const bool ok = imu_weight_and_prediction(sp, c, B, &c->x1);
+  if (ok && (tid >> 5) == 0) warp_write_transforms(c, c->x0, c->x1, B.rot);
 }
 
 __device__ void frame_end_body(const SolveParams& sp) {
@@ -1144,7 +1220,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_linearise_begin(SolveParams s
     c->x1 = x1;
   }
   __syncthreads();
-  if (imu_weight_and_prediction(sp, c, B, nullptr) && tid == 0) write_transforms(c);
+  const bool ok = imu_weight_and_prediction(sp, c, B, nullptr);
+  if (ok && (tid >> 5) == 0) warp_write_transforms(c, c->x0, c->x1, B.rot);
 }
 
 __global__ void __launch_bounds__(kSolveThreads) k_linearise_end(SolveParams sp, dri_linearisation* out) {
