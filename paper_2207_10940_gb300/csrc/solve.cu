@@ -261,139 +261,237 @@ struct ImuLin {
   double r[3], v[3], c[3];
   double e[18];
   double Jla[9], Jlg[9], Jra[9], Jrg[9];
+  // intermediates of the lane-parallel passes
+  double QR[9], Mg[9], M[9];
+  double t1[3], t2[3], t3[3], t4[3], t5[3], w9[3];
+  double KR[9], RP[9];
+  double B[13][9];                    // Jacobian blocks, indexed by the kB* codes of imu_linearise
 };
 
+// Element e (0..8, row-major) of the rotation matrix of the unit quaternion q:
+// (w^2 - |v|^2) I + 2 v v^T + 2 w [v]x.
+__device__ __forceinline__ double quat_rot_e(const double* q, int e) {
+  const int r = e / 3, c = e % 3;
+  const double w = q[0];
+  double m = 2.0 * q[1 + r] * q[1 + c];
+  if (r == c) m += w * w - (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  else m += 2.0 * w * ((((c - r + 3) % 3) == 1) ? -q[4 - r - c] : q[4 - r - c]);
+  return m;
+}
+
+// ---- element-wise 3x3 algebra: one output element per lane ----
+// element e of op(A) op(B) (row-major; ta / tb transpose A / B)
+__device__ __forceinline__ double mm_e(const double* A, const double* B, int e, bool ta, bool tb) {
+  const int r = e / 3, c = e % 3;
+  double v = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v = fma(ta ? A[3 * k + r] : A[3 * r + k], tb ? B[3 * c + k] : B[3 * k + c], v);
+  return v;
+}
+// element i of op(A) x
+__device__ __forceinline__ double mv_e(const double* A, const double* x, int i, bool ta) {
+  double v = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v = fma(ta ? A[3 * k + i] : A[3 * i + k], x[k], v);
+  return v;
+}
+// element e of [u]x
+__device__ __forceinline__ double hat_e(const double* u, int e) {
+  const int r = e / 3, c = e % 3;
+  if (r == c) return 0.0;
+  const double w = u[3 - r - c];
+  return (((c - r + 3) % 3) == 1) ? -w : w;
+}
+// element e of [u]x M: (u x column c of M)_r
+__device__ __forceinline__ double hatm_e(const double* u, const double* M, int e) {
+  const int r = e / 3, c = e % 3, r1 = (r + 1) % 3, r2 = (r + 2) % 3;
+  return u[r1] * M[3 * r2 + c] - u[r2] * M[3 * r1 + c];
+}
+// element e of op(M) [w]x: (row r of op(M) x w)_c
+__device__ __forceinline__ double mhat_e(const double* M, bool tm, const double* w, int e) {
+  const int r = e / 3, c = e % 3, c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+  const double m1 = tm ? M[3 * c1 + r] : M[3 * r + c1];
+  const double m2 = tm ? M[3 * c2 + r] : M[3 * r + c2];
+  return m1 * w[c2] - m2 * w[c1];
+}
+// component i of the rotation vector of R (so3_log, as one lane's share)
+__device__ __forceinline__ double log_i(const double* R, int i) {
+  const double c = 0.5 * (R[0] + R[4] + R[8] - 1.0);
+  const double v0 = R[7] - R[5], v1 = R[2] - R[6], v2 = R[3] - R[1];
+  double f;
+  if (c > 0.99875) {
+    const double s2 = 0.25 * (v0 * v0 + v1 * v1 + v2 * v2);
+    f = 0.5 * (1.0 + s2 * (1.0 / 6 + s2 * (3.0 / 40 + s2 * (5.0 / 112 + s2 * (35.0 / 1152 +
+               s2 * (63.0 / 2816 + s2 * (231.0 / 13312)))))));
+  } else {
+    const double t = acos(fmin(1.0, fmax(-1.0, c)));
+    f = t / (2.0 * sin(t));
+  }
+  return f * (i == 0 ? v0 : i == 1 ? v1 : v2);
+}
+// element e of Jl^-1(s w) (s = +1, or -1 for Jr^-1(w) = Jl^-1(-w))
+__device__ __forceinline__ double jlinv_e(const double* w0, double s, int e) {
+  const double w[3] = {s * w0[0], s * w0[1], s * w0[2]};
+  const double t2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double c;
+  if (t2 < kSeriesT2) {
+    c = 1.0 / 12 + t2 * (1.0 / 720 + t2 * (1.0 / 30240 + t2 * (1.0 / 1209600 + t2 * (1.0 / 47900160))));
+  } else {
+    const double t = sqrt(t2);
+    double sn, co;
+    sincos(t, &sn, &co);
+    c = 1.0 / t2 - (1.0 + co) / (2.0 * t * sn);
+  }
+  const int r = e / 3, q = e % 3;
+  // I - K/2 + c K^2,  K^2 = w w^T - t2 I
+  return (r == q ? 1.0 - c * t2 : 0.0) - 0.5 * hat_e(w, e) + c * w[r] * w[q];
+}
+
+// Jacobian-block codes of imu_linearise: 0 zero, 1 +I, 2 -I, 16 + 2 m + neg: block B[m] / J*
+constexpr int kBJra = 0, kBJrg = 1, kB7 = 2, kBJla = 3, kB9 = 4, kB10 = 5, kB12 = 6, kB13 = 7,
+              kB14 = 8, kB16 = 9, kB17 = 10, kB19 = 11, kB20 = 12, kBJlg = 13;
+__device__ constexpr unsigned char kJBlk[2][6][6] = {
+    // x0 columns: r, alpha, v, b_g, b_a, gravity (2 columns)
+    {{1, 16 + 2 * kB7, 16 + 2 * kB10, 16 + 2 * kB12, 16 + 2 * kB16, 16 + 2 * kB19},
+     {0, 16 + 2 * kBJla, 0, 16 + 2 * kB13, 0, 0},
+     {0, 16 + 2 * kB9, 1, 16 + 2 * kB14, 16 + 2 * kB17, 16 + 2 * kB20},
+     {0, 0, 0, 1, 0, 0},
+     {0, 0, 0, 0, 1, 0},
+     {0, 0, 0, 0, 0, 16 + 2 * kBJlg}},
+    // x1 columns
+    {{2, 0, 0, 0, 0, 0},
+     {0, 17 + 2 * kBJra, 0, 0, 0, 0},
+     {0, 0, 2, 0, 0, 0},
+     {0, 0, 0, 2, 0, 0},
+     {0, 0, 0, 0, 2, 0},
+     {0, 0, 0, 0, 0, 17 + 2 * kBJrg}}};
+
 // Whole block: prediction x^1(x0), error e = x^1 boxminus x1 and (when J) the
-// 18 x 34 Jacobian (row-major).  cols: x0 tangent 0..16, x1 tangent 17..33.
+// 18 x 34 Jacobian (row-major; columns: x0 tangent 0..16, x1 tangent 17..33).
+// Warp 0 runs the chain of small products one output element per lane, up to
+// three independent products per pass (lanes 0-8, 9-17, 18-26).
+//   R^ = R0 Rc dR Rc^T,  r^ = r0 + R0 rc + Q0^T c + A0 dp - R^ rc  (A0 = R0 Rc),
+//   v^ = v0 + g T + Q0 A0 dv,  c = v0 T + g T^2 / 2,
+//   e = (r^ - r1, log(R^ R1^T), v^ - v1, b0 - b1, log(Q0 Q1^T)).
 __device__ void imu_linearise(const DState& x0, const DState& x1, const Preint& P,
                               const SolveParams& sp, ImuLin& L, double* J) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  if (tid == 0) quat_to_rot(x0.q, L.R0);          // independent serial pieces go to
-  else if (tid == 32) quat_to_rot(x0.qg, L.Q0);   // different warps so they overlap
-  else if (tid == 64) quat_to_rot(x1.q, L.R1);
-  else if (tid == 96) quat_to_rot(x1.qg, L.Q1);
-  __syncthreads();
-  if (tid == 0) {
-    const double T = P.T;
-    const double gI[3] = {0.0, 0.0, -sp.g};
-    m3_mul(L.R0, sp.R_CS, L.A0);
-    m3_mul(L.A0, P.dR, L.RWS1);
-    m3_mult(L.RWS1, sp.R_CS, L.Rh);                 // R^ = R0 Rc dR Rc^T
-    double c[3], t1[3], t2[3], t3[3], t4[3], M[9];
-    for (int i = 0; i < 3; ++i) c[i] = x0.v[i] * T + 0.5 * gI[i] * T * T;
-    m3_vec(L.R0, sp.r_CS, t1);
-    m3_tvec(L.Q0, c, t2);
-    m3_vec(L.A0, P.dp, t3);
-    m3_vec(L.Rh, sp.r_CS, t4);
-    for (int i = 0; i < 3; ++i) {
-      L.r[i] = x0.r[i] + t1[i] + t2[i] + t3[i] - t4[i];
-      L.e[i] = L.r[i] - x1.r[i];
+  const int g3 = lane / 9, e9 = lane % 9;
+  const double T = P.T;
+  const double* Rc = sp.R_CS;
+  const double* rc = sp.r_CS;
+  if (warp == 0) {
+    // rotations of the four quaternions, c
+    if (lane < 27) (g3 == 0 ? L.R0 : g3 == 1 ? L.Q0 : L.R1)[e9] =
+        quat_rot_e(g3 == 0 ? x0.q : g3 == 1 ? x0.qg : x1.q, e9);
+    __syncwarp();
+    if (lane < 9) L.Q1[lane] = quat_rot_e(x1.qg, lane);
+    else if (lane < 12) L.c[lane - 9] = x0.v[lane - 9] * T + (lane == 11 ? -0.5 * sp.g * T * T : 0.0);
+    else if (lane < 18) L.e[9 + lane - 12] = lane < 15 ? x0.bg[lane - 12] - x1.bg[lane - 12]
+                                                       : x0.ba[lane - 15] - x1.ba[lane - 15];
+    __syncwarp();
+    // A0 = R0 Rc, QR = Q0 R0, Mg = Q0 Q1^T
+    if (lane < 27) {
+      const double* A = g3 == 0 ? L.R0 : L.Q0;
+      const double* B = g3 == 0 ? Rc : g3 == 1 ? L.R0 : L.Q1;
+      (g3 == 0 ? L.A0 : g3 == 1 ? L.QR : L.Mg)[e9] = mm_e(A, B, e9, false, g3 == 2);
     }
-    m3_mult(L.Rh, L.R1, M);
-    so3_log(M, L.e + 3);
-  } else if (tid == 32) {
-    const double T = P.T;
-    double QR[9], t5[3];
-    m3_mul(L.Q0, L.R0, QR);
-    m3_mul(QR, sp.R_CS, L.QA);                      // Q0 R0 Rc
-    m3_vec(L.QA, P.dv, t5);
-    for (int i = 0; i < 3; ++i) {
-      L.c[i] = x0.v[i] * T + 0.5 * (i == 2 ? -sp.g : 0.0) * T * T;
-      L.v[i] = x0.v[i] + (i == 2 ? -sp.g : 0.0) * T + t5[i];
-      L.e[6 + i] = L.v[i] - x1.v[i];
+    __syncwarp();
+    // RWS1 = A0 dR, QA = QR Rc, t1 = R0 rc, t2 = Q0^T c, t3 = A0 dp
+    if (lane < 18) {
+      (g3 == 0 ? L.RWS1 : L.QA)[e9] = mm_e(g3 == 0 ? L.A0 : L.QR, g3 == 0 ? P.dR : Rc, e9, false, false);
+    } else if (lane < 27) {
+      const int k = (lane - 18) / 3, i = (lane - 18) % 3;
+      const double* A = k == 0 ? L.R0 : k == 1 ? L.Q0 : L.A0;
+      const double* x = k == 0 ? rc : k == 1 ? L.c : P.dp;
+      (k == 0 ? L.t1 : k == 1 ? L.t2 : L.t3)[i] = mv_e(A, x, i, k == 1);
     }
-  } else if (tid == 64) {
-    double M[9];
-    for (int i = 0; i < 3; ++i) {
-      L.e[9 + i] = x0.bg[i] - x1.bg[i];
-      L.e[12 + i] = x0.ba[i] - x1.ba[i];
+    __syncwarp();
+    // Rh = RWS1 Rc^T, t5 = QA dv, w9 = A0 dv
+    if (lane < 9) L.Rh[lane] = mm_e(L.RWS1, Rc, lane, false, true);
+    else if (lane < 15) {
+      const int k = (lane - 9) / 3, i = (lane - 9) % 3;
+      (k == 0 ? L.t5 : L.w9)[i] = mv_e(k == 0 ? L.QA : L.A0, P.dv, i, false);
     }
-    m3_mult(L.Q0, L.Q1, M);
-    so3_log(M, L.e + 15);
+    __syncwarp();
+    // t4 = Rh rc, M = Rh R1^T, v^, e_v
+    if (lane < 3) L.t4[lane] = mv_e(L.Rh, rc, lane, false);
+    else if (lane < 12) L.M[lane - 3] = mm_e(L.Rh, L.R1, lane - 3, false, true);
+    else if (lane < 15) {
+      const int i = lane - 12;
+      const double vi = x0.v[i] + (i == 2 ? -sp.g : 0.0) * T + L.t5[i];
+      L.v[i] = vi;
+      L.e[6 + i] = vi - x1.v[i];
+    }
+    __syncwarp();
+    // r^, e_r; e_a = log(R^ R1^T), e_g = log(Q0 Q1^T)
+    if (lane < 3) {
+      const double ri = x0.r[lane] + L.t1[lane] + L.t2[lane] + L.t3[lane] - L.t4[lane];
+      L.r[lane] = ri;
+      L.e[lane] = ri - x1.r[lane];
+    } else if (lane < 9) {
+      const int k = (lane - 3) / 3, i = (lane - 3) % 3;
+      L.e[(k == 0 ? 3 : 15) + i] = log_i(k == 0 ? L.M : L.Mg, i);
+    }
+    __syncwarp();
   }
   __syncthreads();
-  if (tid == 0) so3_jl_inv(L.e + 3, L.Jla);
-  else if (tid == 32) so3_jl_inv(L.e + 15, L.Jlg);
-  else if (tid == 64) so3_jr_inv(L.e + 3, L.Jra);
-  else if (tid == 96) so3_jr_inv(L.e + 15, L.Jrg);
-  if (J == nullptr) {
-    __syncthreads();
-    return;
+  if (J == nullptr) return;
+  // Jacobians of the two orientation errors, and the product blocks (warps 0-1)
+  if (warp == 0) {
+    if (lane < 27) (g3 == 0 ? L.Jla : g3 == 1 ? L.Jlg : L.Jra)[e9] =
+        jlinv_e(g3 == 1 ? L.e + 15 : L.e + 3, g3 == 2 ? -1.0 : 1.0, e9);
+    __syncwarp();
+    if (lane < 9) L.Jrg[lane] = jlinv_e(L.e + 15, -1.0, lane);
+    __syncwarp();
+    // B13 = Jla RWS1 Phig (via RP), B14 = QA Vg, B16 = A0 Pa
+    if (lane < 9) L.RP[lane] = mm_e(L.RWS1, P.Phig, lane, false, false);
+    else if (lane < 18) L.B[kB14][e9] = mm_e(L.QA, P.Vg, e9, false, false);
+    else if (lane < 27) L.B[kB16][e9] = mm_e(L.A0, P.Pa, e9, false, false);
+    __syncwarp();
+    if (lane < 9) L.B[kB13][lane] = mm_e(L.Jla, L.RP, lane, false, false);
+    __syncwarp();
+  } else if (warp == 1) {
+    // B12 = A0 Pg + [Rh rc]x RWS1 Phig (via KR), B17 = QA Va
+    if (lane < 9) L.KR[lane] = hatm_e(L.t4, L.RWS1, lane);
+    else if (lane < 18) L.B[kB17][e9] = mm_e(L.QA, P.Va, e9, false, false);
+    __syncwarp();
+    if (lane < 9) L.B[kB12][lane] = mm_e(L.A0, P.Pg, lane, false, false) + mm_e(L.KR, P.Phig, lane, false, false);
+    __syncwarp();
+  } else if (warp == 2) {
+    // B7 = -[r^ - r0 - Q0^T c]x, B9 = -Q0 [A0 dv]x, B10 = T Q0^T
+    if (lane < 9) {
+      const double u[3] = {L.r[0] - x0.r[0] - L.t2[0], L.r[1] - x0.r[1] - L.t2[1], L.r[2] - x0.r[2] - L.t2[2]};
+      L.B[kB7][lane] = -hat_e(u, lane);
+    } else if (lane < 18) {
+      L.B[kB9][e9] = -mhat_e(L.Q0, false, L.w9, e9);
+    } else if (lane < 27) {
+      L.B[kB10][e9] = T * L.Q0[3 * (e9 % 3) + e9 / 3];
+    }
+    __syncwarp();
+  } else if (warp == 3) {
+    // B19 = Q0^T [c]x, B20 = -[Q0 A0 dv]x (first two columns used)
+    if (lane < 9) L.B[kB19][lane] = mhat_e(L.Q0, true, L.c, lane);
+    else if (lane < 18) L.B[kB20][e9] = -hat_e(L.t5, e9);
+    __syncwarp();
   }
-  for (int i = tid; i < 18 * 34; i += blockDim.x) J[i] = 0.0;
   __syncthreads();
-  auto put3 = [&](int r0, int c0, const double* B, double s) {
-    for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c) J[(r0 + r) * 34 + c0 + c] = s * B[r * 3 + c];
-  };
-  auto put32 = [&](int r0, int c0, const double* B, double s) {   // B P2: first two columns
-    for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 2; ++c) J[(r0 + r) * 34 + c0 + c] = s * B[r * 3 + c];
-  };
-  auto ident = [&](int r0, int c0, double s) {
-    for (int r = 0; r < 3; ++r) J[(r0 + r) * 34 + c0 + r] = s;
-  };
-  // 22 blocks: heavy ones alone on their warp (lane 0), light ones share warps
-  constexpr int kTab[8][4] = {{12, -1, -1, -1}, {13, -1, -1, -1}, {7, 0, 2, -1}, {9, 3, 4, -1},
-                              {14, 6, 11, -1},  {16, 15, 18, -1}, {17, 19, 1, -1}, {20, 21, 5, 8}};
-  int blk = -1;
-  if (lane < 4) blk = kTab[warp][lane];
-  if (warp == 0 && lane == 4) blk = 10;
-  double t[9], K[9], u[3];
-  switch (blk) {
-    // x1 columns 17..33
-    case 0: ident(0, 17, -1.0); break;
-    case 1: put3(3, 20, L.Jra, -1.0); break;
-    case 2: ident(6, 23, -1.0); break;
-    case 3: ident(9, 26, -1.0); break;
-    case 4: ident(12, 29, -1.0); break;
-    case 5: put32(15, 32, L.Jrg, -1.0); break;
-    // x0 columns 0..16
-    case 6: ident(0, 0, 1.0); break;
-    case 7: {                                          // -[r^ - r0 - Q0^T c]x
-      m3_tvec(L.Q0, L.c, u);
-      for (int i = 0; i < 3; ++i) u[i] = L.r[i] - x0.r[i] - u[i];
-      hat3(u, K);
-      put3(0, 3, K, -1.0);
-    } break;
-    case 8: put3(3, 3, L.Jla, 1.0); break;
-    case 9: {                                          // -Q0 [A0 dv]x
-      m3_vec(L.A0, P.dv, u);
-      hat3(u, K);
-      m3_mul(L.Q0, K, t);
-      put3(6, 3, t, -1.0);
-    } break;
-    case 10: {                                         // Q0^T T
-      for (int i = 0; i < 9; ++i) t[i] = L.Q0[(i % 3) * 3 + i / 3];
-      put3(0, 6, t, P.T);
-    } break;
-    case 11: ident(6, 6, 1.0); break;
-    case 12: {                                         // A0 Pg + [R^ rc]x RWS1 Phig
-      double KR[9], KRP[9], AP[9];
-      m3_vec(L.Rh, sp.r_CS, u);
-      hat3(u, K);
-      m3_mul(K, L.RWS1, KR);
-      m3_mul(KR, P.Phig, KRP);
-      m3_mul(L.A0, P.Pg, AP);
-      for (int i = 0; i < 9; ++i) t[i] = AP[i] + KRP[i];
-      put3(0, 9, t, 1.0);
-    } break;
-    case 13: {                                         // Jl^-1(e_a) RWS1 Phig
-      double RP[9];
-      m3_mul(L.RWS1, P.Phig, RP);
-      m3_mul(L.Jla, RP, t);
-      put3(3, 9, t, 1.0);
-    } break;
-    case 14: m3_mul(L.QA, P.Vg, t); put3(6, 9, t, 1.0); break;
-    case 15: ident(9, 9, 1.0); break;
-    case 16: m3_mul(L.A0, P.Pa, t); put3(0, 12, t, 1.0); break;
-    case 17: m3_mul(L.QA, P.Va, t); put3(6, 12, t, 1.0); break;
-    case 18: ident(12, 12, 1.0); break;
-    case 19: hat3(L.c, K); m3_tmul(L.Q0, K, t); put32(0, 15, t, 1.0); break;   // Q0^T [c]x P2
-    case 20: m3_vec(L.QA, P.dv, u); hat3(u, K); put32(6, 15, K, -1.0); break;  // -[Q0 A0 dv]x P2
-    case 21: put32(15, 15, L.Jlg, 1.0); break;                                  // Jl^-1(e_g) P2
-    default: break;
+  const double* src[14] = {L.Jra, L.Jrg, L.B[kB7], L.Jla, L.B[kB9], L.B[kB10], L.B[kB12],
+                           L.B[kB13], L.B[kB14], L.B[kB16], L.B[kB17], L.B[kB19], L.B[kB20], L.Jlg};
+  for (int idx = tid; idx < 18 * 34; idx += blockDim.x) {
+    const int r = idx / 34, col = idx % 34;
+    const int side = col >= 17 ? 1 : 0, cl = col - 17 * side;
+    const int cg = cl < 15 ? cl / 3 : 5, cc = cl < 15 ? cl % 3 : cl - 15;
+    const int rb = r / 3, rr = r % 3;
+    const int code = kJBlk[side][rb][cg];
+    double v = 0.0;
+    if (code == 1 || code == 2) v = rr == cc ? (code == 1 ? 1.0 : -1.0) : 0.0;
+    else if (code >= 16) {
+      const double m = src[(code - 16) >> 1][3 * rr + cc];
+      v = (code & 1) ? -m : m;
+    }
+    J[idx] = v;
   }
   __syncthreads();
 }
@@ -429,16 +527,6 @@ __device__ __forceinline__ double quat_mul_k(const double a[4], const double* b,
   return o;
 }
 
-// Element e (0..8, row-major) of the rotation matrix of the unit quaternion q:
-// (w^2 - |v|^2) I + 2 v v^T + 2 w [v]x.
-__device__ __forceinline__ double quat_rot_e(const double* q, int e) {
-  const int r = e / 3, c = e % 3;
-  const double w = q[0];
-  double m = 2.0 * q[1 + r] * q[1 + c];
-  if (r == c) m += w * w - (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-  else m += 2.0 * w * ((((c - r + 3) % 3) == 1) ? -q[4 - r - c] : q[4 - r - c]);
-  return m;
-}
 
 // 2 asin(s) / s for s^2 below 6.25e-4 (s = sin(theta / 2), theta < 0.05): the
 // angle / |v| factor of a unit quaternion's log, from the series of asin.
