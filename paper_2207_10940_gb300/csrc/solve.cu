@@ -55,27 +55,40 @@ __device__ __forceinline__ const dri_imu_sample* imu_samples(const ImuHeader* h)
   return reinterpret_cast<const dri_imu_sample*>(h + 1);
 }
 
-// Zero-order-hold pieces of [t0, t1] from the sample times ts[0..n): sample index
-// and duration; -1 if the samples do not cover the interval or there are more than
-// kMaxPieces pieces.
-__device__ int imu_pieces(const double* ts, int n, double t0, double t1, int* pk, double* pdt) {
-  if (n <= 0 || ts[0] > t0 || ts[n - 1] < t1 || !(t1 > t0)) return -1;
-  int k = 0;
-  while (k + 1 < n && ts[k + 1] <= t0) ++k;
-  double tau = t0;
-  int np = 0;
-  while (tau < t1) {
-    const double nxt = (k + 1 >= n) ? t1 : fmin(ts[k + 1], t1);
-    if (nxt > tau) {
-      if (np >= kMaxPieces) return -1;
-      pk[np] = k;
-      pdt[np] = nxt - tau;
-      ++np;
-    }
-    tau = nxt;
-    ++k;
-  }
-  return np;
+// ---- element-wise 3x3 algebra: one output element per lane ----
+// element e of op(A) op(B) (row-major; ta / tb transpose A / B)
+__device__ __forceinline__ double mm_e(const double* A, const double* B, int e, bool ta, bool tb) {
+  const int r = e / 3, c = e % 3;
+  double v = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v = fma(ta ? A[3 * k + r] : A[3 * r + k], tb ? B[3 * c + k] : B[3 * k + c], v);
+  return v;
+}
+// element i of op(A) x
+__device__ __forceinline__ double mv_e(const double* A, const double* x, int i, bool ta) {
+  double v = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) v = fma(ta ? A[3 * k + i] : A[3 * i + k], x[k], v);
+  return v;
+}
+// element e of [u]x
+__device__ __forceinline__ double hat_e(const double* u, int e) {
+  const int r = e / 3, c = e % 3;
+  if (r == c) return 0.0;
+  const double w = u[3 - r - c];
+  return (((c - r + 3) % 3) == 1) ? -w : w;
+}
+// element e of [u]x M: (u x column c of M)_r
+__device__ __forceinline__ double hatm_e(const double* u, const double* M, int e) {
+  const int r = e / 3, c = e % 3, r1 = (r + 1) % 3, r2 = (r + 2) % 3;
+  return u[r1] * M[3 * r2 + c] - u[r2] * M[3 * r1 + c];
+}
+// element e of op(M) [w]x: (row r of op(M) x w)_c
+__device__ __forceinline__ double mhat_e(const double* M, bool tm, const double* w, int e) {
+  const int r = e / 3, c = e % 3, c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+  const double m1 = tm ? M[3 * c1 + r] : M[3 * r + c1];
+  const double m2 = tm ? M[3 * c2 + r] : M[3 * r + c2];
+  return m1 * w[c2] - m2 * w[c1];
 }
 
 struct Preint {
@@ -96,7 +109,9 @@ struct ImuWork {
   double Cv[kMaxPieces + 1][3];       // suffix sums of u_k dt_k
   double Dv[kMaxPieces + 1][3];       // suffix sums of u_k w_k
   double ts[kMaxPieces + 2];          // sample times
+  double S2[kMaxPieces][9];           // scan scratch
   int pk[kMaxPieces];
+  int wcount[kSolveThreads / 32];     // valid pieces per warp (compaction)
   int np;
 };
 
@@ -126,37 +141,77 @@ __device__ __forceinline__ void gyro_gain_row(const ImuWork& W, int np, int k, i
 __device__ bool preintegrate_block(const ImuHeader* h, const double* bg, const double* ba, bool cov,
                                    double gnd, double and_, ImuWork& W, Preint& P) {
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31;
   const dri_imu_sample* s = imu_samples(h);
   const int ns = h->n;
-  const bool fits = ns > 0 && ns <= kMaxPieces + 2;
+  const double t0 = h->t0, t1 = h->t1;
+  const bool fits = ns > 0 && ns <= kMaxPieces + 2 && ns <= nt;
   if (fits)
     for (int k = tid; k < ns; k += nt) W.ts[k] = s[k].t;   // one coalesced pass
   __syncthreads();
-  if (tid == 0) W.np = fits ? imu_pieces(W.ts, ns, h->t0, h->t1, W.pk, W.dt) : -1;
+  // Zero-order-hold pieces: sample k holds on [max(t_k, t0), min(t_k+1, t1)) (the
+  // last one until t1).  The pieces of positive length, in sample order, are
+  // compacted by warp ballots: the same cut as a sequential walk over the interval.
+  const bool cover = fits && W.ts[0] <= t0 && W.ts[ns - 1] >= t1 && t1 > t0;
+  double lo = 0.0, hi = 0.0;
+  bool valid = false;
+  if (cover && tid < ns) {
+    lo = fmax(W.ts[tid], t0);
+    hi = tid + 1 < ns ? fmin(W.ts[tid + 1], t1) : t1;
+    valid = hi > lo;
+  }
+  const unsigned ball = __ballot_sync(0xffffffffu, valid);
+  if (lane == 0) W.wcount[warp] = __popc(ball);
+  __syncthreads();
+  if (tid == 0) {
+    int tot = 0;
+    for (int w = 0; w < (nt >> 5); ++w) {
+      const int c = W.wcount[w];
+      W.wcount[w] = tot;
+      tot += c;
+    }
+    W.np = (cover && tot <= kMaxPieces) ? tot : -1;
+  }
   __syncthreads();
   const int np = W.np;
   if (np <= 0) return false;
-  for (int k = tid; k < np; k += nt) {
+  if (valid) {
+    const int idx = W.wcount[warp] + __popc(ball & ((1u << lane) - 1u));
+    W.pk[idx] = tid;
+    W.dt[idx] = hi - lo;
+  }
+  __syncthreads();
+  // Exp(theta_k) and Jr(theta_k), one matrix element per lane (Rodrigues forms
+  // I + a K + b K^2 with K = [theta]x, K^2 = theta theta^T - |theta|^2 I);
+  // u_k = a_k - b_a; piece start times on the last lane
+  for (int L = tid; L < 9 * np; L += nt) {
+    const int k = L / 9, e = L % 9;
     const dri_imu_sample& m = s[W.pk[k]];
     const double dt = W.dt[k];
     const double th[3] = {(m.gyr[0] - bg[0]) * dt, (m.gyr[1] - bg[1]) * dt, (m.gyr[2] - bg[2]) * dt};
-    so3_exp(th, W.EP[k]);
-    so3_jr(th, W.Y[k]);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) W.u[k][i] = m.acc[i] - ba[i];
-  }
-  __syncthreads();
-  if (tid < 9) {                       // prefix products dR_{k+1} = dR_k Exp(theta_k)
-    const int r = tid / 3, c = tid % 3;
-    W.dR[0][tid] = (r == c) ? 1.0 : 0.0;
-    __syncwarp(0x1ffu);
-    for (int k = 0; k < np; ++k) {
-      const double* A = W.dR[k];
-      const double* E = W.EP[k];
-      W.dR[k + 1][tid] = A[3 * r] * E[c] + A[3 * r + 1] * E[3 + c] + A[3 * r + 2] * E[6 + c];
-      __syncwarp(0x1ffu);
+    const double t2 = th[0] * th[0] + th[1] * th[1] + th[2] * th[2];
+    double ea, eb, jb;
+    if (t2 < kSeriesT2) {
+      ea = 1.0 + t2 * (-1.0 / 6 + t2 * (1.0 / 120 + t2 * (-1.0 / 5040 + t2 * (1.0 / 362880))));
+      eb = 0.5 + t2 * (-1.0 / 24 + t2 * (1.0 / 720 + t2 * (-1.0 / 40320 + t2 * (1.0 / 3628800))));
+      jb = 1.0 / 6 + t2 * (-1.0 / 120 + t2 * (1.0 / 5040 + t2 * (-1.0 / 362880 + t2 * (1.0 / 39916800))));
+    } else {
+      const double t = sqrt(t2);
+      double sn, cs;
+      sincos(t, &sn, &cs);
+      ea = sn / t;
+      eb = (1.0 - cs) / t2;
+      jb = (t - sn) / (t2 * t);
     }
-  } else if (tid == 32) {              // piece start times (another warp)
+    const int r = e / 3, c = e % 3;
+    const double K = hat_e(th, e);
+    const double K2 = th[r] * th[c] - (r == c ? t2 : 0.0);
+    const double id = r == c ? 1.0 : 0.0;
+    W.EP[k][e] = id + ea * K + eb * K2;            // Exp
+    W.Y[k][e] = id - eb * K + jb * K2;             // Jr
+    if (e < 3) W.u[k][e] = m.acc[e] - ba[e];
+  }
+  if (tid == nt - 1) {
     double acc = 0.0;
     W.tau[0] = 0.0;
     for (int k = 0; k < np; ++k) {
@@ -165,39 +220,76 @@ __device__ bool preintegrate_block(const ImuHeader* h, const double* bg, const d
     }
   }
   __syncthreads();
-  const double T = W.tau[np];
-  for (int k = tid; k < np; k += nt) {
-    const double dt = W.dt[k];
-    double u[3], Yp[9];
-    m3_vec(W.dR[k], W.u[k], u);
-    m3_mul(W.dR[k + 1], W.Y[k], Yp);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) W.u[k][i] = u[i];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) W.Y[k][i] = Yp[i];
-    W.w[k] = dt * (T - W.tau[k + 1]) + 0.5 * dt * dt;
+  // dR_{k+1} = Exp_0 ... Exp_k: inclusive prefix product (Hillis-Steele, earlier
+  // factors on the left), alternating between EP and S2
+  double(*cur)[9] = W.EP;
+  double(*nxt)[9] = W.S2;
+  for (int d = 1; d < np; d <<= 1) {
+    for (int L = tid; L < 9 * np; L += nt) {
+      const int k = L / 9, e = L % 9;
+      nxt[k][e] = k >= d ? mm_e(cur[k - d], cur[k], e, false, false) : cur[k][e];
+    }
+    __syncthreads();
+    double(*t)[9] = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  for (int L = tid; L < 9 * (np + 1); L += nt) {
+    const int k = L / 9, e = L % 9;
+    W.dR[k][e] = k == 0 ? ((e % 4 == 0) ? 1.0 : 0.0) : cur[k - 1][e];
   }
   __syncthreads();
-  if (tid < 9) {                       // Psi_k = -sum_{i<k} Y_i dt_i
-    double acc = 0.0;
-    W.EP[0][tid] = 0.0;
-    for (int k = 0; k < np; ++k) {
-      acc -= W.Y[k][tid] * W.dt[k];
-      W.EP[k + 1][tid] = acc;
+  const double T = W.tau[np];
+  // Y_k <- dR_{k+1} Jr_k and u_k <- dR_k u_k (through S2 / EP), w_k
+  for (int L = tid; L < 9 * np; L += nt) {
+    const int k = L / 9, e = L % 9;
+    W.S2[k][e] = mm_e(W.dR[k + 1], W.Y[k], e, false, false);
+    if (e < 3) W.EP[k][e] = mv_e(W.dR[k], W.u[k], e, false);
+    if (e == 0) W.w[k] = W.dt[k] * (T - W.tau[k + 1]) + 0.5 * W.dt[k] * W.dt[k];
+  }
+  __syncthreads();
+  for (int L = tid; L < 9 * np; L += nt) {
+    const int k = L / 9, e = L % 9;
+    const double y = W.S2[k][e];
+    W.Y[k][e] = y;
+    if (e < 3) W.u[k][e] = W.EP[k][e];
+    W.S2[k][e] = -y * W.dt[k];                     // scan input of Psi
+  }
+  __syncthreads();
+  // Psi_k = -sum_{i<k} Y_i dt_i: inclusive additive scan, shifted by one into EP
+  cur = W.S2;
+  nxt = W.EP;
+  for (int d = 1; d < np; d <<= 1) {
+    for (int L = tid; L < 9 * np; L += nt) {
+      const int k = L / 9, e = L % 9;
+      nxt[k][e] = k >= d ? cur[k - d][e] + cur[k][e] : cur[k][e];
     }
-  } else if (cov && tid >= 32 && tid < 38) {   // suffix sums for the noise transition
-    const int i = (tid - 32) % 3;
-    const bool isD = tid >= 35;
-    double(*S)[3] = isD ? W.Dv : W.Cv;
+    __syncthreads();
+    double(*t)[9] = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  if (cur == W.EP) {                                // move the result out of EP first
+    for (int L = tid; L < 9 * np; L += nt) W.S2[L / 9][L % 9] = W.EP[L / 9][L % 9];
+    __syncthreads();
+  }
+  for (int L = tid; L < 9 * (np + 1); L += nt) {
+    const int k = L / 9, e = L % 9;
+    W.EP[k][e] = k == 0 ? 0.0 : W.S2[k - 1][e];
+  }
+  if (cov && tid >= nt - 6) {                       // suffix sums for the noise transition
+    const int q = tid - (nt - 6);
+    const int i = q % 3;
+    const bool isD = q >= 3;
+    double(*Sx)[3] = isD ? W.Dv : W.Cv;
     double acc = 0.0;
-    S[np][i] = 0.0;
+    Sx[np][i] = 0.0;
     for (int k = np - 1; k >= 0; --k) {
       acc += W.u[k][i] * (isD ? W.w[k] : W.dt[k]);
-      S[k][i] = acc;
+      Sx[k][i] = acc;
     }
   }
   __syncthreads();
-  const int warp = tid >> 5, lane = tid & 31;
   if (warp == 0 && lane < 6) {         // dv, dp
     const int i = lane % 3;
     double acc = 0.0;
@@ -279,41 +371,6 @@ __device__ __forceinline__ double quat_rot_e(const double* q, int e) {
   return m;
 }
 
-// ---- element-wise 3x3 algebra: one output element per lane ----
-// element e of op(A) op(B) (row-major; ta / tb transpose A / B)
-__device__ __forceinline__ double mm_e(const double* A, const double* B, int e, bool ta, bool tb) {
-  const int r = e / 3, c = e % 3;
-  double v = 0.0;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) v = fma(ta ? A[3 * k + r] : A[3 * r + k], tb ? B[3 * c + k] : B[3 * k + c], v);
-  return v;
-}
-// element i of op(A) x
-__device__ __forceinline__ double mv_e(const double* A, const double* x, int i, bool ta) {
-  double v = 0.0;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) v = fma(ta ? A[3 * k + i] : A[3 * i + k], x[k], v);
-  return v;
-}
-// element e of [u]x
-__device__ __forceinline__ double hat_e(const double* u, int e) {
-  const int r = e / 3, c = e % 3;
-  if (r == c) return 0.0;
-  const double w = u[3 - r - c];
-  return (((c - r + 3) % 3) == 1) ? -w : w;
-}
-// element e of [u]x M: (u x column c of M)_r
-__device__ __forceinline__ double hatm_e(const double* u, const double* M, int e) {
-  const int r = e / 3, c = e % 3, r1 = (r + 1) % 3, r2 = (r + 2) % 3;
-  return u[r1] * M[3 * r2 + c] - u[r2] * M[3 * r1 + c];
-}
-// element e of op(M) [w]x: (row r of op(M) x w)_c
-__device__ __forceinline__ double mhat_e(const double* M, bool tm, const double* w, int e) {
-  const int r = e / 3, c = e % 3, c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-  const double m1 = tm ? M[3 * c1 + r] : M[3 * r + c1];
-  const double m2 = tm ? M[3 * c2 + r] : M[3 * r + c2];
-  return m1 * w[c2] - m2 * w[c1];
-}
 // component i of the rotation vector of R (so3_log, as one lane's share)
 __device__ __forceinline__ double log_i(const double* R, int i) {
   const double c = 0.5 * (R[0] + R[4] + R[8] - 1.0);
