@@ -254,6 +254,12 @@ def run_reference(args):
     return 0
 
 
+def dtype_of(flags):
+    maps = "f16 normal/gradient maps, " if flags & 1 else ""
+    red = "f32" if flags & 2 else "f64"
+    return f"{maps}f32 per-pixel, {red} reduction, f64 solve"
+
+
 def config_json(batch=BATCH):
     return {"workload": f"{batch} independent streams of 640x480 RGB-D + 400 Hz IMU per step "
                         f"(one dri_track_batch call), 3 levels 10/5/4 GN iterations; plain: one "
@@ -298,14 +304,15 @@ class Runner:
     """Streams of the benchmark on one device: frame k of stream i shows loop
     frame (offset_i + k) mod 100 at time (offset_i + k) / 30 s."""
 
-    def __init__(self, seq, imu, d_dev, i_dev, d_pin, i_pin, offsets, dev, tiles=None, groups=None):
+    def __init__(self, seq, imu, d_dev, i_dev, d_pin, i_pin, offsets, dev, tiles=None, groups=None,
+                 flags=0):
         import torch
         from paper_2207_10940_gb300 import dri
         self.dri, self.torch = dri, torch
         self.dev = dev
         self.d_dev, self.i_dev, self.d_pin, self.i_pin = d_dev, i_dev, d_pin, i_pin
         self.ts = torch.cuda.Stream(dev)
-        cfg = dri_config(seq)
+        cfg = dri_config(seq, flags)
         self.offsets = list(offsets)
         self.streams = [dri.Stream(cfg, dri.state_from_dict(initial_state_at(seq, o), o / FPS), self.ts)
                         for o in self.offsets]
@@ -474,7 +481,8 @@ def served_pass(args, dev, workers):
         s = seqs[c]
         cam = s.cam
         cfg = dri.config_for(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, LEVELS, ITERS,
-                             q_CS=synth.matrix_to_quat(s.R_CS), r_CS=s.r_CS)
+                             q_CS=synth.matrix_to_quat(s.R_CS), r_CS=s.r_CS,
+                             precision_flags=args.precision_flags)
         g = s.gt[o]
         x0 = dict(t=o / FPS, r_WC=np.zeros(3), q_WC=np.array([1.0, 0, 0, 0]), v_I=g["v_I"].copy(),
                   bg=np.zeros(3), ba=np.zeros(3), q_IW=synth.matrix_to_quat(g["R_IW"]))
@@ -655,7 +663,7 @@ def run_ours(args):
         offsets = [(BATCH_OFFSET * i) % N_UNIQUE for i in range(n_streams)]
         run = Runner(seq, imu, d_dev, i_dev, d_pin, i_pin, offsets, dev,
                      args.rows_per_thread if n_streams > 1 else None,
-                     args.groups if n_streams > 1 else None)
+                     args.groups if n_streams > 1 else None, args.precision_flags)
         res = run.step(wait=True)
         for _ in range(args.warmup):
             run.step()
@@ -698,7 +706,7 @@ def run_ours(args):
         "metric": "tracked frames/s at 640x480 (batched vs plain)",
         "value": b["value"], "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 per-pixel, f64 reduction and solve",
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(args.precision_flags),
         "data": "synthetic", "config": config_json(args.batch),
         "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"],
         "gpu_launches": b["gpu_launches"],
@@ -740,6 +748,9 @@ def main():
     ap.add_argument("--groups", type=int, default=None,
                     help="slot groups of the batched Gauss-Newton loop (default: the library's)")
     ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--precision-flags", type=int, default=0,
+                    help="precision_flags of the timed streams: 1 FP16 maps, 2 FP32 partials, 3 both "
+                         "(default 0: FP32 maps, FP64 partials)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--profile-frames", type=int, default=60)
     args = ap.parse_args()

@@ -198,7 +198,8 @@ StreamLayout make_layout(const dri_stream_config& cfg) {
   }
   int maxb = 1;
   for (int l = 0; l < cfg.levels; ++l)
-    maxb = std::max(maxb, track_grid_blocks(cfg.width >> l, cfg.height >> l, 1));
+    maxb = std::max(maxb, std::max(track_grid_blocks(cfg.width >> l, cfg.height >> l, 1),
+                                   track_mixed_blocks(cfg.width >> l, cfg.height >> l, 1)));
   L.max_blocks = maxb;
   L.counters = off;
   off = align_up(off + (size_t)(1 + fold_groups(maxb)) * sizeof(uint32_t));

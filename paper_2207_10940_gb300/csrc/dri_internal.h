@@ -36,8 +36,8 @@ constexpr int kMaxLevels = DRI_MAX_LEVELS;
 constexpr int kSums = 29;             // per term: 21 (upper J J^T) + 6 (J e) + e^2 + count
 constexpr int kSumsAll = 2 * kSums;   // ICP then photometric
 constexpr int kTrackThreadsX = 32;
-constexpr int kTrackThreadsY = 8;      // warps of the pixel kernel: 4 ICP, 4 photometric
-constexpr int kTrackRows = 4;          // tile rows per unit of rows-per-thread
+constexpr int kTrackThreadsY = 8;      // warps of a pixel-kernel block
+constexpr int kTrackRows = 4;          // mixed-term tiles: rows per unit of rows-per-thread
 constexpr int kFoldGroup = 16;        // blocks per first-level fold of the pixel kernel
 
 struct DState {                       // Eq. 1
@@ -232,7 +232,8 @@ cudaError_t launch_gradient(const LevelMaps& m, const Ctrl* ctrl, int w, int h, 
 cudaError_t launch_track(const TrackParams& p, bool fp16, bool fp32_partials, cudaStream_t s);
 cudaError_t launch_track_batch(const BatchArgs& a, int blocks, bool fp16, bool fp32_partials,
                                cudaStream_t s);
-int track_grid_blocks(int w, int h, int ppt);
+int track_grid_blocks(int w, int h, int ppt);   // batched kernel: single-term blocks
+int track_mixed_blocks(int w, int h, int ppt);  // by-value kernel: mixed-term blocks
 int track_default_ppt(int w, int h);
 inline int fold_groups(int nblocks) { return (nblocks + kFoldGroup - 1) / kFoldGroup; }
 

@@ -221,7 +221,7 @@ extern "C" int dri_linearise_pair_noalloc(const dri_stream_config* cfg, const fl
   p.counters = counters;
   p.flags = flags;
   p.ppt = 1;
-  p.nblocks = track_grid_blocks(g.w, g.h, 1);
+  p.nblocks = track_mixed_blocks(g.w, g.h, 1);
   if (p.nblocks > kNoallocMaxBlocks) return DRI_EINVAL;
   p.depth_min = dmin;
   p.depth_max = dmax;

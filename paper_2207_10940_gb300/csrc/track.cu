@@ -2,11 +2,14 @@
 // point-to-plane ICP (Eq. 4) terms at one pyramid level, block-reduced into the
 // normal equations of Eq. 7 (Sec. IV-B, IV-D).
 //
-// Block: 8 warps over a tile of 32 columns x 4 * ppt rows.  Warps 0-3 evaluate
-// the ICP term and warps 4-7 the photometric term of the same pixels (warp w and
-// w + 4 take rows w, w + 4, w + 8, ... of the tile), so each thread carries the
-// 29 sums of one term only: half the registers of a thread that does both, more
-// warps resident per SM to hide the latency of the dependent gathers.  Each
+// A thread evaluates one term only and carries that term's 29 sums: half the
+// registers of a thread that does both, more warps resident per SM to hide the
+// latency of the dependent gathers.  Batched kernel: a block of 8 warps takes
+// one term over a tile of 32 columns x 8 * ppt rows (warp w: rows w, w + 8, ...),
+// the two terms of a tile being neighbouring blocks, so a block never waits at
+// its final barrier for the other (slower) term.  By-value kernel (parity,
+// per-pixel flags): warps 0-3 ICP and 4-7 photometric over the same 32 x 4 * ppt
+// pixels, so the two validity bits of a pixel meet in shared memory.  Each
 // gather is one vector load of a per-pixel pack (packs.cuh): the ICP term reads
 // pack A (normal + depth) of the live pixel and of the associated reference
 // pixel, the photometric term the live depth and intensity and four pack-B taps
@@ -31,7 +34,7 @@
 // diag(R^T, R^T) (R = R_ref or R_0); the solver rotates the reduced 6x6 systems
 // back in FP64.  Each thread accumulates its term's 29 values (upper J J^T, J e,
 // e^2, count) in FP32; a warp transposes and sums them with 31 shuffles, the
-// block adds its four warps per term in fixed order into one FP64 (or FP32)
+// block adds its warps per term in fixed order into one FP64 (or FP32)
 // partial of 58 values; the partials are folded in two fixed-order levels
 // (groups of blocks, then the groups) into ctrl->sums: deterministic, no float
 // atomics.
@@ -157,17 +160,19 @@ __device__ __forceinline__ bool rgb_pixel(const LevelGeom& g, const float* A, co
   return true;
 }
 
-// One tile (32 columns x 4 * ppt rows) of one image: (bx, by) its tile
+// One tile of one image (single-term: 32 x 8 * ppt pixels of `term`; mixed:
+// 32 x 4 * ppt pixels, both terms): (bx, by) its tile
 // coordinates, bid its index in the image's fold order.
-template <typename T, typename P, bool FLAGS>
-__device__ __forceinline__ void track_tile(const TrackParams& p, const int bx, const int by,
-                                           const int bid) {
+template <typename T, typename P, bool FLAGS, bool SPLIT>
+__device__ __forceinline__ void track_tile(const TrackParams& p, const int term, const int bx,
+                                           const int by, const int bid) {
   Ctrl* __restrict__ ctrl = p.ctrl;
   if (ctrl->status != 0) return;
   const int lane = threadIdx.x;
   const int warp = threadIdx.y;
-  const bool icp = warp < kTrackRows;          // warp-uniform
-  const int wrow = warp & (kTrackRows - 1);
+  constexpr int kR = SPLIT ? kTrackThreadsY : kTrackRows;   // rows between a thread's rows
+  const bool icp = SPLIT ? term == 0 : warp < kTrackRows;    // warp-uniform
+  const int wrow = SPLIT ? warp : (warp & (kTrackRows - 1));
   const int rs = ctrl->ref_index;
   const int cs = 1 - rs;
   const LevelGeom g = p.g;
@@ -195,7 +200,7 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int bx, c
   // live samples of the thread's row r (zero depth outside the image)
   auto load_live = [&](int r) {
     Live L = {0.f, 0.f, 0.f, 0.f};
-    const int v = (by * p.ppt + r) * kTrackRows + wrow;
+    const int v = (by * p.ppt + r) * kR + wrow;
     if (col_ok && v < g.h) {
       const int o = v * g.w + u;
       if (icp) {
@@ -215,9 +220,9 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int bx, c
   Live cur = load_live(0);
   for (int r = 0; r < p.ppt; ++r) {
     const Live nxt = r + 1 < p.ppt ? load_live(r + 1) : Live{0.f, 0.f, 0.f, 0.f};
-    const int v = (by * p.ppt + r) * kTrackRows + wrow;
+    const int v = (by * p.ppt + r) * kR + wrow;
     if (kPrefetchRows > 0 && r + kPrefetchRows < p.ppt) {
-      const int vf = v + kPrefetchRows * kTrackRows;
+      const int vf = v + kPrefetchRows * kR;
       if (col_ok && vf < g.h) {
         const int of = vf * g.w + u;
         if (icp) {
@@ -264,9 +269,10 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int bx, c
   const int tid = warp * kTrackThreadsX + lane;
   s_warp[warp][lane] = w[0];
   __syncthreads();
-  // Block: FP32 sum of each term's four warps, one FP64 (or FP32) partial per
-  // block.  Blocks fold in two deterministic levels: the last block of each group
-  // of kFoldGroup blocks sums the group's partials in block order, the last group
+  // Block: FP32 sum of each term's warps (four, or eight in a single-term block,
+  // whose other term is zero), one FP64 (or FP32) partial per block.  Blocks
+  // fold in two deterministic levels: the last block of each group of
+  // kFoldGroup blocks sums the group's partials in block order, the last group
   // sums the groups.
   const int grp = bid / kFoldGroup;
   const int ngroups = (p.nblocks + kFoldGroup - 1) / kFoldGroup;
@@ -274,10 +280,17 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int bx, c
   P* partials = reinterpret_cast<P*>(p.partials);
   P* gpartials = reinterpret_cast<P*>(p.gpartials);
   if (tid < kSumsAll) {
-    const int term = tid / kSums, k = tid - term * kSums;
-    float s = 0.f;
+    const int tt = tid / kSums, k = tid - tt * kSums;
+    float s = 0.f;                   // zero for the term a single-term block skips
+    if (SPLIT) {
+      if (tt == term) {
 #pragma unroll
-    for (int q = 0; q < kTrackRows; ++q) s += s_warp[term * kTrackRows + q][k];
+        for (int q = 0; q < kTrackThreadsY; ++q) s += s_warp[q][k];
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kTrackRows; ++q) s += s_warp[tt * kTrackRows + q][k];
+    }
     partials[(int64_t)bid * kSumsAll + tid] = (P)s;
     __threadfence();
   }
@@ -312,13 +325,15 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int bx, c
 template <typename T, typename P, bool FLAGS>
 __global__ void __launch_bounds__(kTrackThreadsX * kTrackThreadsY)
 k_track(TrackParams p) {
-  track_tile<T, P, FLAGS>(p, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x);
+  track_tile<T, P, FLAGS, false>(p, 0, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
-// Tiles of every tracking slot at one level: block -> (slot, tile) through the
-// block prefix, tile -> (column, row band) in the slot's image.
+// Tiles of every tracking slot at one level: block -> (slot, tile, term)
+// through the block prefix, tile -> (column, row band) in the slot's image.
+// Three blocks per SM (80 registers) measured faster than four (64 registers,
+// more spill reloads) and than two columns per thread.
 template <typename T, typename P>
-__global__ void __launch_bounds__(kTrackThreadsX * kTrackThreadsY, 4)
+__global__ void __launch_bounds__(kTrackThreadsX * kTrackThreadsY, 3)
 k_track_batch(const BatchArgs a) {
   const int i = batch_slot(a, blockIdx.x);
   const int slot = a.slot0 + i;
@@ -332,7 +347,8 @@ k_track_batch(const BatchArgs a) {
   __syncthreads();
   const int t = blockIdx.x - __ldg(a.start + i);
   const int gx = (p.g.w + kTrackThreadsX - 1) / kTrackThreadsX;
-  track_tile<T, P, false>(p, t % gx, t / gx, t);
+  const int tile = t >> 1;                    // the two terms of a tile are neighbours
+  track_tile<T, P, false, true>(p, t & 1, tile % gx, tile / gx, t);
 }
 
 }  // namespace
@@ -347,12 +363,21 @@ int track_default_ppt(int w, int h) {
 
 int track_grid_blocks(int w, int h, int ppt) {
   const int gx = (w + kTrackThreadsX - 1) / kTrackThreadsX;
+  const int rows = kTrackThreadsY * ppt;
+  const int gy = (h + rows - 1) / rows;
+  return 2 * gx * gy;
+}
+
+int track_mixed_blocks(int w, int h, int ppt) {
+  const int gx = (w + kTrackThreadsX - 1) / kTrackThreadsX;
   const int rows = kTrackRows * ppt;
   const int gy = (h + rows - 1) / rows;
   return gx * gy;
 }
 
-cudaError_t launch_track(const TrackParams& p, bool fp16, bool fp32_partials, cudaStream_t s) {
+cudaError_t launch_track(const TrackParams& p0, bool fp16, bool fp32_partials, cudaStream_t s) {
+  TrackParams p = p0;
+  p.nblocks = track_mixed_blocks(p.g.w, p.g.h, p.ppt);
   const dim3 block(kTrackThreadsX, kTrackThreadsY);
   const int rows = kTrackRows * p.ppt;
   const dim3 grid((p.g.w + kTrackThreadsX - 1) / kTrackThreadsX, (p.g.h + rows - 1) / rows);
