@@ -7,9 +7,12 @@
 // every stream handle: it takes the oldest pending request of each stream (at
 // most max_batch streams per tick), uploads them and launches one batched frame
 // (dri_track_batch's plan over all the server's streams; streams without a
-// request sit the tick out).  Up to kInflight ticks are on the GPU at once, so
-// requests that arrive while one tick runs go into the next one, whose launch
-// overlaps the running tick.  A stream is admitted only while the device bytes
+// request sit the tick out).  One tick is on the GPU at a time: every request
+// that arrives while it runs joins the next tick, launched when it completes,
+// so a request waits at most for the running tick and its own.  (With a second
+// tick launched behind the running one, that tick takes only the few requests
+// that came in meanwhile and the rest wait for a third: at the 256-stream
+// mixed load p50 / p99 were 40 / 54 ms against 27 / 35 ms.)  A stream is admitted only while the device bytes
 // of all admitted streams stay within the HBM budget.
 #include <algorithm>
 #include <chrono>
@@ -28,7 +31,7 @@ using namespace dri_host;
 
 namespace {
 
-constexpr int kInflight = 2;                 // ticks on the GPU at once
+constexpr int kInflight = 1;                 // ticks on the GPU at once
 constexpr size_t kSlotOverheadBytes = 65536; // plan table, staging and result head of one slot
 constexpr size_t kMaxLatencySamples = 1 << 20;
 
