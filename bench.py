@@ -162,15 +162,46 @@ def oracle_frames_per_s(seq, frames, imu, budget_s):
                         iters=ITERS, R_CS=seq.R_CS, r_CS=seq.r_CS)
     tr = gn.Tracker(cfg, synth.initial_state(seq))
     tr.push_imu(imu)
-    tr.track(frames[0][0], frames[0][1], 0.0)
+    states = [tr.track(frames[0][0], frames[0][1], 0.0)["x1"].to_dict()]
     n, t_total = 0, 0.0
     while t_total < budget_s or n == 0:
         i = n + 1
         t = time.perf_counter()
-        tr.track(frames[i % N_UNIQUE][0], frames[i % N_UNIQUE][1], i / FPS)
+        r = tr.track(frames[i % N_UNIQUE][0], frames[i % N_UNIQUE][1], i / FPS)
         t_total += time.perf_counter() - t
+        states.append(r["x1"].to_dict())
         n += 1
-    return n / t_total, n, t_total
+    return n / t_total, n, t_total, states
+
+
+def odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_frames, flags):
+    """One stream tracked over n_frames frames of the periodic sequence with every
+    result read back: its states, for the odometry errors against ground truth."""
+    run = Runner(seq, imu, d_dev, i_dev, d_pin, i_pin, [0], dev, None, None, flags)
+    states = []
+    for _ in range(n_frames):
+        res = run.step(wait=True)
+        states.append(run.dri.state_to_dict(res.x1))
+    run.close()
+    return states
+
+
+def odometry_report(seq, states, oracle_states):
+    """Errors against ground truth (frame k shows loop frame k mod 100) and the
+    largest pose difference to the oracle over the frames it tracked."""
+    from oracle.so3 import State
+    from paper_2207_10940_gb300 import odometry
+    gt = [seq.gt[k % N_UNIQUE] for k in range(len(states))]
+    ev = odometry.evaluate(states, gt)
+    m = min(len(states), len(oracle_states))
+    da = dr = 0.0
+    for a, b in zip(states[:m], oracle_states[:m]):
+        xa, xb = State.from_dict(a), State.from_dict(b)
+        da = max(da, odometry.rotation_angle(xa.R.T @ xb.R))
+        dr = max(dr, float(np.linalg.norm(xa.r - xb.r)))
+    ev["vs_oracle"] = {"frames": m, "max_rotation_diff_rad": da, "max_position_diff_m": dr}
+    ev["sequence"] = "640x480 sinusoid (peak 1.5 m/s, 90 deg/s yaw), 400 Hz IMU, biases 1e-3 rad/s, 0.05 m/s^2"
+    return ev
 
 
 def oracle_band_steps(seq, frames, imu, steps, warmup, budget_s):
@@ -687,6 +718,11 @@ def run_ours(args):
         run.close()
         del run
         torch.cuda.synchronize(dev)
+    odo_states = None
+    n_odo = min(args.odometry_frames, n_frames - 2)
+    if n_odo > 1 and rank == 0:
+        odo_states = odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_odo, args.precision_flags)
+        torch.cuda.synchronize(dev)
     served = None
     if args.serve_seconds > 0:
         served = served_pass(args, dev, min(16, os.cpu_count() or 4))
@@ -700,7 +736,7 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return 0
     budget = float(os.environ.get("DRI_BENCH_ORACLE_SECONDS", "15"))
-    o_fps, o_n, o_t = oracle_frames_per_s(seq, frames, imu, budget)
+    o_fps, o_n, o_t, o_states = oracle_frames_per_s(seq, frames, imu, budget)
     b, p = out["batched"], out.get("plain")
     line = {
         "metric": "tracked frames/s at 640x480 (batched vs plain)",
@@ -719,6 +755,7 @@ def run_ours(args):
                               "rows_per_thread")},
         "batched_over_plain": None if p is None else b["value"] / p["value"],
         "served": served,
+        "odometry": None if odo_states is None else odometry_report(seq, odo_states, o_states),
         "precision": precision,
         "cpu_baseline": {"value": o_fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
                          "sample": f"{o_n} whole frames of the same sequence tracked by the FP64 "
@@ -753,6 +790,8 @@ def main():
                          "(default 0: FP32 maps, FP64 partials)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--profile-frames", type=int, default=60)
+    ap.add_argument("--odometry-frames", type=int, default=300,
+                    help="frames of the odometry pass against ground truth (< 2: skip it)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
