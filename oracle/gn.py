@@ -17,6 +17,11 @@ Marginalisation (Eq. 8): after the last update the last system is moved to the
 new point to first order (b <- b - H dx_last) and x_0 is removed with the Schur
 complement H* = H_11 - H_10 H_00^-1 H_01, b* = b_1 - H_10 H_00^-1 b_0; xbar := x_1.
 
+IMU term per iteration: re-integrated at x_0's biases (imu_mode 0), or the
+first-order bias update of the pre-integration made at the frame's
+linearisation point, which moves to x_0's current biases (with a
+re-integration) once they leave the thresholds (imu_mode 1, params.py).
+
 Frame loop (reading; the paper does not state the initialisation): x_0 := the
 previous x_1, x_1 := the IMU prediction x^_1(x_0); W_IMU computed there.  The
 first frame only initialises: x_1 := x_init (identity pose, W = first camera
@@ -101,6 +106,20 @@ class Tracker:
         self.Hs, self.bs = first_prior(cfg)
         self.xbar = self.x.copy()
         self.imu = np.zeros((0, 7))
+        self.lin = None             # imu_mode 1: (pre-integration, b_g, b_a) of the frame
+
+    def preintegration(self, x0, t0, t1):
+        """The pre-integration the current iteration uses (module docstring)."""
+        cfg = self.cfg
+        if cfg.imu_mode != 1 or self.lin is None:
+            return imu_mod.preintegrate(self.imu, t0, t1, x0.bg, x0.ba)
+        pre, bg, ba = self.lin
+        dbg, dba = x0.bg - bg, x0.ba - ba
+        if np.linalg.norm(dbg) > cfg.bias_relin_g or np.linalg.norm(dba) > cfg.bias_relin_a:
+            pre = imu_mod.preintegrate(self.imu, t0, t1, x0.bg, x0.ba)
+            self.lin = (pre, x0.bg.copy(), x0.ba.copy())
+            return pre
+        return imu_mod.correct(pre, dbg, dba)
 
     def set_reference(self, ref, R_ref, r_ref):
         """Replaces the reference with uploaded levels (maps.reference_from_upload)."""
@@ -114,7 +133,7 @@ class Tracker:
         """All terms of Eq. 6 at (x0, x1) on level l: returns (H, b, parts)."""
         cfg = self.cfg
         lin = linearise(levels[l], self.ref[l], self.T_ref[0], self.T_ref[1], x0, x1, cfg)
-        pre = imu_mod.preintegrate(self.imu, t0, t1, x0.bg, x0.ba)
+        pre = self.preintegration(x0, t0, t1)
         e, pr = imu_mod.residual(x0, x1, pre, cfg)
         J = imu_mod.jacobian(x0, x1, pre, cfg, e, pr)
         H, b = assemble(lin, J, e, W_imu, x0, self.xbar, self.Hs, self.bs)
@@ -134,6 +153,7 @@ class Tracker:
         x0 = self.x.copy()
         W_imu, _ = imu_mod.weight(x0, self.imu, t0, t1, cfg)
         pre = imu_mod.preintegrate(self.imu, t0, t1, x0.bg, x0.ba)
+        self.lin = (pre, x0.bg.copy(), x0.ba.copy())
         pr = imu_mod.predict(x0, pre, cfg)
         from .so3 import rot_to_quat
         x1 = State(pr["r"], rot_to_quat(pr["R"]), pr["v"], x0.bg.copy(), x0.ba.copy(),

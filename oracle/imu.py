@@ -12,10 +12,12 @@ in this order:
   dp <- dp + dv dt + 1/2 dR a dt^2
   dv <- dv + dR a dt
   dR <- dR Exp(w dt)
-The integration is repeated at x_0's current biases at every Gauss-Newton
-iteration (exact, no first-order bias correction).  Alongside it run the exact
-derivatives of this recursion w.r.t. the biases (right perturbation of dR):
-Phi_g = d(dR)/d(b_g), V_g, P_g = d(dv, dp)/d(b_g), V_a, P_a = d(dv, dp)/d(b_a).
+By default the integration is repeated at x_0's current biases at every
+Gauss-Newton iteration (exact).  Alongside it run the exact derivatives of this
+recursion w.r.t. the biases (right perturbation of dR): Phi_g = d(dR)/d(b_g),
+V_g, P_g = d(dv, dp)/d(b_g), V_a, P_a = d(dv, dp)/d(b_a).  `correct` is the
+alternative of Forster et al. the paper builds on: a first-order update of a
+pre-integration to new biases without re-integrating.
 
 Prediction x^_1(x_0), with R_IS = R_IW R_WC R_CS, r_IS = R_IW (r_WC + R_WC r_CS),
 g_I = (0, 0, -g), T = t1 - t0:
@@ -103,6 +105,27 @@ def preintegrate(samples, t0, t1, bg, ba, gyr_nd=None, acc_nd=None):
         dR = dR @ E
     return dict(dR=dR, dv=dv, dp=dp, Phi_g=Phi_g, V_g=V_g, P_g=P_g, V_a=V_a, P_a=P_a,
                 Sigma=Sig, T=t1 - t0)
+
+
+def correct(pre, dbg, dba):
+    """First-order update of a pre-integration made at biases (b_g, b_a) to
+    (b_g + dbg, b_a + dba), without re-integrating (Forster et al.):
+      dR <- dR Exp(Phi_g dbg),  dv <- dv + V_g dbg + V_a dba,
+      dp <- dp + P_g dbg + P_a dba.
+    The update is linear in the biases except for the rotation, whose bias
+    Jacobian at the new point is Jr(Phi_g dbg) Phi_g (derivative of
+    Exp(Phi_g (dbg + e)) = Exp(Phi_g dbg) Exp(Jr(Phi_g dbg) Phi_g e) to first
+    order in e); the others are unchanged, so the residual's Jacobian stays the
+    exact derivative of the updated model."""
+    dbg = np.asarray(dbg, dtype=np.float64)
+    dba = np.asarray(dba, dtype=np.float64)
+    th = pre["Phi_g"] @ dbg
+    out = dict(pre)
+    out["dR"] = pre["dR"] @ exp_so3(th)
+    out["dv"] = pre["dv"] + pre["V_g"] @ dbg + pre["V_a"] @ dba
+    out["dp"] = pre["dp"] + pre["P_g"] @ dbg + pre["P_a"] @ dba
+    out["Phi_g"] = jr(th) @ pre["Phi_g"]
+    return out
 
 
 def predict(x0, pre, cfg):

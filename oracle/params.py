@@ -22,6 +22,12 @@ or schedule):
   with pose 1e-6 (m, rad), velocity 0.1 m/s, gyro / accelerometer bias
   0.03 rad/s and 0.1 m/s^2 (Table I bias priors), gravity direction 0.1 rad.
 * Gravity-direction process noise between consecutive frames: 1e-4 rad.
+* IMU term per Gauss-Newton iteration (imu_mode): 0 re-integrates the samples
+  at x_0's current biases (exact); 1 applies Forster et al.'s first-order bias
+  update to the pre-integration made at the frame's linearisation point (x_0's
+  biases when the frame starts) and re-integrates, making the current biases
+  the new linearisation point, once |db_g| > 0.01 rad/s or |db_a| > 0.1 m/s^2
+  (Euclidean norms; the paper gives no thresholds).
 """
 from __future__ import annotations
 
@@ -65,6 +71,9 @@ class TrackerConfig:
         pose=1e-6, v=0.1, bg=GYR_BIAS_PRIOR, ba=ACC_BIAS_PRIOR, grav=0.1))
     min_valid: int = 64                 # level-0 correspondences below this: tracking lost
     fp16_maps: bool = False             # normals and intensity gradients rounded to FP16
+    imu_mode: int = 0                   # 0 re-integrate per iteration, 1 first-order bias update
+    bias_relin_g: float = 0.01          # |db_g| (rad/s) above which mode 1 re-integrates
+    bias_relin_a: float = 0.1           # |db_a| (m/s^2) above which mode 1 re-integrates
 
     def level_camera(self, level):
         """Intrinsics at pyramid level l: f_l = f / 2^l, c_l = (c + 0.5) / 2^l - 0.5
