@@ -51,6 +51,18 @@ extern "C" {
 #define DRI_FP16_MAPS     1  /* normal and intensity-gradient maps stored in FP16 */
 #define DRI_FP32_PARTIALS 2  /* per-block partial sums in FP32 instead of FP64     */
 
+/* ---- IMU term per Gauss-Newton iteration (dri_stream_config.imu_mode) ---
+ * The paper pre-integrates the IMU samples between frames (Sec. IV-C, after
+ * Forster et al.).  DRI_IMU_REINTEGRATE repeats the integration at x0's current
+ * biases every iteration (exact).  DRI_IMU_FIRST_ORDER integrates once per
+ * frame at x0's biases when the frame starts and updates that pre-integration
+ * to first order in the bias change every iteration (dR Exp(Phi_g db_g),
+ * dv + V_g db_g + V_a db_a, dp + P_g db_g + P_a db_a), re-integrating and
+ * moving the linearisation point to the current biases once |db_g| exceeds
+ * bias_relin_g or |db_a| exceeds bias_relin_a. */
+#define DRI_IMU_REINTEGRATE 0
+#define DRI_IMU_FIRST_ORDER 1
+
 #define DRI_MAX_LEVELS 4
 
 typedef struct dri_stream_s* dri_stream;
@@ -77,7 +89,9 @@ typedef struct {
     int32_t min_valid;             /* level-0 correspondences below this: DRI_ELOST   */
     int32_t precision_flags;       /* DRI_FP16_MAPS | DRI_FP32_PARTIALS               */
     int32_t max_imu;               /* IMU samples one frame interval may span         */
-    int32_t reserved;
+    int32_t imu_mode;              /* DRI_IMU_REINTEGRATE (default) | _FIRST_ORDER    */
+    double bias_relin_g;           /* first order: re-integrate past |db_g|, rad/s    */
+    double bias_relin_a;           /* first order: re-integrate past |db_a|, m/s^2    */
 } dri_stream_config;
 
 /* One IMU sample: time (s), gyro (rad/s) and accelerometer (m/s^2) in S. */

@@ -47,6 +47,10 @@ int valid_config(const dri_stream_config* c) {
     return DRI_EINVAL;
   if (!(c->depth_min >= 0) || !(c->depth_max > c->depth_min)) return DRI_EINVAL;
   if (c->max_imu < 2 || c->max_imu > 65536) return DRI_EINVAL;
+  if (c->imu_mode != DRI_IMU_REINTEGRATE && c->imu_mode != DRI_IMU_FIRST_ORDER) return DRI_EINVAL;
+  if (!(c->bias_relin_g >= 0) || !(c->bias_relin_a >= 0) || !std::isfinite(c->bias_relin_g) ||
+      !std::isfinite(c->bias_relin_a))
+    return DRI_EINVAL;
   const double qn = c->T_CS[3] * c->T_CS[3] + c->T_CS[4] * c->T_CS[4] + c->T_CS[5] * c->T_CS[5] +
                     c->T_CS[6] * c->T_CS[6];
   if (!(std::fabs(qn - 1.0) < 1e-6)) return DRI_EINVAL;
@@ -273,6 +277,9 @@ SolveParams solve_params(const dri_stream_s* s, int level, int last) {
   for (int i = 0; i < 5; ++i) p.prior_sigma[i] = c.prior_sigma[i];
   p.min_valid = c.min_valid;
   p.imu_cap = s->L.imu_cap;
+  p.imu_mode = c.imu_mode;
+  p.relin_g = c.bias_relin_g;
+  p.relin_a = c.bias_relin_a;
   return p;
 }
 
@@ -889,6 +896,9 @@ int dri_config_default(int32_t width, int32_t height, dri_stream_config* cfg) {
   cfg->min_valid = 64;
   cfg->precision_flags = 0;
   cfg->max_imu = 512;
+  cfg->imu_mode = DRI_IMU_REINTEGRATE;
+  cfg->bias_relin_g = 0.01;
+  cfg->bias_relin_a = 0.1;
   return DRI_OK;
 }
 

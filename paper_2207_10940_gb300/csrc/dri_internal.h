@@ -73,6 +73,10 @@ struct Ctrl {
   double H[34 * 34], b[34], d[34];    // last joint system and step (marginalisation)
   float xf_icp[12];                   // R_ref^T R_1 - I (row-major), R_ref^T (r_1 - r_ref)
   float xf_rgb[12];                   // R_0^T R_1 - I, R_0^T (r_1 - r_0)
+  // DRI_IMU_FIRST_ORDER: the frame's pre-integration at its linearisation point
+  // (dR 9, dv 3, dp 3, Phi_g 9, V_g 9, P_g 9, V_a 9, P_a 9, T) and those biases
+  double pre_lin[61];
+  double b_lin[6];
 };
 
 // Bytes of the result head (x .. pad1) copied back after each frame.
@@ -133,6 +137,9 @@ struct SolveParams {
   double prior_sigma[5];
   int32_t min_valid;
   int32_t imu_cap;
+  int32_t imu_mode;                   // DRI_IMU_REINTEGRATE or DRI_IMU_FIRST_ORDER
+  int32_t pad;
+  double relin_g, relin_a;            // first order: re-integration thresholds
 };
 
 // ---- batched launches --------------------------------------------------------

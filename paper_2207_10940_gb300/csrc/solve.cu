@@ -838,6 +838,104 @@ __device__ bool ep_ldlt_solve(const double* A, const double* b, double* x, doubl
 // joint system (Eq. 6-7)
 // ---------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------
+// First-order bias update of the pre-integration (DRI_IMU_FIRST_ORDER)
+// ---------------------------------------------------------------------------
+
+// Stores a pre-integration and its biases as the frame's linearisation point.
+__device__ void store_lin(Ctrl* c, const Preint& P, const double* bg, const double* ba) {
+  const int tid = threadIdx.x;
+  const double* src[8] = {P.dR, P.dv, P.dp, P.Phig, P.Vg, P.Pg, P.Va, P.Pa};
+  const int off[9] = {0, 9, 12, 15, 24, 33, 42, 51, 60};
+  if (tid < 60) {
+    int k = 0;
+    while (tid >= off[k + 1]) ++k;
+    c->pre_lin[tid] = src[k][tid - off[k]];
+  } else if (tid == 60) {
+    c->pre_lin[60] = P.T;
+  } else if (tid >= 64 && tid < 70) {
+    c->b_lin[tid - 64] = tid < 67 ? bg[tid - 64] : ba[tid - 67];
+  }
+}
+
+// The pre-integration of this iteration at x0's biases (bg, ba) from the
+// linearisation point (Forster et al.'s first-order update):
+//   dR = dR_lin Exp(Phi_g dbg),  dv = dv_lin + V_g dbg + V_a dba,
+//   dp = dp_lin + P_g dbg + P_a dba,  Phi_g <- Jr(Phi_g dbg) Phi_g
+// (the rotation's bias Jacobian at the updated point; the others are linear).
+// Once |dbg| > relin_g or |dba| > relin_a the samples are re-integrated at
+// (bg, ba), which become the linearisation point.  Whole block; P in shared
+// memory; `scratch` 19 doubles of shared memory.
+__device__ bool preint_first_order(const SolveParams& sp, Ctrl* c, const double* bg,
+                                   const double* ba, ImuWork& W, Preint& P, double* scratch) {
+  const int tid = threadIdx.x;
+  double dbg[3], dba[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    dbg[i] = bg[i] - c->b_lin[i];
+    dba[i] = ba[i] - c->b_lin[3 + i];
+  }
+  const double ng = sqrt(dbg[0] * dbg[0] + dbg[1] * dbg[1] + dbg[2] * dbg[2]);
+  const double na = sqrt(dba[0] * dba[0] + dba[1] * dba[1] + dba[2] * dba[2]);
+  if (ng > sp.relin_g || na > sp.relin_a) {      // uniform over the block
+    const bool ok = preintegrate_block(sp.imu, bg, ba, false, 0.0, 0.0, W, P);
+    if (ok) store_lin(c, P, bg, ba);
+    return ok;
+  }
+  const double* L = c->pre_lin;
+  double* th = scratch;                          // Phi_g dbg (3), Exp (9), Jr (9)... in place
+  double* E = scratch + 3;
+  double* Jrm = scratch + 12;
+  // lanes 0-2: theta; 3-8: dv, dp; 9-44: V_g, P_g, V_a, P_a copied; 45: T
+  if (tid < 3) {
+    th[tid] = L[15 + 3 * tid] * dbg[0] + L[16 + 3 * tid] * dbg[1] + L[17 + 3 * tid] * dbg[2];
+  } else if (tid < 9) {
+    const int q = tid - 3, i = q % 3;
+    const double* M = q < 3 ? L + 24 : L + 33;   // V_g or P_g
+    const double* N = q < 3 ? L + 42 : L + 51;   // V_a or P_a
+    double v = L[(q < 3 ? 9 : 12) + i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) v = fma(M[3 * i + j], dbg[j], fma(N[3 * i + j], dba[j], v));
+    (q < 3 ? P.dv : P.dp)[i] = v;
+  } else if (tid < 45) {
+    const int q = tid - 9, m = q / 9, e = q % 9;
+    (m == 0 ? P.Vg : m == 1 ? P.Pg : m == 2 ? P.Va : P.Pa)[e] = L[24 + q];
+  } else if (tid == 45) {
+    P.T = L[60];
+  }
+  __syncthreads();
+  if (tid < 9) {                                 // Exp(theta), Jr(theta): one element per lane
+    const double t2 = th[0] * th[0] + th[1] * th[1] + th[2] * th[2];
+    double ea, eb, jb;
+    if (t2 < kSeriesT2) {
+      ea = 1.0 + t2 * (-1.0 / 6 + t2 * (1.0 / 120 + t2 * (-1.0 / 5040 + t2 * (1.0 / 362880))));
+      eb = 0.5 + t2 * (-1.0 / 24 + t2 * (1.0 / 720 + t2 * (-1.0 / 40320 + t2 * (1.0 / 3628800))));
+      jb = 1.0 / 6 + t2 * (-1.0 / 120 + t2 * (1.0 / 5040 + t2 * (-1.0 / 362880 + t2 * (1.0 / 39916800))));
+    } else {
+      const double t = sqrt(t2);
+      double sn, cs;
+      sincos(t, &sn, &cs);
+      ea = sn / t;
+      eb = (1.0 - cs) / t2;
+      jb = (t - sn) / (t2 * t);
+    }
+    const int r = tid / 3, q = tid % 3;
+    const double K = hat_e(th, tid);
+    const double K2 = th[r] * th[q] - (r == q ? t2 : 0.0);
+    const double id = r == q ? 1.0 : 0.0;
+    E[tid] = id + ea * K + eb * K2;
+    Jrm[tid] = id - eb * K + jb * K2;
+  }
+  __syncthreads();
+  if (tid < 9) {
+    P.dR[tid] = mm_e(L, E, tid, false, false);
+  } else if (tid >= 32 && tid < 41) {
+    P.Phig[tid - 32] = mm_e(Jrm, L + 15, tid - 32, false, false);
+  }
+  __syncthreads();
+  return true;
+}
+
 struct GnSmem {
   ImuWork W;
   Preint P;
@@ -857,6 +955,7 @@ struct GnSmem {
   double xr[26], piv[26];
   double col[2 * 27];
   double Lsm[26 * 26];                // L rows of the solver
+  double fo[21];                      // first-order bias update scratch
   double Bg[6], Ag[6];                // gravity Jacobian blocks of x1 and x0 (3 x 2)
   double rot[18];                     // R_1, R_0 of the pixel transforms
   double cost_imu;
@@ -909,7 +1008,9 @@ __device__ void assemble(const SolveParams& sp, GnSmem& S) {
       for (int q = 0; q < 3; ++q) S.M6[(3 + r) * 6 + q] = K[r * 3 + q];
   }
   __syncthreads();
-  S.ok = preintegrate_block(sp.imu, S.x0.bg, S.x0.ba, false, 0.0, 0.0, S.W, S.P);
+  S.ok = sp.imu_mode == DRI_IMU_FIRST_ORDER
+             ? preint_first_order(sp, c, S.x0.bg, S.x0.ba, S.W, S.P, S.fo)
+             : preintegrate_block(sp.imu, S.x0.bg, S.x0.ba, false, 0.0, 0.0, S.W, S.P);
   if (!S.ok) return;
   imu_linearise(S.x0, S.x1, S.P, sp, S.L, S.J);
   // W_IMU = blockdiag(W_9, diag): W_9 J_a (columns 0..25) and W_9 e_a
@@ -1158,6 +1259,7 @@ __device__ bool imu_weight_and_prediction(const SolveParams& sp, Ctrl* c, BeginS
     if (tid == 0) c->status = DRI_ENOTREADY;
     return false;
   }
+  if (sp.imu_mode == DRI_IMU_FIRST_ORDER) store_lin(c, B.P, x0.bg, x0.ba);   // the frame's point
   imu_linearise(x0, x0, B.P, sp, B.L, nullptr);   // prediction only (x1 unused)
   // G = d(r^, a^, v^) / d(dphi, dv, dp)
   if (tid < 81) {

@@ -29,6 +29,8 @@ DRI_HOST = 0
 DRI_DEVICE = 1
 DRI_FP16_MAPS = 1
 DRI_FP32_PARTIALS = 2
+DRI_IMU_REINTEGRATE = 0
+DRI_IMU_FIRST_ORDER = 1
 DRI_MAX_LEVELS = 4
 
 c_double_p = ctypes.POINTER(ctypes.c_double)
@@ -49,7 +51,8 @@ class dri_stream_config(ctypes.Structure):
         ("icp_dist_thr", ctypes.c_double), ("icp_angle_thr_deg", ctypes.c_double),
         ("depth_min", ctypes.c_double), ("depth_max", ctypes.c_double),
         ("min_valid", ctypes.c_int32), ("precision_flags", ctypes.c_int32),
-        ("max_imu", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("max_imu", ctypes.c_int32), ("imu_mode", ctypes.c_int32),
+        ("bias_relin_g", ctypes.c_double), ("bias_relin_a", ctypes.c_double),
     ]
 
 
