@@ -22,6 +22,10 @@ first-order bias update of the pre-integration made at the frame's
 linearisation point, which moves to x_0's current biases (with a
 re-integration) once they leave the thresholds (imu_mode 1, params.py).
 
+RGB-D-only baseline (track_mode 1, params.py): Gauss-Newton on x_1's pose
+alone with H_icp + lambda H_rgb, x_0 fixed, no IMU term, prior or
+marginalisation (`track_pose_only`).
+
 Frame loop (reading; the paper does not state the initialisation): x_0 := the
 previous x_1, x_1 := the IMU prediction x^_1(x_0); W_IMU computed there.  The
 first frame only initialises: x_1 := x_init (identity pose, W = first camera
@@ -149,6 +153,8 @@ class Tracker:
             self.ref = reference_from_frame(levels, *self.T_ref, fp16=self.cfg.fp16_maps)
             self.xbar = self.x.copy()
             return dict(status="init", x1=self.x.copy())
+        if cfg.track_mode == 1:
+            return self.track_pose_only(levels, t)
         t0, t1 = self.t, t
         x0 = self.x.copy()
         W_imu, _ = imu_mod.weight(x0, self.imu, t0, t1, cfg)
@@ -185,3 +191,34 @@ class Tracker:
         self.imu = self.imu[max(keep, 0):]
         return dict(status="ok", x0=x0, x1=x1, counts=counts, H=H, b=b, d_last=d,
                     H_prior=Hs, b_prior=bs)
+
+    def track_pose_only(self, levels, t):
+        """RGB-D-only baseline (track_mode 1, params.py): Gauss-Newton on x_1's
+        pose with H = H_icp + lambda H_rgb(x_1 block), x_0 fixed."""
+        cfg = self.cfg
+        x0 = self.x.copy()
+        x1 = self.x.copy()
+        lam = cfg.rgbd_lambda
+        counts = {}
+        H = b = None
+        for l in range(cfg.levels - 1, -1, -1):
+            for _ in range(cfg.iters[l]):
+                lin = linearise(levels[l], self.ref[l], self.T_ref[0], self.T_ref[1], x0, x1, cfg)
+                counts[l] = (lin["n_icp"], lin["n_rgb"])
+                H = lin["H_icp"] + lam * lin["H_rgb"][6:, 6:]
+                b = lin["b_icp"] + lam * lin["b_rgb"][6:]
+                try:
+                    d = cholesky_solve(H, b)
+                except np.linalg.LinAlgError as exc:
+                    raise TrackingLost("Cholesky failed") from exc
+                if not np.all(np.isfinite(d)):
+                    raise TrackingLost("non-finite step")
+                x1 = boxplus(x1, np.concatenate([d, np.zeros(11)]))
+        if counts[0][0] + counts[0][1] < cfg.min_valid:
+            raise TrackingLost("too few correspondences")
+        self.x = x1.copy()
+        self.xbar = x1.copy()
+        self.t = t
+        self.T_ref = (x1.R, x1.r.copy())
+        self.ref = reference_from_frame(levels, *self.T_ref, fp16=self.cfg.fp16_maps)
+        return dict(status="ok", x0=x0, x1=x1, counts=counts, H=H, b=b)

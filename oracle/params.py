@@ -28,6 +28,13 @@ or schedule):
   biases when the frame starts) and re-integrates, making the current biases
   the new linearisation point, once |db_g| > 0.01 rad/s or |db_a| > 0.1 m/s^2
   (Euclidean norms; the paper gives no thresholds).
+* RGB-D-only baseline (track_mode 1; the vision-only tracker the paper
+  compares with, Sec. III: ElasticFusion estimates the current pose only and
+  weighs the photometric against the geometric term with a tuning parameter
+  lambda): the unknowns are x_1's pose; x_0 (the previous result) stays fixed
+  and the photometric term still warps with it; x_1 starts at x_0; the system
+  is H_icp + lambda H_rgb on x_1's pose (the per-pixel weights W_ICP, W_RGB
+  kept, lambda = 1 by default); no IMU term, prior or marginalisation.
 """
 from __future__ import annotations
 
@@ -74,6 +81,8 @@ class TrackerConfig:
     imu_mode: int = 0                   # 0 re-integrate per iteration, 1 first-order bias update
     bias_relin_g: float = 0.01          # |db_g| (rad/s) above which mode 1 re-integrates
     bias_relin_a: float = 0.1           # |db_a| (m/s^2) above which mode 1 re-integrates
+    track_mode: int = 0                 # 0 RGB-D-inertial (joint), 1 RGB-D-only pose
+    rgbd_lambda: float = 1.0            # track_mode 1: weight of the photometric term
 
     def level_camera(self, level):
         """Intrinsics at pyramid level l: f_l = f / 2^l, c_l = (c + 0.5) / 2^l - 0.5
