@@ -72,12 +72,12 @@ def make_inputs(n_frames_total, workers):
     return seq, frames, imu
 
 
-def dri_config(seq, flags=0, imu_mode=0):
+def dri_config(seq, flags=0, imu_mode=0, track_mode=0):
     from paper_2207_10940_gb300 import dri, synth
     cam = seq.cam
     return dri.config_for(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, LEVELS, ITERS,
                           q_CS=synth.matrix_to_quat(seq.R_CS), r_CS=seq.r_CS, precision_flags=flags,
-                          imu_mode=imu_mode)
+                          imu_mode=imu_mode, track_mode=track_mode)
 
 
 def measured_peaks():
@@ -175,16 +175,26 @@ def oracle_frames_per_s(seq, frames, imu, budget_s):
     return n / t_total, n, t_total, states
 
 
-def odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_frames, flags, imu_mode):
+def odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_frames, flags, imu_mode, track_mode=0):
     """One stream tracked over n_frames frames of the periodic sequence with every
     result read back: its states, for the odometry errors against ground truth."""
-    run = Runner(seq, imu, d_dev, i_dev, d_pin, i_pin, [0], dev, None, None, flags, imu_mode)
+    run = Runner(seq, imu, d_dev, i_dev, d_pin, i_pin, [0], dev, None, None, flags, imu_mode, track_mode)
     states = []
     for _ in range(n_frames):
         res = run.step(wait=True)
         states.append(run.dri.state_to_dict(res.x1))
     run.close()
     return states
+
+
+def rgbd_only_report(seq, states):
+    """Errors of the RGB-D-only baseline (DRI_TRACK_RGBD_ONLY, lambda 1) against
+    ground truth over the same frames as the odometry pass."""
+    from paper_2207_10940_gb300 import odometry
+    gt = [seq.gt[k % N_UNIQUE] for k in range(len(states))]
+    ev = odometry.evaluate(states, gt)
+    return {k: ev[k] for k in ("frames", "ate_rmse_m", "ate_rmse_unaligned_m", "final_position_error_m",
+                               "rotation_rmse_rad")}
 
 
 def odometry_report(seq, states, oracle_states):
@@ -337,14 +347,14 @@ class Runner:
     frame (offset_i + k) mod 100 at time (offset_i + k) / 30 s."""
 
     def __init__(self, seq, imu, d_dev, i_dev, d_pin, i_pin, offsets, dev, tiles=None, groups=None,
-                 flags=0, imu_mode=0):
+                 flags=0, imu_mode=0, track_mode=0):
         import torch
         from paper_2207_10940_gb300 import dri
         self.dri, self.torch = dri, torch
         self.dev = dev
         self.d_dev, self.i_dev, self.d_pin, self.i_pin = d_dev, i_dev, d_pin, i_pin
         self.ts = torch.cuda.Stream(dev)
-        cfg = dri_config(seq, flags, imu_mode)
+        cfg = dri_config(seq, flags, imu_mode, track_mode)
         self.offsets = list(offsets)
         self.streams = [dri.Stream(cfg, dri.state_from_dict(initial_state_at(seq, o), o / FPS), self.ts)
                         for o in self.offsets]
@@ -731,11 +741,14 @@ def run_ours(args):
         run.close()
         del run
         torch.cuda.synchronize(dev)
-    odo_states = None
+    odo_states = odo_rgbd = None
     n_odo = min(args.odometry_frames, n_frames - 2)
     if n_odo > 1 and rank == 0:
         odo_states = odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_odo, args.precision_flags,
                                    args.imu_mode)
+        # the vision-only, pose-only baseline the paper compares with (same frames)
+        odo_rgbd = odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_odo, args.precision_flags,
+                                 args.imu_mode, track_mode=1)
         torch.cuda.synchronize(dev)
     served = None
     if args.serve_seconds > 0:
@@ -770,6 +783,7 @@ def run_ours(args):
         "batched_over_plain": None if p is None else b["value"] / p["value"],
         "served": served,
         "odometry": None if odo_states is None else odometry_report(seq, odo_states, o_states),
+        "odometry_rgbd_only": None if odo_rgbd is None else rgbd_only_report(seq, odo_rgbd),
         "precision": precision,
         "cpu_baseline": {"value": o_fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
                          "sample": f"{o_n} whole frames of the same sequence tracked by the FP64 "

@@ -63,6 +63,17 @@ extern "C" {
 #define DRI_IMU_REINTEGRATE 0
 #define DRI_IMU_FIRST_ORDER 1
 
+/* ---- what a stream tracks (dri_stream_config.track_mode) ----------------
+ * DRI_TRACK_INERTIAL: the paper's joint RGB-D-inertial tracker (Eq. 6-9).
+ * DRI_TRACK_RGBD_ONLY: the vision-only baseline it compares with (Sec. III,
+ * ElasticFusion's tracking): Gauss-Newton on the current pose only, x1 starting
+ * at the previous result x0, which stays fixed (the photometric term warps
+ * with it), over H_icp + rgbd_lambda H_rgb with the per-pixel weights kept; no
+ * IMU term, prior or marginalisation, and no IMU samples are needed.  Velocity,
+ * biases and gravity are carried over unchanged. */
+#define DRI_TRACK_INERTIAL  0
+#define DRI_TRACK_RGBD_ONLY 1
+
 #define DRI_MAX_LEVELS 4
 
 typedef struct dri_stream_s* dri_stream;
@@ -92,6 +103,9 @@ typedef struct {
     int32_t imu_mode;              /* DRI_IMU_REINTEGRATE (default) | _FIRST_ORDER    */
     double bias_relin_g;           /* first order: re-integrate past |db_g|, rad/s    */
     double bias_relin_a;           /* first order: re-integrate past |db_a|, m/s^2    */
+    int32_t track_mode;            /* DRI_TRACK_INERTIAL (default) | _RGBD_ONLY       */
+    int32_t reserved;
+    double rgbd_lambda;            /* RGB-D-only: photometric weight (default 1)      */
 } dri_stream_config;
 
 /* One IMU sample: time (s), gyro (rad/s) and accelerometer (m/s^2) in S. */

@@ -51,6 +51,8 @@ int valid_config(const dri_stream_config* c) {
   if (!(c->bias_relin_g >= 0) || !(c->bias_relin_a >= 0) || !std::isfinite(c->bias_relin_g) ||
       !std::isfinite(c->bias_relin_a))
     return DRI_EINVAL;
+  if (c->track_mode != DRI_TRACK_INERTIAL && c->track_mode != DRI_TRACK_RGBD_ONLY) return DRI_EINVAL;
+  if (!(c->rgbd_lambda >= 0) || !std::isfinite(c->rgbd_lambda)) return DRI_EINVAL;
   const double qn = c->T_CS[3] * c->T_CS[3] + c->T_CS[4] * c->T_CS[4] + c->T_CS[5] * c->T_CS[5] +
                     c->T_CS[6] * c->T_CS[6];
   if (!(std::fabs(qn - 1.0) < 1e-6)) return DRI_EINVAL;
@@ -280,6 +282,8 @@ SolveParams solve_params(const dri_stream_s* s, int level, int last) {
   p.imu_mode = c.imu_mode;
   p.relin_g = c.bias_relin_g;
   p.relin_a = c.bias_relin_a;
+  p.track_mode = c.track_mode;
+  p.rgbd_lambda = c.rgbd_lambda;
   return p;
 }
 
@@ -742,6 +746,11 @@ SlotWork plan_slot_work(const dri_stream_s* s) {
     w.status = DRI_OK;
     return w;
   }
+  if (s->cfg.track_mode == DRI_TRACK_RGBD_ONLY) {   // no IMU term: no samples staged
+    w.mode = kSlotTrack;
+    w.status = DRI_OK;
+    return w;
+  }
   const int r = select_imu(s, s->t_prev, s->t_frame, &w.k0, &w.k1);
   if (r != DRI_OK) {
     w.status = r;
@@ -899,6 +908,8 @@ int dri_config_default(int32_t width, int32_t height, dri_stream_config* cfg) {
   cfg->imu_mode = DRI_IMU_REINTEGRATE;
   cfg->bias_relin_g = 0.01;
   cfg->bias_relin_a = 0.1;
+  cfg->track_mode = DRI_TRACK_INERTIAL;
+  cfg->rgbd_lambda = 1.0;
   return DRI_OK;
 }
 

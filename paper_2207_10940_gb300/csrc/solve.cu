@@ -963,6 +963,38 @@ struct GnSmem {
 };
 
 // Assemble the joint system at (ctrl->x0, ctrl->x1) into S.H (full), S.b.
+// Entry e (0..71) of the two pixel systems rotated into W: term e / 36 (0 ICP
+// with R_ref, 1 photometric with R_0), element e % 36 of its 6x6 (and, for
+// column 0, the row of its 6-vector), weighted by W_ICP / W_RGB.
+__device__ void pixel_system_entry(const SolveParams& sp, const Ctrl* c, GnSmem& S, int e) {
+  const int term = e / 36, idx = e % 36;
+  const int i = idx / 6, j = idx % 6;
+  double R[9];
+  if (term == 0) {
+    for (int k = 0; k < 9; ++k) R[k] = c->Rref[k];
+  } else {
+    quat_to_rot(c->x0.q, R);
+  }
+  const double* s = c->sums + term * kSums;
+  auto hloc = [&](int a, int b) {
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return s[lo * 6 - lo * (lo - 1) / 2 + (hi - lo)];
+  };
+  // Hw = Q Hloc Q^T with Q = diag(R, R)
+  double acc = 0.0;
+  const int bi = i / 3, ri = i % 3, bj = j / 3, rj = j % 3;
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) acc += R[ri * 3 + k] * hloc(bi * 3 + k, bj * 3 + l) * R[rj * 3 + l];
+  const double w = term == 0 ? sp.W_icp : sp.W_rgb;
+  S.Hl[term][idx] = w * acc;
+  if (j == 0) {
+    double g = 0.0;
+    for (int k = 0; k < 3; ++k) g += R[ri * 3 + k] * s[21 + bi * 3 + k];
+    S.gl[term][i] = -w * g;
+  }
+}
+
+
 __device__ void assemble(const SolveParams& sp, GnSmem& S) {
   Ctrl* c = sp.ctrl;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -972,31 +1004,7 @@ __device__ void assemble(const SolveParams& sp, GnSmem& S) {
   }
   // pixel systems into W (term 0 ICP with R_ref, term 1 photometric with R_0)
   if (tid >= 32 && tid < 32 + 2 * 36) {
-    const int term = (tid - 32) / 36, idx = (tid - 32) % 36;
-    const int i = idx / 6, j = idx % 6;
-    double R[9];
-    if (term == 0) {
-      for (int k = 0; k < 9; ++k) R[k] = c->Rref[k];
-    } else {
-      quat_to_rot(c->x0.q, R);
-    }
-    const double* s = c->sums + term * kSums;
-    auto hloc = [&](int a, int b) {
-      const int lo = a < b ? a : b, hi = a < b ? b : a;
-      return s[lo * 6 - lo * (lo - 1) / 2 + (hi - lo)];
-    };
-    // Hw = Q Hloc Q^T with Q = diag(R, R)
-    double acc = 0.0;
-    const int bi = i / 3, ri = i % 3, bj = j / 3, rj = j % 3;
-    for (int k = 0; k < 3; ++k)
-      for (int l = 0; l < 3; ++l) acc += R[ri * 3 + k] * hloc(bi * 3 + k, bj * 3 + l) * R[rj * 3 + l];
-    const double w = term == 0 ? sp.W_icp : sp.W_rgb;
-    S.Hl[term][idx] = w * acc;
-    if (j == 0) {
-      double g = 0.0;
-      for (int k = 0; k < 3; ++k) g += R[ri * 3 + k] * s[21 + bi * 3 + k];
-      S.gl[term][i] = -w * g;
-    }
+    pixel_system_entry(sp, c, S, tid - 32);
   } else if ((tid >> 5) == 4) {
     warp_state_boxminus(c->x0, c->xbar, S.dprior);
   } else if (tid == 160) {
@@ -1159,9 +1167,57 @@ __device__ void assemble(const SolveParams& sp, GnSmem& S) {
   __syncthreads();
 }
 
+// RGB-D-only baseline (DRI_TRACK_RGBD_ONLY): one Gauss-Newton step on x1's pose
+// with H_icp + lambda H_rgb (x1's blocks of the two pixel systems in W), x0
+// fixed; 6x6 LDL^T; x1's other components unchanged.
+__device__ void gn_step_pose_only(const SolveParams& sp, GnSmem& S) {
+  Ctrl* c = sp.ctrl;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    S.x0 = c->x0;
+    S.x1 = c->x1;
+  }
+  if (tid >= 32 && tid < 32 + 2 * 36) pixel_system_entry(sp, c, S, tid - 32);
+  __syncthreads();
+  const double lam = sp.rgbd_lambda;
+  if (tid < 36) S.A[tid] = S.Hl[0][tid] + lam * S.Hl[1][tid];
+  else if (tid < 42) S.x[tid - 36] = S.gl[0][tid - 36] + lam * S.gl[1][tid - 36];
+  else if (tid < 53) S.x[tid - 36] = 0.0;                  // the other 11 tangent components
+  __syncthreads();
+  const bool pd = block_ldlt(S.A, 6, 6, S.col, &S.fail);
+  if (tid == 0) ldlt_solve_thread(S.A, 6, 6, S.x);
+  __syncthreads();
+  bool good = pd;
+  for (int i = 0; i < 6; ++i) good = good && isfinite(S.x[i]);
+  if (!good) {
+    if (tid == 0) c->status = DRI_ELOST;
+    return;
+  }
+  const int warp = tid >> 5;
+  if (warp == 0) {
+    warp_state_boxplus(S.x1, S.x);
+  } else if (tid == 64) {
+    const double* s = c->sums;
+    c->n_icp[sp.level] = (int32_t)s[28];
+    c->n_rgb[sp.level] = (int32_t)s[kSums + 28];
+    c->cost = sp.W_icp * s[27] + lam * sp.W_rgb * s[kSums + 27];
+    c->iterations += 1;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    warp_write_transforms(c, S.x0, S.x1, S.rot);
+  } else if (tid == 32) {
+    c->x1 = S.x1;
+  }
+}
+
 __device__ void gn_step_body(const SolveParams& sp, GnSmem& S) {
   Ctrl* c = sp.ctrl;
   if (c->status != 0) return;
+  if (sp.track_mode == DRI_TRACK_RGBD_ONLY) {
+    gn_step_pose_only(sp, S);
+    return;
+  }
   const int tid = threadIdx.x, nt = blockDim.x;
   assemble(sp, S);
   if (!S.ok) {
@@ -1349,6 +1405,16 @@ __device__ void frame_begin_body(const SolveParams& sp, BeginSmem& B) {
     for (int l = 0; l < kMaxLevels; ++l) c->n_icp[l] = c->n_rgb[l] = 0;
   }
   __syncthreads();
+  if (sp.track_mode == DRI_TRACK_RGBD_ONLY) {     // x1 starts at x0; no IMU term
+    if (tid == 0) {
+      B.ok = c->initialised && !(fabs(sp.imu->t0 - c->t_state) > 1e-9);
+      if (B.ok) c->x1 = c->x;
+      else c->status = DRI_ENOTREADY;
+    }
+    __syncthreads();
+    if (B.ok && (tid >> 5) == 0) warp_write_transforms(c, c->x0, c->x1, B.rot);
+    return;
+  }
   const bool ok = imu_weight_and_prediction(sp, c, B, &c->x1);
   if (ok && (tid >> 5) == 0) warp_write_transforms(c, c->x0, c->x1, B.rot);
 }
@@ -1364,6 +1430,16 @@ __device__ void frame_end_body(const SolveParams& sp) {
   __syncthreads();
   if (!s_ok) {
     if (tid == 0) c->x = c->xstart;
+    return;
+  }
+  if (sp.track_mode == DRI_TRACK_RGBD_ONLY) {     // no prior to carry over
+    if (tid == 0) {
+      c->x = c->x1;
+      c->xbar = c->x1;
+      c->t_state = sp.imu->t1;
+      load_pose_ref(c);
+      c->ref_index = 1 - c->ref_index;
+    }
     return;
   }
   // b' = b - H d; Schur complement of the x0 block (Eq. 8)

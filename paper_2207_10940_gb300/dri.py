@@ -31,6 +31,8 @@ DRI_FP16_MAPS = 1
 DRI_FP32_PARTIALS = 2
 DRI_IMU_REINTEGRATE = 0
 DRI_IMU_FIRST_ORDER = 1
+DRI_TRACK_INERTIAL = 0
+DRI_TRACK_RGBD_ONLY = 1
 DRI_MAX_LEVELS = 4
 
 c_double_p = ctypes.POINTER(ctypes.c_double)
@@ -53,6 +55,8 @@ class dri_stream_config(ctypes.Structure):
         ("min_valid", ctypes.c_int32), ("precision_flags", ctypes.c_int32),
         ("max_imu", ctypes.c_int32), ("imu_mode", ctypes.c_int32),
         ("bias_relin_g", ctypes.c_double), ("bias_relin_a", ctypes.c_double),
+        ("track_mode", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("rgbd_lambda", ctypes.c_double),
     ]
 
 
