@@ -35,6 +35,11 @@ or schedule):
   and the photometric term still warps with it; x_1 starts at x_0; the system
   is H_icp + lambda H_rgb on x_1's pose (the per-pixel weights W_ICP, W_RGB
   kept, lambda = 1 by default); no IMU term, prior or marginalisation.
+* Occlusion test (occlusion_thr > 0; off by default, the paper gives none):
+  a photometric residual is used only where the warped point's depth in x_0's
+  camera agrees within occlusion_thr with the reference depth at the nearest
+  reference pixel floor(x + 0.5), when that depth is valid (> 0); a point
+  behind or in front of what the reference saw there changed visibility.
 """
 from __future__ import annotations
 
@@ -83,6 +88,7 @@ class TrackerConfig:
     bias_relin_a: float = 0.1           # |db_a| (m/s^2) above which mode 1 re-integrates
     track_mode: int = 0                 # 0 RGB-D-inertial (joint), 1 RGB-D-only pose
     rgbd_lambda: float = 1.0            # track_mode 1: weight of the photometric term
+    occlusion_thr: float = 0.0          # > 0: photometric depth-consistency test (m)
 
     def level_camera(self, level):
         """Intrinsics at pyramid level l: f_l = f / 2^l, c_l = (c + 0.5) / 2^l - 0.5

@@ -147,6 +147,16 @@ def linearise(cur: FrameLevel, ref: RefLevel, R_ref, r_ref, x0, x1, cfg):
     xp = fx * X0 / z0s + cx
     yp = fy * Y0 / z0s + cy
     rgb_valid = dv & z0pos & (xp >= 0) & (xp < rw - 1) & (yp >= 0) & (yp < rh - 1)
+    # depth consistency (occlusion) test, when enabled: the point's depth in x_0's
+    # camera against the reference depth at the nearest reference pixel
+    occ_thr = getattr(cfg, "occlusion_thr", 0.0)
+    if occ_thr > 0:
+        xn = np.clip(np.floor(np.where(rgb_valid, xp, 0.0) + 0.5), 0, rw - 1).astype(np.int64)
+        yn = np.clip(np.floor(np.where(rgb_valid, yp, 0.0) + 0.5), 0, rh - 1).astype(np.int64)
+        dref = ref.depth[yn, xn]
+        occ_gap = np.abs(z0 - dref)
+        inside = rgb_valid.copy()
+        rgb_valid &= ~((dref > 0) & (occ_gap > occ_thr))
     xs = np.where(rgb_valid, xp, 0.0)
     ys = np.where(rgb_valid, yp, 0.0)
     I0 = _bilinear(ref.I, xs, ys)
@@ -164,6 +174,12 @@ def linearise(cur: FrameLevel, ref: RefLevel, R_ref, r_ref, x0, x1, cfg):
     m_rgb |= dv & (np.abs(z0) <= REL_MARGIN * np.linalg.norm(p0, axis=-1))
     m_rgb |= dv & z0pos & ((np.abs(xp) <= PX_MARGIN) | (np.abs(xp - (rw - 1)) <= PX_MARGIN) |
                            (np.abs(yp) <= PX_MARGIN) | (np.abs(yp - (rh - 1)) <= PX_MARGIN))
+    if occ_thr > 0:
+        # the nearest reference pixel's rounding and the depth gap's threshold
+        fxn, fyn = xp + 0.5, yp + 0.5
+        m_rgb |= inside & ((np.abs(fxn - np.round(fxn)) < PX_MARGIN) |
+                           (np.abs(fyn - np.round(fyn)) < PX_MARGIN))
+        m_rgb |= inside & (dref > 0) & _near_rel(occ_gap, occ_thr)
 
     W_icp = 1.0 / cfg.sigma_d ** 2
     W_rgb = 1.0 / cfg.sigma_I ** 2

@@ -187,7 +187,7 @@ def _bf_pixel_lookup(img, x, y):
             + (1 - ax) * ay * img[y0 + 1][x0] + ax * ay * img[y0 + 1][x0 + 1])
 
 
-def _bf_linearise(D1, I1, D0, I0, K, cfg, Rref, rref, R0, r0, R1, r1):
+def _bf_linearise(D1, I1, D0, I0, K, cfg, Rref, rref, R0, r0, R1, r1, occ_thr=0.0):
     h, w = D1.shape
     fx, fy, cx, cy = K
     # reference gradient, border zero
@@ -236,6 +236,10 @@ def _bf_linearise(D1, I1, D0, I0, K, cfg, Rref, rref, R0, r0, R1, r1):
                 x = fx * q0[0] / q0[2] + cx
                 y = fy * q0[1] / q0[2] + cy
                 if 0 <= x < w - 1 and 0 <= y < h - 1:
+                    if occ_thr > 0:             # depth consistency at the nearest pixel
+                        dref = D0[int(np.floor(y + 0.5)), int(np.floor(x + 0.5))]
+                        if dref > 0 and abs(q0[2] - dref) > occ_thr:
+                            continue
                     e = _bf_pixel_lookup(I0, x, y) - I1[v, u]
                     gx = _bf_pixel_lookup(Gx, x, y)
                     gy = _bf_pixel_lookup(Gy, x, y)
@@ -251,11 +255,11 @@ def _bf_linearise(D1, I1, D0, I0, K, cfg, Rref, rref, R0, r0, R1, r1):
     return Wi * Hi, Wi * bi, ni, Wr * Hr, Wr * br, nr
 
 
-@pytest.mark.parametrize("seed", [11, 12, 13])
-def test_brute_force_8x8(seed):
+@pytest.mark.parametrize("seed,occ", [(11, 0.0), (12, 0.0), (13, 0.0), (11, 0.004), (12, 0.004)])
+def test_brute_force_8x8(seed, occ):
     cam = synth.Camera(8, 8, 8.0, 8.0, 4.0, 4.0)
     seq = synth.frame_pair(seed=seed, cam=cam, rot_deg=3.0, trans_m=0.05)
-    cfg = oracle_config(seq, levels=1, iters=(1,))
+    cfg = oracle_config(seq, levels=1, iters=(1,), occlusion_thr=occ)
     rng = np.random.default_rng(seed)
     x0, x1, L1, ref = _setup(seq, cfg)
     xr = x0
@@ -267,9 +271,12 @@ def test_brute_force_8x8(seed):
     D0 = seq.depth[0].astype(np.float64)
     Hi, bi, ni, Hr, br, nr = _bf_linearise(D1, seq.intensity[1].astype(np.float64), D0,
                                            seq.intensity[0].astype(np.float64), K, cfg,
-                                           xr.R, xr.r, x0.R, x0.r, x1.R, x1.r)
+                                           xr.R, xr.r, x0.R, x0.r, x1.R, x1.r, occ)
     assert ni == lin["n_icp"] and nr == lin["n_rgb"]
-    assert nr > 20
+    assert nr > 20 if occ == 0 else nr > 0
+    if occ > 0:                        # the test rejects something on these scenes
+        assert nr < photogeo.linearise(L1[0], ref[0], xr.R, xr.r, x0, x1,
+                                       oracle_config(seq, levels=1, iters=(1,)))["n_rgb"]
     np.testing.assert_allclose(lin["H_icp"], Hi, rtol=1e-12, atol=1e-9 * max(1, np.abs(Hi).max()))
     np.testing.assert_allclose(lin["b_icp"], bi, rtol=1e-12, atol=1e-9 * max(1, np.abs(bi).max()))
     np.testing.assert_allclose(lin["H_rgb"], Hr, rtol=1e-12, atol=1e-9 * np.abs(Hr).max())
