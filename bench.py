@@ -72,12 +72,12 @@ def make_inputs(n_frames_total, workers):
     return seq, frames, imu
 
 
-def dri_config(seq, flags=0, imu_mode=0, track_mode=0):
+def dri_config(seq, flags=0, imu_mode=0, track_mode=0, occlusion_thr=0.0):
     from paper_2207_10940_gb300 import dri, synth
     cam = seq.cam
     return dri.config_for(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, LEVELS, ITERS,
                           q_CS=synth.matrix_to_quat(seq.R_CS), r_CS=seq.r_CS, precision_flags=flags,
-                          imu_mode=imu_mode, track_mode=track_mode)
+                          imu_mode=imu_mode, track_mode=track_mode, occlusion_thr=occlusion_thr)
 
 
 def measured_peaks():
@@ -175,10 +175,12 @@ def oracle_frames_per_s(seq, frames, imu, budget_s):
     return n / t_total, n, t_total, states
 
 
-def odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_frames, flags, imu_mode, track_mode=0):
+def odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_frames, flags, imu_mode, track_mode=0,
+                  occlusion_thr=0.0):
     """One stream tracked over n_frames frames of the periodic sequence with every
     result read back: its states, for the odometry errors against ground truth."""
-    run = Runner(seq, imu, d_dev, i_dev, d_pin, i_pin, [0], dev, None, None, flags, imu_mode, track_mode)
+    run = Runner(seq, imu, d_dev, i_dev, d_pin, i_pin, [0], dev, None, None, flags, imu_mode, track_mode,
+                 occlusion_thr)
     states = []
     for _ in range(n_frames):
         res = run.step(wait=True)
@@ -187,9 +189,12 @@ def odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_frames, flags, im
     return states
 
 
+ODOMETRY_OCCLUSION_THR = 0.03    # m, the occlusion test's threshold in the odometry comparison
+
+
 def rgbd_only_report(seq, states):
-    """Errors of the RGB-D-only baseline (DRI_TRACK_RGBD_ONLY, lambda 1) against
-    ground truth over the same frames as the odometry pass."""
+    """Trajectory errors against ground truth over the same frames as the
+    odometry pass (for the RGB-D-only baseline and the occlusion variant)."""
     from paper_2207_10940_gb300 import odometry
     gt = [seq.gt[k % N_UNIQUE] for k in range(len(states))]
     ev = odometry.evaluate(states, gt)
@@ -347,14 +352,14 @@ class Runner:
     frame (offset_i + k) mod 100 at time (offset_i + k) / 30 s."""
 
     def __init__(self, seq, imu, d_dev, i_dev, d_pin, i_pin, offsets, dev, tiles=None, groups=None,
-                 flags=0, imu_mode=0, track_mode=0):
+                 flags=0, imu_mode=0, track_mode=0, occlusion_thr=0.0):
         import torch
         from paper_2207_10940_gb300 import dri
         self.dri, self.torch = dri, torch
         self.dev = dev
         self.d_dev, self.i_dev, self.d_pin, self.i_pin = d_dev, i_dev, d_pin, i_pin
         self.ts = torch.cuda.Stream(dev)
-        cfg = dri_config(seq, flags, imu_mode, track_mode)
+        cfg = dri_config(seq, flags, imu_mode, track_mode, occlusion_thr)
         self.offsets = list(offsets)
         self.streams = [dri.Stream(cfg, dri.state_from_dict(initial_state_at(seq, o), o / FPS), self.ts)
                         for o in self.offsets]
@@ -524,7 +529,8 @@ def served_pass(args, dev, workers):
         cam = s.cam
         cfg = dri.config_for(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, LEVELS, ITERS,
                              q_CS=synth.matrix_to_quat(s.R_CS), r_CS=s.r_CS,
-                             precision_flags=args.precision_flags, imu_mode=args.imu_mode)
+                             precision_flags=args.precision_flags, imu_mode=args.imu_mode,
+                             occlusion_thr=args.occlusion_thr)
         g = s.gt[o]
         x0 = dict(t=o / FPS, r_WC=np.zeros(3), q_WC=np.array([1.0, 0, 0, 0]), v_I=g["v_I"].copy(),
                   bg=np.zeros(3), ba=np.zeros(3), q_IW=synth.matrix_to_quat(g["R_IW"]))
@@ -717,7 +723,8 @@ def run_ours(args):
         offsets = [(BATCH_OFFSET * i) % N_UNIQUE for i in range(n_streams)]
         run = Runner(seq, imu, d_dev, i_dev, d_pin, i_pin, offsets, dev,
                      args.rows_per_thread if n_streams > 1 else None,
-                     args.groups if n_streams > 1 else None, args.precision_flags, args.imu_mode)
+                     args.groups if n_streams > 1 else None, args.precision_flags, args.imu_mode, 0,
+                     args.occlusion_thr)
         res = run.step(wait=True)
         for _ in range(args.warmup):
             run.step()
@@ -741,14 +748,18 @@ def run_ours(args):
         run.close()
         del run
         torch.cuda.synchronize(dev)
-    odo_states = odo_rgbd = None
+    odo_states = odo_rgbd = odo_occ = None
     n_odo = min(args.odometry_frames, n_frames - 2)
     if n_odo > 1 and rank == 0:
         odo_states = odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_odo, args.precision_flags,
-                                   args.imu_mode)
+                                   args.imu_mode, occlusion_thr=args.occlusion_thr)
         # the vision-only, pose-only baseline the paper compares with (same frames)
         odo_rgbd = odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_odo, args.precision_flags,
-                                 args.imu_mode, track_mode=1)
+                                 args.imu_mode, track_mode=1, occlusion_thr=args.occlusion_thr)
+        # the joint tracker with the occlusion test (when the timed passes run without it)
+        if args.occlusion_thr <= 0:
+            odo_occ = odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_odo, args.precision_flags,
+                                    args.imu_mode, occlusion_thr=ODOMETRY_OCCLUSION_THR)
         torch.cuda.synchronize(dev)
     served = None
     if args.serve_seconds > 0:
@@ -770,7 +781,8 @@ def run_ours(args):
         "value": b["value"], "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(args.precision_flags),
-        "data": "synthetic", "config": dict(config_json(args.batch), imu_mode=args.imu_mode),
+        "data": "synthetic", "config": dict(config_json(args.batch), imu_mode=args.imu_mode,
+                                            occlusion_thr=args.occlusion_thr),
         "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"],
         "gpu_launches": b["gpu_launches"],
         "frames_failed": b["frames_failed"], "frames_ok": b["frames_ok"],
@@ -784,6 +796,8 @@ def run_ours(args):
         "served": served,
         "odometry": None if odo_states is None else odometry_report(seq, odo_states, o_states),
         "odometry_rgbd_only": None if odo_rgbd is None else rgbd_only_report(seq, odo_rgbd),
+        "odometry_occlusion": None if odo_occ is None else dict(
+            rgbd_only_report(seq, odo_occ), occlusion_thr_m=ODOMETRY_OCCLUSION_THR),
         "precision": precision,
         "cpu_baseline": {"value": o_fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
                          "sample": f"{o_n} whole frames of the same sequence tracked by the FP64 "
@@ -816,6 +830,8 @@ def main():
     ap.add_argument("--imu-mode", type=int, default=0, choices=(0, 1),
                     help="IMU term per Gauss-Newton iteration of the timed streams: 0 re-integrate "
                          "(default), 1 first-order bias update (DRI_IMU_FIRST_ORDER)")
+    ap.add_argument("--occlusion-thr", type=float, default=0.0,
+                    help="photometric occlusion test of the timed streams, m (default 0: off)")
     ap.add_argument("--precision-flags", type=int, default=0,
                     help="precision_flags of the timed streams: 1 FP16 maps, 2 FP32 partials, 3 both "
                          "(default 0: FP32 maps, FP64 partials)")

@@ -74,6 +74,13 @@ extern "C" {
 #define DRI_TRACK_INERTIAL  0
 #define DRI_TRACK_RGBD_ONLY 1
 
+/* Occlusion test (dri_stream_config.occlusion_thr > 0; the paper has none,
+ * the readings add it as an option): a photometric residual (Eq. 3) is used
+ * only where the warped point's depth in x0's camera agrees within
+ * occlusion_thr metres with the reference depth at the nearest reference pixel
+ * (when that depth is valid); elsewhere the point changed visibility between
+ * the frames and its intensity belongs to another surface. */
+
 #define DRI_MAX_LEVELS 4
 
 typedef struct dri_stream_s* dri_stream;
@@ -106,6 +113,7 @@ typedef struct {
     int32_t track_mode;            /* DRI_TRACK_INERTIAL (default) | _RGBD_ONLY       */
     int32_t reserved;
     double rgbd_lambda;            /* RGB-D-only: photometric weight (default 1)      */
+    double occlusion_thr;          /* > 0: photometric depth-consistency test, m; 0 off */
 } dri_stream_config;
 
 /* One IMU sample: time (s), gyro (rad/s) and accelerometer (m/s^2) in S. */

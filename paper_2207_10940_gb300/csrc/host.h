@@ -83,6 +83,7 @@ struct Plan {
   int S = 0, levels = 0;
   int iters[kMaxLevels] = {};
   bool fp16 = false, fp32p = false;
+  bool occ = false;                 // the occlusion test is on (occlusion_thr > 0) for every slot
   bool owns_device = false;         // table / dyn / heads allocated by the plan
   int groups = 1;                   // slot groups of the Gauss-Newton loop, one CUDA stream each
   std::vector<int> gfirst, gcount;

@@ -138,7 +138,7 @@ __device__ __forceinline__ void gradient_px(const LevelMaps& m, int set, int w, 
     gx = 0.5f * (__ldg(I + o + 1) - __ldg(I + o - 1));
     gy = 0.5f * (__ldg(I + o + w) - __ldg(I + o - w));
   }
-  Packs<T>::store_b(m.packB[set], o, __ldg(I + o), gx, gy);
+  Packs<T>::store_b(m.packB[set], o, __ldg(I + o), gx, gy, __ldg(m.depth[set] + o));
 }
 
 // Block -> (slot, 32 x 8 tile of the slot's level-`a.level` image); false for an

@@ -120,10 +120,10 @@ __device__ __forceinline__ bool icp_pixel(const TrackParams& p, const LevelGeom&
 }
 
 // Photometric term (Eq. 3) of the pixel (u, v) with live depth d and intensity i1.
-template <typename T>
+template <typename T, bool OCC>
 __device__ __forceinline__ bool rgb_pixel(const LevelGeom& g, const float* A, const float* t,
-                                          const void* __restrict__ B0, int u, int v, const Live& L,
-                                          float* acc) {
+                                          const void* __restrict__ B0, const float* __restrict__ D0,
+                                          float occ_thr, int u, int v, const Live& L, float* acc) {
   const float d = L.d;
   const float rx = ((float)u - g.cx) * g.ifx;
   const float ry = ((float)v - g.cy) * g.ify;
@@ -144,8 +144,15 @@ __device__ __forceinline__ bool rgb_pixel(const LevelGeom& g, const float* A, co
   if (xb < 0 || xb >= g.w - 1 || yb < 0 || yb >= g.h - 1) return false;
   const float ax = sxp - fxp, ay = syp - fyp;
   const int q = yb * g.w + xb;
-  const float3 s00 = Packs<T>::load_b(B0, q), s01 = Packs<T>::load_b(B0, q + 1);
-  const float3 s10 = Packs<T>::load_b(B0, q + g.w), s11 = Packs<T>::load_b(B0, q + g.w + 1);
+  const float4 s00 = Packs<T>::load_b(B0, q), s01 = Packs<T>::load_b(B0, q + 1);
+  const float4 s10 = Packs<T>::load_b(B0, q + g.w), s11 = Packs<T>::load_b(B0, q + g.w + 1);
+  if (OCC) {                     // depth consistency at the nearest reference pixel
+    const bool right = floorf(sxp + 0.5f) != fxp, down = floorf(syp + 0.5f) != fyp;
+    const float dr = Packs<T>::kDepthInB
+                         ? (down ? (right ? s11.w : s10.w) : (right ? s01.w : s00.w))
+                         : __ldg(D0 + (yb + (down ? 1 : 0)) * g.w + xb + (right ? 1 : 0));
+    if (dr > 0.f && fabsf(z - dr) > occ_thr) return false;
+  }
   const float w00 = (1.f - ax) * (1.f - ay), w01 = ax * (1.f - ay);
   const float w10 = (1.f - ax) * ay, w11 = ax * ay;
   const float iv = w00 * s00.x + w01 * s01.x + w10 * s10.x + w11 * s11.x;
@@ -163,7 +170,7 @@ __device__ __forceinline__ bool rgb_pixel(const LevelGeom& g, const float* A, co
 // One tile of one image (single-term: 32 x 8 * ppt pixels of `term`; mixed:
 // 32 x 4 * ppt pixels, both terms): (bx, by) its tile
 // coordinates, bid its index in the image's fold order.
-template <typename T, typename P, bool FLAGS, bool SPLIT>
+template <typename T, typename P, bool FLAGS, bool SPLIT, bool OCC>
 __device__ __forceinline__ void track_tile(const TrackParams& p, const int term, const int bx,
                                            const int by, const int bid) {
   Ctrl* __restrict__ ctrl = p.ctrl;
@@ -237,7 +244,7 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int term,
     bool ok = false;
     if (col_ok && v < g.h && cur.d >= dmin && cur.d <= dmax) {
       ok = icp ? icp_pixel<T>(p, g, A, t, A0, D0, u, v, cur, acc)
-               : rgb_pixel<T>(g, A, t, B0, u, v, cur, acc);
+               : rgb_pixel<T, OCC>(g, A, t, B0, D0, p.occ_thr, u, v, cur, acc);
     }
     if (FLAGS) {             // bit 0 ICP, bit 1 photometric, combined through shared memory
       if (icp) s_flag[wrow][lane] = ok ? 1 : 0;
@@ -322,17 +329,17 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int term,
   if (tid == 0) p.counters[0] = 0u;
 }
 
-template <typename T, typename P, bool FLAGS>
+template <typename T, typename P, bool FLAGS, bool OCC>
 __global__ void __launch_bounds__(kTrackThreadsX * kTrackThreadsY)
 k_track(TrackParams p) {
-  track_tile<T, P, FLAGS, false>(p, 0, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x);
+  track_tile<T, P, FLAGS, false, OCC>(p, 0, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // Tiles of every tracking slot at one level: block -> (slot, tile, term)
 // through the block prefix, tile -> (column, row band) in the slot's image.
 // Three blocks per SM (80 registers) measured faster than four (64 registers,
 // more spill reloads) and than two columns per thread.
-template <typename T, typename P>
+template <typename T, typename P, bool OCC>
 __global__ void __launch_bounds__(kTrackThreadsX * kTrackThreadsY, 3)
 k_track_batch(const BatchArgs a) {
   const int i = batch_slot(a, blockIdx.x);
@@ -348,7 +355,7 @@ k_track_batch(const BatchArgs a) {
   const int t = blockIdx.x - __ldg(a.start + i);
   const int gx = (p.g.w + kTrackThreadsX - 1) / kTrackThreadsX;
   const int tile = t >> 1;                    // the two terms of a tile are neighbours
-  track_tile<T, P, false, true>(p, t & 1, tile % gx, tile / gx, t);
+  track_tile<T, P, false, true, OCC>(p, t & 1, tile % gx, tile / gx, t);
 }
 
 }  // namespace
@@ -382,10 +389,16 @@ cudaError_t launch_track(const TrackParams& p0, bool fp16, bool fp32_partials, c
   const int rows = kTrackRows * p.ppt;
   const dim3 grid((p.g.w + kTrackThreadsX - 1) / kTrackThreadsX, (p.g.h + rows - 1) / rows);
   const bool flags = p.flags != nullptr;
+  const bool occ = p.occ_thr > 0.f;
 #define DRI_TRACK_LAUNCH(T, P)                                              \
   do {                                                                      \
-    if (flags) k_track<T, P, true><<<grid, block, 0, s>>>(p);               \
-    else k_track<T, P, false><<<grid, block, 0, s>>>(p);                    \
+    if (occ) {                                                              \
+      if (flags) k_track<T, P, true, true><<<grid, block, 0, s>>>(p);       \
+      else k_track<T, P, false, true><<<grid, block, 0, s>>>(p);            \
+    } else {                                                                \
+      if (flags) k_track<T, P, true, false><<<grid, block, 0, s>>>(p);      \
+      else k_track<T, P, false, false><<<grid, block, 0, s>>>(p);           \
+    }                                                                       \
   } while (0)
   if (fp16) {
     if (fp32_partials) DRI_TRACK_LAUNCH(__half, float);
@@ -399,15 +412,21 @@ cudaError_t launch_track(const TrackParams& p0, bool fp16, bool fp32_partials, c
 }
 
 cudaError_t launch_track_batch(const BatchArgs& a, int blocks, bool fp16, bool fp32_partials,
-                               cudaStream_t s) {
+                               bool occ, cudaStream_t s) {
   const dim3 block(kTrackThreadsX, kTrackThreadsY);
+#define DRI_TRACK_BATCH(T, P)                                               \
+  do {                                                                      \
+    if (occ) k_track_batch<T, P, true><<<blocks, block, 0, s>>>(a);         \
+    else k_track_batch<T, P, false><<<blocks, block, 0, s>>>(a);            \
+  } while (0)
   if (fp16) {
-    if (fp32_partials) k_track_batch<__half, float><<<blocks, block, 0, s>>>(a);
-    else k_track_batch<__half, double><<<blocks, block, 0, s>>>(a);
+    if (fp32_partials) DRI_TRACK_BATCH(__half, float);
+    else DRI_TRACK_BATCH(__half, double);
   } else {
-    if (fp32_partials) k_track_batch<float, float><<<blocks, block, 0, s>>>(a);
-    else k_track_batch<float, double><<<blocks, block, 0, s>>>(a);
+    if (fp32_partials) DRI_TRACK_BATCH(float, float);
+    else DRI_TRACK_BATCH(float, double);
   }
+#undef DRI_TRACK_BATCH
   return cudaGetLastError();
 }
 

@@ -56,7 +56,7 @@ class dri_stream_config(ctypes.Structure):
         ("max_imu", ctypes.c_int32), ("imu_mode", ctypes.c_int32),
         ("bias_relin_g", ctypes.c_double), ("bias_relin_a", ctypes.c_double),
         ("track_mode", ctypes.c_int32), ("reserved", ctypes.c_int32),
-        ("rgbd_lambda", ctypes.c_double),
+        ("rgbd_lambda", ctypes.c_double), ("occlusion_thr", ctypes.c_double),
     ]
 
 
