@@ -141,9 +141,11 @@ __device__ __forceinline__ void gradient_px(const LevelMaps& m, int set, int w, 
   Packs<T>::store_b(m.packB[set], o, __ldg(I + o), gx, gy, __ldg(m.depth[set] + o));
 }
 
-// Block -> (slot, 32 x 8 tile of the slot's level-`a.level` image); false for an
-// idle slot or a thread outside the image.
-__device__ __forceinline__ bool map_pixel(const BatchArgs& a, int* slot, int* x, int* y) {
+// Block -> (slot, 32 x 8 kMapRows tile of the slot's level-`a.level` image):
+// the thread's column x and first row y (its rows are y, y + 8, ...); false for
+// an idle slot.  w, h: the level's size.
+__device__ __forceinline__ bool map_tile(const BatchArgs& a, int* slot, int* x, int* y, int* w,
+                                         int* h) {
   const int i = batch_slot(a, blockIdx.x);
   *slot = a.slot0 + i;
   if (batch_dyn(a, *slot).mode == kSlotIdle) return false;
@@ -151,34 +153,42 @@ __device__ __forceinline__ bool map_pixel(const BatchArgs& a, int* slot, int* x,
   const int t = blockIdx.x - __ldg(a.start + i);
   const int gx = (g.w + kMapTileW - 1) / kMapTileW;
   *x = (t % gx) * kMapTileW + threadIdx.x;
-  *y = (t / gx) * kMapTileH + threadIdx.y;
-  return *x < g.w && *y < g.h;
+  *y = (t / gx) * kMapTileH * kMapRows + threadIdx.y;
+  *w = g.w;
+  *h = g.h;
+  return true;
 }
 
 __global__ void __launch_bounds__(256) k_pyr_down_batch(const BatchArgs a) {
-  int slot, x, y;
-  if (!map_pixel(a, &slot, &x, &y)) return;
+  int slot, x, y, w, h;
+  if (!map_tile(a, &slot, &x, &y, &w, &h) || x >= w) return;
   const SlotStatic& st = a.slots[slot];
   const int cs = 1 - st.tp[0].ctrl->ref_index;
-  pyr_down_px(st.tp[a.level - 1].m, st.tp[a.level].m, cs, st.tp[a.level - 1].g.w,
-              st.tp[a.level].g.w, x, y);
+#pragma unroll
+  for (int k = 0; k < kMapRows; ++k, y += kMapTileH)
+    if (y < h) pyr_down_px(st.tp[a.level - 1].m, st.tp[a.level].m, cs, st.tp[a.level - 1].g.w, w, x, y);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_normals_batch(const BatchArgs a) {
-  int slot, x, y;
-  if (!map_pixel(a, &slot, &x, &y)) return;
+  int slot, x, y, w, h;
+  if (!map_tile(a, &slot, &x, &y, &w, &h) || x >= w) return;
   const TrackParams& tp = a.slots[slot].tp[a.level];
-  normal_px<T>(tp.m, 1 - tp.ctrl->ref_index, tp.g, tp.depth_min, tp.depth_max, x, y);
+  const int cs = 1 - tp.ctrl->ref_index;
+#pragma unroll
+  for (int k = 0; k < kMapRows; ++k, y += kMapTileH)
+    if (y < h) normal_px<T>(tp.m, cs, tp.g, tp.depth_min, tp.depth_max, x, y);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_gradient_batch(const BatchArgs a) {
-  int slot, x, y;
-  if (!map_pixel(a, &slot, &x, &y)) return;
+  int slot, x, y, w, h;
+  if (!map_tile(a, &slot, &x, &y, &w, &h) || x >= w) return;
   const TrackParams& tp = a.slots[slot].tp[a.level];
-  // the set that is (or just became) the reference
-  gradient_px<T>(tp.m, tp.ctrl->ref_index, tp.g.w, tp.g.h, x, y);
+  const int rs = tp.ctrl->ref_index;     // the set that is (or just became) the reference
+#pragma unroll
+  for (int k = 0; k < kMapRows; ++k, y += kMapTileH)
+    if (y < h) gradient_px<T>(tp.m, rs, w, h, x, y);
 }
 
 template <typename T>
