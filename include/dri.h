@@ -74,6 +74,13 @@ extern "C" {
 #define DRI_TRACK_INERTIAL  0
 #define DRI_TRACK_RGBD_ONLY 1
 
+/* Depth-dependent ICP weight (dri_stream_config.icp_depth_weight = 1; the
+ * paper weighs each term by its noise covariance, Sec. III, and a structured-
+ * light or stereo sensor's axial noise grows with the square of the depth):
+ * sigma_d(z) = sigma_d (z / 1 m)^2, so a pixel's ICP weight is W_ICP / z^4 with
+ * z its live depth in metres.  Streams tracked in one batch or served together
+ * must agree on this option and on whether occlusion_thr is > 0. */
+
 /* Occlusion test (dri_stream_config.occlusion_thr > 0; the paper has none,
  * the readings add it as an option): a photometric residual (Eq. 3) is used
  * only where the warped point's depth in x0's camera agrees within
@@ -114,6 +121,8 @@ typedef struct {
     int32_t reserved;
     double rgbd_lambda;            /* RGB-D-only: photometric weight (default 1)      */
     double occlusion_thr;          /* > 0: photometric depth-consistency test, m; 0 off */
+    int32_t icp_depth_weight;      /* 1: ICP weight W_ICP / z^4 (sigma_d at 1 m); 0 off */
+    int32_t reserved2;
 } dri_stream_config;
 
 /* One IMU sample: time (s), gyro (rad/s) and accelerometer (m/s^2) in S. */

@@ -40,6 +40,11 @@ or schedule):
   camera agrees within occlusion_thr with the reference depth at the nearest
   reference pixel floor(x + 0.5), when that depth is valid (> 0); a point
   behind or in front of what the reference saw there changed visibility.
+* Depth-dependent ICP weight (icp_depth_weight = 1; off by default, the
+  synthetic sensor's depth noise is constant): the axial noise of a
+  structured-light or stereo sensor grows with the square of the depth, so
+  sigma_d(z) = sigma_d (z / 1 m)^2 and a pixel's ICP weight is W_ICP / z^4
+  with z its live depth in metres.
 """
 from __future__ import annotations
 
@@ -89,6 +94,7 @@ class TrackerConfig:
     track_mode: int = 0                 # 0 RGB-D-inertial (joint), 1 RGB-D-only pose
     rgbd_lambda: float = 1.0            # track_mode 1: weight of the photometric term
     occlusion_thr: float = 0.0          # > 0: photometric depth-consistency test (m)
+    icp_depth_weight: int = 0           # 1: ICP weight W_ICP / z^4 (sigma_d at 1 m)
 
     def level_camera(self, level):
         """Intrinsics at pyramid level l: f_l = f / 2^l, c_l = (c + 0.5) / 2^l - 0.5

@@ -184,6 +184,10 @@ def linearise(cur: FrameLevel, ref: RefLevel, R_ref, r_ref, x0, x1, cfg):
     W_icp = 1.0 / cfg.sigma_d ** 2
     W_rgb = 1.0 / cfg.sigma_I ** 2
     Ji, ei = J_icp[icp_valid], e_icp[icp_valid]
+    if getattr(cfg, "icp_depth_weight", 0):
+        # per-pixel weight 1 / z^4 (sigma_d(z) = sigma_d z^2): scale J and e by 1 / z^2
+        sw = 1.0 / cur.depth[icp_valid].astype(np.float64) ** 2
+        Ji, ei = Ji * sw[:, None], ei * sw
     Jr, er = J_rgb[rgb_valid], e_rgb[rgb_valid]
     return dict(
         H_icp=W_icp * Ji.T @ Ji, b_icp=-W_icp * Ji.T @ ei, cost_icp=W_icp * float(ei @ ei),

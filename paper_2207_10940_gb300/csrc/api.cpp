@@ -54,6 +54,7 @@ int valid_config(const dri_stream_config* c) {
   if (c->track_mode != DRI_TRACK_INERTIAL && c->track_mode != DRI_TRACK_RGBD_ONLY) return DRI_EINVAL;
   if (!(c->rgbd_lambda >= 0) || !std::isfinite(c->rgbd_lambda)) return DRI_EINVAL;
   if (!(c->occlusion_thr >= 0) || !std::isfinite(c->occlusion_thr)) return DRI_EINVAL;
+  if (c->icp_depth_weight != 0 && c->icp_depth_weight != 1) return DRI_EINVAL;
   const double qn = c->T_CS[3] * c->T_CS[3] + c->T_CS[4] * c->T_CS[4] + c->T_CS[5] * c->T_CS[5] +
                     c->T_CS[6] * c->T_CS[6];
   if (!(std::fabs(qn - 1.0) < 1e-6)) return DRI_EINVAL;
@@ -305,6 +306,7 @@ TrackParams track_params(const dri_stream_s* s, int level, int ppt, uint8_t* fla
   p.icp_dist2 = (float)(s->cfg.icp_dist_thr * s->cfg.icp_dist_thr);
   p.icp_cos = (float)std::cos(s->cfg.icp_angle_thr_deg * 3.14159265358979323846 / 180.0);
   p.occ_thr = (float)s->cfg.occlusion_thr;
+  p.icp_dw = s->cfg.icp_depth_weight;
   return p;
 }
 
@@ -416,7 +418,7 @@ int plan_create(dri_stream_s* const* streams, int n, int ring, bool in_workspace
   for (int l = 0; l < kMaxLevels; ++l) p->iters[l] = l < p->levels ? streams[0]->cfg.iters[l] : 0;
   p->fp16 = (streams[0]->cfg.precision_flags & DRI_FP16_MAPS) != 0;
   p->fp32p = (streams[0]->cfg.precision_flags & DRI_FP32_PARTIALS) != 0;
-  p->occ = streams[0]->cfg.occlusion_thr > 0;
+  p->opt = pixel_options(streams[0]->cfg);
   plan_set_groups(p, groups);
   // a batch plan's table has room for any group count; a stream's own plan has
   // one group and exactly the workspace's table region
@@ -628,7 +630,7 @@ int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
           const BatchArgs at = plan_args(p, track_start(p, l, g), l, 0, p->gfirst[g], p->gcount[g]);
           const int nb = track_blocks(p, l, g);
           CK(launch(prof, DRI_KC_TRACK, plan_pixels(p, l) * px_scale,
-                    [&] { return launch_track_batch(at, nb, p->fp16, p->fp32p, p->occ, sg); }));
+                    [&] { return launch_track_batch(at, nb, p->fp16, p->fp32p, p->opt, sg); }));
           const BatchArgs as = plan_args(p, p->tv.copy_off, l, remaining == 0, p->gfirst[g], p->gcount[g]);
           CK(launch(prof, DRI_KC_SOLVE, 0.0, [&] { return launch_gn_step_batch(as, sg); }));
           k += 2;
@@ -676,7 +678,7 @@ int plan_autotune(Plan* p, int64_t* kernels) {
       auto all_groups = [&] {
         for (int g = 0; g < p->groups; ++g) {
           const BatchArgs at = plan_args(p, track_start(p, l, g), l, 0, p->gfirst[g], p->gcount[g]);
-          if (launch_track_batch(at, track_blocks(p, l, g), p->fp16, p->fp32p, p->occ, p->stream) !=
+          if (launch_track_batch(at, track_blocks(p, l, g), p->fp16, p->fp32p, p->opt, p->stream) !=
               cudaSuccess)
             return false;
         }
@@ -915,6 +917,7 @@ int dri_config_default(int32_t width, int32_t height, dri_stream_config* cfg) {
   cfg->track_mode = DRI_TRACK_INERTIAL;
   cfg->rgbd_lambda = 1.0;
   cfg->occlusion_thr = 0.0;
+  cfg->icp_depth_weight = 0;
   return DRI_OK;
 }
 
@@ -1167,7 +1170,7 @@ int batch_plan(const dri_stream* streams, int32_t n, Plan** out) {
     const dri_stream_s* s0 = streams[0];
     if (s->stream != s0->stream || s->cfg.levels != s0->cfg.levels ||
         s->cfg.precision_flags != s0->cfg.precision_flags ||
-        (s->cfg.occlusion_thr > 0) != (s0->cfg.occlusion_thr > 0))
+        pixel_options(s->cfg) != pixel_options(s0->cfg))
       return DRI_EINVAL;
     for (int l = 0; l < s->cfg.levels; ++l)
       if (s->cfg.iters[l] != s0->cfg.iters[l]) return DRI_EINVAL;

@@ -124,7 +124,7 @@ struct TrackParams {
   float depth_min, depth_max;
   float icp_dist2, icp_cos;
   float occ_thr;                      // > 0: photometric depth-consistency test (m)
-  float pad;
+  int32_t icp_dw;                     // 1: ICP weight 1 / d^4 (depth-dependent noise)
 };
 
 struct SolveParams {
@@ -244,7 +244,8 @@ cudaError_t launch_normals(const LevelMaps& m, const Ctrl* ctrl, const LevelGeom
 cudaError_t launch_gradient(const LevelMaps& m, const Ctrl* ctrl, int w, int h, bool fp16,
                             cudaStream_t s);
 cudaError_t launch_track(const TrackParams& p, bool fp16, bool fp32_partials, cudaStream_t s);
-cudaError_t launch_track_batch(const BatchArgs& a, int blocks, bool fp16, bool fp32_partials, bool occ,
+// opt: the pixel-kernel variant, bit 0 the occlusion test, bit 1 the depth-dependent ICP weight
+cudaError_t launch_track_batch(const BatchArgs& a, int blocks, bool fp16, bool fp32_partials, int opt,
                                cudaStream_t s);
 int track_grid_blocks(int w, int h, int ppt);   // batched kernel: single-term blocks
 int track_mixed_blocks(int w, int h, int ppt);  // by-value kernel: mixed-term blocks

@@ -83,7 +83,7 @@ struct Plan {
   int S = 0, levels = 0;
   int iters[kMaxLevels] = {};
   bool fp16 = false, fp32p = false;
-  bool occ = false;                 // the occlusion test is on (occlusion_thr > 0) for every slot
+  int opt = 0;                      // pixel-kernel options of every slot: 1 occlusion test, 2 depth weight
   bool owns_device = false;         // table / dyn / heads allocated by the plan
   int groups = 1;                   // slot groups of the Gauss-Newton loop, one CUDA stream each
   std::vector<int> gfirst, gcount;
@@ -110,6 +110,13 @@ struct Plan {
   std::vector<std::array<int, kMaxLevels>> ppt;   // rows per thread of each slot's pixel kernel
   int64_t kernels_per_frame = 0;
 };
+
+// Pixel-kernel variant a stream's configuration selects: bit 0 the photometric
+// occlusion test, bit 1 the depth-dependent ICP weight.  The streams of one
+// batch or server share it.
+inline int pixel_options(const dri_stream_config& c) {
+  return (c.occlusion_thr > 0 ? 1 : 0) | (c.icp_depth_weight ? 2 : 0);
+}
 
 namespace dri_host {
 

@@ -93,7 +93,7 @@ struct dri_server_s {
   bool have_tiles = false;                    // rows per thread chosen by the first plan
   int32_t tiles[DRI_MAX_LEVELS] = {};
   int32_t levels = 0, iters[DRI_MAX_LEVELS] = {}, flags = 0;
-  bool occ = false;                           // occlusion test on (every stream alike)
+  int opt = 0;                                // pixel-kernel options (every stream alike)
   std::unordered_map<uint64_t, Ticket> tickets;
   uint64_t next_ticket = 1;
   std::deque<Tick> inflight;
@@ -341,7 +341,7 @@ int dri_server_open_stream(dri_server S, const dri_stream_config* cfg, const dri
     if (S->stop) return DRI_EINVAL;
     if (!S->streams.empty()) {
       bool same = cfg->levels == S->levels && cfg->precision_flags == S->flags &&
-                  (cfg->occlusion_thr > 0) == S->occ;
+                  pixel_options(*cfg) == S->opt;
       for (int l = 0; l < cfg->levels && same; ++l) same = cfg->iters[l] == S->iters[l];
       if (!same) return DRI_EINVAL;
     }
@@ -358,7 +358,7 @@ int dri_server_open_stream(dri_server S, const dri_stream_config* cfg, const dri
   if (S->streams.empty()) {
     S->levels = cfg->levels;
     S->flags = cfg->precision_flags;
-    S->occ = cfg->occlusion_thr > 0;
+    S->opt = pixel_options(*cfg);
     for (int l = 0; l < DRI_MAX_LEVELS; ++l) S->iters[l] = l < cfg->levels ? cfg->iters[l] : 0;
   }
   S->streams.push_back(s);

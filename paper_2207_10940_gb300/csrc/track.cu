@@ -78,7 +78,7 @@ struct Live {
 };
 
 // ICP term (Eq. 4) of the pixel (u, v) with live depth d and normal n1.
-template <typename T>
+template <typename T, bool DW>
 __device__ __forceinline__ bool icp_pixel(const TrackParams& p, const LevelGeom& g, const float* A,
                                           const float* t, const void* __restrict__ A0,
                                           const float* __restrict__ D0, int u, int v, const Live& L,
@@ -115,6 +115,12 @@ __device__ __forceinline__ bool icp_pixel(const TrackParams& p, const LevelGeom&
   const float e = Nx * dx + Ny * dy + Nz * dz;
   const float sx = px + (ex - t[0]), sy = py + (ey - t[1]), sz = pz + (ez - t[2]);
   const float J[6] = {Nx, Ny, Nz, sy * Nz - sz * Ny, sz * Nx - sx * Nz, sx * Ny - sy * Nx};
+  if (DW) {                      // weight 1 / d^4 (sigma_d(d) = sigma_d d^2): J, e scaled by 1 / d^2
+    const float w = __fdividef(1.f, d * d);
+    const float Jw[6] = {J[0] * w, J[1] * w, J[2] * w, J[3] * w, J[4] * w, J[5] * w};
+    accumulate(acc, Jw, e * w);
+    return true;
+  }
   accumulate(acc, J, e);
   return true;
 }
@@ -170,7 +176,11 @@ __device__ __forceinline__ bool rgb_pixel(const LevelGeom& g, const float* A, co
 // One tile of one image (single-term: 32 x 8 * ppt pixels of `term`; mixed:
 // 32 x 4 * ppt pixels, both terms): (bx, by) its tile
 // coordinates, bid its index in the image's fold order.
-template <typename T, typename P, bool FLAGS, bool SPLIT, bool OCC>
+// Optional terms, compile-time variants of the pixel kernels (OPT bits): the
+// photometric occlusion test and the depth-dependent ICP weight.
+constexpr int kOptOcc = 1, kOptDepthWeight = 2;
+
+template <typename T, typename P, bool FLAGS, bool SPLIT, int OPT>
 __device__ __forceinline__ void track_tile(const TrackParams& p, const int term, const int bx,
                                            const int by, const int bid) {
   Ctrl* __restrict__ ctrl = p.ctrl;
@@ -243,8 +253,8 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int term,
     }
     bool ok = false;
     if (col_ok && v < g.h && cur.d >= dmin && cur.d <= dmax) {
-      ok = icp ? icp_pixel<T>(p, g, A, t, A0, D0, u, v, cur, acc)
-               : rgb_pixel<T, OCC>(g, A, t, B0, D0, p.occ_thr, u, v, cur, acc);
+      ok = icp ? icp_pixel<T, (OPT & kOptDepthWeight) != 0>(p, g, A, t, A0, D0, u, v, cur, acc)
+               : rgb_pixel<T, (OPT & kOptOcc) != 0>(g, A, t, B0, D0, p.occ_thr, u, v, cur, acc);
     }
     if (FLAGS) {             // bit 0 ICP, bit 1 photometric, combined through shared memory
       if (icp) s_flag[wrow][lane] = ok ? 1 : 0;
@@ -329,17 +339,17 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int term,
   if (tid == 0) p.counters[0] = 0u;
 }
 
-template <typename T, typename P, bool FLAGS, bool OCC>
+template <typename T, typename P, bool FLAGS, int OPT>
 __global__ void __launch_bounds__(kTrackThreadsX * kTrackThreadsY)
 k_track(TrackParams p) {
-  track_tile<T, P, FLAGS, false, OCC>(p, 0, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x);
+  track_tile<T, P, FLAGS, false, OPT>(p, 0, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // Tiles of every tracking slot at one level: block -> (slot, tile, term)
 // through the block prefix, tile -> (column, row band) in the slot's image.
 // Three blocks per SM (80 registers) measured faster than four (64 registers,
 // more spill reloads) and than two columns per thread.
-template <typename T, typename P, bool OCC>
+template <typename T, typename P, int OPT>
 __global__ void __launch_bounds__(kTrackThreadsX * kTrackThreadsY, 3)
 k_track_batch(const BatchArgs a) {
   const int i = batch_slot(a, blockIdx.x);
@@ -355,7 +365,7 @@ k_track_batch(const BatchArgs a) {
   const int t = blockIdx.x - __ldg(a.start + i);
   const int gx = (p.g.w + kTrackThreadsX - 1) / kTrackThreadsX;
   const int tile = t >> 1;                    // the two terms of a tile are neighbours
-  track_tile<T, P, false, true, OCC>(p, t & 1, tile % gx, tile / gx, t);
+  track_tile<T, P, false, true, OPT>(p, t & 1, tile % gx, tile / gx, t);
 }
 
 }  // namespace
@@ -389,16 +399,18 @@ cudaError_t launch_track(const TrackParams& p0, bool fp16, bool fp32_partials, c
   const int rows = kTrackRows * p.ppt;
   const dim3 grid((p.g.w + kTrackThreadsX - 1) / kTrackThreadsX, (p.g.h + rows - 1) / rows);
   const bool flags = p.flags != nullptr;
-  const bool occ = p.occ_thr > 0.f;
+  const int opt = (p.occ_thr > 0.f ? kOptOcc : 0) | (p.icp_dw ? kOptDepthWeight : 0);
+#define DRI_TRACK_OPT(T, P, O)                                              \
+  do {                                                                      \
+    if (flags) k_track<T, P, true, O><<<grid, block, 0, s>>>(p);            \
+    else k_track<T, P, false, O><<<grid, block, 0, s>>>(p);                 \
+  } while (0)
 #define DRI_TRACK_LAUNCH(T, P)                                              \
   do {                                                                      \
-    if (occ) {                                                              \
-      if (flags) k_track<T, P, true, true><<<grid, block, 0, s>>>(p);       \
-      else k_track<T, P, false, true><<<grid, block, 0, s>>>(p);            \
-    } else {                                                                \
-      if (flags) k_track<T, P, true, false><<<grid, block, 0, s>>>(p);      \
-      else k_track<T, P, false, false><<<grid, block, 0, s>>>(p);           \
-    }                                                                       \
+    if (opt == 0) DRI_TRACK_OPT(T, P, 0);                                   \
+    else if (opt == 1) DRI_TRACK_OPT(T, P, 1);                              \
+    else if (opt == 2) DRI_TRACK_OPT(T, P, 2);                              \
+    else DRI_TRACK_OPT(T, P, 3);                                            \
   } while (0)
   if (fp16) {
     if (fp32_partials) DRI_TRACK_LAUNCH(__half, float);
@@ -408,16 +420,19 @@ cudaError_t launch_track(const TrackParams& p0, bool fp16, bool fp32_partials, c
     else DRI_TRACK_LAUNCH(float, double);
   }
 #undef DRI_TRACK_LAUNCH
+#undef DRI_TRACK_OPT
   return cudaGetLastError();
 }
 
 cudaError_t launch_track_batch(const BatchArgs& a, int blocks, bool fp16, bool fp32_partials,
-                               bool occ, cudaStream_t s) {
+                               int opt, cudaStream_t s) {
   const dim3 block(kTrackThreadsX, kTrackThreadsY);
 #define DRI_TRACK_BATCH(T, P)                                               \
   do {                                                                      \
-    if (occ) k_track_batch<T, P, true><<<blocks, block, 0, s>>>(a);         \
-    else k_track_batch<T, P, false><<<blocks, block, 0, s>>>(a);            \
+    if (opt == 0) k_track_batch<T, P, 0><<<blocks, block, 0, s>>>(a);       \
+    else if (opt == 1) k_track_batch<T, P, 1><<<blocks, block, 0, s>>>(a);  \
+    else if (opt == 2) k_track_batch<T, P, 2><<<blocks, block, 0, s>>>(a);  \
+    else k_track_batch<T, P, 3><<<blocks, block, 0, s>>>(a);                \
   } while (0)
   if (fp16) {
     if (fp32_partials) DRI_TRACK_BATCH(__half, float);

@@ -57,6 +57,7 @@ class dri_stream_config(ctypes.Structure):
         ("bias_relin_g", ctypes.c_double), ("bias_relin_a", ctypes.c_double),
         ("track_mode", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("rgbd_lambda", ctypes.c_double), ("occlusion_thr", ctypes.c_double),
+        ("icp_depth_weight", ctypes.c_int32), ("reserved2", ctypes.c_int32),
     ]
 
 

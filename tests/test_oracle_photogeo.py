@@ -187,7 +187,7 @@ def _bf_pixel_lookup(img, x, y):
             + (1 - ax) * ay * img[y0 + 1][x0] + ax * ay * img[y0 + 1][x0 + 1])
 
 
-def _bf_linearise(D1, I1, D0, I0, K, cfg, Rref, rref, R0, r0, R1, r1, occ_thr=0.0):
+def _bf_linearise(D1, I1, D0, I0, K, cfg, Rref, rref, R0, r0, R1, r1, occ_thr=0.0, dw=0):
     h, w = D1.shape
     fx, fy, cx, cy = K
     # reference gradient, border zero
@@ -227,8 +227,9 @@ def _bf_linearise(D1, I1, D0, I0, K, cfg, Rref, rref, R0, r0, R1, r1, occ_thr=0.
                             if np.linalg.norm(pw - V) < cfg.icp_dist_thr and (R1 @ n1) @ N > cos_thr:
                                 e = N @ (pw - V)
                                 J = np.r_[N, np.cross(s1, N)]
-                                Hi += np.outer(J, J)
-                                bi -= J * e
+                                wz = 1.0 / D1[v, u] ** 4 if dw else 1.0
+                                Hi += wz * np.outer(J, J)
+                                bi -= wz * J * e
                                 ni += 1
             # photometric
             q0 = R0.T @ (pw - r0)
@@ -255,11 +256,12 @@ def _bf_linearise(D1, I1, D0, I0, K, cfg, Rref, rref, R0, r0, R1, r1, occ_thr=0.
     return Wi * Hi, Wi * bi, ni, Wr * Hr, Wr * br, nr
 
 
-@pytest.mark.parametrize("seed,occ", [(11, 0.0), (12, 0.0), (13, 0.0), (11, 0.004), (12, 0.004)])
-def test_brute_force_8x8(seed, occ):
+@pytest.mark.parametrize("seed,occ,dw", [(11, 0.0, 0), (12, 0.0, 0), (13, 0.0, 0), (11, 0.004, 0),
+                                         (12, 0.004, 0), (13, 0.0, 1)])
+def test_brute_force_8x8(seed, occ, dw):
     cam = synth.Camera(8, 8, 8.0, 8.0, 4.0, 4.0)
     seq = synth.frame_pair(seed=seed, cam=cam, rot_deg=3.0, trans_m=0.05)
-    cfg = oracle_config(seq, levels=1, iters=(1,), occlusion_thr=occ)
+    cfg = oracle_config(seq, levels=1, iters=(1,), occlusion_thr=occ, icp_depth_weight=dw)
     rng = np.random.default_rng(seed)
     x0, x1, L1, ref = _setup(seq, cfg)
     xr = x0
@@ -271,7 +273,7 @@ def test_brute_force_8x8(seed, occ):
     D0 = seq.depth[0].astype(np.float64)
     Hi, bi, ni, Hr, br, nr = _bf_linearise(D1, seq.intensity[1].astype(np.float64), D0,
                                            seq.intensity[0].astype(np.float64), K, cfg,
-                                           xr.R, xr.r, x0.R, x0.r, x1.R, x1.r, occ)
+                                           xr.R, xr.r, x0.R, x0.r, x1.R, x1.r, occ, dw)
     assert ni == lin["n_icp"] and nr == lin["n_rgb"]
     assert nr > 20 if occ == 0 else nr > 0
     if occ > 0:                        # the test rejects something on these scenes
