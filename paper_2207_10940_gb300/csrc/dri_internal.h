@@ -244,6 +244,17 @@ cudaError_t launch_normals(const LevelMaps& m, const Ctrl* ctrl, const LevelGeom
 cudaError_t launch_gradient(const LevelMaps& m, const Ctrl* ctrl, int w, int h, bool fp16,
                             cudaStream_t s);
 cudaError_t launch_track(const TrackParams& p, bool fp16, bool fp32_partials, cudaStream_t s);
+
+#ifdef __CUDACC__
+// Programmatic dependent launch between the batched pixel kernel and the
+// Gauss-Newton step (each launched with programmatic stream serialization):
+// grid_dep_wait blocks until the preceding kernel has completed and its writes
+// are visible (immediately when there is no programmatic dependency);
+// grid_dep_launch lets the next kernel's blocks start once every block of this
+// one has reached it.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+#endif
 // opt: the pixel-kernel variant, bit 0 the occlusion test, bit 1 the depth-dependent ICP weight
 cudaError_t launch_track_batch(const BatchArgs& a, int blocks, bool fp16, bool fp32_partials, int opt,
                                cudaStream_t s);

@@ -1002,10 +1002,7 @@ __device__ void assemble(const SolveParams& sp, GnSmem& S) {
     S.x0 = c->x0;
     S.x1 = c->x1;
   }
-  // pixel systems into W (term 0 ICP with R_ref, term 1 photometric with R_0)
-  if (tid >= 32 && tid < 32 + 2 * 36) {
-    pixel_system_entry(sp, c, S, tid - 32);
-  } else if ((tid >> 5) == 4) {
+  if ((tid >> 5) == 4) {
     warp_state_boxminus(c->x0, c->xbar, S.dprior);
   } else if (tid == 160) {
     for (int i = 0; i < 36; ++i) S.M6[i] = (i % 7 == 0) ? 1.0 : 0.0;
@@ -1034,13 +1031,18 @@ __device__ void assemble(const SolveParams& sp, GnSmem& S) {
     for (int m = 0; m < 9; ++m) acc += c->Wimu[r * 18 + m] * S.L.e[m];
     S.We[r] = acc;
   }
+  // everything above depends on the states only; the pixel sums come from the
+  // preceding pixel kernel.  Pixel systems into W (term 0 ICP with R_ref, term 1
+  // photometric with R_0).
+  grid_dep_wait();
+  if (tid >= 32 && tid < 32 + 2 * 36) pixel_system_entry(sp, c, S, tid - 32);
+  __syncthreads();
   if (tid < 36) {                       // MH6 = M H6 (photometric term)
     const int i = tid / 6, j = tid % 6;
     double acc = 0.0;
     for (int k = 0; k < 6; ++k) acc += S.M6[i * 6 + k] * S.Hl[1][k * 6 + j];
     S.MH6[tid] = acc;
   }
-  __syncthreads();
   // H upper from J_a^T W_9 J_a, b from -J_a^T W_9 e_a
   for (int idx = tid; idx < 34 * 34; idx += nt) {
     const int i = idx / 34, j = idx % 34;
@@ -1177,6 +1179,7 @@ __device__ void gn_step_pose_only(const SolveParams& sp, GnSmem& S) {
     S.x0 = c->x0;
     S.x1 = c->x1;
   }
+  grid_dep_wait();                      // the pixel sums
   if (tid >= 32 && tid < 32 + 2 * 36) pixel_system_entry(sp, c, S, tid - 32);
   __syncthreads();
   const double lam = sp.rgbd_lambda;
@@ -1609,7 +1612,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_frame_begin_batch(const Batch
 __global__ void __launch_bounds__(kSolveThreads) k_gn_step_batch(const BatchArgs a) {
   __shared__ SolveParams sp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  grid_dep_launch();                    // the next pixel kernel waits for this step itself
   if (load_slot_params(a, sp) == kSlotTrack) gn_step_body(sp, *reinterpret_cast<GnSmem*>(smem_raw));
+  else grid_dep_wait();                 // idle slot: nothing to read, keep the ordering
 }
 
 __global__ void __launch_bounds__(kSolveThreads) k_frame_end_batch(const BatchArgs a) {
@@ -1649,8 +1654,17 @@ cudaError_t launch_frame_begin_batch(const BatchArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_gn_step_batch(const BatchArgs& a, cudaStream_t s) {
-  k_gn_step_batch<<<a.nslots, kSolveThreads, sizeof(GnSmem), s>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.nslots);
+  cfg.blockDim = dim3(kSolveThreads);
+  cfg.dynamicSmemBytes = sizeof(GnSmem);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_gn_step_batch, a);
 }
 cudaError_t launch_frame_end_batch(const BatchArgs& a, cudaStream_t s) {
   k_frame_end_batch<<<a.nslots, kSolveThreads, 0, s>>>(a);

@@ -362,6 +362,8 @@ k_track_batch(const BatchArgs a) {
     reinterpret_cast<uint32_t*>(&p)[tid] =
         __ldg(reinterpret_cast<const uint32_t*>(&a.slots[slot].tp[a.level]) + tid);
   __syncthreads();
+  grid_dep_wait();               // the transforms of the preceding Gauss-Newton step
+  grid_dep_launch();             // the next step's state-only work may start now
   const int t = blockIdx.x - __ldg(a.start + i);
   const int gx = (p.g.w + kTrackThreadsX - 1) / kTrackThreadsX;
   const int tile = t >> 1;                    // the two terms of a tile are neighbours
@@ -426,23 +428,29 @@ cudaError_t launch_track(const TrackParams& p0, bool fp16, bool fp32_partials, c
 
 cudaError_t launch_track_batch(const BatchArgs& a, int blocks, bool fp16, bool fp32_partials,
                                int opt, cudaStream_t s) {
-  const dim3 block(kTrackThreadsX, kTrackThreadsY);
-#define DRI_TRACK_BATCH(T, P)                                               \
-  do {                                                                      \
-    if (opt == 0) k_track_batch<T, P, 0><<<blocks, block, 0, s>>>(a);       \
-    else if (opt == 1) k_track_batch<T, P, 1><<<blocks, block, 0, s>>>(a);  \
-    else if (opt == 2) k_track_batch<T, P, 2><<<blocks, block, 0, s>>>(a);  \
-    else k_track_batch<T, P, 3><<<blocks, block, 0, s>>>(a);                \
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kTrackThreadsX, kTrackThreadsY);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+#define DRI_TRACK_BATCH(T, P)                                                            \
+  do {                                                                                   \
+    if (opt == 0) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 0>, a);            \
+    if (opt == 1) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 1>, a);            \
+    if (opt == 2) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 2>, a);            \
+    return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 3>, a);                          \
   } while (0)
   if (fp16) {
     if (fp32_partials) DRI_TRACK_BATCH(__half, float);
-    else DRI_TRACK_BATCH(__half, double);
-  } else {
-    if (fp32_partials) DRI_TRACK_BATCH(float, float);
-    else DRI_TRACK_BATCH(float, double);
+    DRI_TRACK_BATCH(__half, double);
   }
+  if (fp32_partials) DRI_TRACK_BATCH(float, float);
+  DRI_TRACK_BATCH(float, double);
 #undef DRI_TRACK_BATCH
-  return cudaGetLastError();
 }
 
 }  // namespace dri
