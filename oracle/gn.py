@@ -26,6 +26,12 @@ RGB-D-only baseline (track_mode 1, params.py): Gauss-Newton on x_1's pose
 alone with H_icp + lambda H_rgb, x_0 fixed, no IMU term, prior or
 marginalisation (`track_pose_only`).
 
+Gyro-only variant (track_mode 2, params.py): the joint system with the IMU
+term's accelerometer-related rows at zero weight (`imu.weight_gyro_only`) and
+the velocity, accelerometer bias and gravity of both states held (`hold`);
+x_1 starts at x_0's position with the gyro's rotation prediction; the prior
+keeps no information on the held components.
+
 Frame loop (reading; the paper does not state the initialisation): x_0 := the
 previous x_1, x_1 := the IMU prediction x^_1(x_0); W_IMU computed there.  The
 first frame only initialises: x_1 := x_init (identity pose, W = first camera
@@ -44,6 +50,7 @@ from .so3 import State, boxminus, boxplus
 
 POSE0 = slice(0, 6)
 POSE1 = slice(17, 23)
+HELD_GYRO_ONLY = np.r_[6:9, 12:17]      # v, b_a, gravity of one state (track_mode 2)
 
 
 def first_prior(cfg):
@@ -79,6 +86,17 @@ def assemble(lin, J_imu, e_imu, W_imu, x0, xbar, Hs, bs):
     H[0:17, 0:17] += Hp
     b[0:17] += bp
     return H, b
+
+
+def hold(H, b, dims):
+    """Removes the tangent components `dims` from the system H dx = b (in
+    place): their rows and columns become the identity's and their right-hand
+    side zero, so their step is exactly zero and the other components solve
+    the system without them."""
+    H[dims, :] = 0.0
+    H[:, dims] = 0.0
+    H[dims, dims] = 1.0
+    b[dims] = 0.0
 
 
 def cholesky_solve(H, b):
@@ -125,6 +143,17 @@ class Tracker:
             return pre
         return imu_mod.correct(pre, dbg, dba)
 
+    def first_iterate(self, x0, pre):
+        """x_1's starting point: the IMU prediction x^_1(x_0) with x_0's biases
+        and gravity; in the gyro-only variant x_0's position and velocity with
+        the predicted rotation R_WC0 R_CS dR R_CS^T."""
+        from .so3 import rot_to_quat
+        pr = imu_mod.predict(x0, pre, self.cfg)
+        q = rot_to_quat(pr["R"])
+        if self.cfg.track_mode == 2:
+            return State(x0.r.copy(), q, x0.v.copy(), x0.bg.copy(), x0.ba.copy(), x0.qg.copy())
+        return State(pr["r"], q, pr["v"], x0.bg.copy(), x0.ba.copy(), x0.qg.copy())
+
     def set_reference(self, ref, R_ref, r_ref):
         """Replaces the reference with uploaded levels (maps.reference_from_upload)."""
         self.ref = ref
@@ -141,6 +170,8 @@ class Tracker:
         e, pr = imu_mod.residual(x0, x1, pre, cfg)
         J = imu_mod.jacobian(x0, x1, pre, cfg, e, pr)
         H, b = assemble(lin, J, e, W_imu, x0, self.xbar, self.Hs, self.bs)
+        if cfg.track_mode == 2:
+            hold(H, b, np.r_[HELD_GYRO_ONLY, 17 + HELD_GYRO_ONLY])
         parts = dict(lin=lin, e_imu=e, J_imu=J, cost_imu=float(e @ W_imu @ e))
         return H, b, parts
 
@@ -157,13 +188,12 @@ class Tracker:
             return self.track_pose_only(levels, t)
         t0, t1 = self.t, t
         x0 = self.x.copy()
-        W_imu, _ = imu_mod.weight(x0, self.imu, t0, t1, cfg)
+        W_imu, S_imu = imu_mod.weight(x0, self.imu, t0, t1, cfg)
         pre = imu_mod.preintegrate(self.imu, t0, t1, x0.bg, x0.ba)
         self.lin = (pre, x0.bg.copy(), x0.ba.copy())
-        pr = imu_mod.predict(x0, pre, cfg)
-        from .so3 import rot_to_quat
-        x1 = State(pr["r"], rot_to_quat(pr["R"]), pr["v"], x0.bg.copy(), x0.ba.copy(),
-                   x0.qg.copy())
+        if cfg.track_mode == 2:
+            W_imu = imu_mod.weight_gyro_only(S_imu)
+        x1 = self.first_iterate(x0, pre)
         counts = {}
         H = b = d = None
         for l in range(cfg.levels - 1, -1, -1):
@@ -181,6 +211,10 @@ class Tracker:
         if counts[0][0] + counts[0][1] < cfg.min_valid:
             raise TrackingLost("too few correspondences")
         Hs, bs = schur(H, b - H @ d)
+        if cfg.track_mode == 2:                # no information on the held components
+            Hs[HELD_GYRO_ONLY, :] = 0.0
+            Hs[:, HELD_GYRO_ONLY] = 0.0
+            bs[HELD_GYRO_ONLY] = 0.0
         self.Hs, self.bs = Hs, bs
         self.xbar = x1.copy()
         self.x = x1.copy()

@@ -209,3 +209,16 @@ def weight(x0, samples, t0, t1, cfg):
     S[12:15, 12:15] = np.eye(3) * cfg.acc_rw ** 2 * T
     S[15:18, 15:18] = np.eye(3) * cfg.sigma_grav_rw ** 2
     return np.linalg.inv(S), S
+
+
+GYRO_ROWS = np.r_[3:6, 9:12]      # rotation and gyro-bias rows of e_IMU
+
+
+def weight_gyro_only(S):
+    """Weight of the gyro-only IMU term (track_mode 2, params.py) from the full
+    covariance S of `weight`: the rotation and gyro-bias rows get the inverse
+    of their own block of S (their marginal covariance), every
+    accelerometer-related row zero weight."""
+    W = np.zeros((18, 18))
+    W[np.ix_(GYRO_ROWS, GYRO_ROWS)] = np.linalg.inv(S[np.ix_(GYRO_ROWS, GYRO_ROWS)])
+    return W

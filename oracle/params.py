@@ -35,6 +35,17 @@ or schedule):
   and the photometric term still warps with it; x_1 starts at x_0; the system
   is H_icp + lambda H_rgb on x_1's pose (the per-pixel weights W_ICP, W_RGB
   kept, lambda = 1 by default); no IMU term, prior or marginalisation.
+* Gyro-only variant (track_mode 2; Sec. VII, Fig. 5 and Table VI, where the
+  accelerometer-related residuals are ignored): the IMU term keeps its rotation
+  rows and the gyro-bias random walk, weighted by the inverse of their own
+  covariance (the (rotation, b_g) block of Sigma, so that the dropped rows'
+  correlations do not leak in); the position, velocity, accelerometer-bias and
+  gravity rows are dropped.  Nothing then measures the velocity, the
+  accelerometer bias or the gravity direction, so they are held at their
+  values (removed from both states' tangent spaces: identity rows in the
+  system, no prior on them).  x_1 starts at x_0's position with the gyro's
+  rotation prediction R_WC0 R_CS dR R_CS^T; the prior and the marginalisation
+  act on the remaining 9 components of each state (pose and b_g).
 * Occlusion test (occlusion_thr > 0; off by default, the paper gives none):
   a photometric residual is used only where the warped point's depth in x_0's
   camera agrees within occlusion_thr with the reference depth at the nearest
@@ -91,7 +102,7 @@ class TrackerConfig:
     imu_mode: int = 0                   # 0 re-integrate per iteration, 1 first-order bias update
     bias_relin_g: float = 0.01          # |db_g| (rad/s) above which mode 1 re-integrates
     bias_relin_a: float = 0.1           # |db_a| (m/s^2) above which mode 1 re-integrates
-    track_mode: int = 0                 # 0 RGB-D-inertial (joint), 1 RGB-D-only pose
+    track_mode: int = 0                 # 0 RGB-D-inertial (joint), 1 RGB-D-only pose, 2 gyro only
     rgbd_lambda: float = 1.0            # track_mode 1: weight of the photometric term
     occlusion_thr: float = 0.0          # > 0: photometric depth-consistency test (m)
     icp_depth_weight: int = 0           # 1: ICP weight W_ICP / z^4 (sigma_d at 1 m)
