@@ -196,7 +196,8 @@ ODOMETRY_OCCLUSION_THR = 0.03    # m, the occlusion test's threshold in the odom
 
 def rgbd_only_report(seq, states):
     """Trajectory errors against ground truth over the same frames as the
-    odometry pass (for the RGB-D-only baseline and the occlusion variant)."""
+    odometry pass (for the RGB-D-only baseline, the gyro-only setup and the
+    occlusion variant)."""
     from paper_2207_10940_gb300 import odometry
     gt = [seq.gt[k % N_UNIQUE] for k in range(len(states))]
     ev = odometry.evaluate(states, gt)
@@ -766,7 +767,7 @@ def run_ours(args):
         run.close()
         del run
         torch.cuda.synchronize(dev)
-    odo_states = odo_rgbd = odo_occ = None
+    odo_states = odo_rgbd = odo_occ = odo_gyro = None
     n_odo = min(args.odometry_frames, n_frames - 2)
     if n_odo > 1 and rank == 0:
         odo_states = odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_odo, args.precision_flags,
@@ -774,6 +775,9 @@ def run_ours(args):
         # the vision-only, pose-only baseline the paper compares with (same frames)
         odo_rgbd = odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_odo, args.precision_flags,
                                  args.imu_mode, track_mode=1, occlusion_thr=args.occlusion_thr)
+        # the gyroscope-only setup (accelerometer residuals ignored), between the two
+        odo_gyro = odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_odo, args.precision_flags,
+                                 args.imu_mode, track_mode=2, occlusion_thr=args.occlusion_thr)
         # the joint tracker with the occlusion test (when the timed passes run without it)
         if args.occlusion_thr <= 0:
             odo_occ = odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_odo, args.precision_flags,
@@ -814,6 +818,7 @@ def run_ours(args):
         "served": served,
         "odometry": None if odo_states is None else odometry_report(seq, odo_states, o_states),
         "odometry_rgbd_only": None if odo_rgbd is None else rgbd_only_report(seq, odo_rgbd),
+        "odometry_gyro_only": None if odo_gyro is None else rgbd_only_report(seq, odo_gyro),
         "odometry_occlusion": None if odo_occ is None else dict(
             rgbd_only_report(seq, odo_occ), occlusion_thr_m=ODOMETRY_OCCLUSION_THR),
         "precision": precision,

@@ -73,6 +73,16 @@ extern "C" {
  * biases and gravity are carried over unchanged. */
 #define DRI_TRACK_INERTIAL  0
 #define DRI_TRACK_RGBD_ONLY 1
+/* DRI_TRACK_GYRO_ONLY: the paper's gyroscope-only setup (Sec. VII, Fig. 5 and
+ * Table VI: the accelerometer-related residuals ignored).  The joint tracker
+ * of Eq. 6-9 with the IMU term reduced to its rotation rows and the gyro-bias
+ * random walk, weighted by the inverse of their own covariance block; the
+ * velocity, accelerometer bias and gravity direction of both states are held
+ * (not estimated: they keep x_init's values, and the marginalisation prior
+ * carries no information on them).  x1 starts at x0's position with the
+ * gyro's rotation prediction.  IMU samples are needed as for the inertial
+ * mode; their accelerometer readings do not affect the result. */
+#define DRI_TRACK_GYRO_ONLY 2
 
 /* Depth-dependent ICP weight (dri_stream_config.icp_depth_weight = 1; the
  * paper weighs each term by its noise covariance, Sec. III, and a structured-
@@ -117,7 +127,7 @@ typedef struct {
     int32_t imu_mode;              /* DRI_IMU_REINTEGRATE (default) | _FIRST_ORDER    */
     double bias_relin_g;           /* first order: re-integrate past |db_g|, rad/s    */
     double bias_relin_a;           /* first order: re-integrate past |db_a|, m/s^2    */
-    int32_t track_mode;            /* DRI_TRACK_INERTIAL (default) | _RGBD_ONLY       */
+    int32_t track_mode;            /* DRI_TRACK_INERTIAL (default) | _RGBD_ONLY | _GYRO_ONLY */
     int32_t reserved;
     double rgbd_lambda;            /* RGB-D-only: photometric weight (default 1)      */
     double occlusion_thr;          /* > 0: photometric depth-consistency test, m; 0 off */

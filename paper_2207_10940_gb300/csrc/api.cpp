@@ -51,7 +51,9 @@ int valid_config(const dri_stream_config* c) {
   if (!(c->bias_relin_g >= 0) || !(c->bias_relin_a >= 0) || !std::isfinite(c->bias_relin_g) ||
       !std::isfinite(c->bias_relin_a))
     return DRI_EINVAL;
-  if (c->track_mode != DRI_TRACK_INERTIAL && c->track_mode != DRI_TRACK_RGBD_ONLY) return DRI_EINVAL;
+  if (c->track_mode != DRI_TRACK_INERTIAL && c->track_mode != DRI_TRACK_RGBD_ONLY &&
+      c->track_mode != DRI_TRACK_GYRO_ONLY)
+    return DRI_EINVAL;
   if (!(c->rgbd_lambda >= 0) || !std::isfinite(c->rgbd_lambda)) return DRI_EINVAL;
   if (!(c->occlusion_thr >= 0) || !std::isfinite(c->occlusion_thr)) return DRI_EINVAL;
   if (c->icp_depth_weight != 0 && c->icp_depth_weight != 1) return DRI_EINVAL;

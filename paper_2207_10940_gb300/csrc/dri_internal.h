@@ -142,7 +142,7 @@ struct SolveParams {
   int32_t imu_mode;                   // DRI_IMU_REINTEGRATE or DRI_IMU_FIRST_ORDER
   int32_t pad;
   double relin_g, relin_a;            // first order: re-integration thresholds
-  int32_t track_mode;                 // DRI_TRACK_INERTIAL or DRI_TRACK_RGBD_ONLY
+  int32_t track_mode;                 // DRI_TRACK_INERTIAL, _RGBD_ONLY or _GYRO_ONLY
   int32_t pad2;
   double rgbd_lambda;                 // RGB-D-only: photometric weight
 };

@@ -962,6 +962,15 @@ struct GnSmem {
   int ok, fail, pd;
 };
 
+// Gyro-only variant (DRI_TRACK_GYRO_ONLY): tangent component k (0..33) of the
+// joint state is held -- velocity (6..8), accelerometer bias (12..14) and
+// gravity (15, 16) of either state, which nothing measures without the
+// accelerometer rows.
+__device__ __forceinline__ bool held_gyro_only(int k) {
+  const int m = k < 17 ? k : k - 17;
+  return (m >= 6 && m < 9) || m >= 12;
+}
+
 // Assemble the joint system at (ctrl->x0, ctrl->x1) into S.H (full), S.b.
 // Entry e (0..71) of the two pixel systems rotated into W: term e / 36 (0 ICP
 // with R_ref, 1 photometric with R_0), element e % 36 of its 6x6 (and, for
@@ -1167,6 +1176,23 @@ __device__ void assemble(const SolveParams& sp, GnSmem& S) {
     if (j < i) S.H[idx] = S.H[j * 34 + i];
   }
   __syncthreads();
+  if (sp.track_mode == DRI_TRACK_GYRO_ONLY) {
+    // held components: identity rows and columns, zero right-hand side (their
+    // step is zero; the reduced system is the leading 26 x 26 block of H)
+    for (int idx = tid; idx < 34 * 34; idx += nt) {
+      const int i = idx / 34, j = idx % 34;
+      if (held_gyro_only(i) || held_gyro_only(j)) {
+        const double v = i == j ? 1.0 : 0.0;
+        S.H[idx] = v;
+        if (i < 26 && j < 26) S.Hr[i * 26 + j] = v;
+      }
+    }
+    if (tid < 34 && held_gyro_only(tid)) {
+      S.b[tid] = 0.0;
+      if (tid < 26) S.br[tid] = 0.0;
+    }
+    __syncthreads();
+  }
 }
 
 // RGB-D-only baseline (DRI_TRACK_RGBD_ONLY): one Gauss-Newton step on x1's pose
@@ -1258,6 +1284,10 @@ __device__ void gn_step_body(const SolveParams& sp, GnSmem& S) {
     S.x[33] = -(m00 * q1 - m01 * q0) * idet;
   }
   __syncthreads();
+  if (sp.track_mode == DRI_TRACK_GYRO_ONLY) {   // exactly zero, whatever e_g's rounding
+    if (tid < 34 && held_gyro_only(tid)) S.x[tid] = 0.0;
+    __syncthreads();
+  }
   bool good = S.pd;
   for (int i = 0; i < 34; ++i) good = good && isfinite(S.x[i]);
   if (!good) {
@@ -1354,8 +1384,16 @@ __device__ bool imu_weight_and_prediction(const SolveParams& sp, Ctrl* c, BeginS
     B.Sg[tid] = acc;
   }
   __syncthreads();
+  // gyro only: the rotation rows (3..5) keep the inverse of their own block
+  // of the covariance; the position and velocity rows are dropped (identity
+  // here, zero weight below)
+  const bool gyro = sp.track_mode == DRI_TRACK_GYRO_ONLY;
   double sym = 0.0;
-  if (tid < 81) sym = 0.5 * (B.Sg[tid] + B.Sg[(tid % 9) * 9 + tid / 9]);
+  if (tid < 81) {
+    const int r = tid / 9, q = tid % 9;
+    const bool rot = r >= 3 && r < 6 && q >= 3 && q < 6;
+    sym = gyro && !rot ? (r == q ? 1.0 : 0.0) : 0.5 * (B.Sg[tid] + B.Sg[q * 9 + r]);
+  }
   __syncthreads();
   if (tid < 81) B.Sg[tid] = sym;
   __syncthreads();
@@ -1371,9 +1409,10 @@ __device__ bool imu_weight_and_prediction(const SolveParams& sp, Ctrl* c, BeginS
     const int r = idx / 18, q = idx % 18;
     double w = 0.0;
     if (r < 9 && q < 9) {
-      w = 0.5 * (B.Winv[r * 9 + q] + B.Winv[q * 9 + r]);
+      if (!gyro || (r >= 3 && r < 6 && q >= 3 && q < 6)) w = 0.5 * (B.Winv[r * 9 + q] + B.Winv[q * 9 + r]);
     } else if (r == q) {
       if (r < 12) w = 1.0 / (sp.gyr_rw * sp.gyr_rw * B.P.T);
+      else if (gyro) w = 0.0;                  // accelerometer bias and gravity rows
       else if (r < 15) w = 1.0 / (sp.acc_rw * sp.acc_rw * B.P.T);
       else w = 1.0 / (sp.sigma_grav * sp.sigma_grav);
     }
@@ -1382,9 +1421,10 @@ __device__ bool imu_weight_and_prediction(const SolveParams& sp, Ctrl* c, BeginS
   if (tid == 0) {
     if (!pd) c->status = DRI_ELOST;
     if (x1_pred) {
-      // x1 := x^1(x0): biases and q_IW carried over
+      // x1 := x^1(x0): biases and q_IW carried over; gyro only: the predicted
+      // rotation at x0's position and velocity
       DState x1 = x0;
-      for (int i = 0; i < 3; ++i) {
+      for (int i = 0; i < 3 && !gyro; ++i) {
         x1.r[i] = B.L.r[i];
         x1.v[i] = B.L.v[i];
       }
@@ -1488,11 +1528,12 @@ __device__ void frame_end_body(const SolveParams& sp) {
     }
     return;
   }
+  const bool gyro = sp.track_mode == DRI_TRACK_GYRO_ONLY;   // no information on held parts
   for (int idx = tid; idx < 17 * 17; idx += blockDim.x) {
     const int i = idx / 17, j = idx % 17;
-    c->Hs[idx] = 0.5 * (Hs[i * 17 + j] + Hs[j * 17 + i]);
+    c->Hs[idx] = gyro && (held_gyro_only(i) || held_gyro_only(j)) ? 0.0 : 0.5 * (Hs[i * 17 + j] + Hs[j * 17 + i]);
   }
-  if (tid < 17) c->bs[tid] = bs[tid];
+  if (tid < 17) c->bs[tid] = gyro && held_gyro_only(tid) ? 0.0 : bs[tid];
   if (tid == 0) {
     c->x = c->x1;
     c->xbar = c->x1;

@@ -33,6 +33,7 @@ DRI_IMU_REINTEGRATE = 0
 DRI_IMU_FIRST_ORDER = 1
 DRI_TRACK_INERTIAL = 0
 DRI_TRACK_RGBD_ONLY = 1
+DRI_TRACK_GYRO_ONLY = 2
 DRI_MAX_LEVELS = 4
 
 c_double_p = ctypes.POINTER(ctypes.c_double)

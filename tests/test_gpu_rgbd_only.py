@@ -78,7 +78,7 @@ def test_mixed_batch_equals_each_stream_alone():
 def test_track_mode_validation():
     _torch()
     seq = synth.frame_pair(seed=2, cam=synth.scaled_camera(64, 48))
-    for kw in (dict(track_mode=2), dict(track_mode=1, rgbd_lambda=-1.0)):
+    for kw in (dict(track_mode=3), dict(track_mode=-1), dict(track_mode=1, rgbd_lambda=-1.0)):
         _, dcfg = configs(seq, 2, (3, 2), **kw)
         with pytest.raises(dri.DriError) as e:
             new_stream(dcfg, synth.initial_state(seq))
