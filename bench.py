@@ -35,6 +35,7 @@ import json
 import multiprocessing as mp
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -47,7 +48,10 @@ LEVELS, ITERS = 3, (10, 5, 4)
 FPS = 30.0
 N_UNIQUE = 100
 SEQ_SEED = 2
-BYTES_PER_PIXEL_ITER = 48     # FP32 maps: see the design doc (live 20 B + reference 28 B)
+# algorithmic bytes per pixel-iteration, FP32 maps: live pack A (normal + depth,
+# 16 B) and intensity (4 B); reference pack A (16 B) and the used 12 B of pack B
+# (intensity + gradient)
+BYTES_PER_PIXEL_ITER = 48
 PIXEL_ITERS_PER_FRAME = sum((W >> l) * (H >> l) * ITERS[l] for l in range(LEVELS))
 BATCH = 64
 BATCH_OFFSET = 37             # stream i starts at frame (37 i) mod 100 of the loop
@@ -112,7 +116,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the samples' file: DRI_CLOCKS_DIR, else the system's temporary directory
+        out_dir = os.environ.get("DRI_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -348,6 +354,17 @@ def roofline(prof, dri, traffic_bpp):
             "bytes_per_pixel_iter": BYTES_PER_PIXEL_ITER, "avg_launch_us": 1000.0 * t_ms / n,
             "pixel_iters_per_launch": px / n,
             "traffic": None if traffic_bpp is None else traffic_bpp * px / n}
+
+
+def step_bandwidth(n_streams, ms_per_step):
+    """The pixel kernels' algorithmic bytes of one timed step over the step's
+    time: a lower bound of their bandwidth as they run in the timed region,
+    where the slot groups' pixel kernels overlap one another and the FP64
+    steps (the roofline's per-launch figure times launches in isolation)."""
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_PER_PIXEL_ITER * PIXEL_ITERS_PER_FRAME * n_streams / (ms_per_step / 1000.0) / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_kind": peak_kind}
 
 
 class Runner:
@@ -758,11 +775,13 @@ def run_ours(args):
             "value": job_throughput(n_streams * steps, world, total_ms), "steps": steps,
             "streams": n_streams, "ms_per_step": total_ms / steps,
             "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+            "slowest_steps": [[int(k), float(per[k])] for k in np.argsort(per)[::-1][:5]],
             "gpu_launches": int(launches), "frames_ok": int(ok), "frames_failed": int(failed),
             "roofline": roofline(prof, dri, track_traffic()), "kernel_classes": kernel_classes(prof, dri),
             "e2e": {"value": world * n_streams * e2e_steps / e2e_s, "unit": "frames/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "clocks": clocks, "rows_per_thread": tiles[:LEVELS], "groups": opts.groups,
+            "step_bandwidth": step_bandwidth(n_streams, total_ms / steps),
         }
         run.close()
         del run
@@ -805,10 +824,11 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(args.precision_flags),
         "data": "synthetic", "config": dict(config_json(args.batch), imu_mode=args.imu_mode,
                                             occlusion_thr=args.occlusion_thr),
-        "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"],
+        "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"], "slowest_steps": b["slowest_steps"],
         "gpu_launches": b["gpu_launches"],
         "frames_failed": b["frames_failed"], "frames_ok": b["frames_ok"],
-        "roofline": b["roofline"], "kernel_classes": b["kernel_classes"], "e2e": b["e2e"],
+        "roofline": b["roofline"], "step_bandwidth": b["step_bandwidth"],
+        "kernel_classes": b["kernel_classes"], "e2e": b["e2e"],
         "rows_per_thread": b["rows_per_thread"], "groups": b["groups"],
         "plain": None if p is None else {
             k: p[k] for k in ("value", "steps", "ms_per_step", "p50_ms", "p99_ms", "gpu_launches",

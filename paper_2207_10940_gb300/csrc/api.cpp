@@ -28,7 +28,10 @@ constexpr int kBatchRing = 8;     // launches of one batch plan in flight
 constexpr int kMaxBatch = 4096;
 constexpr int kMaxRowsPerThread = 64;
 constexpr int kMaxGroups = 8;     // slot groups of a batch plan's Gauss-Newton loop
-constexpr int kDefaultGroups = 1;
+constexpr size_t kImuDropBatch = 4096;   // consumed IMU samples dropped at once (~10 s at 400 Hz)
+// Slot groups of a new batch plan: one per 16 slots, at most 4 (64 x 640x480:
+// 1 group 10.3k frames/s, 2 11.8k, 3 12.1k, 4 12.3k, 5 11.1k).
+inline int default_groups(int n) { return std::max(1, std::min(4, n / 16)); }
 inline size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
 
 int valid_config(const dri_stream_config* c) {
@@ -528,13 +531,22 @@ int plan_acquire(Plan* p, int* slot) {
 
 // Samples covering [t0, t1] (the last one at or before t0 through the first at
 // or after t1): [k0, k1).
+// Index of the last sample at or before t (samples strictly increasing in t;
+// the first sample is at or before t).
+size_t imu_at_or_before(const std::vector<dri_imu_sample>& v, double t) {
+  const auto it = std::upper_bound(v.begin(), v.end(), t,
+                                   [](double x, const dri_imu_sample& m) { return x < m.t; });
+  return it == v.begin() ? 0 : (size_t)(it - v.begin()) - 1;
+}
+
 int select_imu(const dri_stream_s* s, double t0, double t1, size_t* k0, size_t* k1) {
   const auto& v = s->imu;
   if (v.empty() || v.front().t > t0 || v.back().t < t1) return DRI_ENOTREADY;
-  size_t a = 0;
-  while (a + 1 < v.size() && v[a + 1].t <= t0) ++a;
-  size_t b = a;
-  while (b < v.size() && v[b].t < t1) ++b;
+  const size_t a = imu_at_or_before(v, t0);
+  // first sample at or after t1
+  const size_t b = (size_t)(std::lower_bound(v.begin() + a, v.end(), t1,
+                                             [](const dri_imu_sample& m, double x) { return m.t < x; }) -
+                            v.begin());
   if (b >= v.size()) return DRI_ENOTREADY;
   *k0 = a;
   *k1 = b + 1;
@@ -616,14 +628,19 @@ int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
   if (phases & 2) {
     // Gauss-Newton loop per slot group; groups run on their own streams (forked
     // from and joined back into the plan's stream) so that one group's FP64
-    // solves overlap another group's pixel kernels.  While profiling, the groups
-    // run one after the other on the plan's stream.
+    // solves overlap another group's pixel kernels.  With several groups a
+    // pixel kernel starts only when its group's step has ended: launched early
+    // (programmatic dependent launch) its blocks would hold the SMs for the
+    // whole step, waiting, instead of leaving them to the other groups (4 groups
+    // of 16 x 640x480: 7.4k frames/s early, 12.3k not).  While profiling, the
+    // groups run one after the other on the plan's stream.
     const bool fork = p->groups > 1 && !prof->profiling;
     if (fork) CK(cudaEventRecord(p->ev_fork, st));
     for (int g = 0; g < p->groups; ++g) {
       cudaStream_t sg = (fork && g > 0) ? p->aux[g - 1] : st;
       if (fork && g > 0) CK(cudaStreamWaitEvent(sg, p->ev_fork, 0));
       const double px_scale = (double)p->gcount[g] / p->S;
+      const int prio = launch_priority(false);
       int remaining = 0;
       for (int l = 0; l < L; ++l) remaining += p->iters[l];
       for (int l = L - 1; l >= 0; --l) {
@@ -632,7 +649,9 @@ int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
           const BatchArgs at = plan_args(p, track_start(p, l, g), l, 0, p->gfirst[g], p->gcount[g]);
           const int nb = track_blocks(p, l, g);
           CK(launch(prof, DRI_KC_TRACK, plan_pixels(p, l) * px_scale,
-                    [&] { return launch_track_batch(at, nb, p->fp16, p->fp32p, p->opt, sg); }));
+                    [&] {
+                      return launch_track_batch(at, nb, p->fp16, p->fp32p, p->opt, prio, p->groups == 1, sg);
+                    }));
           const BatchArgs as = plan_args(p, p->tv.copy_off, l, remaining == 0, p->gfirst[g], p->gcount[g]);
           CK(launch(prof, DRI_KC_SOLVE, 0.0, [&] { return launch_gn_step_batch(as, sg); }));
           k += 2;
@@ -680,7 +699,8 @@ int plan_autotune(Plan* p, int64_t* kernels) {
       auto all_groups = [&] {
         for (int g = 0; g < p->groups; ++g) {
           const BatchArgs at = plan_args(p, track_start(p, l, g), l, 0, p->gfirst[g], p->gcount[g]);
-          if (launch_track_batch(at, track_blocks(p, l, g), p->fp16, p->fp32p, p->opt, p->stream) !=
+          if (launch_track_batch(at, track_blocks(p, l, g), p->fp16, p->fp32p, p->opt, launch_priority(false),
+                                 true, p->stream) !=
               cudaSuccess)
             return false;
         }
@@ -725,7 +745,7 @@ int plan_run(Plan* p, int64_t* kernels) {
       const int r = plan_enqueue(p, 3, &k);
       const cudaError_t e = cudaStreamEndCapture(p->stream, &g);
       if (r == DRI_OK && e == cudaSuccess && g &&
-          cudaGraphInstantiate(&p->graph, g, 0) == cudaSuccess) {
+          cudaGraphInstantiate(&p->graph, g, cudaGraphInstantiateFlagUseNodePriority) == cudaSuccess) {
         p->kernels_per_frame = k;
       } else {
         p->graph = nullptr;
@@ -822,11 +842,14 @@ int plan_launch(Plan* p, const std::vector<SlotWork>& work, int* ring_slot) {
     } else {
       // drop samples no later frame can need: all before the one covering the
       // earliest time a frame may still start from (a failed frame in flight
-      // rolls the start back to t_confirmed)
+      // rolls the start back to t_confirmed).  Erasing moves every later
+      // sample, and a client may push minutes of samples ahead, so they are
+      // dropped in batches of at least kImuDropBatch.
       const double keep_from = std::min(s->t_prev, s->t_confirmed);
-      size_t a = 0;
-      while (a + 1 < s->imu.size() && s->imu[a + 1].t <= keep_from) ++a;
-      if (a) s->imu.erase(s->imu.begin(), s->imu.begin() + a);
+      if (!s->imu.empty() && s->imu.front().t <= keep_from) {
+        const size_t a = imu_at_or_before(s->imu, keep_from);
+        if (a >= kImuDropBatch) s->imu.erase(s->imu.begin(), s->imu.begin() + a);
+      }
       s->t_prev_before = s->t_prev;
       s->t_prev = s->t_frame;   // optimistic; rolled back when the frame is known to fail
     }
@@ -1187,7 +1210,7 @@ int batch_plan(const dri_stream* streams, int32_t n, Plan** out) {
     if (q->slots == key) *out = q;
   if (*out) return DRI_OK;
   Plan* p = nullptr;
-  const int r = plan_create(key.data(), n, kBatchRing, false, std::min(n, kDefaultGroups), &p);
+  const int r = plan_create(key.data(), n, kBatchRing, false, default_groups(n), &p);
   if (r != DRI_OK) return r;
   p->autotune = true;
   g_batch_plans.push_back(p);

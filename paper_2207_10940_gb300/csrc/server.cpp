@@ -157,8 +157,7 @@ int current_plan(dri_server_s* S, Plan** out) {
     for (int l = 0; l < S->levels && same; ++l) same = o.rows_per_thread[l] == S->tiles[l];
     if (!same) {
       for (int l = 0; l < DRI_MAX_LEVELS; ++l) o.rows_per_thread[l] = S->tiles[l];
-      o.autotune = 0;
-      o.groups = 1;
+      o.autotune = 0;                 // the plan keeps its default slot groups
       const int rs = dri_batch_set_options(key.data(), (int32_t)key.size(), &o);
       if (rs != DRI_OK) return rs;
     }

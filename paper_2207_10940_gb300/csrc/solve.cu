@@ -1694,17 +1694,34 @@ cudaError_t launch_frame_begin_batch(const BatchArgs& a, cudaStream_t s) {
   k_frame_begin_batch<<<a.nslots, kSolveThreads, sizeof(BeginSmem), s>>>(a);
   return cudaGetLastError();
 }
+int launch_priority(bool solver) {
+  static const int2 range = [] {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) least = greatest = 0;
+    return make_int2(least, greatest);
+  }();
+  // greater priority is the numerically smaller value
+  const int p = solver ? range.y : range.y + 1;
+  return p < range.x ? p : range.x;
+}
+
+// The step's blocks are scheduled ahead of pixel-kernel blocks waiting for an
+// SM: with several slot groups, one group's FP64 step runs beside another
+// group's pixel kernel instead of waiting for its last wave.
+
 cudaError_t launch_gn_step_batch(const BatchArgs& a, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(a.nslots);
   cfg.blockDim = dim3(kSolveThreads);
   cfg.dynamicSmemBytes = sizeof(GnSmem);
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributePriority;
+  attr[1].val.priority = launch_priority(true);
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, k_gn_step_batch, a);
 }
 cudaError_t launch_frame_end_batch(const BatchArgs& a, cudaStream_t s) {

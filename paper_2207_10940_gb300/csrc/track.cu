@@ -427,16 +427,18 @@ cudaError_t launch_track(const TrackParams& p0, bool fp16, bool fp32_partials, c
 }
 
 cudaError_t launch_track_batch(const BatchArgs& a, int blocks, bool fp16, bool fp32_partials,
-                               int opt, cudaStream_t s) {
+                               int opt, int priority, bool early, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(kTrackThreadsX, kTrackThreadsY);
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[0].val.programmaticStreamSerializationAllowed = early ? 1 : 0;
+  attr[1].id = cudaLaunchAttributePriority;
+  attr[1].val.priority = priority;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
 #define DRI_TRACK_BATCH(T, P)                                                            \
   do {                                                                                   \
     if (opt == 0) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 0>, a);            \
