@@ -277,7 +277,8 @@ int dri_track_batch(const dri_stream* streams, int32_t n, dri_track_result* out)
  *                    each on its own CUDA stream forked from and joined to the
  *                    plan's stream, so one group's FP64 solves overlap another
  *                    group's pixel kernels (1 .. min(n, 8); default n / 16
- *                    clamped to 1 .. 4; a stream's own plan has 1)
+ *                    clamped to 1 .. 4; a stream's own plan has 1); 0 in
+ *                    dri_batch_set_options keeps the plan's current groups
  *   autotune         1: the next tracked frame times rows per thread
  *                    2, 4, 8, 16, 32 per level and keeps the fastest (batch
  *                    plans start with it on); 0: rows_per_thread as given, so

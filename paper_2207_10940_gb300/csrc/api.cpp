@@ -1408,7 +1408,7 @@ int dri_batch_set_options(const dri_stream* streams, int32_t n, const dri_batch_
   Plan* p = nullptr;
   const int r = batch_plan(streams, n, &p);
   if (r != DRI_OK) return r;
-  if (opt->groups < 1 || opt->groups > std::min(p->S, kMaxGroups)) return DRI_EINVAL;
+  if (opt->groups < 0 || opt->groups > std::min(p->S, kMaxGroups)) return DRI_EINVAL;
   if (!opt->autotune)
     for (int l = 0; l < p->levels; ++l)
       if (opt->rows_per_thread[l] < 1 || opt->rows_per_thread[l] > kMaxRowsPerThread) return DRI_EINVAL;
@@ -1418,7 +1418,7 @@ int dri_batch_set_options(const dri_stream* streams, int32_t n, const dri_batch_
       for (int l = 0; l < p->levels; ++l) v[l] = opt->rows_per_thread[l];
   p->autotune = opt->autotune != 0;
   p->tuned = !p->autotune;
-  plan_set_groups(p, opt->groups);
+  if (opt->groups > 0) plan_set_groups(p, opt->groups);
   if (p->graph) {
     cudaGraphExecDestroy(p->graph);
     p->graph = nullptr;

@@ -337,9 +337,9 @@ def dri_batch_set_options(streams, rows_per_thread=None, groups=None, autotune=N
     """Updates the given fields of this stream list's plan options."""
     try:
         opt = dri_batch_get_options(streams)
-    except DriError:
+    except DriError:                       # no plan yet: it is made with its defaults
         opt = dri_batch_options()
-        opt.groups = 1
+        opt.groups = 0                     # keep the plan's own (default) groups
         opt.autotune = 0 if len(streams) == 1 else 1
     if rows_per_thread is not None:
         rows = list(rows_per_thread) + [1] * (DRI_MAX_LEVELS - len(rows_per_thread))

@@ -196,12 +196,50 @@ def test_batch_options_are_checked():
     torch = _torch()
     seqs = _sequences(2)[:2]
     batch = _streams(seqs, torch.cuda.Stream())
-    for kw in ({"groups": 0}, {"groups": 3}, {"rows_per_thread": [0, 1, 1]},
+    for kw in ({"groups": -1}, {"groups": 3}, {"rows_per_thread": [0, 1, 1]},
                {"rows_per_thread": [65, 1, 1]}):
         with pytest.raises(dri.DriError) as e:
             dri.dri_batch_set_options(batch, **kw)
         assert e.value.code == dri.DRI_EINVAL
+    # groups 0 keeps the plan's groups
+    dri.dri_batch_set_options(batch, rows_per_thread=[4, 4, 2], groups=2)
+    dri.dri_batch_set_options(batch, rows_per_thread=[8, 4, 2], groups=0)
+    opts = dri.dri_batch_get_options(batch)
+    assert opts.groups == 2 and list(opts.rows_per_thread[:3]) == [8, 4, 2]
     own = dri.dri_batch_get_options([batch[0]])        # a stream's own plan
     assert own.groups == 1 and own.autotune == 0
     for st in batch:
         st.close()
+
+
+def test_default_slot_groups():
+    """A new batch plan runs its Gauss-Newton loop as one slot group per 16
+    slots (at most 4); results match the one-group plan."""
+    torch = _torch()
+    seq = synth.frame_pair(seed=5, cam=synth.scaled_camera(64, 48))
+    _, dcfg = configs(seq, 2, (3, 2))
+    x_init = synth.initial_state(seq)
+    for n, groups in ((16, 1), (32, 2)):
+        states = []
+        for forced in (None, 1):
+            ts = torch.cuda.Stream()
+            batch = [dri.Stream(dcfg, dri.state_from_dict(x_init, 0.0), ts) for _ in range(n)]
+            for st in batch:
+                dri.dri_push_imu(st.handle, seq.imu)
+            if forced is not None:
+                dri.dri_batch_set_options(batch, rows_per_thread=[4, 2], groups=forced)
+            else:
+                dri.dri_batch_set_options(batch, rows_per_thread=[4, 2])
+            for i in range(2):
+                for st in batch:
+                    dri.dri_upload_frame(st.handle, seq.frame_times[i], seq.depth[i], seq.intensity[i])
+                res = dri.dri_track_batch(batch)
+                assert [r.status for r in res] == [0] * n
+            assert dri.dri_batch_get_options(batch).groups == (groups if forced is None else 1)
+            states.append([dri.dri_get_state(st.handle) for st in batch])
+            for st in batch:
+                st.close()
+        # the same fixed tiles: every slot sums its pixels in the same order
+        for a, b in zip(*states):
+            for f in ("r_WC", "q_WC", "v_I", "bg", "ba", "q_IW"):
+                assert list(getattr(a, f)) == list(getattr(b, f)), f
