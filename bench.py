@@ -130,6 +130,15 @@ class ClockSampler:
                 stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return self
+        # the sampler's start-up (its NVML initialisation) stays out of the timed
+        # region: wait for its first sample, at most 1.5 s (by then the start-up
+        # is over even if the samples are still in its output buffer)
+        t = time.perf_counter()
+        while time.perf_counter() - t < 1.5 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
         return self
 
     def __exit__(self, *a):
