@@ -384,6 +384,7 @@ void plan_free(Plan* p) {
   for (cudaStream_t a : p->aux)
     if (a) cudaStreamDestroy(a);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_grad) cudaEventDestroy(p->ev_grad);
   for (cudaEvent_t e : p->ev_join)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : p->ev)
@@ -460,7 +461,8 @@ int plan_create(dri_stream_s* const* streams, int n, int ring, bool in_workspace
   p->aux.assign(kMaxGroups - 1, nullptr);
   p->ev_join.assign(kMaxGroups - 1, nullptr);
   if (!in_workspace) {
-    if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_grad, cudaEventDisableTiming) != cudaSuccess) {
       plan_free(p);
       return DRI_ENOMEM;
     }
@@ -635,7 +637,20 @@ int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
     // of 16 x 640x480: 7.4k frames/s early, 12.3k not).  While profiling, the
     // groups run one after the other on the plan's stream.
     const bool fork = p->groups > 1 && !prof->profiling;
-    if (fork) CK(cudaEventRecord(p->ev_fork, st));
+    // The gradient maps of the frame's own set (the next reference's pack B)
+    // depend on its intensity pyramid only: they run on a spare stream beside
+    // the Gauss-Newton loop and are joined before the frame end.
+    cudaStream_t sgrad = st;
+    if (!prof->profiling && p->groups < kMaxGroups && p->aux[kMaxGroups - 2]) sgrad = p->aux[kMaxGroups - 2];
+    if (fork || sgrad != st) CK(cudaEventRecord(p->ev_fork, st));
+    if (sgrad != st) CK(cudaStreamWaitEvent(sgrad, p->ev_fork, 0));
+    for (int l = 0; l < L; ++l) {
+      const BatchArgs a = plan_args(p, p->tv.map_off[l], l, 0);
+      CK(launch(prof, DRI_KC_GRAD, plan_pixels(p, l),
+                [&] { return launch_gradient_batch(a, p->pre_map[l][p->S], p->fp16, sgrad); }));
+      ++k;
+    }
+    if (sgrad != st) CK(cudaEventRecord(p->ev_grad, sgrad));
     for (int g = 0; g < p->groups; ++g) {
       cudaStream_t sg = (fork && g > 0) ? p->aux[g - 1] : st;
       if (fork && g > 0) CK(cudaStreamWaitEvent(sg, p->ev_fork, 0));
@@ -662,15 +677,10 @@ int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
         CK(cudaStreamWaitEvent(st, p->ev_join[g - 1], 0));
       }
     }
+    if (sgrad != st) CK(cudaStreamWaitEvent(st, p->ev_grad, 0));
     const BatchArgs ae = plan_args(p, p->tv.copy_off, 0, 0);
     CK(launch(prof, DRI_KC_FRAME, 0.0, [&] { return launch_frame_end_batch(ae, st); }));
     ++k;
-    for (int l = 0; l < L; ++l) {
-      const BatchArgs a = plan_args(p, p->tv.map_off[l], l, 0);
-      CK(launch(prof, DRI_KC_GRAD, plan_pixels(p, l),
-                [&] { return launch_gradient_batch(a, p->pre_map[l][p->S], p->fp16, st); }));
-      ++k;
-    }
     if (p->heads) {
       CK(launch_gather_heads(ae, p->heads, st));
       ++k;

@@ -89,6 +89,7 @@ struct Plan {
   std::vector<int> gfirst, gcount;
   std::vector<cudaStream_t> aux;    // streams of groups 1 .. groups - 1
   cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_grad = nullptr;    // the gradient maps' side stream is done
   std::vector<cudaEvent_t> ev_join;
   char* table = nullptr;
   TableView tv;
