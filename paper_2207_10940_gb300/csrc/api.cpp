@@ -385,6 +385,8 @@ void plan_free(Plan* p) {
     if (a) cudaStreamDestroy(a);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_grad) cudaEventDestroy(p->ev_grad);
+  if (p->ev_maps) cudaEventDestroy(p->ev_maps);
+  if (p->ev_norm) cudaEventDestroy(p->ev_norm);
   for (cudaEvent_t e : p->ev_join)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : p->ev)
@@ -462,7 +464,9 @@ int plan_create(dri_stream_s* const* streams, int n, int ring, bool in_workspace
   p->ev_join.assign(kMaxGroups - 1, nullptr);
   if (!in_workspace) {
     if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_grad, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&p->ev_grad, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_maps, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_norm, cudaEventDisableTiming) != cudaSuccess) {
       plan_free(p);
       return DRI_ENOMEM;
     }
@@ -599,12 +603,23 @@ double plan_pixels(const Plan* p, int level) {
   return n;
 }
 
+// The spare stream of a batch plan (the last of its group streams when the
+// groups leave it free; none while profiling or for a stream's own plan).
+cudaStream_t side_stream(const Plan* p, bool profiling) {
+  if (profiling || p->groups >= kMaxGroups || !p->aux[kMaxGroups - 2]) return p->stream;
+  return p->aux[kMaxGroups - 2];
+}
+
 // Kernel launches of one frame, in order.  phase 1: maps and frame begin;
 // phase 2: the Gauss-Newton loop, frame end, gradients and the head gather.
+// On a batch plan's spare stream, beside the loop: the normal maps of the
+// finer levels (the loop starts at the coarsest; each group waits for them
+// before its first finer-level pixel kernel) and the gradient maps.
 int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
   dri_stream_s* prof = p->slots[0];
   cudaStream_t st = p->stream;
   const int L = p->levels;
+  const cudaStream_t sside = side_stream(p, prof->profiling);
   int64_t k = 0;
   if (phases & 1) {
     const BatchArgs a0 = plan_args(p, p->tv.copy_off, 0, 0);
@@ -617,12 +632,19 @@ int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
                 [&] { return launch_pyr_down_batch(a, p->pre_map[l][p->S], st); }));
       ++k;
     }
-    for (int l = 0; l < L; ++l) {
+    p->norm_side = sside != st && L > 1;
+    if (p->norm_side) {
+      CK(cudaEventRecord(p->ev_maps, st));
+      CK(cudaStreamWaitEvent(sside, p->ev_maps, 0));
+    }
+    for (int l = L - 1; l >= 0; --l) {          // coarsest first
       const BatchArgs a = plan_args(p, p->tv.map_off[l], l, 0);
+      const cudaStream_t sn = (p->norm_side && l < L - 1) ? sside : st;
       CK(launch(prof, DRI_KC_MAPS, plan_pixels(p, l),
-                [&] { return launch_normals_batch(a, p->pre_map[l][p->S], p->fp16, st); }));
+                [&] { return launch_normals_batch(a, p->pre_map[l][p->S], p->fp16, sn); }));
       ++k;
     }
+    if (p->norm_side) CK(cudaEventRecord(p->ev_norm, sside));
     const BatchArgs ab = plan_args(p, p->tv.copy_off, 0, 0);
     CK(launch(prof, DRI_KC_FRAME, 0.0, [&] { return launch_frame_begin_batch(ab, st); }));
     ++k;
@@ -640,8 +662,7 @@ int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
     // The gradient maps of the frame's own set (the next reference's pack B)
     // depend on its intensity pyramid only: they run on a spare stream beside
     // the Gauss-Newton loop and are joined before the frame end.
-    cudaStream_t sgrad = st;
-    if (!prof->profiling && p->groups < kMaxGroups && p->aux[kMaxGroups - 2]) sgrad = p->aux[kMaxGroups - 2];
+    const cudaStream_t sgrad = sside;
     if (fork || sgrad != st) CK(cudaEventRecord(p->ev_fork, st));
     if (sgrad != st) CK(cudaStreamWaitEvent(sgrad, p->ev_fork, 0));
     for (int l = 0; l < L; ++l) {
@@ -659,6 +680,7 @@ int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
       int remaining = 0;
       for (int l = 0; l < L; ++l) remaining += p->iters[l];
       for (int l = L - 1; l >= 0; --l) {
+        if (p->norm_side && l == L - 2) CK(cudaStreamWaitEvent(sg, p->ev_norm, 0));
         for (int it = 0; it < p->iters[l]; ++it) {
           --remaining;
           const BatchArgs at = plan_args(p, track_start(p, l, g), l, 0, p->gfirst[g], p->gcount[g]);
@@ -695,6 +717,7 @@ int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
 // candidates 2, 4, 8, 16 and 32, three launches each, the fastest mean wins.
 int plan_autotune(Plan* p, int64_t* kernels) {
   static const int cand[] = {2, 4, 8, 16, 32};
+  if (p->norm_side) CK(cudaStreamWaitEvent(p->stream, p->ev_norm, 0));   // every level's maps
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));

@@ -185,14 +185,12 @@ __global__ void __launch_bounds__(256) k_gradient_batch(const BatchArgs a) {
   int slot, x, y, w, h;
   if (!map_tile(a, &slot, &x, &y, &w, &h) || x >= w) return;
   const TrackParams& tp = a.slots[slot].tp[a.level];
-  // the frame's own map set, which becomes the reference: launched after the
-  // frame start (which swaps the sets of a first frame at once) and before the
-  // frame end (which swaps them after a tracked frame)
-  const int ri = tp.ctrl->ref_index;
-  const int set = batch_dyn(a, slot).mode == kSlotInit ? ri : 1 - ri;
+  // the frame's own map set, which becomes the reference at the frame end
+  // (launched before it)
+  const int cs = 1 - tp.ctrl->ref_index;
 #pragma unroll
   for (int k = 0; k < kMapRows; ++k, y += kMapTileH)
-    if (y < h) gradient_px<T>(tp.m, set, w, h, x, y);
+    if (y < h) gradient_px<T>(tp.m, cs, w, h, x, y);
 }
 
 template <typename T>

@@ -1645,9 +1645,7 @@ __device__ int load_slot_params(const BatchArgs& a, SolveParams& sp) {
 __global__ void __launch_bounds__(kSolveThreads) k_frame_begin_batch(const BatchArgs a) {
   __shared__ SolveParams sp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int mode = load_slot_params(a, sp);
-  if (mode == kSlotInit) frame_init_body(sp);
-  else if (mode == kSlotTrack) frame_begin_body(sp, *reinterpret_cast<BeginSmem*>(smem_raw));
+  if (load_slot_params(a, sp) == kSlotTrack) frame_begin_body(sp, *reinterpret_cast<BeginSmem*>(smem_raw));
 }
 
 __global__ void __launch_bounds__(kSolveThreads) k_gn_step_batch(const BatchArgs a) {
@@ -1658,9 +1656,14 @@ __global__ void __launch_bounds__(kSolveThreads) k_gn_step_batch(const BatchArgs
   else grid_dep_wait();                 // idle slot: nothing to read, keep the ordering
 }
 
+// A first frame is initialised here too, so that the map sets of every slot
+// swap only at the frame end: the map kernels of the frame, which may run
+// beside its start, read which set is the reference.
 __global__ void __launch_bounds__(kSolveThreads) k_frame_end_batch(const BatchArgs a) {
   __shared__ SolveParams sp;
-  if (load_slot_params(a, sp) == kSlotTrack) frame_end_body(sp);
+  const int mode = load_slot_params(a, sp);
+  if (mode == kSlotTrack) frame_end_body(sp);
+  else if (mode == kSlotInit) frame_init_body(sp);
 }
 
 // Result heads of all slots into one contiguous buffer (one copy to the host).
