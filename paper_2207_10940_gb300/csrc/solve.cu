@@ -9,7 +9,8 @@
 //                 34x34 system of Eq. 7; x0, x1 boxplus= dx (Eq. 2)
 //   frame_end     marginalise x0 by the Schur complement (Eq. 8) at the updated point,
 //                 make the frame the reference (flip of the map sets)
-//   frame_init    first frame: first-frame prior, the frame becomes the reference
+//   frame_init    first frame (run by the frame-end kernel): first-frame prior, the
+//                 frame becomes the reference
 //
 // Readings (the paper gives no integration scheme, Jacobians or prior sign):
 // zero-order-hold integration cut at sample times, update order p, v, R; the bias
