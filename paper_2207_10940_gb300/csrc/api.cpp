@@ -386,6 +386,8 @@ void plan_free(Plan* p) {
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_grad) cudaEventDestroy(p->ev_grad);
   if (p->ev_maps) cudaEventDestroy(p->ev_maps);
+  if (p->ev_start) cudaEventDestroy(p->ev_start);
+  if (p->ev_begin) cudaEventDestroy(p->ev_begin);
   if (p->ev_norm) cudaEventDestroy(p->ev_norm);
   for (cudaEvent_t e : p->ev_join)
     if (e) cudaEventDestroy(e);
@@ -466,6 +468,8 @@ int plan_create(dri_stream_s* const* streams, int n, int ring, bool in_workspace
     if (cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_grad, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_maps, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_begin, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_norm, cudaEventDisableTiming) != cudaSuccess) {
       plan_free(p);
       return DRI_ENOMEM;
@@ -612,9 +616,12 @@ cudaStream_t side_stream(const Plan* p, bool profiling) {
 
 // Kernel launches of one frame, in order.  phase 1: maps and frame begin;
 // phase 2: the Gauss-Newton loop, frame end, gradients and the head gather.
-// On a batch plan's spare stream, beside the loop: the normal maps of the
-// finer levels (the loop starts at the coarsest; each group waits for them
-// before its first finer-level pixel kernel) and the gradient maps.
+// On a batch plan's spare stream: the frame start, beside the map kernels
+// (it reads and writes the slots' control blocks and their IMU blocks, the map
+// kernels only which set is the reference, which changes at the frame end),
+// and beside the loop the normal maps of the finer levels (the loop starts at
+// the coarsest; each group waits for them before its first finer-level pixel
+// kernel) and the gradient maps.
 int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
   dri_stream_s* prof = p->slots[0];
   cudaStream_t st = p->stream;
@@ -622,6 +629,15 @@ int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
   const cudaStream_t sside = side_stream(p, prof->profiling);
   int64_t k = 0;
   if (phases & 1) {
+    const bool side = sside != st;
+    const BatchArgs ab = plan_args(p, p->tv.copy_off, 0, 0);
+    if (side) {
+      CK(cudaEventRecord(p->ev_start, st));
+      CK(cudaStreamWaitEvent(sside, p->ev_start, 0));
+      CK(launch(prof, DRI_KC_FRAME, 0.0, [&] { return launch_frame_begin_batch(ab, sside); }));
+      ++k;
+      CK(cudaEventRecord(p->ev_begin, sside));
+    }
     const BatchArgs a0 = plan_args(p, p->tv.copy_off, 0, 0);
     CK(launch(prof, DRI_KC_MAPS, plan_pixels(p, 0),
               [&] { return launch_copy_batch(a0, p->pre_copy[p->S], st); }));
@@ -645,9 +661,12 @@ int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
       ++k;
     }
     if (p->norm_side) CK(cudaEventRecord(p->ev_norm, sside));
-    const BatchArgs ab = plan_args(p, p->tv.copy_off, 0, 0);
-    CK(launch(prof, DRI_KC_FRAME, 0.0, [&] { return launch_frame_begin_batch(ab, st); }));
-    ++k;
+    if (side) {
+      CK(cudaStreamWaitEvent(st, p->ev_begin, 0));
+    } else {
+      CK(launch(prof, DRI_KC_FRAME, 0.0, [&] { return launch_frame_begin_batch(ab, st); }));
+      ++k;
+    }
   }
   if (phases & 2) {
     // Gauss-Newton loop per slot group; groups run on their own streams (forked

@@ -90,6 +90,8 @@ struct Plan {
   std::vector<cudaStream_t> aux;    // streams of groups 1 .. groups - 1
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_grad = nullptr;    // the gradient maps' side stream is done
+  cudaEvent_t ev_start = nullptr;   // the frame's inputs are staged (frame start may run)
+  cudaEvent_t ev_begin = nullptr;   // the frame start is done
   cudaEvent_t ev_maps = nullptr;    // the pyramid is built (fine-level normals may start)
   cudaEvent_t ev_norm = nullptr;    // the fine-level normal maps are built
   bool norm_side = false;           // this frame's fine-level normals are on the side stream
