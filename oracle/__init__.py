@@ -20,6 +20,8 @@ SLAM with Map Deformations", IROS 2017):
 * gn      -- joint cost (Eq. 6), Gauss-Newton system (Eq. 7), marginalisation
              (Eq. 8) and first-order prior correction (Eq. 9), and the per-frame
              tracker that chains them
+* gravity3-- the paper's 3-D gravity-with-gauge form of the state (Sec. II,
+             IV-A) with a damped step, beside the 2-DoF form the rest uses
 
 Every floating-point step is FP64 (inputs are FP32 images, which convert
 exactly).  Where the paper is silent (Jacobians, pyramid construction, data

@@ -153,6 +153,16 @@ def residual(x0, x1, pre, cfg):
     return e, pr
 
 
+def gravity_blocks(x0, pre, cfg, e, pr):
+    """The IMU error's derivatives by a rotation dg of q_IW about all three of
+    I's axes (q_IW <- exp(dg) (x) q_IW): rows r and v by x_0's dg, rows g by
+    x_0's and by x_1's (3 x 3 each).  The 2-DoF state keeps their x and y
+    columns; the 3-D gravity variant (gravity3.py) all three."""
+    Q0, A0 = x0.Rg, x0.R @ cfg.R_CS
+    return dict(r0=Q0.T @ hat(pr["c"]), v0=-hat(Q0 @ A0 @ pre["dv"]), g0=jl_inv(e[15:18]),
+                g1=-jr_inv(e[15:18]))
+
+
 def jacobian(x0, x1, pre, cfg, e=None, pr=None):
     """Analytic de_IMU / d(dx_0, dx_1), 18 x 34 (columns: x_0 tangent then x_1's)."""
     if e is None:
@@ -163,7 +173,7 @@ def jacobian(x0, x1, pre, cfg, e=None, pr=None):
     R_WS1 = pr["R_WS1"]
     A0 = R0 @ Rc
     Jla = jl_inv(e[3:6])
-    Jlg = jl_inv(e[15:18])
+    G = gravity_blocks(x0, pre, cfg, e, pr)
     J = np.zeros((18, 34))
     # x_1 (columns 17..33)
     J[0:3, 17:20] = -I3
@@ -171,7 +181,7 @@ def jacobian(x0, x1, pre, cfg, e=None, pr=None):
     J[6:9, 23:26] = -I3
     J[9:12, 26:29] = -I3
     J[12:15, 29:32] = -I3
-    J[15:18, 32:34] = -jr_inv(e[15:18]) @ P2
+    J[15:18, 32:34] = G["g1"] @ P2
     # x_0 (columns 0..16)
     J[0:3, 0:3] = I3
     J[0:3, 3:6] = -hat(pr["r"] - x0.r - Q0.T @ pr["c"])
@@ -186,9 +196,9 @@ def jacobian(x0, x1, pre, cfg, e=None, pr=None):
     J[0:3, 12:15] = A0 @ pre["P_a"]
     J[6:9, 12:15] = Q0 @ A0 @ pre["V_a"]
     J[12:15, 12:15] = I3
-    J[0:3, 15:17] = Q0.T @ hat(pr["c"]) @ P2
-    J[6:9, 15:17] = -hat(Q0 @ A0 @ pre["dv"]) @ P2
-    J[15:18, 15:17] = Jlg @ P2
+    J[0:3, 15:17] = G["r0"] @ P2
+    J[6:9, 15:17] = G["v0"] @ P2
+    J[15:18, 15:17] = G["g0"] @ P2
     return J
 
 
