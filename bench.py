@@ -963,7 +963,7 @@ def main():
     ap.add_argument("--batch", type=int, default=BATCH, help="streams of the batched pass")
     ap.add_argument("--precision-frames", type=int, default=3,
                     help="frames of the precision study against the FP64 oracle (< 2: skip it)")
-    ap.add_argument("--serve-seconds", type=float, default=15.0,
+    ap.add_argument("--serve-seconds", type=float, default=30.0,
                     help="seconds of arrivals in the serving pass (0: skip it)")
     ap.add_argument("--rows-per-thread", type=lambda v: [int(x) for x in v.split(",")], default=None,
                     help="pixel-kernel rows per thread per level for the batched pass, e.g. 8,8,8 "
