@@ -505,6 +505,43 @@ def job_throughput(units_per_rank, world, ms_max):
     return world * units_per_rank / (ms_max / 1000.0)
 
 
+def cpu_throttle():
+    """The process's CPU-bandwidth throttling counters from its cgroup (v2
+    cpu.stat / cpu.max, else v1 cpu/cpu.stat and the CFS quota): throttled
+    periods, throttled milliseconds and the quota in CPUs (None: no quota).
+    A throttled period stops every thread of the process until it ends."""
+    def read(path):
+        try:
+            with open(path) as f:
+                return f.read()
+        except OSError:
+            return None
+    stat, scale, quota = read("/sys/fs/cgroup/cpu.stat"), 1e-3, None
+    if stat is not None and "nr_throttled" in stat:
+        m = (read("/sys/fs/cgroup/cpu.max") or "").split()
+        if len(m) == 2 and m[0] != "max":
+            quota = float(m[0]) / float(m[1])
+    else:
+        stat, scale = read("/sys/fs/cgroup/cpu/cpu.stat"), 1e-6
+        q, per = read("/sys/fs/cgroup/cpu/cpu.cfs_quota_us"), read("/sys/fs/cgroup/cpu/cpu.cfs_period_us")
+        if q and per and int(q) > 0:
+            quota = int(q) / int(per)
+    if not stat:
+        return None
+    kv = dict(line.split()[:2] for line in stat.splitlines() if len(line.split()) >= 2)
+    t = kv.get("throttled_usec", kv.get("throttled_time", "0"))
+    return {"periods": int(kv.get("nr_periods", 0)), "throttled_periods": int(kv.get("nr_throttled", 0)),
+            "throttled_ms": float(t) * scale, "quota_cpus": quota}
+
+
+def throttle_delta(a, b):
+    if a is None or b is None:
+        return None
+    return {"throttled_periods": b["throttled_periods"] - a["throttled_periods"],
+            "throttled_ms": b["throttled_ms"] - a["throttled_ms"], "periods": b["periods"] - a["periods"],
+            "quota_cpus": b["quota_cpus"]}
+
+
 class NoCyclicGC:
     """The harness's cyclic garbage collector frozen and off: a full pass over
     the interpreter's heap (torch's objects included) can hold the thread that
@@ -529,6 +566,7 @@ def timed_pass(run, steps, world, local):
     h0 = run.streams[0].handle
     n0 = dri.dri_launch_count(h0)
     barrier(run.dev, world)
+    thr0 = cpu_throttle()
     with ClockSampler(local) as clk, NoCyclicGC():
         with torch.cuda.stream(run.ts):
             evs[0].record(run.ts)
@@ -540,7 +578,8 @@ def timed_pass(run, steps, world, local):
     launches = dri.dri_launch_count(h0) - n0
     per = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(steps)])
     total_ms = evs[0].elapsed_time(evs[-1])
-    return max_over_ranks(total_ms, run.dev, world), per, launches, clk.summary()
+    summary = dict(clk.summary(), host_cpu_throttle=throttle_delta(thr0, cpu_throttle()))
+    return max_over_ranks(total_ms, run.dev, world), per, launches, summary
 
 
 def profiled_pass(run, steps):
@@ -730,8 +769,10 @@ def served_pass(args, dev, workers):
         time.sleep(0.05)
     warm_s = time.perf_counter() - t_w
     dri.dri_server_stats_read(srv, reset=True)
+    thr0 = cpu_throttle()
     for t in th:
         t.join()
+    thr = throttle_delta(thr0, cpu_throttle())
     gc.enable()
     gc.unfreeze()
     wall = time.perf_counter() - t_start
@@ -748,6 +789,7 @@ def served_pass(args, dev, workers):
         "hbm_budget_gb": SERVE_BUDGET / 1e9, "inputs": "device-resident frames (30-frame loops per "
         "resolution, period-30 sinusoid), IMU copied per request",
         "warmup_s": warm_s, "client_max_lag_ms": 1000.0 * lag[0], "client_max_lag_at_s": lag[1],
+        "host_cpu_throttle": thr,
         "latency_from": "submit to result (warm-up excluded: 2 s and until the start's backlog is "
                         "drained)"}
 
