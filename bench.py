@@ -505,7 +505,7 @@ def job_throughput(units_per_rank, world, ms_max):
     return world * units_per_rank / (ms_max / 1000.0)
 
 
-def cpu_throttle():
+def cpu_throttle(root="/sys/fs/cgroup"):
     """The process's CPU-bandwidth throttling counters from its cgroup (v2
     cpu.stat / cpu.max, else v1 cpu/cpu.stat and the CFS quota): throttled
     periods, throttled milliseconds and the quota in CPUs (None: no quota).
@@ -516,14 +516,14 @@ def cpu_throttle():
                 return f.read()
         except OSError:
             return None
-    stat, scale, quota = read("/sys/fs/cgroup/cpu.stat"), 1e-3, None
+    stat, scale, quota = read(os.path.join(root, "cpu.stat")), 1e-3, None
     if stat is not None and "nr_throttled" in stat:
-        m = (read("/sys/fs/cgroup/cpu.max") or "").split()
+        m = (read(os.path.join(root, "cpu.max")) or "").split()
         if len(m) == 2 and m[0] != "max":
             quota = float(m[0]) / float(m[1])
     else:
-        stat, scale = read("/sys/fs/cgroup/cpu/cpu.stat"), 1e-6
-        q, per = read("/sys/fs/cgroup/cpu/cpu.cfs_quota_us"), read("/sys/fs/cgroup/cpu/cpu.cfs_period_us")
+        stat, scale = read(os.path.join(root, "cpu", "cpu.stat")), 1e-6
+        q, per = read(os.path.join(root, "cpu", "cpu.cfs_quota_us")), read(os.path.join(root, "cpu", "cpu.cfs_period_us"))
         if q and per and int(q) > 0:
             quota = int(q) / int(per)
     if not stat:
