@@ -48,10 +48,15 @@ LEVELS, ITERS = 3, (10, 5, 4)
 FPS = 30.0
 N_UNIQUE = 100
 SEQ_SEED = 2
-# algorithmic bytes per pixel-iteration, FP32 maps: live pack A (normal + depth,
-# 16 B) and intensity (4 B); reference pack A (16 B) and the used 12 B of pack B
-# (intensity + gradient)
-BYTES_PER_PIXEL_ITER = 48
+# Algorithmic bytes per pixel-iteration (the method's unique reads, FP32 maps):
+# live depth 4, intensity 4 and normal 12; reference vertex 12, normal 12,
+# intensity 4 and gradient 8.  FP16 normal and gradient maps: 40 B.  The
+# kernel itself reads 48 B (32 B with FP16 maps): it keeps the reference as
+# depth + normal in its own camera and rebuilds the vertex from the depth.
+BYTES_PER_PIXEL_ITER = 56
+BYTES_PER_PIXEL_ITER_FP16 = 40
+KERNEL_BYTES_PER_PIXEL_ITER = 48
+KERNEL_BYTES_PER_PIXEL_ITER_FP16 = 32
 PIXEL_ITERS_PER_FRAME = sum((W >> l) * (H >> l) * ITERS[l] for l in range(LEVELS))
 BATCH = 64
 BATCH_OFFSET = 37             # stream i starts at frame (37 i) mod 100 of the loop
@@ -375,8 +380,9 @@ def run_reference(args):
         "value": value, "unit": "frames/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * el / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_json(),
+        "data": "synthetic", "config": config_json(args),
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                         "impl": "FP64 numpy oracle (vectorised over pixels; not a C++ program)",
                          "sample": f"per step one oracle Gauss-Newton iteration on {rows} level-0 rows "
                                    f"of a 640x480 frame; frames/s = pixel-iterations/s / "
                                    f"{PIXEL_ITERS_PER_FRAME}"},
@@ -392,7 +398,9 @@ def dtype_of(flags):
     return f"{maps}f32 per-pixel, {red} reduction, f64 solve"
 
 
-def config_json(batch=BATCH):
+def config_json(args):
+    """The workload of the line, the same for both arms."""
+    batch = args.batch
     return {"workload": f"{batch} independent streams of 640x480 RGB-D + 400 Hz IMU per step "
                         f"(one dri_track_batch call), 3 levels 10/5/4 GN iterations; plain: one "
                         f"stream, one frame per step",
@@ -400,7 +408,9 @@ def config_json(batch=BATCH):
             "global_batch": batch, "seq_len": 1, "parallelism": "replicas (independent streams per GPU)",
             "width": W, "height": H, "levels": LEVELS, "iters": list(ITERS),
             "l2": "inputs larger than L2 (100 distinct frames, 245 MB, cycled; a batched step "
-                  f"reads {min(batch, N_UNIQUE)} of them)"}
+                  f"reads {min(batch, N_UNIQUE)} of them)",
+            "imu_mode": args.imu_mode, "occlusion_thr": args.occlusion_thr,
+            "precision_flags": args.precision_flags}
 
 
 def initial_state_at(seq, i):
@@ -418,29 +428,48 @@ def kernel_classes(prof, dri):
                             ("grad", dri.DRI_KC_GRAD))}
 
 
-def roofline(prof, dri, traffic_bpp):
+def bytes_per_pixel_iter(flags):
+    """(algorithmic, kernel) bytes per pixel-iteration for the precision flags."""
+    if flags & 1:
+        return BYTES_PER_PIXEL_ITER_FP16, KERNEL_BYTES_PER_PIXEL_ITER_FP16
+    return BYTES_PER_PIXEL_ITER, KERNEL_BYTES_PER_PIXEL_ITER
+
+
+def roofline(prof, dri, traffic_bpp, n_streams, ms_per_step, flags=0):
+    """The pixel kernel against HBM: `frac` from its launches timed one by one
+    with CUDA events (the profiled pass: slot groups one after the other), and
+    `step_frac` from the timed region (every pixel kernel's bytes of a step over
+    the step's time, in which the groups' pixel kernels overlap one another and
+    the FP64 steps; a lower bound of the kernel's bandwidth in the timed run)."""
     t_ms = prof.ms[dri.DRI_KC_TRACK]
     px = prof.pixels[dri.DRI_KC_TRACK]
     n = max(1, prof.launches[dri.DRI_KC_TRACK])
-    achieved = BYTES_PER_PIXEL_ITER * px / (t_ms / 1000.0) / 1e9
+    bpp, kbpp = bytes_per_pixel_iter(flags)
+    achieved = bpp * px / (t_ms / 1000.0) / 1e9
+    step_px = PIXEL_ITERS_PER_FRAME * n_streams
+    step_achieved = bpp * step_px / (ms_per_step / 1000.0) / 1e9
     peak, peak_kind = measured_peaks()
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind,
             "kernel": "k_track_batch (fused photometric + ICP linearisation)",
-            "bytes_per_pixel_iter": BYTES_PER_PIXEL_ITER, "avg_launch_us": 1000.0 * t_ms / n,
+            "bytes_per_pixel_iter": bpp, "avg_launch_us": 1000.0 * t_ms / n,
             "pixel_iters_per_launch": px / n,
+            "step_achieved": step_achieved, "step_frac": step_achieved / peak,
+            "step_pixel_iters": step_px, "ms_per_step": ms_per_step,
+            "kernel_bytes_per_pixel_iter": kbpp, "kernel_bytes_frac": achieved * kbpp / bpp / peak,
             "traffic": None if traffic_bpp is None else traffic_bpp * px / n}
 
 
-def step_bandwidth(n_streams, ms_per_step):
+def step_bandwidth(n_streams, ms_per_step, flags=0):
     """The pixel kernels' algorithmic bytes of one timed step over the step's
     time: a lower bound of their bandwidth as they run in the timed region,
     where the slot groups' pixel kernels overlap one another and the FP64
     steps (the roofline's per-launch figure times launches in isolation)."""
     peak, peak_kind = measured_peaks()
-    achieved = BYTES_PER_PIXEL_ITER * PIXEL_ITERS_PER_FRAME * n_streams / (ms_per_step / 1000.0) / 1e9
+    bpp, _ = bytes_per_pixel_iter(flags)
+    achieved = bpp * PIXEL_ITERS_PER_FRAME * n_streams / (ms_per_step / 1000.0) / 1e9
     return {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_kind": peak_kind}
+            "peak_kind": peak_kind, "bytes_per_pixel_iter": bpp}
 
 
 class Runner:
@@ -913,11 +942,13 @@ def run_ours(args):
             "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
             "slowest_steps": [[int(k), float(per[k])] for k in np.argsort(per)[::-1][:5]],
             "gpu_launches": int(launches), "frames_ok": int(ok), "frames_failed": int(failed),
-            "roofline": roofline(prof, dri, track_traffic()), "kernel_classes": kernel_classes(prof, dri),
+            "roofline": roofline(prof, dri, track_traffic(), n_streams, total_ms / steps,
+                                 args.precision_flags),
+            "kernel_classes": kernel_classes(prof, dri),
             "e2e": {"value": world * n_streams * e2e_steps / e2e_s, "unit": "frames/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "clocks": clocks, "rows_per_thread": tiles[:LEVELS], "groups": opts.groups,
-            "step_bandwidth": step_bandwidth(n_streams, total_ms / steps),
+            "step_bandwidth": step_bandwidth(n_streams, total_ms / steps, args.precision_flags),
         }
         run.close()
         del run
@@ -960,8 +991,7 @@ def run_ours(args):
         "value": b["value"], "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_of(args.precision_flags),
-        "data": "synthetic", "config": dict(config_json(args.batch), imu_mode=args.imu_mode,
-                                            occlusion_thr=args.occlusion_thr),
+        "data": "synthetic", "config": config_json(args),
         "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"], "slowest_steps": b["slowest_steps"],
         "gpu_launches": b["gpu_launches"],
         "frames_failed": b["frames_failed"], "frames_ok": b["frames_ok"],
@@ -981,6 +1011,7 @@ def run_ours(args):
             rgbd_only_report(seq, odo_occ), occlusion_thr_m=ODOMETRY_OCCLUSION_THR),
         "precision": precision,
         "cpu_baseline": {"value": o_fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                         "impl": "FP64 numpy oracle (vectorised over pixels; not a C++ program)",
                          "sample": f"{o_n} whole frames of the same sequence tracked by the FP64 "
                                    f"numpy oracle in {o_t:.1f} s"},
         "cpu_baseline_all_cores": {"value": a_fps, "unit": "frames/s", "cores": n_cores, "kind": "oracle",

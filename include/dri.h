@@ -424,8 +424,10 @@ int dri_profile_read(dri_stream s, dri_profile* out);
  * capture).  Creating a stream allocates, so such code cannot use the stream
  * API on the fly; this call needs only the caller's buffers.
  *
- * Inputs: cfg (intrinsics of the images, sigma_I, sigma_d, ICP thresholds and
- * the depth range; levels, iterations and IMU fields are ignored); the
+ * Inputs: cfg (intrinsics of the images, sigma_I, sigma_d, ICP thresholds, the
+ * depth range, precision_flags, occlusion_thr and icp_depth_weight, each with
+ * the meaning it has for a stream; levels, iterations and IMU fields are
+ * ignored); the
  * reference and live depth / intensity images, width * height FP32 each,
  * row-major, packed, in device memory; the pose the reference images were taken
  * at (x_ref) and the states x0, x1 to linearise at.  Output (device memory):
@@ -435,11 +437,17 @@ int dri_profile_read(dri_stream s, dri_profile* out);
  * flags (nullable, device, width * height bytes) the per-pixel validity bits.
  * Work is enqueued on cuda_stream; the call does not wait.
  *
+ * DRI_EINVAL for a NULL argument, an option value a stream would reject, or a
+ * state that is not finite or whose q_WC is zero.
+ *
  * Every intermediate (normal and gradient maps, per-block partial sums, the
- * block counter and per-call transforms) lives in one static device array that
- * the library reserves when it is loaded (about 4.0 MB per GPU, held until the
- * process exits), sized for at most 320 x 240 pixels: larger images return
- * DRI_EINVAL.  The array is shared by all calls on a device and keeps the last
+ * block counter and per-call transforms) lives in one static device array of
+ * the library (about 4.0 MB per GPU, held until the process exits), sized for
+ * at most 320 x 240 pixels: larger images return DRI_EINVAL.  The CUDA runtime
+ * reserves the array when it loads the library's device code on a GPU; with
+ * lazy module loading (the default since CUDA 12.2) that is the first call made
+ * with that GPU current, so the first call reserves it and later calls reserve
+ * nothing.  The array is shared by all calls on a device and keeps the last
  * call's contents; each call clears what must start at zero.  Calls whose GPU
  * work overlaps race on it: order them on one stream.  The first call made with
  * a device current looks up the array's device address for that device

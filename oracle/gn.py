@@ -195,9 +195,11 @@ class Tracker:
             W_imu = imu_mod.weight_gyro_only(S_imu)
         x1 = self.first_iterate(x0, pre)
         counts = {}
+        points = {}                              # per level: the last (x0, x1) linearised at
         H = b = d = None
         for l in range(cfg.levels - 1, -1, -1):
             for _ in range(cfg.iters[l]):
+                points[l] = (x0.copy(), x1.copy())
                 H, b, parts = self.linearise_all(levels, l, x0, x1, t0, t1, W_imu)
                 counts[l] = (parts["lin"]["n_icp"], parts["lin"]["n_rgb"])
                 try:
@@ -223,7 +225,7 @@ class Tracker:
         self.ref = reference_from_frame(levels, *self.T_ref, fp16=self.cfg.fp16_maps)
         keep = np.searchsorted(self.imu[:, 0], t1, side="right") - 1
         self.imu = self.imu[max(keep, 0):]
-        return dict(status="ok", x0=x0, x1=x1, counts=counts, H=H, b=b, d_last=d,
+        return dict(status="ok", x0=x0, x1=x1, counts=counts, points=points, H=H, b=b, d_last=d,
                     H_prior=Hs, b_prior=bs)
 
     def track_pose_only(self, levels, t):

@@ -1371,19 +1371,33 @@ int dri_linearise(dri_stream s, int32_t level, const dri_state* x0, const dri_st
     CK(launch(s, DRI_KC_MAPS, 0.0,
               [&] { return launch_normals_batch(a, p->pre_map[l][1], p->fp16, s->stream); }));
   }
-  s->launches += 1 + 2 * L - 1 + 3;
   const SolveParams sp = solve_params(s, level, 0);
-  const TrackParams tp = track_params(s, level, s->ppt[level], flags ? s->flags : nullptr);
   CK(launch(s, DRI_KC_FRAME, 0.0,
             [&] { return launch_linearise_begin(sp, to_dstate(*x0), to_dstate(*x1), s->stream); }));
-  CK(launch(s, DRI_KC_TRACK, (double)tp.g.w * tp.g.h,
-            [&] { return launch_track(tp, p->fp16, p->fp32p, s->stream); }));
-  CK(launch(s, DRI_KC_SOLVE, 0.0, [&] { return launch_linearise_end(sp, s->lin_dev, s->stream); }));
-  CK(cudaMemcpyAsync(out, s->lin_dev, sizeof(*out), cudaMemcpyDeviceToHost, s->stream));
+  // The pixel terms come from the batched kernel that tracking runs, over the
+  // stream's own one-slot plan (its rows per thread included).  The per-pixel
+  // validity bits come from the same kernel's flag-writing instantiation,
+  // launched first; the production instantiation then recomputes the sums the
+  // system is assembled from.
+  const BatchArgs at = plan_args(p, track_start(p, level, 0), level, 0, 0, 1);
+  const int nb = track_blocks(p, level, 0);
+  const double px = (double)s->geom[level].w * s->geom[level].h;
+  const size_t nflags = (size_t)s->geom[level].w * s->geom[level].h;
   if (flags) {
-    const size_t n = (size_t)s->geom[level].w * s->geom[level].h;
-    CK(cudaMemcpyAsync(flags, s->flags, n, cudaMemcpyDeviceToHost, s->stream));
+    BatchArgs af = at;
+    af.flags = s->flags;
+    CK(cudaMemsetAsync(s->flags, 0, nflags, s->stream));
+    CK(launch(s, DRI_KC_TRACK, px, [&] {
+      return launch_track_batch(af, nb, p->fp16, p->fp32p, p->opt, launch_priority(false), false, s->stream);
+    }));
   }
+  CK(launch(s, DRI_KC_TRACK, px, [&] {
+    return launch_track_batch(at, nb, p->fp16, p->fp32p, p->opt, launch_priority(false), false, s->stream);
+  }));
+  CK(launch(s, DRI_KC_SOLVE, 0.0, [&] { return launch_linearise_end(sp, s->lin_dev, s->stream); }));
+  s->launches += 1 + 2 * L - 1 + 3 + (flags ? 1 : 0);
+  CK(cudaMemcpyAsync(out, s->lin_dev, sizeof(*out), cudaMemcpyDeviceToHost, s->stream));
+  if (flags) CK(cudaMemcpyAsync(flags, s->flags, nflags, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaMemcpyAsync(s->pin_ctrl, s->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   return s->pin_ctrl->status;

@@ -196,6 +196,8 @@ struct BatchArgs {
   int32_t nslots;
   int32_t level;
   int32_t last;                       // 1 on the frame's last Gauss-Newton iteration
+  uint8_t* flags;                     // pixel kernel, parity entry only: per-pixel validity bits
+                                      // (one slot, zeroed before the launch); nullptr otherwise
 };
 
 // Index (0 .. nslots - 1, relative to slot0) of the launch slot owning `block`.

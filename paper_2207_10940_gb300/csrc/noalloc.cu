@@ -10,7 +10,11 @@
 // and a caller-owned device output and keeps every intermediate it needs (the
 // normal and gradient maps, the pixel kernel's per-block partial sums and its
 // completion counter, the per-call transforms) in one file-scope static device
-// array, reserved when the library is loaded and held until the process exits.
+// array, held until the process exits.  The array is device memory of the
+// library's module: the CUDA runtime reserves it when it loads the module on a
+// device, which with lazy module loading (the default since CUDA 12.2) happens
+// at the first call made with that device current, so that first call itself
+// reserves about 4 MB; later calls reserve nothing.
 //
 // Limits and rules:
 //  * at most kNoallocMaxPixels = 320 * 240 pixels per image; larger images are
@@ -129,6 +133,20 @@ __global__ void k_noalloc_end(const Ctrl* c, double W_icp, double W_rgb, dri_lin
   }
 }
 
+// A state the kernels can use: finite, with a non-zero orientation quaternion.
+bool usable_state(const dri_state& s) {
+  double nq = 0.0;
+  for (int i = 0; i < 4; ++i) nq += s.q_WC[i] * s.q_WC[i];
+  if (!(nq > 0.0) || !std::isfinite(nq)) return false;
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(s.r_WC[i]) || !std::isfinite(s.v_I[i]) || !std::isfinite(s.bg[i]) ||
+        !std::isfinite(s.ba[i]))
+      return false;
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(s.q_IW[i])) return false;
+  return true;
+}
+
 DState dstate_of(const dri_state& s) {
   DState d;
   for (int i = 0; i < 3; ++i) {
@@ -185,6 +203,13 @@ extern "C" int dri_linearise_pair_noalloc(const dri_stream_config* cfg, const fl
   if (!(cfg->fx > 0) || !(cfg->fy > 0) || !(cfg->sigma_I > 0) || !(cfg->sigma_d > 0) ||
       !(cfg->depth_max > cfg->depth_min) || !(cfg->icp_dist_thr > 0))
     return DRI_EINVAL;
+  if ((cfg->precision_flags & ~(DRI_FP16_MAPS | DRI_FP32_PARTIALS)) != 0 ||
+      !(cfg->occlusion_thr >= 0.0) || !std::isfinite(cfg->occlusion_thr) ||
+      (cfg->icp_depth_weight != 0 && cfg->icp_depth_weight != 1))
+    return DRI_EINVAL;
+  if (!usable_state(*x_ref) || !usable_state(*x0) || !usable_state(*x1)) return DRI_EINVAL;
+  const bool fp16 = (cfg->precision_flags & DRI_FP16_MAPS) != 0;
+  const bool fp32p = (cfg->precision_flags & DRI_FP32_PARTIALS) != 0;
   unsigned char* base = nullptr;
   const int r = scratch_address(&base);
   if (r != DRI_OK) return r;
@@ -207,9 +232,9 @@ extern "C" int dri_linearise_pair_noalloc(const dri_stream_config* cfg, const fl
   k_noalloc_begin<<<1, 32, 0, s>>>(ctrl, counters, dstate_of(*x_ref), dstate_of(*x0), dstate_of(*x1));
   if (cudaGetLastError() != cudaSuccess) return DRI_ECUDA;
   const float dmin = (float)cfg->depth_min, dmax = (float)cfg->depth_max;
-  if (launch_normals(m, ctrl, g, dmin, dmax, false, 0, s) != cudaSuccess) return DRI_ECUDA;
-  if (launch_normals(m, ctrl, g, dmin, dmax, false, 1, s) != cudaSuccess) return DRI_ECUDA;
-  if (launch_gradient(m, ctrl, g.w, g.h, false, s) != cudaSuccess) return DRI_ECUDA;
+  if (launch_normals(m, ctrl, g, dmin, dmax, fp16, 0, s) != cudaSuccess) return DRI_ECUDA;
+  if (launch_normals(m, ctrl, g, dmin, dmax, fp16, 1, s) != cudaSuccess) return DRI_ECUDA;
+  if (launch_gradient(m, ctrl, g.w, g.h, fp16, s) != cudaSuccess) return DRI_ECUDA;
 
   TrackParams p;
   std::memset(&p, 0, sizeof(p));
@@ -227,7 +252,9 @@ extern "C" int dri_linearise_pair_noalloc(const dri_stream_config* cfg, const fl
   p.depth_max = dmax;
   p.icp_dist2 = (float)(cfg->icp_dist_thr * cfg->icp_dist_thr);
   p.icp_cos = (float)std::cos(cfg->icp_angle_thr_deg * 3.14159265358979323846 / 180.0);
-  if (launch_track(p, false, false, s) != cudaSuccess) return DRI_ECUDA;
+  p.occ_thr = (float)cfg->occlusion_thr;
+  p.icp_dw = cfg->icp_depth_weight;
+  if (launch_track(p, fp16, fp32p, s) != cudaSuccess) return DRI_ECUDA;
   k_noalloc_end<<<1, 128, 0, s>>>(ctrl, 1.0 / (cfg->sigma_d * cfg->sigma_d),
                                   1.0 / (cfg->sigma_I * cfg->sigma_I), out);
   if (cudaGetLastError() != cudaSuccess) return DRI_ECUDA;

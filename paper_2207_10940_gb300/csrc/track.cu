@@ -256,7 +256,12 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int term,
       ok = icp ? icp_pixel<T, (OPT & kOptDepthWeight) != 0>(p, g, A, t, A0, D0, u, v, cur, acc)
                : rgb_pixel<T, (OPT & kOptOcc) != 0>(g, A, t, B0, D0, p.occ_thr, u, v, cur, acc);
     }
-    if (FLAGS) {             // bit 0 ICP, bit 1 photometric, combined through shared memory
+    if (FLAGS && SPLIT) {    // bit 0 ICP, bit 1 photometric, or-ed into the zeroed flag bytes
+      if (ok) {
+        const int o = v * g.w + u;
+        atomicOr(reinterpret_cast<unsigned int*>(p.flags + (o & ~3)), (icp ? 1u : 2u) << (8 * (o & 3)));
+      }
+    } else if (FLAGS) {      // bit 0 ICP, bit 1 photometric, combined through shared memory
       if (icp) s_flag[wrow][lane] = ok ? 1 : 0;
       __syncthreads();
       if (!icp && col_ok && v < g.h) p.flags[v * g.w + u] = (uint8_t)(s_flag[wrow][lane] | (ok ? 2 : 0));
@@ -349,7 +354,9 @@ k_track(TrackParams p) {
 // through the block prefix, tile -> (column, row band) in the slot's image.
 // Three blocks per SM (80 registers) measured faster than four (64 registers,
 // more spill reloads) and than two columns per thread.
-template <typename T, typename P, int OPT>
+// FLAGS (parity entry only): the same kernel that also or-s each pixel's
+// validity bits into a.flags (the slot's level image, zeroed before the launch).
+template <typename T, typename P, int OPT, bool FLAGS>
 __global__ void __launch_bounds__(kTrackThreadsX * kTrackThreadsY, 3)
 k_track_batch(const BatchArgs a) {
   const int i = batch_slot(a, blockIdx.x);
@@ -362,12 +369,14 @@ k_track_batch(const BatchArgs a) {
     reinterpret_cast<uint32_t*>(&p)[tid] =
         __ldg(reinterpret_cast<const uint32_t*>(&a.slots[slot].tp[a.level]) + tid);
   __syncthreads();
+  if (FLAGS && tid == 0) p.flags = a.flags;
+  if (FLAGS) __syncthreads();
   grid_dep_wait();               // the transforms of the preceding Gauss-Newton step
   grid_dep_launch();             // the next step's state-only work may start now
   const int t = blockIdx.x - __ldg(a.start + i);
   const int gx = (p.g.w + kTrackThreadsX - 1) / kTrackThreadsX;
   const int tile = t >> 1;                    // the two terms of a tile are neighbours
-  track_tile<T, P, false, true, OPT>(p, t & 1, tile % gx, tile / gx, t);
+  track_tile<T, P, FLAGS, true, OPT>(p, t & 1, tile % gx, tile / gx, t);
 }
 
 }  // namespace
@@ -439,12 +448,17 @@ cudaError_t launch_track_batch(const BatchArgs& a, int blocks, bool fp16, bool f
   attr[1].val.priority = priority;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
+#define DRI_TRACK_BATCH_F(T, P, F)                                                       \
+  do {                                                                                   \
+    if (opt == 0) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 0, F>, a);         \
+    if (opt == 1) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 1, F>, a);         \
+    if (opt == 2) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 2, F>, a);         \
+    return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 3, F>, a);                       \
+  } while (0)
 #define DRI_TRACK_BATCH(T, P)                                                            \
   do {                                                                                   \
-    if (opt == 0) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 0>, a);            \
-    if (opt == 1) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 1>, a);            \
-    if (opt == 2) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 2>, a);            \
-    return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 3>, a);                          \
+    if (a.flags) DRI_TRACK_BATCH_F(T, P, true);                                          \
+    DRI_TRACK_BATCH_F(T, P, false);                                                      \
   } while (0)
   if (fp16) {
     if (fp32_partials) DRI_TRACK_BATCH(__half, float);
@@ -453,6 +467,7 @@ cudaError_t launch_track_batch(const BatchArgs& a, int blocks, bool fp16, bool f
   if (fp32_partials) DRI_TRACK_BATCH(float, float);
   DRI_TRACK_BATCH(float, double);
 #undef DRI_TRACK_BATCH
+#undef DRI_TRACK_BATCH_F
 }
 
 }  // namespace dri

@@ -234,10 +234,12 @@ def dri_create_stream(cfg, x_init, cuda_stream=None, workspace=None, workspace_b
                                             ctypes.c_void_p(cs or 0), ctypes.c_void_p(ws or 0),
                                             ctypes.c_size_t(workspace_bytes), ctypes.byref(h)),
            "dri_create_stream")
+    _shapes[h.value] = (int(cfg.width), int(cfg.height))
     return h
 
 
 def dri_destroy_stream(s):
+    _shapes.pop(_hval(s), None)
     return _check(load_library().dri_destroy_stream(s), "dri_destroy_stream")
 
 
@@ -247,19 +249,68 @@ def _ptr(a):
     return a.ctypes.data
 
 
+# (width, height) of each open stream handle, for the argument checks below
+_shapes = {}
+
+
+def _hval(s):
+    s = getattr(s, "handle", s)
+    return s.value if isinstance(s, ctypes.c_void_p) else s
+
+
+def _buffer(a, name, dtype, n_min, device):
+    """Pointer of an image or output argument after checking it: a torch tensor
+    must be on the GPU exactly when `device` is set, contiguous, of `dtype`
+    ("float32" or "uint8") and hold at least n_min elements; a numpy array must
+    be host memory (device unset), C-contiguous, of `dtype`, large enough.  A
+    raw integer pointer is passed as it is (the caller vouches for it)."""
+    if isinstance(a, (int, ctypes.c_void_p)):
+        return a.value if isinstance(a, ctypes.c_void_p) else a
+    if hasattr(a, "data_ptr"):
+        if bool(a.is_cuda) != bool(device):
+            raise DriError(DRI_EINVAL, f"{name}: a {'device' if device else 'host'} tensor is required")
+        if not a.is_contiguous():
+            raise DriError(DRI_EINVAL, f"{name}: tensor must be contiguous")
+        if str(a.dtype) != "torch." + dtype:
+            raise DriError(DRI_EINVAL, f"{name}: dtype must be {dtype}")
+        if a.numel() < n_min:
+            raise DriError(DRI_EINVAL, f"{name}: {a.numel()} elements, at least {n_min} needed")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if device:
+            raise DriError(DRI_EINVAL, f"{name}: device memory is required")
+        if not a.flags.c_contiguous:
+            raise DriError(DRI_EINVAL, f"{name}: host arrays must be C-contiguous")
+        if a.dtype != np.dtype(dtype):
+            raise DriError(DRI_EINVAL, f"{name}: dtype must be {dtype}")
+        if a.size < n_min:
+            raise DriError(DRI_EINVAL, f"{name}: {a.size} elements, at least {n_min} needed")
+        return a.ctypes.data
+    raise TypeError(f"{name}: expected a torch tensor, a numpy array or a pointer")
+
+
+def _image_elems(s, pitch_bytes):
+    """Floats an image of stream s spans (rows pitch_bytes apart), or 0 if the
+    stream's size is unknown here."""
+    wh = _shapes.get(_hval(s))
+    if wh is None:
+        return 0
+    w, h = wh
+    pitch = pitch_bytes // 4 if pitch_bytes else w
+    return (h - 1) * pitch + w
+
+
 def dri_upload_frame(s, t, depth, intensity, pitch_bytes=0, mem_kind=None):
-    """depth / intensity: float32 numpy arrays (host) or torch tensors (host or device)."""
+    """depth / intensity: float32 numpy arrays (host) or torch tensors (host or
+    device) of at least the stream's image size; checked before the call."""
     if mem_kind is None:
         mem_kind = DRI_DEVICE if (hasattr(depth, "is_cuda") and depth.is_cuda) else DRI_HOST
-    for a in (depth, intensity):
-        dt = getattr(a, "dtype", None)
-        if str(dt) not in ("float32", "torch.float32"):
-            raise TypeError("depth and intensity must be float32")
-    if isinstance(depth, np.ndarray) and not (depth.flags.c_contiguous and intensity.flags.c_contiguous):
-        raise ValueError("host arrays must be C-contiguous")
-    return _check(load_library().dri_upload_frame(s, float(t), ctypes.c_void_p(_ptr(depth)),
-                                                  ctypes.c_void_p(_ptr(intensity)), pitch_bytes,
-                                                  mem_kind), "dri_upload_frame")
+    n = _image_elems(s, pitch_bytes)
+    dev = mem_kind == DRI_DEVICE
+    pd = _buffer(depth, "depth", "float32", n, dev)
+    pi = _buffer(intensity, "intensity", "float32", n, dev)
+    return _check(load_library().dri_upload_frame(s, float(t), ctypes.c_void_p(pd), ctypes.c_void_p(pi),
+                                                  pitch_bytes, mem_kind), "dri_upload_frame")
 
 
 def dri_upload_reference(s, vertex_W, normal_W, intensity, T_WC_ref, pitch_px=0, mem_kind=None):
@@ -267,16 +318,17 @@ def dri_upload_reference(s, vertex_W, normal_W, intensity, T_WC_ref, pitch_px=0,
     or CUDA tensors (device); T_WC_ref: r (3) + q (w, x, y, z)."""
     if mem_kind is None:
         mem_kind = DRI_DEVICE if (hasattr(vertex_W, "is_cuda") and vertex_W.is_cuda) else DRI_HOST
-    for a in (vertex_W, normal_W, intensity):
-        if str(getattr(a, "dtype", None)) not in ("float32", "torch.float32"):
-            raise TypeError("reference maps must be float32")
-        if isinstance(a, np.ndarray) and not a.flags.c_contiguous:
-            raise ValueError("host arrays must be C-contiguous")
+    n = _image_elems(s, 4 * pitch_px)
+    dev = mem_kind == DRI_DEVICE
+    pv = _buffer(vertex_W, "vertex_W", "float32", 3 * n, dev)
+    pn = _buffer(normal_W, "normal_W", "float32", 3 * n, dev)
+    pi = _buffer(intensity, "intensity", "float32", n, dev)
     T = np.ascontiguousarray(T_WC_ref, dtype=np.float64)
+    if T.size != 7:
+        raise DriError(DRI_EINVAL, "T_WC_ref: 7 values (r, q) are required")
     return _check(load_library().dri_upload_reference(
-        s, ctypes.c_void_p(_ptr(vertex_W)), ctypes.c_void_p(_ptr(normal_W)),
-        ctypes.c_void_p(_ptr(intensity)), T.ctypes.data_as(c_double_p), pitch_px, mem_kind),
-        "dri_upload_reference")
+        s, ctypes.c_void_p(pv), ctypes.c_void_p(pn), ctypes.c_void_p(pi), T.ctypes.data_as(c_double_p),
+        pitch_px, mem_kind), "dri_upload_reference")
 
 
 def imu_array(samples):
@@ -394,19 +446,21 @@ def dri_launch_count(s):
 
 def dri_linearise_pair_noalloc(cfg, ref_depth, ref_intensity, live_depth, live_intensity, x_ref,
                                x0, x1, out_ptr, flags_ptr=None, cuda_stream=None):
-    """All image and output arguments are device pointers (ints) or CUDA tensors;
-    out_ptr points to device memory of sizeof(dri_linearisation) bytes."""
+    """All image and output arguments are device pointers (ints) or CUDA tensors.
+    Tensors are checked before the call: images float32 with cfg.width *
+    cfg.height elements, out_ptr uint8 with sizeof(dri_linearisation) bytes,
+    flags_ptr uint8 with cfg.width * cfg.height bytes."""
     cs = getattr(cuda_stream, "cuda_stream", cuda_stream)
+    n = int(cfg.width) * int(cfg.height)
+    imgs = [_buffer(a, k, "float32", n, True) for a, k in
+            ((ref_depth, "ref_depth"), (ref_intensity, "ref_intensity"), (live_depth, "live_depth"),
+             (live_intensity, "live_intensity"))]
+    out = _buffer(out_ptr, "out", "uint8", ctypes.sizeof(dri_linearisation), True)
+    flags = 0 if flags_ptr is None else _buffer(flags_ptr, "flags", "uint8", n, True)
     return _check(load_library().dri_linearise_pair_noalloc(
-        ctypes.byref(cfg), ctypes.c_void_p(_dev_ptr(ref_depth)), ctypes.c_void_p(_dev_ptr(ref_intensity)),
-        ctypes.c_void_p(_dev_ptr(live_depth)), ctypes.c_void_p(_dev_ptr(live_intensity)),
-        ctypes.byref(x_ref), ctypes.byref(x0), ctypes.byref(x1), ctypes.c_void_p(_dev_ptr(out_ptr)),
-        ctypes.c_void_p(_dev_ptr(flags_ptr) if flags_ptr is not None else 0),
-        ctypes.c_void_p(cs or 0)), "dri_linearise_pair_noalloc")
-
-
-def _dev_ptr(a):
-    return a.data_ptr() if hasattr(a, "data_ptr") else int(a)
+        ctypes.byref(cfg), *[ctypes.c_void_p(p) for p in imgs], ctypes.byref(x_ref), ctypes.byref(x0),
+        ctypes.byref(x1), ctypes.c_void_p(out), ctypes.c_void_p(flags), ctypes.c_void_p(cs or 0)),
+        "dri_linearise_pair_noalloc")
 
 
 def dri_frame_counts(s):
@@ -519,23 +573,30 @@ def dri_server_open_stream(srv, cfg, x_init):
     h = ctypes.c_void_p()
     _check(load_library().dri_server_open_stream(srv, ctypes.byref(cfg), ctypes.byref(x_init),
                                                  ctypes.byref(h)), "dri_server_open_stream")
+    _shapes[h.value] = (int(cfg.width), int(cfg.height))
     return h
 
 
 def dri_server_close_stream(srv, s):
+    _shapes.pop(_hval(s), None)
     return _check(load_library().dri_server_close_stream(srv, s), "dri_server_close_stream")
 
 
 def dri_server_submit(srv, s, t, depth, intensity, imu=(), pitch_bytes=0, mem_kind=None):
-    """Queues a frame; the images must stay alive until the ticket is done."""
+    """Queues a frame; the images (checked as in dri_upload_frame) must stay
+    alive until the ticket is done."""
     if mem_kind is None:
         mem_kind = DRI_DEVICE if (hasattr(depth, "is_cuda") and depth.is_cuda) else DRI_HOST
+    n_px = _image_elems(s, pitch_bytes)
+    dev = mem_kind == DRI_DEVICE
+    pd = _buffer(depth, "depth", "float32", n_px, dev)
+    pi = _buffer(intensity, "intensity", "float32", n_px, dev)
     arr = imu if isinstance(imu, ctypes.Array) else (imu_array(imu) if len(imu) else None)
     n = 0 if arr is None else len(arr)
     ticket = ctypes.c_uint64()
-    _check(load_library().dri_server_submit(srv, s, float(t), ctypes.c_void_p(_ptr(depth)),
-                                            ctypes.c_void_p(_ptr(intensity)), pitch_bytes, mem_kind,
-                                            arr, n, ctypes.byref(ticket)), "dri_server_submit")
+    _check(load_library().dri_server_submit(srv, s, float(t), ctypes.c_void_p(pd), ctypes.c_void_p(pi),
+                                            pitch_bytes, mem_kind, arr, n, ctypes.byref(ticket)),
+           "dri_server_submit")
     return ticket.value
 
 

@@ -1,0 +1,112 @@
+"""The pixel kernel that tracking runs (the batched kernel, through the stream's
+own one-slot plan) against the FP64 oracle at the benchmark's image sizes.
+
+dri_linearise evaluates the pixel terms with the same batched kernel and rows
+per thread that dri_track / dri_track_batch launch, so these tests compare the
+production kernel with the oracle per pixel and per system entry:
+
+* 640x480 with 32 / 32 / 8 rows per thread (the benchmark's tiles: 8,192
+  pixels summed in FP32 per thread group before the FP64 partial) and
+  1280x720 with 32 / 16 / 8, both with 1% of the depth pixels dropped (holes
+  that exercise depth validity in the pyramid, the normals and association);
+* at the oracle's last linearisation point of every pyramid level of a tracked
+  frame (Sec. IV-D), so the per-pixel validity that the oracle's per-level
+  counts come from is checked bit-exactly outside the margin pixels, and the
+  systems within the 1e-5 normalised bar (Eq. 7);
+* then the frame is tracked and its pose compared within 1e-6 rad / 1e-6 m.
+"""
+import copy
+
+import numpy as np
+import pytest
+
+from oracle import gn, imu, maps
+from oracle.so3 import State, boxminus, boxplus
+from paper_2207_10940_gb300 import dri, synth
+from parity import POSE_M, POSE_RAD, check_system, configs, new_stream, pose_error, to_dri, to_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _check_level(st, tr, seq, ocfg, level, x0, x1):
+    """dri_linearise at (x0, x1) against the oracle tracker `tr` (state before the
+    frame): validity per pixel outside margins, counts, systems."""
+    shape = (ocfg.height >> level, ocfg.width >> level)
+    out, flags = dri.dri_linearise(st.handle, level, to_dri(x0), to_dri(x1), want_flags=True, shape=shape)
+    lv = maps.frame_levels(seq.depth[1], seq.intensity[1], ocfg)
+    t0, t1 = seq.frame_times[0], seq.frame_times[1]
+    W, _ = imu.weight(x0, tr.imu, t0, t1, ocfg)
+    H, b, parts = tr.linearise_all(lv, level, x0, x1, t0, t1, W)
+    lin = parts["lin"]
+    gi, gr = (flags & 1) != 0, (flags & 2) != 0
+    mi, mr = lin["icp_margin"], lin["rgb_margin"]
+    bad_i = np.argwhere(gi[~mi] != lin["icp_valid"][~mi])
+    bad_r = np.argwhere(gr[~mr] != lin["rgb_valid"][~mr])
+    assert bad_i.size == 0, f"level {level}: ICP validity differs at {len(bad_i)} pixels"
+    assert bad_r.size == 0, f"level {level}: photometric validity differs at {len(bad_r)} pixels"
+    # the kernel's counts are the sums of its own validity bits, and differ from
+    # the oracle's only by margin pixels decided the other way
+    assert out.n_icp == gi.sum() and out.n_rgb == gr.sum()
+    assert abs(out.n_icp - lin["n_icp"]) <= (mi & (gi != lin["icp_valid"])).sum()
+    assert abs(out.n_rgb - lin["n_rgb"]) <= (mr & (gr != lin["rgb_valid"])).sum()
+    check_system(np.array(out.H_icp).reshape(6, 6), out.b_icp, lin["H_icp"], lin["b_icp"],
+                 lin["cost_icp"], what=f"ICP level {level}")
+    check_system(np.array(out.H_rgb).reshape(6, 6), out.b_rgb, lin["H_rgb"][6:, 6:], lin["b_rgb"][6:],
+                 lin["cost_rgb"], what=f"RGB level {level}")
+    d = boxminus(x0, tr.xbar)
+    cost = lin["cost_icp"] + lin["cost_rgb"] + parts["cost_imu"] + float(d @ tr.Hs @ d)
+    check_system(np.array(out.H).reshape(34, 34), out.b, H, b, cost, what=f"joint level {level}")
+    return lin
+
+
+def _full_size_case(cam, seed, rows):
+    _torch()
+    seq = synth.frame_pair(seed=seed, cam=cam, dropout=0.01)
+    assert (seq.depth[1] == 0).mean() > 0.005                 # the holes are there
+    ocfg, dcfg = configs(seq, 3, (10, 5, 4))
+    x_init = synth.initial_state(seq)
+    st = new_stream(dcfg, x_init)
+    dri.dri_batch_set_options([st.handle], rows_per_thread=rows)
+    assert list(dri.dri_batch_get_options([st.handle]).rows_per_thread)[:3] == list(rows)
+    dri.dri_push_imu(st.handle, seq.imu)
+    dri.dri_upload_frame(st.handle, seq.frame_times[0], seq.depth[0], seq.intensity[0])
+    assert dri.dri_track(st.handle).initialised == 1
+    dri.dri_upload_frame(st.handle, seq.frame_times[1], seq.depth[1], seq.intensity[1])
+    tr = gn.Tracker(ocfg, x_init)
+    tr.push_imu(seq.imu)
+    tr.track(seq.depth[0], seq.intensity[0], seq.frame_times[0])
+    before = copy.deepcopy(tr)
+    ores = tr.track(seq.depth[1], seq.intensity[1], seq.frame_times[1])
+    for level in (2, 1, 0):
+        x0, x1 = ores["points"][level]
+        lin = _check_level(st, before, seq, ocfg, level, x0, x1)
+        assert (lin["n_icp"], lin["n_rgb"]) == ores["counts"][level]
+    # a perturbed state at level 0 as well (projections away from the optimum)
+    rng = np.random.default_rng(seed)
+    gt0, gt1 = State.from_dict(seq.gt[0]), State.from_dict(seq.gt[1])
+    _check_level(st, before, seq, ocfg, 0, boxplus(gt0, rng.normal(size=17) * 1e-3),
+                 boxplus(gt1, rng.normal(size=17) * 5e-3))
+    res = dri.dri_track(st.handle)
+    assert res.status == 0
+    da, dr = pose_error(res.x1, ores["x1"])
+    assert da < POSE_RAD and dr < POSE_M, (da, dr)
+    x1 = to_oracle(res.x1)
+    np.testing.assert_allclose(x1.v, ores["x1"].v, atol=1e-5)
+    np.testing.assert_allclose(x1.bg, ores["x1"].bg, atol=1e-6)
+    np.testing.assert_allclose(x1.ba, ores["x1"].ba, atol=1e-5)
+    st.close()
+
+
+def test_production_kernel_matches_oracle_640x480_with_holes():
+    _full_size_case(synth.CAM_640, 11, (32, 32, 8))
+
+
+def test_production_kernel_matches_oracle_1280x720_with_holes():
+    _full_size_case(synth.CAM_1280, 12, (32, 16, 8))

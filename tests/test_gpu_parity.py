@@ -109,8 +109,16 @@ def test_track_pair_matches_oracle():
         assert abs(res.n_icp[l] - n_icp) <= max(3, 1e-3 * n_icp)
         assert abs(res.n_rgb[l] - n_rgb) <= max(3, 1e-3 * n_rgb)
     _, Hs, bs = dri.dri_get_state(st.handle, with_prior=True)
-    d = np.sqrt(np.diag(ores["H_prior"]))
-    assert np.all(np.abs(Hs - ores["H_prior"]) <= 1e-4 * np.outer(d, d))
+    # H* = H_11 - H_10 H_00^-1 H_01 (Eq. 8) is gated on the scale of the system it
+    # is computed from, the x1 block of the last joint system: the Schur
+    # complement removes the information x0 carried, so H*'s own diagonal can be
+    # far below the scale at which the system's entries are rounded
+    d1 = np.sqrt(np.diag(ores["H"])[17:])
+    ds = np.sqrt(np.diag(ores["H_prior"]))
+    err = np.abs(Hs - ores["H_prior"])
+    r_sys = np.max(err / np.outer(d1, d1))
+    r_own = np.max(err / np.outer(ds, ds))
+    assert r_sys <= 1e-5, f"H*: err / system scale {r_sys:.3g}, err / own diagonal {r_own:.3g}"
     st.close()
 
 
