@@ -373,7 +373,10 @@ int dri_set_state(dri_stream s, const dri_state* x1, const double* H_prior, cons
  * on pyramid level `level` of the uploaded frame against the stream's
  * reference, prior and IMU, without changing the stream.  W_IMU is taken at x0.
  * flags (nullable, host, width_l * height_l bytes) receives per pixel
- * bit 0 = ICP correspondence valid, bit 1 = photometric valid. */
+ * bit 0 = ICP correspondence valid, bit 1 = photometric valid and, for a
+ * valid ICP correspondence, its reference pixel (x_i, y_i) as x_i mod 4 in
+ * bits 2-3 and y_i mod 4 in bits 4-5.  The terms are evaluated by the same
+ * pixel kernel (and rows per thread) that dri_track runs for the stream. */
 int dri_linearise(dri_stream s, int32_t level, const dri_state* x0, const dri_state* x1,
                   dri_linearisation* out, uint8_t* flags);
 
@@ -434,7 +437,8 @@ int dri_profile_read(dri_stream s, dri_profile* out);
  * *out receives the ICP and photometric fields of dri_linearisation exactly as
  * dri_linearise fills them for a one-level stream (H_icp, b_icp, H_rgb, b_rgb,
  * cost_icp, cost_rgb, n_icp, n_rgb; H, b, e_imu and cost_imu are zeroed);
- * flags (nullable, device, width * height bytes) the per-pixel validity bits.
+ * flags (nullable, device, width * height bytes) the per-pixel validity and
+ * association bits, encoded as by dri_linearise.
  * Work is enqueued on cuda_stream; the call does not wait.
  *
  * DRI_EINVAL for a NULL argument, an option value a stream would reject, or a

@@ -8,6 +8,12 @@ maps, without describing how they are built.  Readings used here:
 * Pyramid: level l halves level l-1 (floor of odd sizes).  Depth is the mean
   of the samples > 0 in each 2x2 block (0 if none); intensity is the plain
   2x2 mean.  Intrinsics scale as f_l = f / 2^l, c_l = (c + 0.5) / 2^l - 0.5.
+  Every level is an FP32 map, as the level-0 images are: the depth mean adds
+  the valid samples one at a time in FP32 in the block's row-major order and
+  divides the sum by their count in FP32; the intensity mean is
+  ((I00 + I01) + (I10 + I11)) / 4 in FP32.  (Each IEEE operation rounds to
+  nearest even, so the level is defined to the bit; the normals and vertices
+  built from it are then FP64 functions of the same stored values.)
 * Vertex map: v = d K_l^-1 [u, v, 1]^T for depths in [depth_min, depth_max].
 * Normal map: n = normalise((v(x+1,y) - v) x (v(x,y+1) - v)), flipped so that
   n . v < 0 (facing the camera); invalid on the last row / column, where a
@@ -40,20 +46,31 @@ import numpy as np
 
 
 def downsample_depth(d):
-    """2x2 mean of the valid (> 0) samples; 0 where none is valid."""
-    d = np.asarray(d, dtype=np.float64)
+    """2x2 mean of the valid (> 0) samples; 0 where none is valid.  FP32 map:
+    the finer level's stored (FP32) values are added one at a time in FP32 in
+    the order (0, 0), (0, 1), (1, 0), (1, 1) of the block, and the sum is
+    divided by the count in FP32."""
+    d = np.asarray(d, dtype=np.float64).astype(np.float32)
     h, w = d.shape[0] // 2, d.shape[1] // 2
-    blk = d[: 2 * h, : 2 * w].reshape(h, 2, w, 2)
-    valid = blk > 0
-    s = np.where(valid, blk, 0.0).sum(axis=(1, 3))
-    n = valid.sum(axis=(1, 3))
-    return np.where(n > 0, s / np.maximum(n, 1), 0.0)
+    s = np.zeros((h, w), dtype=np.float32)
+    n = np.zeros((h, w), dtype=np.float32)
+    for dy in (0, 1):
+        for dx in (0, 1):
+            v = d[dy: 2 * h: 2, dx: 2 * w: 2]
+            ok = v > 0
+            s = np.where(ok, s + v, s)
+            n = n + ok.astype(np.float32)
+    out = np.where(n > 0, s / np.maximum(n, np.float32(1)), np.float32(0))
+    return out.astype(np.float64)
 
 
 def downsample_intensity(img):
-    img = np.asarray(img, dtype=np.float64)
-    h, w = img.shape[0] // 2, img.shape[1] // 2
-    return img[: 2 * h, : 2 * w].reshape(h, 2, w, 2).mean(axis=(1, 3))
+    """2x2 mean, FP32 map: ((I00 + I01) + (I10 + I11)) * 0.25 in FP32."""
+    I = np.asarray(img, dtype=np.float64).astype(np.float32)
+    h, w = I.shape[0] // 2, I.shape[1] // 2
+    top = I[0: 2 * h: 2, 0: 2 * w: 2] + I[0: 2 * h: 2, 1: 2 * w: 2]
+    bottom = I[1: 2 * h: 2, 0: 2 * w: 2] + I[1: 2 * h: 2, 1: 2 * w: 2]
+    return ((top + bottom) * np.float32(0.25)).astype(np.float64)
 
 
 def pyramid(depth, intensity, levels):

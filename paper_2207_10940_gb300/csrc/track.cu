@@ -77,12 +77,14 @@ struct Live {
   float d, a, b, c;
 };
 
-// ICP term (Eq. 4) of the pixel (u, v) with live depth d and normal n1.
+// ICP term (Eq. 4) of the pixel (u, v) with live depth d and normal n1.  *assoc
+// receives the associated reference pixel of an accepted correspondence as
+// (x_i mod 4) | (y_i mod 4) << 2 (parity output; unused otherwise).
 template <typename T, bool DW>
 __device__ __forceinline__ bool icp_pixel(const TrackParams& p, const LevelGeom& g, const float* A,
                                           const float* t, const void* __restrict__ A0,
                                           const float* __restrict__ D0, int u, int v, const Live& L,
-                                          float* acc) {
+                                          float* acc, unsigned* assoc) {
   const float n1x = L.a, n1y = L.b, n1z = L.c;
   if (n1x == 0.f && n1y == 0.f && n1z == 0.f) return false;
   const float d = L.d;
@@ -112,6 +114,7 @@ __device__ __forceinline__ bool icp_pixel(const TrackParams& p, const LevelGeom&
   const float mz = n1z + (A[6] * n1x + A[7] * n1y + A[8] * n1z);
   const float cosang = mx * Nx + my * Ny + mz * Nz;
   if (!(dist2 < p.icp_dist2 && cosang > p.icp_cos)) return false;
+  *assoc = (unsigned)(xi & 3) | ((unsigned)(yi & 3) << 2);
   const float e = Nx * dx + Ny * dy + Nz * dz;
   const float sx = px + (ex - t[0]), sy = py + (ey - t[1]), sz = pz + (ez - t[2]);
   const float J[6] = {Nx, Ny, Nz, sy * Nz - sz * Ny, sz * Nx - sx * Nz, sx * Ny - sy * Nx};
@@ -252,19 +255,22 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int term,
       }
     }
     bool ok = false;
+    unsigned assoc = 0u;
     if (col_ok && v < g.h && cur.d >= dmin && cur.d <= dmax) {
-      ok = icp ? icp_pixel<T, (OPT & kOptDepthWeight) != 0>(p, g, A, t, A0, D0, u, v, cur, acc)
+      ok = icp ? icp_pixel<T, (OPT & kOptDepthWeight) != 0>(p, g, A, t, A0, D0, u, v, cur, acc, &assoc)
                : rgb_pixel<T, (OPT & kOptOcc) != 0>(g, A, t, B0, D0, p.occ_thr, u, v, cur, acc);
     }
-    if (FLAGS && SPLIT) {    // bit 0 ICP, bit 1 photometric, or-ed into the zeroed flag bytes
+    // flag byte: bit 0 ICP, bit 1 photometric, bits 2-5 the ICP association
+    const unsigned fbits = ok ? (icp ? 1u | (assoc << 2) : 2u) : 0u;
+    if (FLAGS && SPLIT) {    // or-ed into the zeroed flag bytes
       if (ok) {
         const int o = v * g.w + u;
-        atomicOr(reinterpret_cast<unsigned int*>(p.flags + (o & ~3)), (icp ? 1u : 2u) << (8 * (o & 3)));
+        atomicOr(reinterpret_cast<unsigned int*>(p.flags + (o & ~3)), fbits << (8 * (o & 3)));
       }
-    } else if (FLAGS) {      // bit 0 ICP, bit 1 photometric, combined through shared memory
-      if (icp) s_flag[wrow][lane] = ok ? 1 : 0;
+    } else if (FLAGS) {      // the two terms' bits combined through shared memory
+      if (icp) s_flag[wrow][lane] = (uint8_t)fbits;
       __syncthreads();
-      if (!icp && col_ok && v < g.h) p.flags[v * g.w + u] = (uint8_t)(s_flag[wrow][lane] | (ok ? 2 : 0));
+      if (!icp && col_ok && v < g.h) p.flags[v * g.w + u] = (uint8_t)(s_flag[wrow][lane] | fbits);
       __syncthreads();
     }
     cur = nxt;

@@ -5,7 +5,8 @@ import pytest
 from oracle import gn, imu, maps
 from oracle.so3 import State, boxminus, boxplus
 from paper_2207_10940_gb300 import dri, synth
-from parity import check_system, configs, new_stream, pose_error, to_dri, to_oracle, POSE_M, POSE_RAD
+from parity import (POSE_M, POSE_RAD, REL, compare_linearisation, configs, new_stream, pose_error, to_dri,
+                    to_oracle)
 
 pytestmark = pytest.mark.gpu
 
@@ -42,36 +43,23 @@ def _oracle_system(tr, seq, ocfg, level, x0, x1):
     H, b, parts = tr.linearise_all(levels, level, x0, x1, t0, t1, W)
     d = boxminus(x0, tr.xbar)
     prior_cost = float(d @ tr.Hs @ d)
-    return H, b, parts, prior_cost
+    return H, b, parts, prior_cost, levels
 
 
 def _compare_linearisation(st, tr, seq, ocfg, level, x0, x1, rel=None):
+    """dri_linearise at (x0, x1) against the oracle tracker `tr` (its state
+    before the frame): per-pixel validity and association outside margins,
+    counts, every system (parity.compare_linearisation) and the IMU term."""
     lvl_shape = (ocfg.height >> level, ocfg.width >> level)
     out, flags = dri.dri_linearise(st.handle, level, to_dri(x0), to_dri(x1), want_flags=True,
                                    shape=lvl_shape)
-    H, b, parts, prior_cost = _oracle_system(tr, seq, ocfg, level, x0, x1)
+    H, b, parts, prior_cost, levels = _oracle_system(tr, seq, ocfg, level, x0, x1)
     lin = parts["lin"]
-    # counts: per pixel, outside the margin pixels
-    gi = (flags & 1) != 0
-    gr = (flags & 2) != 0
-    mi, mr = lin["icp_margin"], lin["rgb_margin"]
-    assert np.array_equal(gi[~mi], lin["icp_valid"][~mi]), \
-        f"ICP validity differs at {np.argwhere(gi[~mi] != lin['icp_valid'][~mi])[:5]}"
-    assert np.array_equal(gr[~mr], lin["rgb_valid"][~mr])
-    assert abs(out.n_icp - lin["n_icp"]) <= mi.sum()
-    assert abs(out.n_rgb - lin["n_rgb"]) <= mr.sum()
-    assert out.n_icp == gi.sum() and out.n_rgb == gr.sum()
-    # per term (x1 pose block, world frame)
-    kw = {} if rel is None else {"rel": rel}
-    check_system(np.array(out.H_icp).reshape(6, 6), out.b_icp, lin["H_icp"], lin["b_icp"],
-                 lin["cost_icp"], what="ICP", **kw)
-    check_system(np.array(out.H_rgb).reshape(6, 6), out.b_rgb, lin["H_rgb"][6:, 6:],
-                 lin["b_rgb"][6:], lin["cost_rgb"], what="RGB", **kw)
     np.testing.assert_allclose(out.e_imu, parts["e_imu"], rtol=1e-9, atol=1e-12)
     np.testing.assert_allclose(out.cost_imu, parts["cost_imu"], rtol=1e-8, atol=1e-9)
-    # the assembled 34x34 system
     cost = lin["cost_icp"] + lin["cost_rgb"] + parts["cost_imu"] + prior_cost
-    check_system(np.array(out.H).reshape(34, 34), out.b, H, b, cost, what="joint", **kw)
+    compare_linearisation(out, flags, lin, H, b, cost, levels[level], tr.ref[level], x0, x1, ocfg,
+                          rel=REL if rel is None else rel, what=f"level {level}")
     return out, lin
 
 

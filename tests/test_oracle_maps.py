@@ -20,6 +20,30 @@ def test_depth_downsample_means_valid_samples():
     assert maps.downsample_depth(np.zeros((4, 4))).sum() == 0.0
 
 
+def test_depth_downsample_is_an_fp32_map_summed_in_block_order():
+    """Each level is stored in FP32 and its mean is computed in FP32: within a
+    few FP32 units of the exact mean; with one large and three tiny samples the
+    row-major order (large one first) decides the bits, worked by hand in IEEE
+    single precision: 1 + 2^-24 rounds to 1 (a tie, to even) three times, so
+    the sum is 1 and the mean 0.25, where adding the tiny ones first would give
+    (1 + 2^-22) / 4."""
+    rng = np.random.default_rng(3)
+    d = rng.uniform(0.3, 8.0, size=(64, 64)).astype(np.float32).astype(np.float64)
+    d[rng.uniform(size=d.shape) < 0.2] = 0.0
+    out = maps.downsample_depth(d)
+    assert out.dtype == np.float64 and np.all(out.astype(np.float32) == out)   # FP32 values
+    blk = d.reshape(32, 2, 32, 2)
+    n = (blk > 0).sum(axis=(1, 3))
+    exact = np.where(n > 0, blk.sum(axis=(1, 3)) / np.maximum(n, 1), 0.0)
+    assert np.all(np.abs(out - exact) <= 4 * 2.0 ** -23 * exact)
+    t = 2.0 ** -24
+    assert maps.downsample_depth(np.array([[1.0, t], [t, t]]))[0, 0] == 0.25
+    assert maps.downsample_depth(np.array([[t, t], [t, 1.0]]))[0, 0] == (1.0 + 2.0 ** -22) / 4
+    # three valid samples: the FP32 quotient of the FP32 sum
+    three = maps.downsample_depth(np.array([[0.0, 1.0], [1.0, 2.0 ** -23 + 1.0]]))[0, 0]
+    assert three == float(np.float32(np.float32(3.0 + 2.0 ** -23) / np.float32(3.0)))
+
+
 def test_intensity_downsample_is_block_mean_and_odd_sizes_floor():
     img = np.arange(35, dtype=np.float64).reshape(5, 7)
     out = maps.downsample_intensity(img)
