@@ -678,10 +678,36 @@ def _serve_sequence(c, render=False):
                                    period_frames=SERVE_LOOP, render_frames=render)
 
 
+def tick_summary(trace):
+    """Phases of the serving loop's ticks from their host timestamps: staging
+    (IMU samples and frame uploads enqueued), launch (the batched frame
+    enqueued), GPU (until the worker saw the results) and the gap before the
+    next tick; percentiles, and the slowest tick with its phases."""
+    if not trace:
+        return None
+    ph = {"stage": [t.staged_ms - t.dequeue_ms for t in trace],
+          "launch": [t.launched_ms - t.staged_ms for t in trace],
+          "gpu": [t.done_ms - t.launched_ms for t in trace],
+          "tick": [t.done_ms - t.dequeue_ms for t in trace],
+          "gap": [b.dequeue_ms - a.done_ms for a, b in zip(trace, trace[1:])] or [0.0]}
+    out = {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99)),
+               "max": float(np.max(v))} for k, v in ph.items()}
+    w = max(trace, key=lambda t: t.done_ms - t.dequeue_ms)
+    out["slowest"] = {"at_ms": w.dequeue_ms - trace[0].dequeue_ms, "requests": int(w.requests),
+                      "stage_ms": w.staged_ms - w.dequeue_ms, "launch_ms": w.launched_ms - w.staged_ms,
+                      "gpu_ms": w.done_ms - w.launched_ms}
+    out["ticks"] = len(trace)
+    out["ticks_over_50ms"] = int(sum(1 for v in ph["tick"] if v > 50.0))
+    return out
+
+
 def served_pass(args, dev, workers):
     """Serving loop: SERVE_STREAMS streams (resolution by id mod 3), 30 Hz each with
-    exponential arrival jitter, for args.serve_seconds of arrivals; frames on the
-    device, one client thread submitting on schedule and one polling tickets."""
+    exponential arrival jitter, for args.serve_seconds of arrivals.  Frames are
+    rendered in advance into pinned host memory and each request's frame is
+    uploaded by the server (DRI_HOST); one client thread submits on schedule and
+    one polls tickets.  Then a saturation run: every stream keeps two requests
+    queued (the next is submitted as one completes) for args.saturate_seconds."""
     import threading
     import torch
     from paper_2207_10940_gb300 import dri, synth
@@ -692,12 +718,13 @@ def served_pass(args, dev, workers):
     frames = [[None] * SERVE_LOOP for _ in SERVE_CLASSES]
     for c, i, f in out:
         frames[c][i] = f
-    D = [torch.stack([torch.from_numpy(f[0]) for f in fc]).to(dev) for fc in frames]
-    I = [torch.stack([torch.from_numpy(f[1]) for f in fc]).to(dev) for fc in frames]
-    torch.cuda.synchronize(dev)
+    D = [torch.stack([torch.from_numpy(f[0]) for f in fc]).pin_memory() for fc in frames]
+    I = [torch.stack([torch.from_numpy(f[1]) for f in fc]).pin_memory() for fc in frames]
     secs = float(args.serve_seconds)
+    sat_secs = float(args.saturate_seconds)
     n_per = int(secs * FPS)
-    t_end = (SERVE_LOOP + n_per + 2) / FPS
+    n_sat = int(max(sat_secs, 0.0) * FPS * 3) + 4           # frames a stream may use when saturated
+    t_end = (SERVE_LOOP + n_per + n_sat + 2) / FPS
     imu = [synth.sequence_imu(s, t_end, seed=SERVE_SEED + c) for c, s in enumerate(seqs)]
     imu_t = [m[:, 0] for m in imu]
     ts = torch.cuda.Stream(dev)
@@ -719,6 +746,24 @@ def served_pass(args, dev, workers):
         handles.append(dri.dri_server_open_stream(srv, cfg, dri.state_from_dict(x0, o / FPS)))
         cls.append(c)
         off.append(o)
+    covering = []   # per class: index of the first sample at or after each frame time
+    for c in range(len(SERVE_CLASSES)):
+        ft = (np.arange(SERVE_LOOP + n_per + n_sat + 1)) / FPS
+        covering.append(np.searchsorted(imu_t[c], ft))
+    lib = dri.load_library()
+    frame_bytes = [2 * 4 * w * h for w, h in SERVE_CLASSES]
+
+    def request(i, k):
+        """Arguments of stream i's frame k (its k-th request): time, pinned host
+        images and the IMU samples since its previous frame."""
+        c, o = cls[i], off[i]
+        j = o + k                                      # global frame index of the class
+        lo = 0 if k == 0 else covering[c][j - 1] + 1
+        hi = covering[c][j] + 1
+        arr = dri.imu_array(imu[c][lo:hi]) if hi > lo else None
+        return (handles[i], float(j / FPS), ctypes.c_void_p(D[c][j % SERVE_LOOP].data_ptr()),
+                ctypes.c_void_p(I[c][j % SERVE_LOOP].data_ptr()), arr, 0 if arr is None else len(arr))
+
     # arrival schedule: stream i's frame k at phase_i + k / 30 s + Exp(3 ms) jitter
     phase = rng.uniform(0.0, 1.0 / FPS, SERVE_STREAMS)
     events = []
@@ -727,22 +772,9 @@ def served_pass(args, dev, workers):
         for k in range(n_per):
             events.append((phase[i] + k / FPS + jit[k], i, k))
     events.sort()
-    covering = []   # per class: index of the first sample at or after each frame time
-    for c in range(len(SERVE_CLASSES)):
-        ft = (np.arange(SERVE_LOOP + n_per + 1)) / FPS
-        covering.append(np.searchsorted(imu_t[c], ft))
     # every request's arguments are built before the run, so the client thread
     # only sleeps and calls the library (no allocation on its path)
-    lib = dri.load_library()
-    reqs = []
-    for (ta, i, k) in events:
-        c, o = cls[i], off[i]
-        j = o + k                                      # global frame index of the class
-        lo = 0 if k == 0 else covering[c][j - 1] + 1
-        hi = covering[c][j] + 1
-        arr = dri.imu_array(imu[c][lo:hi]) if hi > lo else None
-        reqs.append((ta, handles[i], float(j / FPS), ctypes.c_void_p(D[c][j % SERVE_LOOP].data_ptr()),
-                     ctypes.c_void_p(I[c][j % SERVE_LOOP].data_ptr()), arr, 0 if arr is None else len(arr)))
+    reqs = [(ta,) + request(i, k) for (ta, i, k) in events]
     n_req = len(reqs)
     tickets = [0] * n_req
     statuses = [0] * n_req
@@ -759,7 +791,7 @@ def served_pass(args, dev, workers):
                 time.sleep(t0 + ta - now)
             elif now - (t0 + ta) > lag[0]:
                 lag[0], lag[1] = now - (t0 + ta), ta      # submitted late by the client itself
-            code = lib.dri_server_submit(srv, h, t, dp, ip, 0, dri.DRI_DEVICE, arr, n, ctypes.byref(tk))
+            code = lib.dri_server_submit(srv, h, t, dp, ip, 0, dri.DRI_HOST, arr, n, ctypes.byref(tk))
             tickets[idx] = tk.value if code == dri.DRI_OK else 0
             statuses[idx] = 0 if code == dri.DRI_OK else code
             with lock:
@@ -802,25 +834,70 @@ def served_pass(args, dev, workers):
     for t in th:
         t.join()
     thr = throttle_delta(thr0, cpu_throttle())
-    gc.enable()
-    gc.unfreeze()
     wall = time.perf_counter() - t_start
-    st = dri.dri_server_stats_read(srv)
+    trace = dri.dri_server_trace_read(srv)             # read before the reset clears it
+    st = dri.dri_server_stats_read(srv, reset=True)
+    ticks = tick_summary(trace)
     bad = sum(1 for s in statuses if s != 0)
-    dri.dri_server_destroy(srv)
-    return {
+    served = {
         "streams": SERVE_STREAMS, "mix": "stream i: " + ", ".join(f"{w}x{h}" for w, h in SERVE_CLASSES)
         + " by i mod 3", "rate_hz_per_stream": FPS, "arrival_jitter": "exponential, mean 3 ms",
         "seconds": secs, "offered_frames_per_s": SERVE_STREAMS * FPS,
         "requests": len(events), "wall_s": wall, "value": st.frames_per_s, "unit": "frames/s",
         "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "max_ms": st.max_ms, "failed": int(bad),
         "mean_batch": st.mean_batch, "ticks": int(st.ticks), "hbm_used_gb": st.hbm_used / 1e9,
-        "hbm_budget_gb": SERVE_BUDGET / 1e9, "inputs": "device-resident frames (30-frame loops per "
-        "resolution, period-30 sinusoid), IMU copied per request",
+        "hbm_budget_gb": SERVE_BUDGET / 1e9,
+        "inputs": "frames rendered in advance into pinned host memory (30-frame loops per resolution, "
+                  "period-30 sinusoid), uploaded per request by the server (DRI_HOST); IMU copied per "
+                  "request",
+        "h2d_bytes_per_s": st.frames_per_s * float(np.mean(frame_bytes)),
         "warmup_s": warm_s, "client_max_lag_ms": 1000.0 * lag[0], "client_max_lag_at_s": lag[1],
-        "host_cpu_throttle": thr,
+        "host_cpu_throttle": thr, "tick_phases_ms": ticks,
         "latency_from": "submit to result (warm-up excluded: 2 s and until the start's backlog is "
                         "drained)"}
+
+    # saturation: each stream keeps two requests queued; the poller submits a
+    # stream's next frame when one of its requests completes
+    if sat_secs > 0:
+        from collections import deque
+        nxt = [n_per] * SERVE_STREAMS                  # next frame index per stream
+        fifo = deque()
+        tk = ctypes.c_uint64()
+        res = dri.dri_track_result()
+        sat_bad = [0]
+
+        def submit(i):
+            h, t, dp, ip, arr, n = request(i, nxt[i])
+            nxt[i] += 1
+            code = lib.dri_server_submit(srv, h, t, dp, ip, 0, dri.DRI_HOST, arr, n, ctypes.byref(tk))
+            if code == dri.DRI_OK:
+                fifo.append((tk.value, i))
+            else:
+                sat_bad[0] += 1
+
+        t_s = time.perf_counter()
+        for _ in range(2):
+            for i in range(SERVE_STREAMS):
+                submit(i)
+        while fifo:
+            ticket, i = fifo.popleft()
+            if lib.dri_server_poll(srv, ctypes.c_uint64(ticket), ctypes.byref(res), -1) != dri.DRI_OK:
+                sat_bad[0] += 1
+            if time.perf_counter() - t_s < sat_secs:
+                submit(i)
+        sat_wall = time.perf_counter() - t_s
+        sat_trace = dri.dri_server_trace_read(srv)
+        st2 = dri.dri_server_stats_read(srv)
+        served["saturation"] = {
+            "seconds": sat_wall, "queued_per_stream": 2, "value": st2.frames_per_s, "unit": "frames/s",
+            "completed": int(st2.completed), "failed": int(sat_bad[0]), "p50_ms": st2.p50_ms,
+            "p99_ms": st2.p99_ms, "mean_batch": st2.mean_batch, "ticks": int(st2.ticks),
+            "tick_phases_ms": tick_summary(sat_trace),
+            "note": "latency here includes the queueing of two requests per stream"}
+    gc.enable()
+    gc.unfreeze()
+    dri.dri_server_destroy(srv)
+    return served
 
 
 PRECISION_VARIANTS = (("fp32_pixel_fp64_partials", 0), ("fp32_pixel_fp32_partials", 2),
@@ -1003,7 +1080,6 @@ def run_ours(args):
                               "frames_ok", "frames_failed", "roofline", "kernel_classes", "e2e",
                               "rows_per_thread")},
         "batched_over_plain": None if p is None else b["value"] / p["value"],
-        "served": served,
         "odometry": None if odo_states is None else odometry_report(seq, odo_states, o_states),
         "odometry_rgbd_only": None if odo_rgbd is None else rgbd_only_report(seq, odo_rgbd),
         "odometry_gyro_only": None if odo_gyro is None else rgbd_only_report(seq, odo_gyro),
@@ -1020,6 +1096,8 @@ def run_ours(args):
                                              f"{a_t:.1f} s; frames/s = pixel-iterations / wall time / "
                                              f"{PIXEL_ITERS_PER_FRAME}"},
         "clocks": b["clocks"], "clocks_plain": None if p is None else p["clocks"],
+        # last, so that the end of the line (which logs keep) shows the serving results
+        "served": served,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -1038,6 +1116,8 @@ def main():
                     help="frames of the precision study against the FP64 oracle (< 2: skip it)")
     ap.add_argument("--serve-seconds", type=float, default=30.0,
                     help="seconds of arrivals in the serving pass (0: skip it)")
+    ap.add_argument("--saturate-seconds", type=float, default=10.0,
+                    help="seconds of the serving saturation run after it (0: skip it)")
     ap.add_argument("--rows-per-thread", type=lambda v: [int(x) for x in v.split(",")], default=None,
                     help="pixel-kernel rows per thread per level for the batched pass, e.g. 8,8,8 "
                          "(default: the plan's autotuner)")

@@ -119,7 +119,7 @@ typedef struct {
     double sigma_grav_rw;          /* gravity-direction noise between frames, rad     */
     double prior_sigma[5];         /* first-frame prior: pose, v, b_g, b_a, gravity   */
     double icp_dist_thr;           /* ICP association distance threshold, m           */
-    double icp_angle_thr_deg;      /* ICP normal-angle threshold, degrees             */
+    double icp_angle_thr_deg;      /* ICP normal-angle threshold, degrees, in (0, 90) */
     double depth_min, depth_max;   /* valid depth range, m                            */
     int32_t min_valid;             /* level-0 correspondences below this: DRI_ELOST   */
     int32_t precision_flags;       /* DRI_FP16_MAPS | DRI_FP32_PARTIALS               */
@@ -358,8 +358,25 @@ typedef struct {
     int32_t reserved;
 } dri_server_stats;
 
-/* Counters since creation or the last reset (reset = 1 clears them). */
+/* Counters since creation or the last reset (reset = 1 clears them and the
+ * tick trace). */
 int dri_server_stats_read(dri_server srv, int32_t reset, dri_server_stats* out);
+
+/* Host timestamps of one tick of the serving loop (a tracing aid, not part of
+ * the paper): milliseconds since dri_server_create on the host's steady clock. */
+typedef struct {
+    int64_t tick;                  /* tick number since creation                      */
+    int32_t requests;              /* requests the tick took                          */
+    int32_t status;                /* DRI_OK or the error of the tick's launch        */
+    double dequeue_ms;             /* the worker took the tick's requests             */
+    double staged_ms;              /* their IMU samples and frame uploads were enqueued */
+    double launched_ms;            /* the tick's batched frame was enqueued           */
+    double done_ms;                /* the worker saw the tick's results complete      */
+} dri_server_tick;
+
+/* Copies the most recent min(cap, recorded) ticks (the server keeps the last
+ * 65536 since creation or the last stats reset), oldest first, into out[0 .. *n). */
+int dri_server_trace_read(dri_server srv, dri_server_tick* out, int32_t cap, int32_t* n);
 
 /* Waits for the stream and copies out x1 and, when non-NULL, the prior
  * H* (17 x 17, row-major) and b* (17) that the next frame will use. */

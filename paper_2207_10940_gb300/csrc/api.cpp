@@ -46,7 +46,8 @@ int valid_config(const dri_stream_config* c) {
   if (!(c->gyr_rw > 0) || !(c->acc_rw > 0) || !(c->g > 0) || !(c->sigma_grav_rw > 0)) return DRI_EINVAL;
   for (int i = 0; i < 5; ++i)
     if (!(c->prior_sigma[i] > 0)) return DRI_EINVAL;
-  if (!(c->icp_dist_thr > 0) || !(c->icp_angle_thr_deg > 0) || !(c->icp_angle_thr_deg < 180))
+  // below 90 degrees: the angle test then also rejects a zero (invalid) normal
+  if (!(c->icp_dist_thr > 0) || !(c->icp_angle_thr_deg > 0) || !(c->icp_angle_thr_deg < 90))
     return DRI_EINVAL;
   if (!(c->depth_min >= 0) || !(c->depth_max > c->depth_min)) return DRI_EINVAL;
   if (c->max_imu < 2 || c->max_imu > 65536) return DRI_EINVAL;

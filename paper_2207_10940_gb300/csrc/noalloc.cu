@@ -9,7 +9,8 @@
 // the stream API on the fly.  This entry point takes the caller's device images
 // and a caller-owned device output and keeps every intermediate it needs (the
 // normal and gradient maps, the pixel kernel's per-block partial sums and its
-// completion counter, the per-call transforms) in one file-scope static device
+// completion counter, the per-call transforms, the per-pixel flag bytes before
+// they are copied to the caller) in one file-scope static device
 // array, held until the process exits.  The array is device memory of the
 // library's module: the CUDA runtime reserves it when it loads the module on a
 // device, which with lazy module loading (the default since CUDA 12.2) happens
@@ -55,7 +56,9 @@ constexpr int kNoallocMaxGroups = (kNoallocMaxBlocks + kFoldGroup - 1) / kFoldGr
 constexpr size_t kOffCounters = na_align(kOffPackB + kPlane * 16);
 constexpr size_t kOffPartials = na_align(kOffCounters + (1 + kNoallocMaxGroups) * sizeof(uint32_t));
 constexpr size_t kOffGPartials = na_align(kOffPartials + (size_t)kNoallocMaxBlocks * kSumsAll * sizeof(double));
-constexpr size_t kNoallocBytes = na_align(kOffGPartials + (size_t)kNoallocMaxGroups * kSumsAll * sizeof(double));
+// per-pixel flag bytes, or-ed in by 32-bit words, then copied to the caller's buffer
+constexpr size_t kOffFlags = na_align(kOffGPartials + (size_t)kNoallocMaxGroups * kSumsAll * sizeof(double));
+constexpr size_t kNoallocBytes = na_align(kOffFlags + (size_t)kPlane);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
@@ -201,7 +204,8 @@ extern "C" int dri_linearise_pair_noalloc(const dri_stream_config* cfg, const fl
       (int64_t)cfg->width * cfg->height > kNoallocMaxPixels)
     return DRI_EINVAL;
   if (!(cfg->fx > 0) || !(cfg->fy > 0) || !(cfg->sigma_I > 0) || !(cfg->sigma_d > 0) ||
-      !(cfg->depth_max > cfg->depth_min) || !(cfg->icp_dist_thr > 0))
+      !(cfg->depth_max > cfg->depth_min) || !(cfg->icp_dist_thr > 0) ||
+      !(cfg->icp_angle_thr_deg > 0) || !(cfg->icp_angle_thr_deg < 90))
     return DRI_EINVAL;
   if ((cfg->precision_flags & ~(DRI_FP16_MAPS | DRI_FP32_PARTIALS)) != 0 ||
       !(cfg->occlusion_thr >= 0.0) || !std::isfinite(cfg->occlusion_thr) ||
@@ -244,7 +248,7 @@ extern "C" int dri_linearise_pair_noalloc(const dri_stream_config* cfg, const fl
   p.partials = base + kOffPartials;
   p.gpartials = base + kOffGPartials;
   p.counters = counters;
-  p.flags = flags;
+  p.flags = flags ? base + kOffFlags : nullptr;
   p.ppt = 1;
   p.nblocks = track_mixed_blocks(g.w, g.h, 1);
   if (p.nblocks > kNoallocMaxBlocks) return DRI_EINVAL;
@@ -254,7 +258,10 @@ extern "C" int dri_linearise_pair_noalloc(const dri_stream_config* cfg, const fl
   p.icp_cos = (float)std::cos(cfg->icp_angle_thr_deg * 3.14159265358979323846 / 180.0);
   p.occ_thr = (float)cfg->occlusion_thr;
   p.icp_dw = cfg->icp_depth_weight;
+  if (flags && cudaMemsetAsync(p.flags, 0, (size_t)g.w * g.h, s) != cudaSuccess) return DRI_ECUDA;
   if (launch_track(p, fp16, fp32p, s) != cudaSuccess) return DRI_ECUDA;
+  if (flags && cudaMemcpyAsync(flags, p.flags, (size_t)g.w * g.h, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return DRI_ECUDA;
   k_noalloc_end<<<1, 128, 0, s>>>(ctrl, 1.0 / (cfg->sigma_d * cfg->sigma_d),
                                   1.0 / (cfg->sigma_I * cfg->sigma_I), out);
   if (cudaGetLastError() != cudaSuccess) return DRI_ECUDA;

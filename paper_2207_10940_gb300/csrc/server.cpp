@@ -34,6 +34,7 @@ namespace {
 constexpr int kInflight = 1;                 // ticks on the GPU at once
 constexpr size_t kSlotOverheadBytes = 65536; // plan table, staging and result head of one slot
 constexpr size_t kMaxLatencySamples = 1 << 20;
+constexpr size_t kTraceTicks = 1 << 16;      // per-tick timestamps kept (a ring)
 
 using Clock = std::chrono::steady_clock;
 
@@ -70,6 +71,7 @@ struct Tick {
   Plan* plan;
   int ring_slot;
   std::vector<TickEntry> entries;
+  dri_server_tick trace;                      // done_ms filled when the tick completes
 };
 
 }  // namespace
@@ -103,9 +105,26 @@ struct dri_server_s {
   std::vector<double> lat_ms;
   Clock::time_point t_first_submit, t_last_done;
   bool any_submit = false;
+  // per-tick host timestamps (ms since creation), the last kTraceTicks ticks
+  Clock::time_point t_created;
+  std::vector<dri_server_tick> trace;
+  size_t trace_next = 0;
+  int64_t tick_seq = 0;
 };
 
 namespace {
+
+double since_created(const dri_server_s* S) { return ms_since(S->t_created, Clock::now()); }
+
+// Records a finished tick's timestamps (lock held).
+void record_tick(dri_server_s* S, const dri_server_tick& t) {
+  if (S->trace.size() < kTraceTicks) {
+    S->trace.push_back(t);
+  } else {
+    S->trace[S->trace_next] = t;
+    S->trace_next = (S->trace_next + 1) % kTraceTicks;
+  }
+}
 
 void finish_ticket(dri_server_s* S, uint64_t id, int status, const dri_track_result* res) {
   auto it = S->tickets.find(id);
@@ -128,6 +147,8 @@ void finish_ticket(dri_server_s* S, uint64_t id, int status, const dri_track_res
 void complete_tick(dri_server_s* S) {
   Tick tk = S->inflight.front();
   S->inflight.pop_front();
+  tk.trace.done_ms = since_created(S);
+  record_tick(S, tk.trace);
   for (const TickEntry& e : tk.entries) {
     dri_stream_s* s = tk.plan->slots[e.slot];
     settle(s, false);                          // this tick's frame has completed
@@ -219,6 +240,11 @@ void worker_main(dri_server_s* S) {
       }
       std::sort(order.begin(), order.end());
       if ((int)order.size() > S->max_batch) order.resize(S->max_batch);
+      dri_server_tick tr;
+      std::memset(&tr, 0, sizeof(tr));
+      tr.tick = S->tick_seq++;
+      tr.requests = (int32_t)order.size();
+      tr.dequeue_ms = since_created(S);
       std::vector<Request> reqs;
       for (auto& o : order) {
         reqs.push_back(std::move(S->queues[o.second].front()));
@@ -235,6 +261,7 @@ void worker_main(dri_server_s* S) {
         if (up[i] == DRI_OK)
           up[i] = dri_upload_frame(q.s, q.t, q.depth, q.inten, q.pitch, q.mem_kind);
       }
+      tr.staged_ms = since_created(S);
       std::vector<SlotWork> work;
       std::vector<double> t0;
       int rs = -1;
@@ -252,8 +279,10 @@ void worker_main(dri_server_s* S) {
         for (const SlotWork& w : work) any = any || w.mode != kSlotIdle;
         if (any) rp = plan_launch(plan, work, &rs);
       }
+      tr.launched_ms = since_created(S);
+      tr.status = rp;
       lk.lock();
-      Tick tk{plan, rs, {}};
+      Tick tk{plan, rs, {}, tr};
       for (size_t i = 0; i < reqs.size(); ++i) {
         int slot = -1;
         if (rp == DRI_OK && rs >= 0)
@@ -273,6 +302,9 @@ void worker_main(dri_server_s* S) {
         S->inflight.push_back(tk);
         S->ticks++;
         S->tick_frames += (int64_t)tk.entries.size();
+      } else {                                 // nothing on the GPU: done as launched
+        tk.trace.done_ms = tk.trace.launched_ms;
+        record_tick(S, tk.trace);
       }
       if (rp == DRI_OK && rs >= 0) remember_tiles(S);
       S->cv_done.notify_all();
@@ -302,6 +334,7 @@ int dri_server_create(size_t hbm_budget_bytes, int32_t max_batch, void* cuda_str
   S->budget = hbm_budget_bytes;
   S->max_batch = max_batch;
   S->stream = (cudaStream_t)cuda_stream;
+  S->t_created = Clock::now();
   try {
     S->worker = std::thread(worker_main, S);
   } catch (...) {
@@ -455,7 +488,21 @@ int dri_server_stats_read(dri_server S, int32_t reset, dri_server_stats* out) {
     S->submitted = S->completed = S->failed = S->ticks = S->tick_frames = 0;
     S->lat_ms.clear();
     S->any_submit = false;
+    S->trace.clear();
+    S->trace_next = 0;
   }
+  return DRI_OK;
+}
+
+int dri_server_trace_read(dri_server S, dri_server_tick* out, int32_t cap, int32_t* n) {
+  if (!S || !n || cap < 0 || (cap > 0 && !out)) return DRI_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  const size_t have = S->trace.size();
+  const size_t k = std::min(have, (size_t)cap);
+  // oldest first: the ring starts at trace_next once it is full
+  const size_t first = have < kTraceTicks ? 0 : S->trace_next;
+  for (size_t i = 0; i < k; ++i) out[i] = S->trace[(first + (have - k) + i) % have];
+  *n = (int32_t)k;
   return DRI_OK;
 }
 

@@ -7,14 +7,19 @@
 // latency of the dependent gathers.  Batched kernel: a block of 8 warps takes
 // one term over a tile of 32 columns x 8 * ppt rows (warp w: rows w, w + 8, ...),
 // the two terms of a tile being neighbouring blocks, so a block never waits at
-// its final barrier for the other (slower) term.  By-value kernel (parity,
-// per-pixel flags): warps 0-3 ICP and 4-7 photometric over the same 32 x 4 * ppt
-// pixels, so the two validity bits of a pixel meet in shared memory.  Each
-// gather is one vector load of a per-pixel pack (packs.cuh): the ICP term reads
-// pack A (normal + depth) of the live pixel and of the associated reference
-// pixel, the photometric term the live depth and intensity and four pack-B taps
-// (intensity + gradient) of the reference.  Each thread loads its next row's
-// live samples before it works on the current one.  Per pixel, in FP32:
+// its final barrier for the other (slower) term.  By-value kernel (per-pixel
+// flags of the allocation-free entry): warps 0-3 ICP and 4-7 photometric over
+// the same 32 x 4 * ppt pixels.  Each gather is one vector load of a per-pixel
+// pack (packs.cuh): the ICP term reads pack A (normal + depth) of the live pixel
+// and of the associated reference pixel, the photometric term the live depth
+// and intensity and four pack-B taps (intensity + gradient) of the reference.
+// A pixel's work is a front half (the point, its projection, the tests that
+// need no reference sample, the gather) and a back half (the tests on the
+// reference sample, residual, Jacobian, sums); every test is a comparison that
+// NaN fails, so no pixel branches away before its gather.  Each thread loads
+// its next row's live samples before it works on the current one, and asks L2
+// for the reference samples its next row is expected to gather.  Per pixel, in
+// FP32:
 //
 //   p   = d K^-1 [u, v, 1]^T                       live point, camera frame C1
 //   ICP: D = A_ref p + t_ref  with A_ref = R_ref^T R_1 - I, t_ref = R_ref^T (r_1 - r_ref),
@@ -62,122 +67,286 @@ __device__ __forceinline__ void accumulate(float* a, const float* J, float e) {
   a[28] += 1.f;
 }
 
-// Rows ahead of the current one whose live and reference samples (at the same
-// pixel) each thread asks L2 to fetch: the gathers of a later row then find
-// their lines in L2 instead of waiting on HBM (0: none).
+// Rows ahead of the current one whose live samples each thread asks L2 to fetch
+// (0: none).  The reference is prefetched where the thread's next row is
+// expected to land: one thread row (kR image rows) below the current gather,
+// which for a smooth surface and a small motion is where the next pixel
+// projects (measured: long-scoreboard stalls 5.9 -> 4.2 per issued
+// instruction, 69 -> 66 us per 16-slot launch).
 constexpr int kPrefetchRows = 4;
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-// Live-frame samples of one pixel: depth and the term's own map (the normal for
-// ICP, the intensity for the photometric term).
-struct Live {
-  float d, a, b, c;
+// What a thread needs of its tile for the whole loop over its rows: the term's
+// transform (A = R^T R_1 - I, t), its column u with the pixel ray's x part and
+// the bounds of an integer displacement that stays inside the reference image,
+// and the maps.
+struct TileCtx {
+  LevelGeom g;
+  float A[9], t[3];
+  int u;
+  bool col_ok;
+  float rx;                     // (u - c_x) / f_x
+  float ucx;                    // u - c_x
+  float lox, hix;               // -u and w - u: x + u in [0, w) <=> lox <= x < hix
+  float ify_cy;                 // -c_y / f_y
+  int row0, kR, nrows;          // the thread's rows: row0, row0 + kR, ... (nrows of them)
+  float dmin, dmax, dist2, cosmin, occ_thr;
+  const void* __restrict__ A1;  // live pack A
+  const float* __restrict__ D1;
+  const float* __restrict__ I1;
+  const void* __restrict__ A0;  // reference packs
+  const float* __restrict__ D0;
+  const void* __restrict__ B0;
+  uint8_t* flags;
 };
 
-// ICP term (Eq. 4) of the pixel (u, v) with live depth d and normal n1.  *assoc
-// receives the associated reference pixel of an accepted correspondence as
-// (x_i mod 4) | (y_i mod 4) << 2 (parity output; unused otherwise).
-template <typename T, bool DW>
-__device__ __forceinline__ bool icp_pixel(const TrackParams& p, const LevelGeom& g, const float* A,
-                                          const float* t, const void* __restrict__ A0,
-                                          const float* __restrict__ D0, int u, int v, const Live& L,
-                                          float* acc, unsigned* assoc) {
-  const float n1x = L.a, n1y = L.b, n1z = L.c;
-  if (n1x == 0.f && n1y == 0.f && n1z == 0.f) return false;
-  const float d = L.d;
-  const float rx = ((float)u - g.cx) * g.ifx;
-  const float ry = ((float)v - g.cy) * g.ify;
-  const float px = d * rx, py = d * ry, pz = d;
-  const float ex = fmaf(A[0], px, fmaf(A[1], py, fmaf(A[2], pz, t[0])));
-  const float ey = fmaf(A[3], px, fmaf(A[4], py, fmaf(A[5], pz, t[1])));
-  const float ez = fmaf(A[6], px, fmaf(A[7], py, fmaf(A[8], pz, t[2])));
-  const float z = d + ez;
-  if (!(z > 0.f)) return false;
-  const float iz = __fdividef(1.f, z);
-  const float sxp = g.fx * (fmaf(-rx, ez, ex) * iz);
-  const float syp = g.fy * (fmaf(-ry, ez, ey) * iz);
-  const bool sane = fabsf(sxp) < 1e7f && fabsf(syp) < 1e7f;   // int conversion in range
-  const int xi = sane ? u + (int)floorf(sxp + 0.5f) : -1;
-  const int yi = sane ? v + (int)floorf(syp + 0.5f) : -1;
-  if (xi < 0 || xi >= g.w || yi < 0 || yi >= g.h) return false;
-  const float4 n0 = Packs<T>::load_a(A0, D0, yi * g.w + xi);   // N (x, y, z), reference depth
-  const float Nx = n0.x, Ny = n0.y, Nz = n0.z, dr = n0.w;
-  if (Nx == 0.f && Ny == 0.f && Nz == 0.f) return false;
-  const float Vx = dr * (((float)xi - g.cx) * g.ifx), Vy = dr * (((float)yi - g.cy) * g.ify);
-  const float dx = (px - Vx) + ex, dy = (py - Vy) + ey, dz = (pz - dr) + ez;
-  const float dist2 = dx * dx + dy * dy + dz * dz;
-  const float mx = n1x + (A[0] * n1x + A[1] * n1y + A[2] * n1z);
-  const float my = n1y + (A[3] * n1x + A[4] * n1y + A[5] * n1z);
-  const float mz = n1z + (A[6] * n1x + A[7] * n1y + A[8] * n1z);
-  const float cosang = mx * Nx + my * Ny + mz * Nz;
-  if (!(dist2 < p.icp_dist2 && cosang > p.icp_cos)) return false;
-  *assoc = (unsigned)(xi & 3) | ((unsigned)(yi & 3) << 2);
-  const float e = Nx * dx + Ny * dy + Nz * dz;
-  const float sx = px + (ex - t[0]), sy = py + (ey - t[1]), sz = pz + (ez - t[2]);
-  const float J[6] = {Nx, Ny, Nz, sy * Nz - sz * Ny, sz * Nx - sx * Nz, sx * Ny - sy * Nx};
-  if (DW) {                      // weight 1 / d^4 (sigma_d(d) = sigma_d d^2): J, e scaled by 1 / d^2
-    const float w = __fdividef(1.f, d * d);
-    const float Jw[6] = {J[0] * w, J[1] * w, J[2] * w, J[3] * w, J[4] * w, J[5] * w};
-    accumulate(acc, Jw, e * w);
-    return true;
-  }
-  accumulate(acc, J, e);
-  return true;
+// Row constants of the thread's pixel (u, v).
+struct RowCtx {
+  int v, o;                     // row and pixel index v w + u
+  bool in;                      // the pixel exists
+  float ry;                     // (v - c_y) / f_y
+  float vcy;                    // v - c_y
+  float loy, hiy;               // -v and h - v
+};
+
+__device__ __forceinline__ RowCtx row_ctx(const TileCtx& c, int r) {
+  RowCtx q;
+  q.v = c.row0 + r * c.kR;
+  q.o = q.v * c.g.w + c.u;
+  q.in = c.col_ok && q.v < c.g.h;
+  const float vf = (float)q.v;
+  q.ry = fmaf(vf, c.g.ify, c.ify_cy);
+  q.vcy = vf - c.g.cy;
+  q.loy = -vf;
+  q.hiy = (float)c.g.h - vf;
+  return q;
 }
 
-// Photometric term (Eq. 3) of the pixel (u, v) with live depth d and intensity i1.
-template <typename T, bool OCC>
-__device__ __forceinline__ bool rgb_pixel(const LevelGeom& g, const float* A, const float* t,
-                                          const void* __restrict__ B0, const float* __restrict__ D0,
-                                          float occ_thr, int u, int v, const Live& L, float* acc) {
-  const float d = L.d;
-  const float rx = ((float)u - g.cx) * g.ifx;
-  const float ry = ((float)v - g.cy) * g.ify;
-  const float px = d * rx, py = d * ry, pz = d;
-  const float ex = fmaf(A[0], px, fmaf(A[1], py, fmaf(A[2], pz, t[0])));
-  const float ey = fmaf(A[3], px, fmaf(A[4], py, fmaf(A[5], pz, t[1])));
-  const float ez = fmaf(A[6], px, fmaf(A[7], py, fmaf(A[8], pz, t[2])));
-  const float z = d + ez;
-  if (!(z > 0.f)) return false;
+// The live point p = d (r_x, r_y, 1) and D = A p + t: p + D is the point in the
+// reference (ICP) or x0 (photometric) camera.
+struct Warp3 {
+  float px, py, d, Dx, Dy, Dz;
+};
+
+__device__ __forceinline__ Warp3 warp_point(const TileCtx& c, float ry, float d) {
+  Warp3 w;
+  w.px = d * c.rx;
+  w.py = d * ry;
+  w.d = d;
+  w.Dx = fmaf(c.A[0], w.px, fmaf(c.A[1], w.py, fmaf(c.A[2], d, c.t[0])));
+  w.Dy = fmaf(c.A[3], w.px, fmaf(c.A[4], w.py, fmaf(c.A[5], d, c.t[1])));
+  w.Dz = fmaf(c.A[6], w.px, fmaf(c.A[7], w.py, fmaf(c.A[8], d, c.t[2])));
+  return w;
+}
+
+// ---- ICP term (Eq. 4) -------------------------------------------------------
+// Front half: association and the gather of the reference pack; back half:
+// residual, Jacobian and accumulation.
+struct IcpPix {
+  float4 ref;                   // reference pack A at the associated pixel: N, d_ref
+  Warp3 w;
+  float ix, iy;                 // integer displacement of the associated pixel
+  float mx, my, mz;             // (I + A) n1: the live normal in the reference camera
+  bool ok;
+};
+
+template <typename T>
+__device__ __forceinline__ void icp_front(const TileCtx& c, const RowCtx& q, const float4 live,
+                                          IcpPix& x) {
+  // live = (n1, d); a zero normal is rejected by the angle test (cos_min > 0)
+  const float d = live.w;
+  x.w = warp_point(c, q.ry, d);
+  const float z = d + x.w.Dz;
   const float iz = __fdividef(1.f, z);
   // displacement of the projection from (u, v): small, so FP32 keeps it to
-  // ~1e-6 px, and integer parts of the position stay exact
-  const float sxp = g.fx * (fmaf(-rx, ez, ex) * iz);
-  const float syp = g.fy * (fmaf(-ry, ez, ey) * iz);
-  const float fxp = floorf(sxp), fyp = floorf(syp);
-  const bool sane = fabsf(sxp) < 1e7f && fabsf(syp) < 1e7f;   // int conversion in range
-  const int xb = sane ? u + (int)fxp : -1, yb = sane ? v + (int)fyp : -1;
-  if (xb < 0 || xb >= g.w - 1 || yb < 0 || yb >= g.h - 1) return false;
-  const float ax = sxp - fxp, ay = syp - fyp;
-  const int q = yb * g.w + xb;
-  const float4 s00 = Packs<T>::load_b(B0, q), s01 = Packs<T>::load_b(B0, q + 1);
-  const float4 s10 = Packs<T>::load_b(B0, q + g.w), s11 = Packs<T>::load_b(B0, q + g.w + 1);
-  if (OCC) {                     // depth consistency at the nearest reference pixel
-    const bool right = floorf(sxp + 0.5f) != fxp, down = floorf(syp + 0.5f) != fyp;
-    const float dr = Packs<T>::kDepthInB
-                         ? (down ? (right ? s11.w : s10.w) : (right ? s01.w : s00.w))
-                         : __ldg(D0 + (yb + (down ? 1 : 0)) * g.w + xb + (right ? 1 : 0));
-    if (dr > 0.f && fabsf(z - dr) > occ_thr) return false;
+  // ~1e-5 px, and the integer parts of the position stay exact
+  const float sx = c.g.fx * (fmaf(-c.rx, x.w.Dz, x.w.Dx) * iz);
+  const float sy = c.g.fy * (fmaf(-q.ry, x.w.Dz, x.w.Dy) * iz);
+  x.ix = floorf(sx + 0.5f);                    // nearest pixel
+  x.iy = floorf(sy + 0.5f);
+  // NaN and out-of-range displacements fail these comparisons
+  x.ok = q.in && d >= c.dmin && d <= c.dmax && z > 0.f && x.ix >= c.lox && x.ix < c.hix &&
+         x.iy >= q.loy && x.iy < q.hiy;
+  x.mx = fmaf(c.A[0], live.x, fmaf(c.A[1], live.y, fmaf(c.A[2], live.z, live.x)));
+  x.my = fmaf(c.A[3], live.x, fmaf(c.A[4], live.y, fmaf(c.A[5], live.z, live.y)));
+  x.mz = fmaf(c.A[6], live.x, fmaf(c.A[7], live.y, fmaf(c.A[8], live.z, live.z)));
+  x.ref = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (x.ok) {
+    const int a = q.o + (int)x.iy * c.g.w + (int)x.ix;
+    x.ref = Packs<T>::load_a(c.A0, c.D0, a);
+    if (x.iy + (float)c.kR < q.hiy)          // the thread's next row, kR reference rows down
+      prefetch_l2(static_cast<const char*>(c.A0) + (size_t)(a + c.kR * c.g.w) * Packs<T>::kBytesA);
   }
-  const float w00 = (1.f - ax) * (1.f - ay), w01 = ax * (1.f - ay);
-  const float w10 = (1.f - ax) * ay, w11 = ax * ay;
-  const float iv = w00 * s00.x + w01 * s01.x + w10 * s10.x + w11 * s11.x;
-  const float gx = w00 * s00.y + w01 * s01.y + w10 * s10.y + w11 * s11.y;
-  const float gy = w00 * s00.z + w01 * s01.z + w10 * s10.z + w11 * s11.z;
-  const float e = iv - L.a;
-  const float a0 = g.fx * gx * iz, a1 = g.fy * gy * iz;
-  const float a2 = -(gx * (((float)u - g.cx) + sxp) + gy * (((float)v - g.cy) + syp)) * iz;
-  const float sx = px + (ex - t[0]), sy = py + (ey - t[1]), sz = pz + (ez - t[2]);
+}
+
+template <bool DW, bool FLAGS>
+__device__ __forceinline__ void icp_back(const TileCtx& c, const RowCtx& q, const IcpPix& x,
+                                         float* acc) {
+  const float Nx = x.ref.x, Ny = x.ref.y, Nz = x.ref.z, dr = x.ref.w;
+  // reference vertex V = d_ref K^-1 [x_i, y_i, 1]^T
+  const float Vx = dr * ((c.ucx + x.ix) * c.g.ifx);
+  const float Vy = dr * ((q.vcy + x.iy) * c.g.ify);
+  const float dx = (x.w.px - Vx) + x.w.Dx, dy = (x.w.py - Vy) + x.w.Dy, dz = (x.w.d - dr) + x.w.Dz;
+  const float dist2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float cosang = fmaf(x.mx, Nx, fmaf(x.my, Ny, x.mz * Nz));
+  const bool ok = x.ok && dist2 < c.dist2 && cosang > c.cosmin;
+  if (FLAGS && ok) {           // bit 0, and the association in bits 2-5
+    const unsigned xi = (unsigned)(c.u + (int)x.ix), yi = (unsigned)(q.v + (int)x.iy);
+    const unsigned bits = 1u | (xi & 3u) << 2 | (yi & 3u) << 4;
+    atomicOr(reinterpret_cast<unsigned int*>(c.flags + (q.o & ~3)), bits << (8 * (q.o & 3)));
+  }
+  if (!ok) return;
+  const float e = fmaf(Nx, dx, fmaf(Ny, dy, Nz * dz));
+  // s = (I + A) p: the live point rotated into the reference camera
+  const float sx = x.w.px + (x.w.Dx - c.t[0]), sy = x.w.py + (x.w.Dy - c.t[1]),
+              sz = x.w.d + (x.w.Dz - c.t[2]);
+  const float J[6] = {Nx, Ny, Nz, sy * Nz - sz * Ny, sz * Nx - sx * Nz, sx * Ny - sy * Nx};
+  if (DW) {                      // weight 1 / d^4 (sigma_d(d) = sigma_d d^2): J, e scaled by 1 / d^2
+    const float wgt = __fdividef(1.f, x.w.d * x.w.d);
+    const float Jw[6] = {J[0] * wgt, J[1] * wgt, J[2] * wgt, J[3] * wgt, J[4] * wgt, J[5] * wgt};
+    accumulate(acc, Jw, e * wgt);
+    return;
+  }
+  accumulate(acc, J, e);
+}
+
+// ---- photometric term (Eq. 3) ------------------------------------------------
+struct RgbPix {
+  float4 s00, s01, s10, s11;    // reference pack B at the four bilinear taps
+  Warp3 w;
+  float ax, ay;                 // bilinear weights of the right / lower taps
+  float xr, yr;                 // x - c_x, y - c_y of the warped point
+  float iz, z;
+  float i1;                     // live intensity
+  bool ok;
+};
+
+template <typename T>
+__device__ __forceinline__ void rgb_front(const TileCtx& c, const RowCtx& q, float d, float i1,
+                                          RgbPix& x) {
+  x.w = warp_point(c, q.ry, d);
+  x.z = d + x.w.Dz;
+  x.iz = __fdividef(1.f, x.z);
+  const float sx = c.g.fx * (fmaf(-c.rx, x.w.Dz, x.w.Dx) * x.iz);
+  const float sy = c.g.fy * (fmaf(-q.ry, x.w.Dz, x.w.Dy) * x.iz);
+  const float fx = floorf(sx), fy = floorf(sy);
+  // the bilinear support [x, x + 1] x [y, y + 1] inside the image
+  x.ok = q.in && d >= c.dmin && d <= c.dmax && x.z > 0.f && fx >= c.lox && fx < c.hix - 1.f &&
+         fy >= q.loy && fy < q.hiy - 1.f;
+  x.ax = sx - fx;
+  x.ay = sy - fy;
+  x.xr = c.ucx + sx;
+  x.yr = q.vcy + sy;
+  x.i1 = i1;
+  x.s00 = x.s01 = x.s10 = x.s11 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (x.ok) {
+    const int b = q.o + (int)fy * c.g.w + (int)fx;
+    x.s00 = Packs<T>::load_b(c.B0, b);
+    x.s01 = Packs<T>::load_b(c.B0, b + 1);
+    x.s10 = Packs<T>::load_b(c.B0, b + c.g.w);
+    x.s11 = Packs<T>::load_b(c.B0, b + c.g.w + 1);
+    if (fy + (float)(c.kR + 1) < q.hiy) {    // the next row's two tap rows, kR rows down
+      const char* B = static_cast<const char*>(c.B0);
+      prefetch_l2(B + (size_t)(b + c.kR * c.g.w) * Packs<T>::kBytesB);
+      prefetch_l2(B + (size_t)(b + (c.kR + 1) * c.g.w) * Packs<T>::kBytesB);
+    }
+  }
+}
+
+template <typename T, bool OCC, bool FLAGS>
+__device__ __forceinline__ void rgb_back(const TileCtx& c, const RowCtx& q, const RgbPix& x,
+                                         float* acc) {
+  bool ok = x.ok;
+  if (OCC && ok) {               // depth consistency at the nearest reference pixel
+    const bool right = x.ax >= 0.5f, down = x.ay >= 0.5f;
+    float dr;
+    if (Packs<T>::kDepthInB) {
+      dr = down ? (right ? x.s11.w : x.s10.w) : (right ? x.s01.w : x.s00.w);
+    } else {
+      const float sx = x.xr - c.ucx, sy = x.yr - q.vcy;
+      dr = __ldg(c.D0 + q.o + (int)(floorf(sy) + (down ? 1.f : 0.f)) * c.g.w +
+                 (int)(floorf(sx) + (right ? 1.f : 0.f)));
+    }
+    if (dr > 0.f && fabsf(x.z - dr) > c.occ_thr) ok = false;
+  }
+  if (FLAGS && ok)
+    atomicOr(reinterpret_cast<unsigned int*>(c.flags + (q.o & ~3)), 2u << (8 * (q.o & 3)));
+  if (!ok) return;
+  const float w00 = (1.f - x.ax) * (1.f - x.ay), w01 = x.ax * (1.f - x.ay);
+  const float w10 = (1.f - x.ax) * x.ay, w11 = x.ax * x.ay;
+  const float iv = w00 * x.s00.x + w01 * x.s01.x + w10 * x.s10.x + w11 * x.s11.x;
+  const float gx = w00 * x.s00.y + w01 * x.s01.y + w10 * x.s10.y + w11 * x.s11.y;
+  const float gy = w00 * x.s00.z + w01 * x.s01.z + w10 * x.s10.z + w11 * x.s11.z;
+  const float e = iv - x.i1;
+  const float a0 = c.g.fx * gx * x.iz, a1 = c.g.fy * gy * x.iz;
+  const float a2 = -(gx * x.xr + gy * x.yr) * x.iz;
+  const float sx = x.w.px + (x.w.Dx - c.t[0]), sy = x.w.py + (x.w.Dy - c.t[1]),
+              sz = x.w.d + (x.w.Dz - c.t[2]);
   const float J[6] = {a0, a1, a2, sy * a2 - sz * a1, sz * a0 - sx * a2, sx * a1 - sy * a0};
   accumulate(acc, J, e);
-  return true;
+}
+
+// L2 prefetch of the live samples kPrefetchRows rows ahead.
+template <typename T>
+__device__ __forceinline__ void prefetch_ahead(const TileCtx& c, int r, bool icp) {
+  if (kPrefetchRows <= 0 || r + kPrefetchRows >= c.nrows) return;
+  const int v = c.row0 + (r + kPrefetchRows) * c.kR;
+  if (!c.col_ok || v >= c.g.h) return;
+  const int o = v * c.g.w + c.u;
+  if (icp) prefetch_l2(static_cast<const char*>(c.A1) + (size_t)o * Packs<T>::kBytesA);
+  else prefetch_l2(c.I1 + o);
+}
+
+// The ICP term over the thread's rows: each row's live pack is loaded one row
+// ahead; its front half (association, reference gather) and back half
+// (residual, Jacobian, sums) follow each other.  (Issuing the next row's front
+// half before the current row's back half, so that its gather is in flight
+// meanwhile, measured slower: the state carried between the halves costs
+// registers -- fewer resident warps or spills -- and moves.)
+template <typename T, bool DW, bool FLAGS>
+__device__ __forceinline__ void icp_rows(const TileCtx& c, float* acc) {
+  auto live = [&](const RowCtx& q) {
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (q.in) a = Packs<T>::load_a(c.A1, c.D1, q.o);
+    return a;
+  };
+  float4 l = live(row_ctx(c, 0));
+  for (int r = 0; r < c.nrows; ++r) {
+    const RowCtx q = row_ctx(c, r);
+    const float4 ln = r + 1 < c.nrows ? live(row_ctx(c, r + 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    prefetch_ahead<T>(c, r, true);
+    IcpPix x;
+    icp_front<T>(c, q, l, x);
+    icp_back<DW, FLAGS>(c, q, x, acc);
+    l = ln;
+  }
+}
+
+// The photometric term over the thread's rows, as icp_rows.
+template <typename T, bool OCC, bool FLAGS>
+__device__ __forceinline__ void rgb_rows(const TileCtx& c, float* acc) {
+  auto live = [&](const RowCtx& q) {
+    float2 a = make_float2(0.f, 0.f);
+    if (q.in) a = make_float2(Packs<T>::depth(c.A1, c.D1, q.o), __ldg(c.I1 + q.o));
+    return a;
+  };
+  float2 l = live(row_ctx(c, 0));
+  for (int r = 0; r < c.nrows; ++r) {
+    const RowCtx q = row_ctx(c, r);
+    const float2 ln = r + 1 < c.nrows ? live(row_ctx(c, r + 1)) : make_float2(0.f, 0.f);
+    prefetch_ahead<T>(c, r, false);
+    RgbPix x;
+    rgb_front<T>(c, q, l.x, l.y, x);
+    rgb_back<T, OCC, FLAGS>(c, q, x, acc);
+    l = ln;
+  }
 }
 
 // One tile of one image (single-term: 32 x 8 * ppt pixels of `term`; mixed:
-// 32 x 4 * ppt pixels, both terms): (bx, by) its tile
+// 32 x 4 * ppt pixels, warps 0-3 ICP and 4-7 photometric): (bx, by) its tile
 // coordinates, bid its index in the image's fold order.
 // Optional terms, compile-time variants of the pixel kernels (OPT bits): the
 // photometric occlusion test and the depth-dependent ICP weight.
@@ -190,91 +359,47 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int term,
   if (ctrl->status != 0) return;
   const int lane = threadIdx.x;
   const int warp = threadIdx.y;
-  constexpr int kR = SPLIT ? kTrackThreadsY : kTrackRows;   // rows between a thread's rows
   const bool icp = SPLIT ? term == 0 : warp < kTrackRows;    // warp-uniform
   const int wrow = SPLIT ? warp : (warp & (kTrackRows - 1));
   const int rs = ctrl->ref_index;
   const int cs = 1 - rs;
-  const LevelGeom g = p.g;
-  const float* __restrict__ D1 = p.m.depth[cs];
-  const float* __restrict__ I1 = p.m.inten[cs];
-  const void* __restrict__ A1 = p.m.packA[cs];
-  const float* __restrict__ D0 = p.m.depth[rs];
-  const void* __restrict__ A0 = p.m.packA[rs];
-  const void* __restrict__ B0 = p.m.packB[rs];
 
-  float A[9], t[3];
+  TileCtx c;
+  c.g = p.g;
   const float* xf = icp ? ctrl->xf_icp : ctrl->xf_rgb;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) A[k] = xf[k];
+  for (int k = 0; k < 9; ++k) c.A[k] = xf[k];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) t[k] = xf[9 + k];
+  for (int k = 0; k < 3; ++k) c.t[k] = xf[9 + k];
+  c.u = bx * kTrackThreadsX + lane;
+  c.col_ok = c.u < c.g.w;
+  const float uf = (float)c.u;
+  c.rx = (uf - c.g.cx) * c.g.ifx;
+  c.ucx = uf - c.g.cx;
+  c.lox = -uf;
+  c.hix = (float)c.g.w - uf;
+  c.ify_cy = -c.g.cy * c.g.ify;
+  c.kR = SPLIT ? kTrackThreadsY : kTrackRows;                // rows between a thread's rows
+  c.row0 = by * p.ppt * c.kR + wrow;
+  c.nrows = p.ppt;
+  c.dmin = p.depth_min;
+  c.dmax = p.depth_max;
+  c.dist2 = p.icp_dist2;
+  c.cosmin = p.icp_cos;
+  c.occ_thr = p.occ_thr;
+  c.A1 = p.m.packA[cs];
+  c.D1 = p.m.depth[cs];
+  c.I1 = p.m.inten[cs];
+  c.A0 = p.m.packA[rs];
+  c.D0 = p.m.depth[rs];
+  c.B0 = p.m.packB[rs];
+  c.flags = p.flags;
 
   float acc[kSums];
 #pragma unroll
   for (int k = 0; k < kSums; ++k) acc[k] = 0.f;
-
-  const int u = bx * kTrackThreadsX + lane;
-  const bool col_ok = u < g.w;
-  const float dmin = p.depth_min, dmax = p.depth_max;
-  // live samples of the thread's row r (zero depth outside the image)
-  auto load_live = [&](int r) {
-    Live L = {0.f, 0.f, 0.f, 0.f};
-    const int v = (by * p.ppt + r) * kR + wrow;
-    if (col_ok && v < g.h) {
-      const int o = v * g.w + u;
-      if (icp) {
-        const float4 a = Packs<T>::load_a(A1, D1, o);
-        L.d = a.w;
-        L.a = a.x;
-        L.b = a.y;
-        L.c = a.z;
-      } else {
-        L.d = Packs<T>::depth(A1, D1, o);
-        L.a = __ldg(I1 + o);
-      }
-    }
-    return L;
-  };
-  __shared__ uint8_t s_flag[kTrackRows][kTrackThreadsX];
-  Live cur = load_live(0);
-  for (int r = 0; r < p.ppt; ++r) {
-    const Live nxt = r + 1 < p.ppt ? load_live(r + 1) : Live{0.f, 0.f, 0.f, 0.f};
-    const int v = (by * p.ppt + r) * kR + wrow;
-    if (kPrefetchRows > 0 && r + kPrefetchRows < p.ppt) {
-      const int vf = v + kPrefetchRows * kR;
-      if (col_ok && vf < g.h) {
-        const int of = vf * g.w + u;
-        if (icp) {
-          prefetch_l2(static_cast<const char*>(A1) + (size_t)of * Packs<T>::kBytesA);
-          prefetch_l2(static_cast<const char*>(A0) + (size_t)of * Packs<T>::kBytesA);
-        } else {
-          prefetch_l2(I1 + of);
-          prefetch_l2(static_cast<const char*>(B0) + (size_t)of * Packs<T>::kBytesB);
-        }
-      }
-    }
-    bool ok = false;
-    unsigned assoc = 0u;
-    if (col_ok && v < g.h && cur.d >= dmin && cur.d <= dmax) {
-      ok = icp ? icp_pixel<T, (OPT & kOptDepthWeight) != 0>(p, g, A, t, A0, D0, u, v, cur, acc, &assoc)
-               : rgb_pixel<T, (OPT & kOptOcc) != 0>(g, A, t, B0, D0, p.occ_thr, u, v, cur, acc);
-    }
-    // flag byte: bit 0 ICP, bit 1 photometric, bits 2-5 the ICP association
-    const unsigned fbits = ok ? (icp ? 1u | (assoc << 2) : 2u) : 0u;
-    if (FLAGS && SPLIT) {    // or-ed into the zeroed flag bytes
-      if (ok) {
-        const int o = v * g.w + u;
-        atomicOr(reinterpret_cast<unsigned int*>(p.flags + (o & ~3)), fbits << (8 * (o & 3)));
-      }
-    } else if (FLAGS) {      // the two terms' bits combined through shared memory
-      if (icp) s_flag[wrow][lane] = (uint8_t)fbits;
-      __syncthreads();
-      if (!icp && col_ok && v < g.h) p.flags[v * g.w + u] = (uint8_t)(s_flag[wrow][lane] | fbits);
-      __syncthreads();
-    }
-    cur = nxt;
-  }
+  if (icp) icp_rows<T, (OPT & kOptDepthWeight) != 0, FLAGS>(c, acc);
+  else rgb_rows<T, (OPT & kOptOcc) != 0, FLAGS>(c, acc);
 
   // ---------------- reduction ----------------
   // Warp: transpose-reduce.  Padded to 32 values, five halving exchanges leave

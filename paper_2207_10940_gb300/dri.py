@@ -115,6 +115,12 @@ class dri_server_stats(ctypes.Structure):
                 ("hbm_budget", ctypes.c_size_t), ("streams", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class dri_server_tick(ctypes.Structure):
+    _fields_ = [("tick", ctypes.c_int64), ("requests", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("dequeue_ms", ctypes.c_double), ("staged_ms", ctypes.c_double),
+                ("launched_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
+
+
 class DriError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -184,6 +190,8 @@ def load_library():
         "dri_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, P(dri_track_result),
                                            ctypes.c_int32]),
         "dri_server_stats_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, P(dri_server_stats)]),
+        "dri_server_trace_read": (ctypes.c_int, [ctypes.c_void_p, P(dri_server_tick), ctypes.c_int32,
+                                                 P(ctypes.c_int32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -617,3 +625,12 @@ def dri_server_stats_read(srv, reset=False):
     _check(load_library().dri_server_stats_read(srv, int(bool(reset)), ctypes.byref(out)),
            "dri_server_stats_read")
     return out
+
+
+def dri_server_trace_read(srv, cap=65536):
+    """The most recent ticks' host timestamps (list of dri_server_tick, oldest first)."""
+    out = (dri_server_tick * cap)()
+    n = ctypes.c_int32()
+    _check(load_library().dri_server_trace_read(srv, out, int(cap), ctypes.byref(n)),
+           "dri_server_trace_read")
+    return list(out[: n.value])

@@ -49,3 +49,17 @@ def test_step_bandwidth_and_throughput():
     assert bench.PIXEL_ITERS_PER_FRAME == 307200 * 10 + 76800 * 5 + 19200 * 4
     # whole-job units/s: every rank does units_per_rank in the slowest rank's time
     assert bench.job_throughput(200 * 64, 4, 1000.0) == 4 * 200 * 64
+
+
+def test_tick_summary_phases():
+    class T:
+        def __init__(self, i, d, s, l, e, n=4):
+            self.tick, self.requests, self.status = i, n, 0
+            self.dequeue_ms, self.staged_ms, self.launched_ms, self.done_ms = d, s, l, e
+    tr = [T(0, 0.0, 0.5, 1.0, 11.0), T(1, 11.2, 11.4, 12.0, 80.0, n=9), T(2, 80.1, 80.3, 80.9, 91.0)]
+    s = bench.tick_summary(tr)
+    assert s["ticks"] == 3 and s["ticks_over_50ms"] == 1
+    assert abs(s["gpu"]["max"] - 68.0) < 1e-9 and abs(s["stage"]["max"] - 0.5) < 1e-9
+    assert abs(s["gap"]["max"] - 0.2) < 1e-9
+    assert s["slowest"]["requests"] == 9 and abs(s["slowest"]["at_ms"] - 11.2) < 1e-9
+    assert bench.tick_summary([]) is None
