@@ -688,6 +688,7 @@ def tick_summary(trace):
     ph = {"stage": [t.staged_ms - t.dequeue_ms for t in trace],
           "launch": [t.launched_ms - t.staged_ms for t in trace],
           "gpu": [t.done_ms - t.launched_ms for t in trace],
+          "device": [t.device_ms for t in trace],
           "tick": [t.done_ms - t.dequeue_ms for t in trace],
           "gap": [b.dequeue_ms - a.done_ms for a, b in zip(trace, trace[1:])] or [0.0]}
     out = {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99)),
@@ -695,13 +696,118 @@ def tick_summary(trace):
     w = max(trace, key=lambda t: t.done_ms - t.dequeue_ms)
     out["slowest"] = {"at_ms": w.dequeue_ms - trace[0].dequeue_ms, "requests": int(w.requests),
                       "stage_ms": w.staged_ms - w.dequeue_ms, "launch_ms": w.launched_ms - w.staged_ms,
-                      "gpu_ms": w.done_ms - w.launched_ms}
+                      "gpu_ms": w.done_ms - w.launched_ms, "device_ms": w.device_ms}
     out["ticks"] = len(trace)
     out["ticks_over_50ms"] = int(sum(1 for v in ph["tick"] if v > 50.0))
     return out
 
 
-def served_pass(args, dev, workers):
+def serve_frames(workers):
+    """The serving classes' looping sequences (320x240, 640x480, 1280x720) and
+    their SERVE_LOOP rendered frames, rendered once for the served, mixed-batch
+    and 320x240-pair passes."""
+    seqs = [_serve_sequence(c) for c in range(len(SERVE_CLASSES))]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers) as pool:
+        out = pool.map(_render_class, [(c, i) for c in range(len(SERVE_CLASSES)) for i in range(SERVE_LOOP)])
+    frames = [[None] * SERVE_LOOP for _ in SERVE_CLASSES]
+    for c, i, f in out:
+        frames[c][i] = f
+    return seqs, frames
+
+
+class ClassRunner:
+    """Streams of the serving classes tracked with dri_track_batch (or dri_track
+    for one stream): stream j of class c starts at loop frame (7 j + 3 c) mod
+    SERVE_LOOP; frames come from device memory (timed passes) or pinned host
+    memory (end-to-end pass)."""
+
+    def __init__(self, rendered, counts, dev, levels=LEVELS, iters=ITERS, n_frames=400, flags=0):
+        import torch
+        from paper_2207_10940_gb300 import dri, synth
+        self.dri, self.torch, self.dev = dri, torch, dev
+        seqs, frames = rendered
+        self.D = [torch.stack([torch.from_numpy(f[0]) for f in fc]).to(dev) for fc in frames]
+        self.I = [torch.stack([torch.from_numpy(f[1]) for f in fc]).to(dev) for fc in frames]
+        self.Dp = [torch.stack([torch.from_numpy(f[0]) for f in fc]).pin_memory() for fc in frames]
+        self.Ip = [torch.stack([torch.from_numpy(f[1]) for f in fc]).pin_memory() for fc in frames]
+        torch.cuda.synchronize(dev)
+        self.ts = torch.cuda.Stream(dev)
+        self.streams, self.cls, self.off = [], [], []
+        for c, count in enumerate(counts):
+            if not count:
+                continue
+            s = seqs[c]
+            cam = s.cam
+            cfg = dri.config_for(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, levels, iters,
+                                 q_CS=synth.matrix_to_quat(s.R_CS), r_CS=s.r_CS, precision_flags=flags)
+            imu = dri.imu_array(synth.sequence_imu(s, (SERVE_LOOP + n_frames + 2) / FPS, seed=SERVE_SEED + c))
+            for j in range(count):
+                o = (7 * j + 3 * c) % SERVE_LOOP
+                g = s.gt[o]
+                x0 = dict(t=o / FPS, r_WC=np.zeros(3), q_WC=np.array([1.0, 0, 0, 0]), v_I=g["v_I"].copy(),
+                          bg=np.zeros(3), ba=np.zeros(3), q_IW=synth.matrix_to_quat(g["R_IW"]))
+                st = dri.Stream(cfg, dri.state_from_dict(x0, o / FPS), self.ts)
+                dri.dri_push_imu(st.handle, imu)
+                self.streams.append(st)
+                self.cls.append(c)
+                self.off.append(o)
+        self.k = 0
+
+    def step(self, device_inputs=True, wait=False):
+        dri = self.dri
+        for st, c, o in zip(self.streams, self.cls, self.off):
+            j = o + self.k
+            if device_inputs:
+                dri.dri_upload_frame(st.handle, j / FPS, self.D[c][j % SERVE_LOOP], self.I[c][j % SERVE_LOOP],
+                                     mem_kind=dri.DRI_DEVICE)
+            else:
+                dri.dri_upload_frame(st.handle, j / FPS, self.Dp[c][j % SERVE_LOOP], self.Ip[c][j % SERVE_LOOP],
+                                     mem_kind=dri.DRI_HOST)
+        self.k += 1
+        if len(self.streams) == 1:
+            return dri.dri_track(self.streams[0].handle, wait=wait)
+        return dri.dri_track_batch(self.streams, wait=wait)
+
+    def close(self):
+        for st in self.streams:
+            st.close()
+
+
+def config_pass(rendered, counts, dev, steps, warmup, world, local, levels=LEVELS, iters=ITERS, flags=0,
+                what=""):
+    """frames/s of one step = one frame of each stream of `counts` (per serving
+    class), the step-level 56 B roofline on its pixel-iterations, and the same
+    metric end to end from pinned host frames."""
+    n_frames = 1 + warmup + steps + max(3, steps // 4) + 4
+    run = ClassRunner(rendered, counts, dev, levels, iters, n_frames, flags)
+    run.step(wait=True)
+    for _ in range(warmup):
+        run.step()
+    total_ms, per, launches, clocks = timed_pass(run, steps, world, local)
+    ok, failed = frame_counts(run)
+    e2e_steps = max(3, steps // 4)
+    e2e_s, h2d, d2h = e2e_pass(run, e2e_steps, world)
+    n = len(run.streams)
+    px = sum(cnt * sum((w >> l) * (h >> l) * iters[l] for l in range(levels))
+             for cnt, (w, h) in zip(counts, SERVE_CLASSES))
+    peak, peak_kind = measured_peaks()
+    bpp, _ = bytes_per_pixel_iter(flags)
+    achieved = bpp * px / (total_ms / steps / 1000.0) / 1e9
+    run.close()
+    return {"workload": what, "streams": n, "value": job_throughput(n * steps, world, total_ms),
+            "unit": "frames/s", "steps": steps, "ms_per_step": total_ms / steps,
+            "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+            "pixel_iters_per_step": px,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind, "bytes_per_pixel_iter": bpp,
+                         "over": "the whole step (every kernel of the frame)"},
+            "e2e": {"value": world * n * e2e_steps / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "frames_ok": int(ok), "frames_failed": int(failed), "gpu_launches": int(launches), "clocks": clocks}
+
+
+def served_pass(args, dev, workers, rendered=None):
     """Serving loop: SERVE_STREAMS streams (resolution by id mod 3), 30 Hz each with
     exponential arrival jitter, for args.serve_seconds of arrivals.  Frames are
     rendered in advance into pinned host memory and each request's frame is
@@ -711,13 +817,7 @@ def served_pass(args, dev, workers):
     import threading
     import torch
     from paper_2207_10940_gb300 import dri, synth
-    seqs = [_serve_sequence(c) for c in range(len(SERVE_CLASSES))]
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(workers) as pool:
-        out = pool.map(_render_class, [(c, i) for c in range(len(SERVE_CLASSES)) for i in range(SERVE_LOOP)])
-    frames = [[None] * SERVE_LOOP for _ in SERVE_CLASSES]
-    for c, i, f in out:
-        frames[c][i] = f
+    seqs, frames = rendered if rendered is not None else serve_frames(workers)
     D = [torch.stack([torch.from_numpy(f[0]) for f in fc]).pin_memory() for fc in frames]
     I = [torch.stack([torch.from_numpy(f[1]) for f in fc]).pin_memory() for fc in frames]
     secs = float(args.serve_seconds)
@@ -1046,9 +1146,24 @@ def run_ours(args):
             odo_occ = odometry_pass(seq, imu, d_dev, i_dev, d_pin, i_pin, dev, n_odo, args.precision_flags,
                                     args.imu_mode, occlusion_thr=ODOMETRY_OCCLUSION_THR)
         torch.cuda.synchronize(dev)
+    rendered = None
+    if args.serve_seconds > 0 or args.config_steps > 0:
+        rendered = serve_frames(min(16, os.cpu_count() or 4))
+    mixed = pair320 = None
+    if args.config_steps > 0:
+        # the mixed batch of uneven sizes: 24 x 320x240, 32 x 640x480, 8 x 1280x720
+        mixed = config_pass(rendered, (24, 32, 8), dev, args.config_steps, args.warmup, world, local,
+                            flags=args.precision_flags,
+                            what="24 x 320x240 + 32 x 640x480 + 8 x 1280x720 streams per step (one "
+                                 "dri_track_batch call), 3 levels 10/5/4")
+        # the 320x240 pair workload: one stream, 2 levels 10/5, one frame per step
+        pair320 = config_pass(rendered, (1, 0, 0), dev, args.config_steps * 4, args.warmup, world, local,
+                              levels=2, iters=(10, 5), flags=args.precision_flags,
+                              what="one 320x240 stream, 2 levels 10/5 (dri_track), one frame per step")
+        torch.cuda.synchronize(dev)
     served = None
     if args.serve_seconds > 0:
-        served = served_pass(args, dev, min(16, os.cpu_count() or 4))
+        served = served_pass(args, dev, min(16, os.cpu_count() or 4), rendered)
     precision = None
     if args.precision_frames > 1 and rank == 0:
         precision = precision_study(seq, frames, imu, dev, args.precision_frames)
@@ -1080,6 +1195,7 @@ def run_ours(args):
                               "frames_ok", "frames_failed", "roofline", "kernel_classes", "e2e",
                               "rows_per_thread")},
         "batched_over_plain": None if p is None else b["value"] / p["value"],
+        "mixed_batch": mixed, "pair_320x240": pair320,
         "odometry": None if odo_states is None else odometry_report(seq, odo_states, o_states),
         "odometry_rgbd_only": None if odo_rgbd is None else rgbd_only_report(seq, odo_rgbd),
         "odometry_gyro_only": None if odo_gyro is None else rgbd_only_report(seq, odo_gyro),
@@ -1118,6 +1234,8 @@ def main():
                     help="seconds of arrivals in the serving pass (0: skip it)")
     ap.add_argument("--saturate-seconds", type=float, default=10.0,
                     help="seconds of the serving saturation run after it (0: skip it)")
+    ap.add_argument("--config-steps", type=int, default=40,
+                    help="timed steps of the mixed-size batch and of the 320x240 pair stream (0: skip)")
     ap.add_argument("--rows-per-thread", type=lambda v: [int(x) for x in v.split(",")], default=None,
                     help="pixel-kernel rows per thread per level for the batched pass, e.g. 8,8,8 "
                          "(default: the plan's autotuner)")

@@ -202,9 +202,13 @@ int dri_destroy_stream(dri_stream s);
 
 /* Uploads the live frame at time t (seconds, strictly increasing): depth and
  * intensity, height rows of width floats, rows pitch_bytes apart (0 = packed,
- * a multiple of 4).  DRI_HOST: host memory, copied into the stream's workspace
- * stream-ordered on the stream's cuda_stream (pinned memory makes the copy
- * asynchronous).  DRI_DEVICE: device memory, not copied here: the first kernel
+ * a multiple of 4).  DRI_HOST: host memory.  Pageable memory is copied into the
+ * stream's workspace, stream-ordered on the stream's cuda_stream, before this
+ * call returns.  Pinned (page-locked) memory is not copied here: the GPU reads
+ * it directly over the host link in the first kernel of the next dri_track /
+ * dri_track_batch of this stream (one pass, no copy-engine transfer), so, as
+ * for DRI_DEVICE, the caller keeps it unchanged until that work has run.
+ * DRI_DEVICE: device memory, not copied here: the first kernel
  * of the next dri_track / dri_track_batch of this stream reads it, so the
  * caller keeps it unchanged until that work has run on cuda_stream, and work
  * that produces it on another stream is ordered before the track call (e.g.
@@ -372,6 +376,10 @@ typedef struct {
     double staged_ms;              /* their IMU samples and frame uploads were enqueued */
     double launched_ms;            /* the tick's batched frame was enqueued           */
     double done_ms;                /* the worker saw the tick's results complete      */
+    double device_ms;              /* device time of the tick's launch sequence (CUDA
+                                      events around it on the server's stream; -1 if
+                                      unavailable): the uploads read in its first
+                                      kernel, the batched frame, the result copy       */
 } dri_server_tick;
 
 /* Copies the most recent min(cap, recorded) ticks (the server keeps the last

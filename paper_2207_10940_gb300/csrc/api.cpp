@@ -1103,6 +1103,23 @@ int dri_destroy_stream(dri_stream s) {
   return DRI_OK;
 }
 
+namespace {
+
+// Device address of pinned (page-locked) host memory, which the GPU reads
+// directly; false for pageable memory or an unknown pointer.
+bool pinned_device_ptr(const void* p, const void** dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type != cudaMemoryTypeHost || a.devicePointer == nullptr) return false;
+  *dev = a.devicePointer;
+  return true;
+}
+
+}  // namespace
+
 int dri_upload_frame(dri_stream s, double t, const float* depth, const float* intensity,
                      size_t pitch_bytes, int32_t mem_kind) {
   if (!s || !depth || !intensity || !std::isfinite(t)) return DRI_EINVAL;
@@ -1112,7 +1129,14 @@ int dri_upload_frame(dri_stream s, double t, const float* depth, const float* in
   if (pitch < row || pitch % sizeof(float) != 0 || pitch / sizeof(float) > (size_t)INT32_MAX)
     return DRI_EINVAL;
   if (s->initialised && !(t > s->t_prev)) return DRI_EINVAL;
-  if (mem_kind == DRI_HOST) {
+  const void *pd = nullptr, *pi = nullptr;
+  if (mem_kind == DRI_HOST && pinned_device_ptr(depth, &pd) && pinned_device_ptr(intensity, &pi)) {
+    // pinned: the frame's first kernel reads the images over the host link
+    s->src_depth = static_cast<const float*>(pd);
+    s->src_inten = static_cast<const float*>(pi);
+    s->src_pitch = (int32_t)(pitch / sizeof(float));
+    s->h2d_frame = (int64_t)(2 * row * s->cfg.height);
+  } else if (mem_kind == DRI_HOST) {
     CK(cudaMemcpy2DAsync(s->in_depth, row, depth, pitch, row, s->cfg.height, cudaMemcpyHostToDevice,
                          s->stream));
     CK(cudaMemcpy2DAsync(s->in_inten, row, intensity, pitch, row, s->cfg.height,

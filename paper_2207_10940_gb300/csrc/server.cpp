@@ -72,7 +72,10 @@ struct Tick {
   int ring_slot;
   std::vector<TickEntry> entries;
   dri_server_tick trace;                      // done_ms filled when the tick completes
+  int ev;                                     // timing events of the tick (-1: none)
 };
+
+constexpr int kTickEvents = 4;                // pairs of timing events (ticks in flight + 1)
 
 }  // namespace
 
@@ -110,6 +113,8 @@ struct dri_server_s {
   std::vector<dri_server_tick> trace;
   size_t trace_next = 0;
   int64_t tick_seq = 0;
+  cudaEvent_t tev[kTickEvents][2] = {};       // device time of a tick's launch sequence
+  int tev_next = 0;
 };
 
 namespace {
@@ -148,6 +153,12 @@ void complete_tick(dri_server_s* S) {
   Tick tk = S->inflight.front();
   S->inflight.pop_front();
   tk.trace.done_ms = since_created(S);
+  float ms = -1.f;
+  if (tk.ev >= 0 && cudaEventElapsedTime(&ms, S->tev[tk.ev][0], S->tev[tk.ev][1]) != cudaSuccess) {
+    cudaGetLastError();
+    ms = -1.f;
+  }
+  tk.trace.device_ms = ms;
   record_tick(S, tk.trace);
   for (const TickEntry& e : tk.entries) {
     dri_stream_s* s = tk.plan->slots[e.slot];
@@ -265,6 +276,7 @@ void worker_main(dri_server_s* S) {
       std::vector<SlotWork> work;
       std::vector<double> t0;
       int rs = -1;
+      int tev = -1;
       if (rp == DRI_OK) {
         work.resize(plan->S);
         t0.resize(plan->S);
@@ -277,12 +289,18 @@ void worker_main(dri_server_s* S) {
         }
         bool any = false;
         for (const SlotWork& w : work) any = any || w.mode != kSlotIdle;
-        if (any) rp = plan_launch(plan, work, &rs);
+        if (any) {
+          tev = S->tev[S->tev_next][0] ? S->tev_next : -1;
+          if (tev >= 0) cudaEventRecord(S->tev[tev][0], S->stream);
+          rp = plan_launch(plan, work, &rs);
+          if (tev >= 0) cudaEventRecord(S->tev[tev][1], S->stream);
+          S->tev_next = (S->tev_next + 1) % kTickEvents;
+        }
       }
       tr.launched_ms = since_created(S);
       tr.status = rp;
       lk.lock();
-      Tick tk{plan, rs, {}, tr};
+      Tick tk{plan, rs, {}, tr, tev};
       for (size_t i = 0; i < reqs.size(); ++i) {
         int slot = -1;
         if (rp == DRI_OK && rs >= 0)
@@ -304,6 +322,7 @@ void worker_main(dri_server_s* S) {
         S->tick_frames += (int64_t)tk.entries.size();
       } else {                                 // nothing on the GPU: done as launched
         tk.trace.done_ms = tk.trace.launched_ms;
+        tk.trace.device_ms = 0.0;
         record_tick(S, tk.trace);
       }
       if (rp == DRI_OK && rs >= 0) remember_tiles(S);
@@ -335,6 +354,12 @@ int dri_server_create(size_t hbm_budget_bytes, int32_t max_batch, void* cuda_str
   S->max_batch = max_batch;
   S->stream = (cudaStream_t)cuda_stream;
   S->t_created = Clock::now();
+  for (int i = 0; i < kTickEvents; ++i)         // without events the trace reports device_ms -1
+    for (int j = 0; j < 2; ++j)
+      if (cudaEventCreate(&S->tev[i][j]) != cudaSuccess) {
+        cudaGetLastError();
+        S->tev[i][j] = nullptr;
+      }
   try {
     S->worker = std::thread(worker_main, S);
   } catch (...) {
@@ -356,6 +381,9 @@ int dri_server_destroy(dri_server S) {
   }
   S->cv_work.notify_all();
   S->worker.join();
+  for (int i = 0; i < kTickEvents; ++i)
+    for (int j = 0; j < 2; ++j)
+      if (S->tev[i][j]) cudaEventDestroy(S->tev[i][j]);
   delete S;
   return DRI_OK;
 }

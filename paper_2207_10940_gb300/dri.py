@@ -118,7 +118,8 @@ class dri_server_stats(ctypes.Structure):
 class dri_server_tick(ctypes.Structure):
     _fields_ = [("tick", ctypes.c_int64), ("requests", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("dequeue_ms", ctypes.c_double), ("staged_ms", ctypes.c_double),
-                ("launched_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
+                ("launched_ms", ctypes.c_double), ("done_ms", ctypes.c_double),
+                ("device_ms", ctypes.c_double)]
 
 
 class DriError(RuntimeError):

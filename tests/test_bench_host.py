@@ -56,6 +56,7 @@ def test_tick_summary_phases():
         def __init__(self, i, d, s, l, e, n=4):
             self.tick, self.requests, self.status = i, n, 0
             self.dequeue_ms, self.staged_ms, self.launched_ms, self.done_ms = d, s, l, e
+            self.device_ms = e - l
     tr = [T(0, 0.0, 0.5, 1.0, 11.0), T(1, 11.2, 11.4, 12.0, 80.0, n=9), T(2, 80.1, 80.3, 80.9, 91.0)]
     s = bench.tick_summary(tr)
     assert s["ticks"] == 3 and s["ticks_over_50ms"] == 1

@@ -215,3 +215,36 @@ def test_pipelined_frames_match_synchronous_tracking():
     for k in a:
         np.testing.assert_array_equal(a[k], b[k])
     np.testing.assert_array_equal(Ha, Hb)
+
+
+def test_pinned_host_upload_matches_device_upload():
+    """Pinned host frames (read by the GPU directly), pageable host frames (copied)
+    and device frames give bit-identical tracking."""
+    torch = _torch()
+    seq = synth.sinusoid_sequence(seed=7, cam=synth.scaled_camera(160, 120), n_frames=4)
+    _, dcfg = configs(seq, 3, (4, 3, 2))
+    x_init = synth.initial_state(seq)
+    kinds = {
+        "device": [(torch.from_numpy(d).cuda(), torch.from_numpy(i).cuda()) for d, i in
+                   zip(seq.depth, seq.intensity)],
+        "pinned": [(torch.from_numpy(d).pin_memory(), torch.from_numpy(i).pin_memory()) for d, i in
+                   zip(seq.depth, seq.intensity)],
+        "pageable": list(zip(seq.depth, seq.intensity)),
+    }
+    torch.cuda.synchronize()
+    out = {}
+    for name, frames in kinds.items():
+        st = new_stream(dcfg, x_init)
+        dri.dri_push_imu(st.handle, seq.imu)
+        for k, (d, i) in enumerate(frames):
+            mk = dri.DRI_DEVICE if name == "device" else dri.DRI_HOST
+            dri.dri_upload_frame(st.handle, seq.frame_times[k], d, i, mem_kind=mk)
+            assert dri.dri_track(st.handle).status == 0
+        out[name] = dri.state_to_dict(dri.dri_get_state(st.handle))
+        h2d, _ = dri.dri_io_bytes(st.handle)
+        if name != "device":
+            assert h2d >= 2 * 4 * seq.cam.width * seq.cam.height
+        st.close()
+    for name in ("pinned", "pageable"):
+        for key in out["device"]:
+            np.testing.assert_array_equal(out[name][key], out["device"][key], err_msg=f"{name} {key}")
