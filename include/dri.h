@@ -98,6 +98,21 @@ extern "C" {
  * (when that depth is valid); elsewhere the point changed visibility between
  * the frames and its intensity belongs to another surface. */
 
+/* Gravity direction in the state (dri_stream_config.gravity_dof).  The paper
+ * keeps q_IW with three degrees of freedom (Sec. II, IV-A) although two fix
+ * gravity's direction; the third, the turn about gravity, is a gauge freedom
+ * that no measurement sees.  DRI_GRAVITY_2DOF perturbs q_IW about I's x and y
+ * axes only (17 tangent dimensions per state; the turn about gravity is fixed
+ * and its freedom taken up by v_I).  DRI_GRAVITY_3D perturbs it about all three
+ * (18 per state, the paper's parameterisation): the first-frame prior holds
+ * all three axes, each Gauss-Newton step is damped on the gravity components of
+ * both states, (H + D_g) dx = b with D_g the identity there (the damping is not
+ * part of the cost; marginalisation takes the Schur complement of the undamped
+ * system), and the prior of dri_get_state / dri_set_state is 18 x 18.  Only
+ * for DRI_TRACK_INERTIAL; dri_linearise does not serve it (DRI_EINVAL). */
+#define DRI_GRAVITY_2DOF 2
+#define DRI_GRAVITY_3D   3
+
 #define DRI_MAX_LEVELS 4
 
 typedef struct dri_stream_s* dri_stream;
@@ -132,7 +147,7 @@ typedef struct {
     double rgbd_lambda;            /* RGB-D-only: photometric weight (default 1)      */
     double occlusion_thr;          /* > 0: photometric depth-consistency test, m; 0 off */
     int32_t icp_depth_weight;      /* 1: ICP weight W_ICP / z^4 (sigma_d at 1 m); 0 off */
-    int32_t reserved2;
+    int32_t gravity_dof;           /* DRI_GRAVITY_2DOF (0, default) | DRI_GRAVITY_3D    */
 } dri_stream_config;
 
 /* One IMU sample: time (s), gyro (rad/s) and accelerometer (m/s^2) in S. */
@@ -387,11 +402,12 @@ typedef struct {
 int dri_server_trace_read(dri_server srv, dri_server_tick* out, int32_t cap, int32_t* n);
 
 /* Waits for the stream and copies out x1 and, when non-NULL, the prior
- * H* (17 x 17, row-major) and b* (17) that the next frame will use. */
+ * H* (n x n, row-major) and b* (n) that the next frame will use: n = 17, or
+ * 18 for a stream with gravity_dof = DRI_GRAVITY_3D. */
 int dri_get_state(dri_stream s, dri_state* x1, double* H_prior, double* b_prior);
 
-/* Replaces x1 and, when non-NULL, the prior (checkpoint / resume).  The prior
- * mean becomes x1. */
+/* Replaces x1 and, when non-NULL, the prior (checkpoint / resume; sizes as
+ * dri_get_state).  The prior mean becomes x1. */
 int dri_set_state(dri_stream s, const dri_state* x1, const double* H_prior, const double* b_prior);
 
 /* Parity / debug entry: linearises every term of Eq. 6 at the given (x0, x1)

@@ -61,6 +61,9 @@ int valid_config(const dri_stream_config* c) {
   if (!(c->rgbd_lambda >= 0) || !std::isfinite(c->rgbd_lambda)) return DRI_EINVAL;
   if (!(c->occlusion_thr >= 0) || !std::isfinite(c->occlusion_thr)) return DRI_EINVAL;
   if (c->icp_depth_weight != 0 && c->icp_depth_weight != 1) return DRI_EINVAL;
+  if (c->gravity_dof != 0 && c->gravity_dof != DRI_GRAVITY_2DOF && c->gravity_dof != DRI_GRAVITY_3D)
+    return DRI_EINVAL;
+  if (c->gravity_dof == DRI_GRAVITY_3D && c->track_mode != DRI_TRACK_INERTIAL) return DRI_EINVAL;
   const double qn = c->T_CS[3] * c->T_CS[3] + c->T_CS[4] * c->T_CS[4] + c->T_CS[5] * c->T_CS[5] +
                     c->T_CS[6] * c->T_CS[6];
   if (!(std::fabs(qn - 1.0) < 1e-6)) return DRI_EINVAL;
@@ -288,6 +291,7 @@ SolveParams solve_params(const dri_stream_s* s, int level, int last) {
   p.min_valid = c.min_valid;
   p.imu_cap = s->L.imu_cap;
   p.imu_mode = c.imu_mode;
+  p.gdof = c.gravity_dof == DRI_GRAVITY_3D ? 3 : 2;
   p.relin_g = c.bias_relin_g;
   p.relin_a = c.bias_relin_a;
   p.track_mode = c.track_mode;
@@ -430,6 +434,7 @@ int plan_create(dri_stream_s* const* streams, int n, int ring, bool in_workspace
   p->fp16 = (streams[0]->cfg.precision_flags & DRI_FP16_MAPS) != 0;
   p->fp32p = (streams[0]->cfg.precision_flags & DRI_FP32_PARTIALS) != 0;
   p->opt = pixel_options(streams[0]->cfg);
+  for (int i = 0; i < n; ++i) p->g3 = p->g3 || streams[i]->cfg.gravity_dof == DRI_GRAVITY_3D;
   plan_set_groups(p, groups);
   // a batch plan's table has room for any group count; a stream's own plan has
   // one group and exactly the workspace's table region
@@ -710,7 +715,7 @@ int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
                       return launch_track_batch(at, nb, p->fp16, p->fp32p, p->opt, prio, p->groups == 1, sg);
                     }));
           const BatchArgs as = plan_args(p, p->tv.copy_off, l, remaining == 0, p->gfirst[g], p->gcount[g]);
-          CK(launch(prof, DRI_KC_SOLVE, 0.0, [&] { return launch_gn_step_batch(as, sg); }));
+          CK(launch(prof, DRI_KC_SOLVE, 0.0, [&] { return launch_gn_step_batch(as, p->g3, sg); }));
           k += 2;
         }
       }
@@ -1332,6 +1337,11 @@ int dri_track_batch(const dri_stream* streams, int32_t n, dri_track_result* out)
   return DRI_OK;
 }
 
+namespace {
+// Tangent dimension of one state of the stream (the prior's size).
+size_t prior_dim(const dri_stream_s* s) { return s->cfg.gravity_dof == DRI_GRAVITY_3D ? 18 : 17; }
+}  // namespace
+
 int dri_get_state(dri_stream s, dri_state* x1, double* H_prior, double* b_prior) {
   if (!s || !x1) return DRI_EINVAL;
   CK(cudaMemcpyAsync(s->pin_ctrl, s->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s->stream));
@@ -1339,8 +1349,9 @@ int dri_get_state(dri_stream s, dri_state* x1, double* H_prior, double* b_prior)
   if (settle(s, true) != DRI_OK) return DRI_ECUDA;
   const Ctrl* h = s->pin_ctrl;
   *x1 = from_dstate(h->x, h->t_state);
-  if (H_prior) std::memcpy(H_prior, h->Hs, sizeof(h->Hs));
-  if (b_prior) std::memcpy(b_prior, h->bs, sizeof(h->bs));
+  const size_t ns = prior_dim(s);
+  if (H_prior) std::memcpy(H_prior, h->Hs, ns * ns * sizeof(double));
+  if (b_prior) std::memcpy(b_prior, h->bs, ns * sizeof(double));
   return DRI_OK;
 }
 
@@ -1352,8 +1363,9 @@ int dri_set_state(dri_stream s, const dri_state* x1, const double* H_prior, cons
   h->x = to_dstate(*x1);
   h->xbar = h->x;
   h->t_state = x1->t;
-  if (H_prior) std::memcpy(h->Hs, H_prior, sizeof(h->Hs));
-  if (b_prior) std::memcpy(h->bs, b_prior, sizeof(h->bs));
+  const size_t ns = prior_dim(s);
+  if (H_prior) std::memcpy(h->Hs, H_prior, ns * ns * sizeof(double));
+  if (b_prior) std::memcpy(h->bs, b_prior, ns * sizeof(double));
   h->status = DRI_OK;
   CK(cudaMemcpyAsync(s->ctrl, h, sizeof(Ctrl), cudaMemcpyHostToDevice, s->stream));
   CK(cudaStreamSynchronize(s->stream));
@@ -1367,6 +1379,7 @@ int dri_linearise(dri_stream s, int32_t level, const dri_state* x0, const dri_st
                   dri_linearisation* out, uint8_t* flags) {
   if (!s || !x0 || !x1 || !out || level < 0 || level >= s->cfg.levels) return DRI_EINVAL;
   if (!finite_state(*x0) || !finite_state(*x1)) return DRI_EINVAL;
+  if (s->cfg.gravity_dof == DRI_GRAVITY_3D) return DRI_EINVAL;   // the output holds the 34-D system
   if (!s->initialised || !s->frame_pending) return DRI_ENOTREADY;
   if (settle(s, true) != DRI_OK) return DRI_ECUDA;
   size_t k0 = 0, k1 = 0;

@@ -65,12 +65,12 @@ struct Ctrl {
   // ---- solver state ----
   DState xbar;                        // prior mean
   DState xstart;                      // state at frame start (restored on DRI_ELOST)
-  double Hs[17 * 17];                 // prior information H* (Eq. 8a)
-  double bs[17];                      // prior vector b* (Eq. 8b)
+  double Hs[18 * 18];                 // prior information H* (Eq. 8a), ns x ns (ns = 17 or 18)
+  double bs[18];                      // prior vector b* (Eq. 8b)
   double Wimu[18 * 18];               // IMU weight
   double Rref[9], rref[3];            // pose T_ref the reference maps were made at
   double sums[64];                    // folded pixel sums of the current iteration
-  double H[34 * 34], b[34], d[34];    // last joint system and step (marginalisation)
+  double H[36 * 36], b[36], d[36];    // last joint system and step (marginalisation), 2 ns
   float xf_icp[12];                   // R_ref^T R_1 - I (row-major), R_ref^T (r_1 - r_ref)
   float xf_rgb[12];                   // R_0^T R_1 - I, R_0^T (r_1 - r_0)
   // DRI_IMU_FIRST_ORDER: the frame's pre-integration at its linearisation point
@@ -140,7 +140,7 @@ struct SolveParams {
   int32_t min_valid;
   int32_t imu_cap;
   int32_t imu_mode;                   // DRI_IMU_REINTEGRATE or DRI_IMU_FIRST_ORDER
-  int32_t pad;
+  int32_t gdof;                       // gravity degrees of freedom: 2 or 3 (state dimension 15 + gdof)
   double relin_g, relin_a;            // first order: re-integration thresholds
   int32_t track_mode;                 // DRI_TRACK_INERTIAL, _RGBD_ONLY or _GYRO_ONLY
   int32_t pad2;
@@ -278,7 +278,8 @@ inline int fold_groups(int nblocks) { return (nblocks + kFoldGroup - 1) / kFoldG
 cudaError_t prepare_solver_kernels();   // opt-in shared memory sizes (current device)
 int solver_max_imu_pieces();
 cudaError_t launch_frame_begin_batch(const BatchArgs& a, cudaStream_t s);
-cudaError_t launch_gn_step_batch(const BatchArgs& a, cudaStream_t s);
+// g3: some slot of the launch has the 3-D gravity form (larger shared memory)
+cudaError_t launch_gn_step_batch(const BatchArgs& a, bool g3, cudaStream_t s);
 cudaError_t launch_frame_end_batch(const BatchArgs& a, cudaStream_t s);
 cudaError_t launch_gather_heads(const BatchArgs& a, unsigned char* out, cudaStream_t s);
 cudaError_t launch_linearise_begin(const SolveParams& p, const DState& x0, const DState& x1,

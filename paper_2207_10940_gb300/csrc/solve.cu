@@ -425,14 +425,16 @@ __device__ constexpr unsigned char kJBlk[2][6][6] = {
      {0, 0, 0, 0, 0, 17 + 2 * kBJrg}}};
 
 // Whole block: prediction x^1(x0), error e = x^1 boxminus x1 and (when J) the
-// 18 x 34 Jacobian (row-major; columns: x0 tangent 0..16, x1 tangent 17..33).
+// 18 x 2 ns Jacobian (row-major; columns: x0 tangent 0..ns-1, x1 tangent
+// ns..2 ns-1; ns = 17 keeps the x and y columns of the gravity blocks, 18 all
+// three).
 // Warp 0 runs the chain of small products one output element per lane, up to
 // three independent products per pass (lanes 0-8, 9-17, 18-26).
 //   R^ = R0 Rc dR Rc^T,  r^ = r0 + R0 rc + Q0^T c + A0 dp - R^ rc  (A0 = R0 Rc),
 //   v^ = v0 + g T + Q0 A0 dv,  c = v0 T + g T^2 / 2,
 //   e = (r^ - r1, log(R^ R1^T), v^ - v1, b0 - b1, log(Q0 Q1^T)).
 __device__ void imu_linearise(const DState& x0, const DState& x1, const Preint& P,
-                              const SolveParams& sp, ImuLin& L, double* J) {
+                              const SolveParams& sp, ImuLin& L, double* J, int ns = 17) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int g3 = lane / 9, e9 = lane % 9;
@@ -537,9 +539,10 @@ __device__ void imu_linearise(const DState& x0, const DState& x1, const Preint& 
   __syncthreads();
   const double* src[14] = {L.Jra, L.Jrg, L.B[kB7], L.Jla, L.B[kB9], L.B[kB10], L.B[kB12],
                            L.B[kB13], L.B[kB14], L.B[kB16], L.B[kB17], L.B[kB19], L.B[kB20], L.Jlg};
-  for (int idx = tid; idx < 18 * 34; idx += blockDim.x) {
-    const int r = idx / 34, col = idx % 34;
-    const int side = col >= 17 ? 1 : 0, cl = col - 17 * side;
+  const int nj = 2 * ns;
+  for (int idx = tid; idx < 18 * nj; idx += blockDim.x) {
+    const int r = idx / nj, col = idx % nj;
+    const int side = col >= ns ? 1 : 0, cl = col - ns * side;
     const int cg = cl < 15 ? cl / 3 : 5, cc = cl < 15 ? cl % 3 : cl - 15;
     const int rb = r / 3, rr = r % 3;
     const int code = kJBlk[side][rb][cg];
@@ -598,12 +601,13 @@ __device__ __forceinline__ double quat_log_factor(double s2, double w) {
 
 // x <- x boxplus d (Eq. 2) by one warp; x, d in shared or global memory.  Lanes
 // 0-11 add the vector parts; lanes 0-3 update q with d[3..5], lanes 4-7 q_IW
-// with (d[15], d[16], 0): q <- exp(d) (x) q, renormalised.
-__device__ void warp_state_boxplus(DState& x, const double* d) {
+// with (d[15], d[16], 0), or d[15..17] with g3 (3-D gravity): q <- exp(d) (x) q,
+// renormalised.
+__device__ void warp_state_boxplus(DState& x, const double* d, bool g3 = false) {
   const int lane = threadIdx.x & 31;
   const int grp = (lane >> 2) & 1, k = lane & 3;
   double* q = grp ? x.qg : x.q;
-  const double d0 = grp ? d[15] : d[3], d1 = grp ? d[16] : d[4], d2 = grp ? 0.0 : d[5];
+  const double d0 = grp ? d[15] : d[3], d1 = grp ? d[16] : d[4], d2 = grp ? (g3 ? d[17] : 0.0) : d[5];
   const double t2 = d0 * d0 + d1 * d1 + d2 * d2;
   double sh, ch;
   if (t2 < kSeriesT2) {
@@ -632,10 +636,10 @@ __device__ void warp_state_boxplus(DState& x, const double* d) {
   __syncwarp();
 }
 
-// d = x boxminus y (17) by one warp: vector parts subtract; orientations
-// log(q_x (x) q_y^-1) (lanes 0-3), gravity the x, y of log(qg_x (x) qg_y^-1)
+// d = x boxminus y (17, or 18 with g3) by one warp: vector parts subtract; orientations
+// log(q_x (x) q_y^-1) (lanes 0-3), gravity the x, y (with g3 also z) of log(qg_x (x) qg_y^-1)
 // (lanes 4-7) -- the rotation vector of R_x R_y^T, taken with w >= 0.
-__device__ void warp_state_boxminus(const DState& x, const DState& y, double* d) {
+__device__ void warp_state_boxminus(const DState& x, const DState& y, double* d, bool g3 = false) {
   const int lane = threadIdx.x & 31;
   const int grp = (lane >> 2) & 1, k = lane & 3;
   const double* qx = grp ? x.qg : x.q;
@@ -656,7 +660,7 @@ __device__ void warp_state_boxminus(const DState& x, const DState& y, double* d)
     d[(g == 0 ? 0 : 3 + 3 * g) + i] = vx[i] - vy[i];
   }
   if (grp == 0 && k > 0 && lane < 4) d[2 + k] = f * o;
-  if (grp == 1 && k > 0 && k < 3 && lane < 8) d[14 + k] = f * o;
+  if (grp == 1 && k > 0 && (k < 3 || g3) && lane < 8) d[14 + k] = f * o;
   __syncwarp();
 }
 
@@ -976,7 +980,8 @@ __device__ __forceinline__ bool held_gyro_only(int k) {
 // Entry e (0..71) of the two pixel systems rotated into W: term e / 36 (0 ICP
 // with R_ref, 1 photometric with R_0), element e % 36 of its 6x6 (and, for
 // column 0, the row of its 6-vector), weighted by W_ICP / W_RGB.
-__device__ void pixel_system_entry(const SolveParams& sp, const Ctrl* c, GnSmem& S, int e) {
+template <class Smem>
+__device__ void pixel_system_entry(const SolveParams& sp, const Ctrl* c, Smem& S, int e) {
   const int term = e / 36, idx = e % 36;
   const int i = idx / 6, j = idx % 6;
   double R[9];
@@ -1323,6 +1328,210 @@ __device__ void gn_step_body(const SolveParams& sp, GnSmem& S) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// 3-D gravity form (gravity_dof = DRI_GRAVITY_3D; Sec. II and IV-A keep q_IW
+// with three degrees of freedom)
+// ---------------------------------------------------------------------------
+// The tangent space of a state has 18 dimensions (dr, da, dv, dbg, dba, dg with
+// dg in R^3, q_IW <- exp(dg) (x) q_IW), the joint system 36.  The turn about
+// gravity is a gauge that only the priors see, so each step is damped on the
+// gravity components of both states: (H + mu D_g) dx = b, D_g the identity on
+// coordinates 15..17 and 33..35, mu = kGravityDamping.  The damping regularises
+// the step only: the cost, the reported system and the marginalisation use the
+// undamped H.  The system is assembled whole (no closed-form elimination) and
+// factorised by the element-parallel LDL^T at N = 36.
+constexpr double kGravityDamping = 1.0;
+constexpr int kNs3 = 18, kNj3 = 36;
+
+__device__ __forceinline__ bool gravity_coord3(int k) { return (k >= 15 && k < 18) || k >= 33; }
+
+struct Gn3Smem {
+  ImuWork W;
+  Preint P;
+  ImuLin L;
+  DState x0, x1;
+  double J[18 * kNj3];
+  double WJ[18 * kNj3];               // W_IMU J
+  double We[18];                      // W_IMU e
+  double H[kNj3 * kNj3];              // undamped joint system
+  double A[kNj3 * kNj3];              // damped, Jacobi-scaled copy for the factorisation
+  double b[kNj3], x[kNj3], scale[kNj3];
+  double Hl[2][36];                   // world-frame 6x6 of ICP, photometric (weighted)
+  double gl[2][6];
+  double M6[36], MH6[36];
+  double dprior[kNs3];
+  double col[2 * (kNj3 + 1)];
+  double Lsm[kNj3 * kNj3];
+  double piv[kNj3];
+  double fo[21];
+  double rot[18];
+  double cost_imu;
+  int ok, pd;
+};
+
+// One Gauss-Newton step of the 3-D form (RGB-D-inertial tracking only).
+__device__ void gn_step_g3(const SolveParams& sp, Gn3Smem& S) {
+  Ctrl* c = sp.ctrl;
+  if (c->status != 0) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    S.x0 = c->x0;
+    S.x1 = c->x1;
+  }
+  if ((tid >> 5) == 4) {
+    warp_state_boxminus(c->x0, c->xbar, S.dprior, true);
+  } else if (tid == 160) {
+    for (int i = 0; i < 36; ++i) S.M6[i] = (i % 7 == 0) ? 1.0 : 0.0;
+    const double d[3] = {c->x1.r[0] - c->x0.r[0], c->x1.r[1] - c->x0.r[1], c->x1.r[2] - c->x0.r[2]};
+    double K[9];
+    hat3(d, K);
+    for (int r = 0; r < 3; ++r)
+      for (int q = 0; q < 3; ++q) S.M6[(3 + r) * 6 + q] = K[r * 3 + q];
+  }
+  __syncthreads();
+  S.ok = sp.imu_mode == DRI_IMU_FIRST_ORDER
+             ? preint_first_order(sp, c, S.x0.bg, S.x0.ba, S.W, S.P, S.fo)
+             : preintegrate_block(sp.imu, S.x0.bg, S.x0.ba, false, 0.0, 0.0, S.W, S.P);
+  if (!S.ok) {
+    if (tid == 0) c->status = DRI_ENOTREADY;
+    return;
+  }
+  imu_linearise(S.x0, S.x1, S.P, sp, S.L, S.J, kNs3);
+  for (int idx = tid; idx < 18 * kNj3; idx += nt) {
+    const int r = idx / kNj3, col = idx % kNj3;
+    double acc = 0.0;
+    for (int m = 0; m < 18; ++m) acc += c->Wimu[r * 18 + m] * S.J[m * kNj3 + col];
+    S.WJ[idx] = acc;
+  }
+  if (tid < 18) {
+    double acc = 0.0;
+    for (int m = 0; m < 18; ++m) acc += c->Wimu[tid * 18 + m] * S.L.e[m];
+    S.We[tid] = acc;
+  }
+  // everything above depends on the states only; now the pixel sums
+  grid_dep_wait();
+  if (tid >= 32 && tid < 32 + 2 * 36) pixel_system_entry(sp, c, S, tid - 32);
+  __syncthreads();
+  if (tid < 36) {                       // MH6 = M H6 (photometric term)
+    const int i = tid / 6, j = tid % 6;
+    double acc = 0.0;
+    for (int k = 0; k < 6; ++k) acc += S.M6[i * 6 + k] * S.Hl[1][k * 6 + j];
+    S.MH6[tid] = acc;
+  }
+  // H upper = J^T W J, b = -J^T W e, the IMU cost
+  for (int idx = tid; idx < kNj3 * kNj3; idx += nt) {
+    const int i = idx / kNj3, j = idx % kNj3;
+    if (j < i) continue;
+    double v = 0.0;
+    for (int m = 0; m < 18; ++m) v += S.J[m * kNj3 + i] * S.WJ[m * kNj3 + j];
+    S.H[idx] = v;
+  }
+  if (tid >= 200 && tid < 200 + kNj3) {
+    const int i = tid - 200;
+    double v = 0.0;
+    for (int m = 0; m < 18; ++m) v -= S.J[m * kNj3 + i] * S.We[m];
+    S.b[i] = v;
+  }
+  if (tid == 0) {
+    double ce = 0.0;
+    for (int m = 0; m < 18; ++m) ce += S.L.e[m] * S.We[m];
+    S.cost_imu = ce;
+  }
+  __syncthreads();
+  // photometric on both poses (H12 = B H6 B^T, B = [-M; I]) and ICP on x1's pose
+  for (int idx = tid; idx < 12 * 12; idx += nt) {
+    const int i = idx / 12, j = idx % 12;
+    if (j < i) continue;
+    const int a = i / 6, bb = j / 6, ii = i % 6, jj = j % 6;
+    double v;
+    if (a == 1 && bb == 1) {
+      v = S.Hl[1][ii * 6 + jj] + S.Hl[0][ii * 6 + jj];
+    } else if (a == 0 && bb == 1) {
+      v = -S.MH6[ii * 6 + jj];
+    } else {
+      v = 0.0;
+      for (int k = 0; k < 6; ++k) v += S.MH6[ii * 6 + k] * S.M6[jj * 6 + k];
+    }
+    const int gi = a == 0 ? ii : kNs3 + ii, gj = bb == 0 ? jj : kNs3 + jj;
+    S.H[gi * kNj3 + gj] += v;
+  }
+  if (tid >= 160 && tid < 166) {
+    const int i = tid - 160;
+    double g0 = 0.0;
+    for (int k = 0; k < 6; ++k) g0 -= S.M6[i * 6 + k] * S.gl[1][k];
+    S.b[i] += g0;
+    S.b[kNs3 + i] += S.gl[1][i] + S.gl[0][i];
+  }
+  __syncthreads();
+  // prior on x0: H00 += H*, b0 += b* - H* (x0 boxminus xbar)
+  for (int idx = tid; idx < kNs3 * kNs3; idx += nt) {
+    const int i = idx / kNs3, j = idx % kNs3;
+    if (j >= i) S.H[i * kNj3 + j] += c->Hs[idx];
+  }
+  if (tid >= 192 && tid < 192 + kNs3) {
+    const int i = tid - 192;
+    double acc = c->bs[i];
+    for (int k = 0; k < kNs3; ++k) acc -= c->Hs[i * kNs3 + k] * S.dprior[k];
+    S.b[i] += acc;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < kNj3 * kNj3; idx += nt) {
+    const int i = idx / kNj3, j = idx % kNj3;
+    if (j < i) S.H[idx] = S.H[j * kNj3 + i];
+  }
+  __syncthreads();
+  // the damped step, Jacobi-scaled
+  if (tid < kNj3)
+    S.scale[tid] = rsqrt(fmax(S.H[tid * kNj3 + tid] + (gravity_coord3(tid) ? kGravityDamping : 0.0), 1e-300));
+  __syncthreads();
+  for (int idx = tid; idx < kNj3 * kNj3; idx += nt) {
+    const int i = idx / kNj3, j = idx % kNj3;
+    const double h = S.H[idx] + ((i == j && gravity_coord3(i)) ? kGravityDamping : 0.0);
+    S.A[idx] = h * S.scale[i] * S.scale[j];
+  }
+  if (tid < kNj3) S.x[tid] = S.b[tid] * S.scale[tid];
+  __syncthreads();
+  if (tid < 128) {
+    const bool pd = ep_ldlt_solve<kNj3, 128>(S.A, S.x, S.x, S.col, S.Lsm, S.piv);
+    if (tid == 0) S.pd = pd;
+  }
+  __syncthreads();
+  if (tid < kNj3) S.x[tid] *= S.scale[tid];
+  __syncthreads();
+  bool good = S.pd;
+  for (int i = 0; i < kNj3; ++i) good = good && isfinite(S.x[i]);
+  if (!good) {
+    if (tid == 0) c->status = DRI_ELOST;
+    return;
+  }
+  const int warp = tid >> 5;
+  if (warp == 0) {
+    warp_state_boxplus(S.x0, S.x, true);
+  } else if (warp == 1) {
+    warp_state_boxplus(S.x1, S.x + kNs3, true);
+  } else if (tid == 64) {
+    const double* s = c->sums;
+    c->n_icp[sp.level] = (int32_t)s[28];
+    c->n_rgb[sp.level] = (int32_t)s[kSums + 28];
+    c->cost = sp.W_icp * s[27] + sp.W_rgb * s[kSums + 27] + S.cost_imu;
+    c->iterations += 1;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    warp_write_transforms(c, S.x0, S.x1, S.rot);
+  } else if (tid == 32) {
+    c->x0 = S.x0;
+    c->x1 = S.x1;
+  }
+  if (sp.last) {
+    for (int idx = tid; idx < kNj3 * kNj3; idx += nt) c->H[idx] = S.H[idx];
+    if (tid >= 64 && tid < 64 + kNj3) {
+      c->b[tid - 64] = S.b[tid - 64];
+      c->d[tid - 64] = S.x[tid - 64];
+    }
+  }
+}
+
 // W_IMU at c->x0 (noise propagated through the recursion, Sigma^-1), and the
 // IMU prediction x^1(x0).  Whole block; false (status set) on failure.
 struct BeginSmem {
@@ -1463,7 +1672,10 @@ __device__ void frame_begin_body(const SolveParams& sp, BeginSmem& B) {
   if (ok && (tid >> 5) == 0) warp_write_transforms(c, c->x0, c->x1, B.rot);
 }
 
+// NS: tangent dimension of a state (17, or 18 for the 3-D gravity form).
+template <int NS>
 __device__ void frame_end_body(const SolveParams& sp) {
+  constexpr int NJ = 2 * NS;
   Ctrl* c = sp.ctrl;
   const int tid = threadIdx.x;
   __shared__ int s_ok, s_fail;
@@ -1487,38 +1699,38 @@ __device__ void frame_end_body(const SolveParams& sp) {
     return;
   }
   // b' = b - H d; Schur complement of the x0 block (Eq. 8)
-  __shared__ double H[34 * 34];
-  __shared__ double bp[34];
-  __shared__ double L[17 * 17];
-  __shared__ double X[17 * 18];
-  __shared__ double colbuf[34];
-  __shared__ double Hs[17 * 17], bs[17];
-  for (int idx = tid; idx < 34 * 34; idx += blockDim.x) H[idx] = c->H[idx];
+  __shared__ double H[NJ * NJ];
+  __shared__ double bp[NJ];
+  __shared__ double L[NS * NS];
+  __shared__ double X[NS * (NS + 1)];
+  __shared__ double colbuf[NJ];
+  __shared__ double Hs[NS * NS], bs[NS];
+  for (int idx = tid; idx < NJ * NJ; idx += blockDim.x) H[idx] = c->H[idx];
   __syncthreads();
-  if (tid < 34) {
+  if (tid < NJ) {
     double acc = c->b[tid];
-    for (int k = 0; k < 34; ++k) acc -= H[tid * 34 + k] * c->d[k];
+    for (int k = 0; k < NJ; ++k) acc -= H[tid * NJ + k] * c->d[k];
     bp[tid] = acc;
   }
-  for (int idx = tid; idx < 17 * 17; idx += blockDim.x) L[idx] = H[(idx / 17) * 34 + idx % 17];
+  for (int idx = tid; idx < NS * NS; idx += blockDim.x) L[idx] = H[(idx / NS) * NJ + idx % NS];
   __syncthreads();
-  const bool pd = block_ldlt(L, 17, 17, colbuf, &s_fail);
-  if (tid < 18) {
-    double colv[17];
-    for (int i = 0; i < 17; ++i) colv[i] = tid < 17 ? H[i * 34 + 17 + tid] : bp[i];
-    ldlt_solve_thread(L, 17, 17, colv);
-    for (int i = 0; i < 17; ++i) X[i * 18 + tid] = colv[i];
+  const bool pd = block_ldlt(L, NS, NS, colbuf, &s_fail);
+  if (tid < NS + 1) {
+    double colv[NS];
+    for (int i = 0; i < NS; ++i) colv[i] = tid < NS ? H[i * NJ + NS + tid] : bp[i];
+    ldlt_solve_thread(L, NS, NS, colv);
+    for (int i = 0; i < NS; ++i) X[i * (NS + 1) + tid] = colv[i];
   }
   __syncthreads();
-  for (int idx = tid; idx < 17 * 17; idx += blockDim.x) {
-    const int i = idx / 17, j = idx % 17;
-    double acc = H[(17 + i) * 34 + 17 + j];
-    for (int k = 0; k < 17; ++k) acc -= H[(17 + i) * 34 + k] * X[k * 18 + j];
+  for (int idx = tid; idx < NS * NS; idx += blockDim.x) {
+    const int i = idx / NS, j = idx % NS;
+    double acc = H[(NS + i) * NJ + NS + j];
+    for (int k = 0; k < NS; ++k) acc -= H[(NS + i) * NJ + k] * X[k * (NS + 1) + j];
     Hs[idx] = acc;
   }
-  if (tid < 17) {
-    double acc = bp[17 + tid];
-    for (int k = 0; k < 17; ++k) acc -= H[(17 + tid) * 34 + k] * X[k * 18 + 17];
+  if (tid < NS) {
+    double acc = bp[NS + tid];
+    for (int k = 0; k < NS; ++k) acc -= H[(NS + tid) * NJ + k] * X[k * (NS + 1) + NS];
     bs[tid] = acc;
   }
   __syncthreads();
@@ -1529,12 +1741,13 @@ __device__ void frame_end_body(const SolveParams& sp) {
     }
     return;
   }
-  const bool gyro = sp.track_mode == DRI_TRACK_GYRO_ONLY;   // no information on held parts
-  for (int idx = tid; idx < 17 * 17; idx += blockDim.x) {
-    const int i = idx / 17, j = idx % 17;
-    c->Hs[idx] = gyro && (held_gyro_only(i) || held_gyro_only(j)) ? 0.0 : 0.5 * (Hs[i * 17 + j] + Hs[j * 17 + i]);
+  // no information on held parts (gyro-only, 2-DoF form only)
+  const bool gyro = NS == 17 && sp.track_mode == DRI_TRACK_GYRO_ONLY;
+  for (int idx = tid; idx < NS * NS; idx += blockDim.x) {
+    const int i = idx / NS, j = idx % NS;
+    c->Hs[idx] = gyro && (held_gyro_only(i) || held_gyro_only(j)) ? 0.0 : 0.5 * (Hs[i * NS + j] + Hs[j * NS + i]);
   }
-  if (tid < 17) c->bs[tid] = gyro && held_gyro_only(tid) ? 0.0 : bs[tid];
+  if (tid < NS) c->bs[tid] = gyro && held_gyro_only(tid) ? 0.0 : bs[tid];
   if (tid == 0) {
     c->x = c->x1;
     c->xbar = c->x1;
@@ -1544,12 +1757,13 @@ __device__ void frame_end_body(const SolveParams& sp) {
   }
 }
 
+template <int NS>
 __device__ void frame_init_body(const SolveParams& sp) {
   const double t_frame = sp.imu->t1;
   Ctrl* c = sp.ctrl;
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < 17 * 17; idx += blockDim.x) {
-    const int i = idx / 17, j = idx % 17;
+  for (int idx = tid; idx < NS * NS; idx += blockDim.x) {
+    const int i = idx / NS, j = idx % NS;
     double v = 0.0;
     if (i == j) {
       const double s = i < 6 ? sp.prior_sigma[0]
@@ -1560,7 +1774,7 @@ __device__ void frame_init_body(const SolveParams& sp) {
     }
     c->Hs[idx] = v;
   }
-  if (tid < 17) c->bs[tid] = 0.0;
+  if (tid < NS) c->bs[tid] = 0.0;
   if (tid == 0) {
     c->status = 0;
     c->xbar = c->x;
@@ -1649,11 +1863,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_frame_begin_batch(const Batch
   if (load_slot_params(a, sp) == kSlotTrack) frame_begin_body(sp, *reinterpret_cast<BeginSmem*>(smem_raw));
 }
 
+constexpr size_t kGnSmemMax = sizeof(Gn3Smem) > sizeof(GnSmem) ? sizeof(Gn3Smem) : sizeof(GnSmem);
+
 __global__ void __launch_bounds__(kSolveThreads) k_gn_step_batch(const BatchArgs a) {
   __shared__ SolveParams sp;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   grid_dep_launch();                    // the next pixel kernel waits for this step itself
-  if (load_slot_params(a, sp) == kSlotTrack) gn_step_body(sp, *reinterpret_cast<GnSmem*>(smem_raw));
+  const int mode = load_slot_params(a, sp);
+  if (mode == kSlotTrack && sp.gdof == 3) gn_step_g3(sp, *reinterpret_cast<Gn3Smem*>(smem_raw));
+  else if (mode == kSlotTrack) gn_step_body(sp, *reinterpret_cast<GnSmem*>(smem_raw));
   else grid_dep_wait();                 // idle slot: nothing to read, keep the ordering
 }
 
@@ -1663,8 +1881,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_gn_step_batch(const BatchArgs
 __global__ void __launch_bounds__(kSolveThreads) k_frame_end_batch(const BatchArgs a) {
   __shared__ SolveParams sp;
   const int mode = load_slot_params(a, sp);
-  if (mode == kSlotTrack) frame_end_body(sp);
-  else if (mode == kSlotInit) frame_init_body(sp);
+  if (mode == kSlotTrack) {
+    if (sp.gdof == 3) frame_end_body<18>(sp);
+    else frame_end_body<17>(sp);
+  } else if (mode == kSlotInit) {
+    if (sp.gdof == 3) frame_init_body<18>(sp);
+    else frame_init_body<17>(sp);
+  }
 }
 
 // Result heads of all slots into one contiguous buffer (one copy to the host).
@@ -1679,7 +1902,7 @@ __global__ void k_gather_heads(const BatchArgs a, unsigned char* __restrict__ ou
 
 cudaError_t prepare_solver_kernels() {
   cudaError_t e = cudaFuncSetAttribute(k_gn_step_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(GnSmem));
+                                       (int)kGnSmemMax);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_linearise_end, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(GnSmem));
@@ -1713,11 +1936,11 @@ int launch_priority(bool solver) {
 // SM: with several slot groups, one group's FP64 step runs beside another
 // group's pixel kernel instead of waiting for its last wave.
 
-cudaError_t launch_gn_step_batch(const BatchArgs& a, cudaStream_t s) {
+cudaError_t launch_gn_step_batch(const BatchArgs& a, bool g3, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(a.nslots);
   cfg.blockDim = dim3(kSolveThreads);
-  cfg.dynamicSmemBytes = sizeof(GnSmem);
+  cfg.dynamicSmemBytes = g3 ? kGnSmemMax : sizeof(GnSmem);
   cfg.stream = s;
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

@@ -58,7 +58,7 @@ class dri_stream_config(ctypes.Structure):
         ("bias_relin_g", ctypes.c_double), ("bias_relin_a", ctypes.c_double),
         ("track_mode", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("rgbd_lambda", ctypes.c_double), ("occlusion_thr", ctypes.c_double),
-        ("icp_depth_weight", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+        ("icp_depth_weight", ctypes.c_int32), ("gravity_dof", ctypes.c_int32),
     ]
 
 
@@ -244,11 +244,13 @@ def dri_create_stream(cfg, x_init, cuda_stream=None, workspace=None, workspace_b
                                             ctypes.c_size_t(workspace_bytes), ctypes.byref(h)),
            "dri_create_stream")
     _shapes[h.value] = (int(cfg.width), int(cfg.height))
+    _prior_dims[h.value] = 18 if cfg.gravity_dof == DRI_GRAVITY_3D else 17
     return h
 
 
 def dri_destroy_stream(s):
     _shapes.pop(_hval(s), None)
+    _prior_dims.pop(_hval(s), None)
     return _check(load_library().dri_destroy_stream(s), "dri_destroy_stream")
 
 
@@ -258,8 +260,12 @@ def _ptr(a):
     return a.ctypes.data
 
 
-# (width, height) of each open stream handle, for the argument checks below
+# (width, height) of each open stream handle, for the argument checks below,
+# and the size of its prior (17, or 18 with the 3-D gravity form)
 _shapes = {}
+_prior_dims = {}
+DRI_GRAVITY_2DOF = 2
+DRI_GRAVITY_3D = 3
 
 
 def _hval(s):
@@ -414,11 +420,17 @@ def dri_batch_set_options(streams, rows_per_thread=None, groups=None, autotune=N
            "dri_batch_set_options")
 
 
+def prior_dim(s):
+    """Size of the stream's prior (17, or 18 for the 3-D gravity form)."""
+    return _prior_dims.get(_hval(s), 17)
+
+
 def dri_get_state(s, with_prior=False):
     x = dri_state()
     if with_prior:
-        H = np.zeros((17, 17))
-        b = np.zeros(17)
+        n = prior_dim(s)
+        H = np.zeros((n, n))
+        b = np.zeros(n)
         _check(load_library().dri_get_state(s, ctypes.byref(x), H.ctypes.data_as(c_double_p),
                                             b.ctypes.data_as(c_double_p)), "dri_get_state")
         return x, H, b
@@ -427,8 +439,11 @@ def dri_get_state(s, with_prior=False):
 
 
 def dri_set_state(s, x1, H_prior=None, b_prior=None):
+    n = prior_dim(s)
     Hp = None if H_prior is None else np.ascontiguousarray(H_prior, dtype=np.float64)
     bp = None if b_prior is None else np.ascontiguousarray(b_prior, dtype=np.float64)
+    if (Hp is not None and Hp.size != n * n) or (bp is not None and bp.size != n):
+        raise DriError(DRI_EINVAL, f"dri_set_state: the prior is {n} x {n} for this stream")
     return _check(load_library().dri_set_state(
         s, ctypes.byref(x1), None if Hp is None else Hp.ctypes.data_as(c_double_p),
         None if bp is None else bp.ctypes.data_as(c_double_p)), "dri_set_state")
@@ -583,11 +598,13 @@ def dri_server_open_stream(srv, cfg, x_init):
     _check(load_library().dri_server_open_stream(srv, ctypes.byref(cfg), ctypes.byref(x_init),
                                                  ctypes.byref(h)), "dri_server_open_stream")
     _shapes[h.value] = (int(cfg.width), int(cfg.height))
+    _prior_dims[h.value] = 18 if cfg.gravity_dof == DRI_GRAVITY_3D else 17
     return h
 
 
 def dri_server_close_stream(srv, s):
     _shapes.pop(_hval(s), None)
+    _prior_dims.pop(_hval(s), None)
     return _check(load_library().dri_server_close_stream(srv, s), "dri_server_close_stream")
 
 

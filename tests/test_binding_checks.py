@@ -85,3 +85,18 @@ def test_noalloc_rejects_options_and_states_before_any_cuda_call(dri):
     nan_r = _state(dri)
     nan_r.r_WC[1] = float("nan")
     assert _noalloc(dri, cfg, nan_r) == dri.DRI_EINVAL
+
+
+def test_gravity_form_is_validated_on_the_host(dri):
+    cfg = dri.dri_config_default(320, 240)
+    assert dri.dri_stream_workspace_bytes(cfg) > 0
+    cfg.gravity_dof = dri.DRI_GRAVITY_3D
+    assert dri.dri_stream_workspace_bytes(cfg) > 0
+    cfg.track_mode = 1                       # the 3-D form serves the inertial tracker only
+    _einval(dri, dri.dri_stream_workspace_bytes, cfg)
+    cfg = dri.dri_config_default(320, 240)
+    cfg.gravity_dof = 5
+    _einval(dri, dri.dri_stream_workspace_bytes, cfg)
+    cfg = dri.dri_config_default(320, 240)
+    cfg.icp_angle_thr_deg = 90.0             # the angle test must reject zero normals
+    _einval(dri, dri.dri_stream_workspace_bytes, cfg)
