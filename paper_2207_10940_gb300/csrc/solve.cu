@@ -763,9 +763,20 @@ __device__ __forceinline__ double pivot_recip(double d) {
 // the number of active lanes, so the work is spread over the lanes of T/32 warps
 // on different sub-partitions.  Scratch: colbuf 2 (N + 1), Lsm N * N, piv N.
 // Returns false (in every calling thread) if a pivot is not positive.
-template <int N, int T>
+//
+// NS > 0 splits the sweep for a system whose trailing (N - NS) x (N - NS) block
+// and right-hand side still lack an additive term that is not known yet: the
+// first NS pivots run on what A and b hold, which leaves the Schur complement
+// of the leading block in the trailing entries; then the calling threads wait
+// for the preceding kernel (grid dependency) and for the other T threads of the
+// block (barrier 2 over 2 T threads), which publish the missing term in Padd
+// ((N - NS) x (N - NS), full) and gadd (N - NS); the owners add it to their
+// trailing entries and the sweep finishes.  Elimination order does not matter
+// for an additive update of entries that no earlier pivot reads.
+template <int N, int T, int NS = 0>
 __device__ bool ep_ldlt_solve(const double* A, const double* b, double* x, double* colbuf,
-                              double* Lsm, double* piv) {
+                              double* Lsm, double* piv, const double* Padd = nullptr,
+                              const double* gadd = nullptr) {
   constexpr int kTri = N * (N + 1) / 2;
   constexpr int kEnt = kTri + N;                     // lower triangle + the b column
   constexpr int kOwn = (kEnt + T - 1) / T;
@@ -790,6 +801,15 @@ __device__ bool ep_ldlt_solve(const double* A, const double* b, double* x, doubl
     v[o] = (i < 0) ? 0.0 : (j == N ? b[i] : A[i * N + j]);
   }
   for (int k = 0; k < N; ++k) {
+    if (NS > 0 && k == NS) {
+      grid_dep_wait();
+      asm volatile("bar.sync 2, %0;" ::"n"(2 * T) : "memory");
+#pragma unroll
+      for (int o = 0; o < kOwn; ++o) {
+        const int i = ei[o], j = ej[o];
+        if (i >= NS && j >= NS) v[o] += j == N ? gadd[i - NS] : Padd[(i - NS) * (N - NS) + (j - NS)];
+      }
+    }
     double* cb = colbuf + (k & 1) * (N + 1);
 #pragma unroll
     for (int o = 0; o < kOwn; ++o) {
@@ -955,6 +975,7 @@ struct GnSmem {
   double Hl[2][36];                   // world-frame 6x6 of ICP, photometric (weighted)
   double gl[2][6];
   double M6[36], MH6[36];
+  double P12[144], g12[12];           // the pixel terms on the poses of (x0, x1), full
   double dprior[17];
   double Hr[26 * 26], br[26];          // reduced system (x1's bias / gravity eliminated)
   double xr[26], piv[26];
@@ -1010,7 +1031,14 @@ __device__ void pixel_system_entry(const SolveParams& sp, const Ctrl* c, Smem& S
 }
 
 
-__device__ void assemble(const SolveParams& sp, GnSmem& S) {
+// State-only part of the joint system (Eq. 7 without the pixel terms) at
+// (ctrl->x0, ctrl->x1): the IMU term (Eq. 5-6), the prior on x0, and the
+// reduced system with x1's biases and gravity eliminated in closed form.
+// Whole block.  Reads no pixel sum, so it runs while the preceding pixel kernel
+// is still at work.  Leaves the upper triangle of the full 34-dimensional S.H,
+// S.b, the reduced 26-dimensional S.Hr (full), S.br, and S.cost_imu; S.ok false
+// (in every thread) if the IMU samples do not cover the interval.
+__device__ void assemble_state(const SolveParams& sp, GnSmem& S) {
   Ctrl* c = sp.ctrl;
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) {
@@ -1046,26 +1074,19 @@ __device__ void assemble(const SolveParams& sp, GnSmem& S) {
     for (int m = 0; m < 9; ++m) acc += c->Wimu[r * 18 + m] * S.L.e[m];
     S.We[r] = acc;
   }
-  // everything above depends on the states only; the pixel sums come from the
-  // preceding pixel kernel.  Pixel systems into W (term 0 ICP with R_ref, term 1
-  // photometric with R_0).
-  grid_dep_wait();
-  if (tid >= 32 && tid < 32 + 2 * 36) pixel_system_entry(sp, c, S, tid - 32);
   __syncthreads();
-  if (tid < 36) {                       // MH6 = M H6 (photometric term)
-    const int i = tid / 6, j = tid % 6;
-    double acc = 0.0;
-    for (int k = 0; k < 6; ++k) acc += S.M6[i * 6 + k] * S.Hl[1][k * 6 + j];
-    S.MH6[tid] = acc;
-  }
-  // H upper from J_a^T W_9 J_a, b from -J_a^T W_9 e_a
-  for (int idx = tid; idx < 34 * 34; idx += nt) {
-    const int i = idx / 34, j = idx % 34;
+  // H upper from J_a^T W_9 J_a (the columns 0..25 it touches; the rest of the
+  // upper triangle zero), b from -J_a^T W_9 e_a
+  for (int idx = tid; idx < 26 * 26; idx += nt) {
+    const int i = idx / 26, j = idx % 26;
     if (j < i) continue;
     double v = 0.0;
-    if (j < 26)
-      for (int m = 0; m < 9; ++m) v += S.J[m * 34 + i] * S.WJa[m * 26 + j];
-    S.H[idx] = v;
+    for (int m = 0; m < 9; ++m) v += S.J[m * 34 + i] * S.WJa[m * 26 + j];
+    S.H[i * 34 + j] = v;
+  }
+  for (int idx = tid; idx < 34 * 8; idx += nt) {
+    const int i = idx / 8, j = 26 + idx % 8;
+    if (j >= i) S.H[i * 34 + j] = 0.0;
   }
   if (tid >= 200 && tid < 200 + 34) {
     const int i = tid - 200;
@@ -1079,31 +1100,6 @@ __device__ void assemble(const SolveParams& sp, GnSmem& S) {
     for (int m = 0; m < 9; ++m) ce += S.L.e[m] * S.We[m];
     for (int m = 9; m < 18; ++m) ce += S.L.e[m] * c->Wimu[m * 18 + m] * S.L.e[m];
     S.cost_imu = ce;
-  }
-  __syncthreads();
-  // photometric on both poses (H12 = B H6 B^T, B = [-M; I]) and ICP on x1's pose
-  for (int idx = tid; idx < 12 * 12; idx += nt) {
-    const int i = idx / 12, j = idx % 12;
-    if (j < i) continue;
-    const int a = i / 6, bb = j / 6, ii = i % 6, jj = j % 6;
-    double v;
-    if (a == 1 && bb == 1) {
-      v = S.Hl[1][ii * 6 + jj] + S.Hl[0][ii * 6 + jj];
-    } else if (a == 0 && bb == 1) {
-      v = -S.MH6[ii * 6 + jj];
-    } else {
-      v = 0.0;
-      for (int k = 0; k < 6; ++k) v += S.MH6[ii * 6 + k] * S.M6[jj * 6 + k];
-    }
-    const int gi = a == 0 ? ii : 17 + ii, gj = bb == 0 ? jj : 17 + jj;
-    S.H[gi * 34 + gj] += v;
-  }
-  if (tid >= 160 && tid < 166) {
-    const int i = tid - 160;
-    double g0 = 0.0;
-    for (int k = 0; k < 6; ++k) g0 -= S.M6[i * 6 + k] * S.gl[1][k];
-    S.b[i] += g0;
-    S.b[17 + i] += S.gl[1][i] + S.gl[0][i];
   }
   __syncthreads();
   // prior on x0: H00 += H*, b0 += b* - H* (x0 boxminus xbar)
@@ -1151,45 +1147,41 @@ __device__ void assemble(const SolveParams& sp, GnSmem& S) {
     S.br[16] -= w * a1 * sn;
   }
   // full system (marginalisation, parity output): bias and gravity rows
-  if (tid < 6) {                        // bias rows 9..14: +I at x0, -I at x1
-    const int i = tid;
+  if (tid >= 32 && tid < 38) {          // bias rows 9..14: +I at x0, -I at x1
+    const int i = tid - 32;
     const double w = c->Wimu[(9 + i) * 18 + 9 + i];
     S.H[(9 + i) * 34 + 9 + i] += w;
     S.H[(26 + i) * 34 + 26 + i] += w;
     S.H[(9 + i) * 34 + 26 + i] -= w;
     S.b[9 + i] -= w * S.L.e[9 + i];
     S.b[26 + i] += w * S.L.e[9 + i];
-  } else if (tid < 16) {                // gravity rows 15..17, columns {15, 16, 32, 33}
+  } else if (tid >= 64 && tid < 74) {   // gravity rows 15..17, columns {15, 16, 32, 33}
     const int G[4] = {15, 16, 32, 33};
-    int e = tid - 6, a = 0;
+    int e = tid - 64, a = 0;
     while (e >= 4 - a) { e -= 4 - a; ++a; }
     const int ci = G[a], cj = G[a + e];
     double v = 0.0;
     for (int k = 0; k < 3; ++k)
       v += S.J[(15 + k) * 34 + ci] * c->Wimu[(15 + k) * 18 + 15 + k] * S.J[(15 + k) * 34 + cj];
     S.H[ci * 34 + cj] += v;
-  } else if (tid < 20) {
+  } else if (tid >= 96 && tid < 100) {
     const int G[4] = {15, 16, 32, 33};
-    const int ci = G[tid - 16];
+    const int ci = G[tid - 96];
     double v = 0.0;
     for (int k = 0; k < 3; ++k)
       v -= S.J[(15 + k) * 34 + ci] * c->Wimu[(15 + k) * 18 + 15 + k] * S.L.e[15 + k];
     S.b[ci] += v;
   }
   __syncthreads();
-  for (int idx = tid; idx < 34 * 34; idx += nt) {
-    const int i = idx / 34, j = idx % 34;
-    if (j < i) S.H[idx] = S.H[j * 34 + i];
-  }
-  __syncthreads();
   if (sp.track_mode == DRI_TRACK_GYRO_ONLY) {
     // held components: identity rows and columns, zero right-hand side (their
-    // step is zero; the reduced system is the leading 26 x 26 block of H)
+    // step is zero; the reduced system is the leading 26 x 26 block of H).  No
+    // pixel term touches them (they are not pose components).
     for (int idx = tid; idx < 34 * 34; idx += nt) {
       const int i = idx / 34, j = idx % 34;
       if (held_gyro_only(i) || held_gyro_only(j)) {
         const double v = i == j ? 1.0 : 0.0;
-        S.H[idx] = v;
+        if (j >= i) S.H[idx] = v;
         if (i < 26 && j < 26) S.Hr[i * 26 + j] = v;
       }
     }
@@ -1199,6 +1191,79 @@ __device__ void assemble(const SolveParams& sp, GnSmem& S) {
     }
     __syncthreads();
   }
+}
+
+// The pixel terms after the pixel kernel (Eq. 3-4): the two 6x6 systems rotated
+// into W (S.Hl, S.gl) and their contribution to the poses of x0 and x1, P12 and
+// g12 in the order (x0 pose, x1 pose): the ICP term on x1's pose, the photometric
+// term on both through B = [-M; I] (H12 = B H6 B^T).  128 threads (t = 0..127,
+// four warps) that sync among themselves on named barrier BAR.
+template <int BAR>
+__device__ void pixel_terms(const SolveParams& sp, GnSmem& S, int t) {
+  const Ctrl* c = sp.ctrl;
+  if (t < 72) pixel_system_entry(sp, c, S, t);
+  asm volatile("bar.sync %0, 128;" ::"n"(BAR) : "memory");
+  if (t < 36) {                         // MH6 = M H6 (photometric term)
+    const int i = t / 6, j = t % 6;
+    double acc = 0.0;
+    for (int k = 0; k < 6; ++k) acc += S.M6[i * 6 + k] * S.Hl[1][k * 6 + j];
+    S.MH6[t] = acc;
+  } else if (t >= 64 && t < 76) {       // g12: -M g6 on x0, g6 + g_icp on x1
+    const int i = t - 64;
+    if (i < 6) {
+      double g0 = 0.0;
+      for (int k = 0; k < 6; ++k) g0 -= S.M6[i * 6 + k] * S.gl[1][k];
+      S.g12[i] = g0;
+    } else {
+      S.g12[i] = S.gl[1][i - 6] + S.gl[0][i - 6];
+    }
+  }
+  asm volatile("bar.sync %0, 128;" ::"n"(BAR) : "memory");
+  for (int idx = t; idx < 144; idx += 128) {
+    const int i = idx / 12, j = idx % 12, a = i / 6, bb = j / 6, ii = i % 6, jj = j % 6;
+    double v;
+    if (a == 1 && bb == 1) {
+      v = S.Hl[1][ii * 6 + jj] + S.Hl[0][ii * 6 + jj];
+    } else if (a == 0 && bb == 1) {
+      v = -S.MH6[ii * 6 + jj];
+    } else if (a == 1 && bb == 0) {
+      v = -S.MH6[jj * 6 + ii];
+    } else {
+      v = 0.0;
+      for (int k = 0; k < 6; ++k) v += S.MH6[ii * 6 + k] * S.M6[jj * 6 + k];
+    }
+    S.P12[idx] = v;
+  }
+}
+
+// Joint index of pose coordinate i (0..11) of (x0, x1).
+__device__ __forceinline__ int pose_coord(int i) { return i < 6 ? i : 11 + i; }
+
+// Adds P12, g12 to the upper triangle of S.H and to S.b (threads t0 .. t0 + n - 1).
+__device__ void add_pixel_terms(GnSmem& S, int t, int n) {
+  for (int idx = t; idx < 144; idx += n) {
+    const int gi = pose_coord(idx / 12), gj = pose_coord(idx % 12);
+    if (gj >= gi) S.H[gi * 34 + gj] += S.P12[idx];
+  }
+  if (t < 12) S.b[pose_coord(t)] += S.g12[t];
+}
+
+// The whole joint system at (ctrl->x0, ctrl->x1) into S.H (full) and S.b, with
+// S.Hl, S.gl and S.cost_imu (dri_linearise).
+__device__ void assemble(const SolveParams& sp, GnSmem& S) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  assemble_state(sp, S);
+  if (!S.ok) return;
+  grid_dep_wait();
+  if (tid < 128) pixel_terms<3>(sp, S, tid);
+  __syncthreads();
+  add_pixel_terms(S, tid, nt);
+  __syncthreads();
+  for (int idx = tid; idx < 34 * 34; idx += nt) {
+    const int i = idx / 34, j = idx % 34;
+    if (j < i) S.H[idx] = S.H[j * 34 + i];
+  }
+  __syncthreads();
 }
 
 // RGB-D-only baseline (DRI_TRACK_RGBD_ONLY): one Gauss-Newton step on x1's pose
@@ -1246,6 +1311,21 @@ __device__ void gn_step_pose_only(const SolveParams& sp, GnSmem& S) {
   }
 }
 
+// Solver order of the reduced system: the 14 components no pixel term touches
+// (x0's velocity, biases and gravity, x1's velocity) first, then the 12 pose
+// components of x0 and x1 in the order of P12.  Reduced index of solver index s.
+__device__ __forceinline__ int solver_coord(int s) {
+  return s < 11 ? 6 + s : (s < 14 ? 12 + s : (s < 20 ? s - 14 : s - 3));
+}
+constexpr int kNonPose = 14;
+
+// One Gauss-Newton step of the joint problem (Eq. 7-8) on (x0, x1).  The
+// state-only system is assembled and the sweep eliminates its 14 non-pose
+// components before the pixel sums are read (they leave the Schur complement
+// on the 12 pose components); warps 4-7 meanwhile wait for the pixel kernel
+// and build the pixel terms, which warps 0-3 add to that complement before the
+// last 12 pivots.  Jacobi scaling on the non-pose components (their diagonal
+// is known before the pixel terms), none on the poses.
 __device__ void gn_step_body(const SolveParams& sp, GnSmem& S) {
   Ctrl* c = sp.ctrl;
   if (c->status != 0) return;
@@ -1254,24 +1334,33 @@ __device__ void gn_step_body(const SolveParams& sp, GnSmem& S) {
     return;
   }
   const int tid = threadIdx.x, nt = blockDim.x;
-  assemble(sp, S);
+  assemble_state(sp, S);
   if (!S.ok) {
     if (tid == 0) c->status = DRI_ENOTREADY;
     return;
   }
-  // Jacobi-scaled LDL^T solve of the reduced 26 x 26 system (4 warps), then the
-  // eliminated x1 biases and gravity in closed form
-  if (tid < 26) S.scale[tid] = rsqrt(fmax(S.Hr[tid * 26 + tid], 1e-300));
-  __syncthreads();
-  for (int idx = tid; idx < 26 * 26; idx += nt) S.A[idx] = S.Hr[idx] * S.scale[idx / 26] * S.scale[idx % 26];
-  if (tid < 26) S.xr[tid] = S.br[tid] * S.scale[tid];
-  __syncthreads();
-  if (tid < 128) {
-    const bool pd = ep_ldlt_solve<26, 128>(S.A, S.xr, S.xr, S.col, S.Lsm, S.piv);
-    if (tid == 0) S.pd = pd;
+  if (tid < 26) {
+    const int k = solver_coord(tid);
+    S.scale[tid] = tid < kNonPose ? rsqrt(fmax(S.Hr[k * 26 + k], 1e-300)) : 1.0;
   }
   __syncthreads();
-  if (tid < 26) S.x[tid] = S.xr[tid] * S.scale[tid];
+  for (int idx = tid; idx < 26 * 26; idx += nt) {
+    const int i = idx / 26, j = idx % 26;
+    S.A[idx] = S.Hr[solver_coord(i) * 26 + solver_coord(j)] * S.scale[i] * S.scale[j];
+  }
+  if (tid < 26) S.xr[tid] = S.br[solver_coord(tid)] * S.scale[tid];
+  __syncthreads();
+  if (tid < 128) {
+    const bool pd = ep_ldlt_solve<26, 128, kNonPose>(S.A, S.xr, S.xr, S.col, S.Lsm, S.piv, S.P12, S.g12);
+    if (tid == 0) S.pd = pd;
+  } else {
+    grid_dep_wait();
+    pixel_terms<3>(sp, S, tid - 128);
+    asm volatile("bar.sync 2, 256;" ::: "memory");     // P12, g12 to the solver warps
+    if (sp.last) add_pixel_terms(S, tid - 128, 128);
+  }
+  __syncthreads();
+  if (tid < 26) S.x[solver_coord(tid)] = S.xr[tid] * S.scale[tid];
   __syncthreads();
   if (tid < 6) {
     S.x[26 + tid] = S.L.e[9 + tid] + S.x[9 + tid];          // x1 bias follows x0 bias
@@ -1290,13 +1379,11 @@ __device__ void gn_step_body(const SolveParams& sp, GnSmem& S) {
     S.x[33] = -(m00 * q1 - m01 * q0) * idet;
   }
   __syncthreads();
-  if (sp.track_mode == DRI_TRACK_GYRO_ONLY) {   // exactly zero, whatever e_g's rounding
-    if (tid < 34 && held_gyro_only(tid)) S.x[tid] = 0.0;
-    __syncthreads();
-  }
-  bool good = S.pd;
-  for (int i = 0; i < 34; ++i) good = good && isfinite(S.x[i]);
-  if (!good) {
+  if (sp.track_mode == DRI_TRACK_GYRO_ONLY && tid < 34 && held_gyro_only(tid))
+    S.x[tid] = 0.0;                                        // exactly zero, whatever e_g's rounding
+  // every component finite (integer test of the exponent: no FP64 instruction)
+  const bool fin = tid >= 34 || ((__double_as_longlong(S.x[tid]) >> 52) & 0x7ff) != 0x7ff;
+  if (!__syncthreads_and(fin && S.pd)) {
     if (tid == 0) c->status = DRI_ELOST;
     return;
   }
@@ -1320,7 +1407,10 @@ __device__ void gn_step_body(const SolveParams& sp, GnSmem& S) {
     c->x1 = S.x1;
   }
   if (sp.last) {
-    for (int idx = tid; idx < 34 * 34; idx += nt) c->H[idx] = S.H[idx];
+    for (int idx = tid; idx < 34 * 34; idx += nt) {
+      const int i = idx / 34, j = idx % 34;
+      c->H[idx] = j >= i ? S.H[idx] : S.H[j * 34 + i];
+    }
     if (tid >= 64 && tid < 98) {
       c->b[tid - 64] = S.b[tid - 64];
       c->d[tid - 64] = S.x[tid - 64];
