@@ -739,13 +739,20 @@ __device__ void ldlt_solve_thread(const double* A, int n, int ld, double* b) {
   }
 }
 
-// Pivot reciprocal: the FP32 seed refined by one Newton-Raphson step
-// (relative error ~2^-48; the factorisation is then exact for a matrix whose
-// pivots are perturbed by that amount, far below what the system's rounding
-// already costs).
+// Pivot reciprocal: an FP32 seed refined by one Newton-Raphson step (relative
+// error below 2^-45; the factorisation is then exact for a matrix whose pivots
+// are perturbed by that amount, far below what the system's rounding already
+// costs).  The seed's conversions are integer operations on the bit patterns
+// (the leading 23 mantissa bits of d, the exponent re-biased between the
+// formats; d and 1 / d are normal in both here): on this GPU every FP64-pipe
+// instruction on the pivot's dependency chain costs tens of cycles.
 __device__ __forceinline__ double pivot_recip(double d) {
   if (d > 1e-30 && d < 1e30) {
-    const double y = (double)__frcp_rn((float)d);
+    const int hi = __double2hiint(d);
+    const unsigned lo = (unsigned)__double2loint(d);
+    const float f = __int_as_float((int)(((unsigned)hi - 0x38000000u) << 3 | lo >> 29));
+    const int yb = __float_as_int(__frcp_rn(f));
+    const double y = __hiloint2double((yb >> 3) + 0x38000000, (int)((unsigned)yb << 29));
     return fma(y, fma(-d, y, 1.0), y);
   }
   return 1.0 / d;

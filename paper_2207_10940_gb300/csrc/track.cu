@@ -38,7 +38,8 @@
 // The local Jacobians are the world-frame ones of Eq. 3-4 rotated by
 // diag(R^T, R^T) (R = R_ref or R_0); the solver rotates the reduced 6x6 systems
 // back in FP64.  Each thread accumulates its term's 29 values (upper J J^T, J e,
-// e^2, count) in FP32; a warp transposes and sums them with 31 shuffles, the
+// e^2, count) in FP32, 28 of them in pairs by packed FP32 x 2 FMAs (14 per
+// pixel instead of 28 scalar ones); a warp transposes and sums them with 31 shuffles, the
 // block adds its warps per term in fixed order into one FP64 (or FP32)
 // partial of 58 values; the partials are folded in two fixed-order levels
 // (groups of blocks, then the groups) into ctrl->sums: deterministic, no float
@@ -52,18 +53,40 @@ namespace dri {
 
 namespace {
 
+// The 29 sums of a thread, stored in pairs for the packed FP32 x 2 FMA: slot
+// acc_slot(k) holds sum k of the row-major upper J J^T (0..20), J e (21..26),
+// e^2 (27), count (28).  Each pair is one fma.rn.f32x2 per pixel, each lane
+// rounded as a scalar fmaf, so every sum is bit-identical to scalar accumulation.
+__host__ __device__ constexpr int acc_slot(int k) {
+  constexpr int pos[29] = {0, 18, 6, 8, 10, 12, 1, 9, 7, 13, 11, 2, 19, 14, 16,
+                           3, 17, 15, 4, 20, 5, 22, 23, 24, 25, 26, 27, 21, 28};
+  return pos[k];
+}
+
+__device__ __forceinline__ void fma2(float* a, float2 x, float2 y) {
+  const float2 r = __ffma2_rn(x, y, make_float2(a[0], a[1]));
+  a[0] = r.x;
+  a[1] = r.y;
+}
+
 __device__ __forceinline__ void accumulate(float* a, const float* J, float e) {
-  int k = 0;
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-#pragma unroll
-    for (int j = i; j < 6; ++j) {
-      a[k] = fmaf(J[i], J[j], a[k]);
-      ++k;
-    }
-#pragma unroll
-  for (int i = 0; i < 6; ++i) a[21 + i] = fmaf(J[i], e, a[21 + i]);
-  a[27] = fmaf(e, e, a[27]);
+  const float2 P0 = make_float2(J[0], J[1]), P1 = make_float2(J[2], J[3]), P2 = make_float2(J[4], J[5]);
+  const float2 S1 = make_float2(J[3], J[2]), S2 = make_float2(J[5], J[4]);
+  const float2 E = make_float2(e, e);
+  fma2(a + 0, P0, P0);
+  fma2(a + 2, P1, P1);
+  fma2(a + 4, P2, P2);
+  fma2(a + 6, P0, P1);
+  fma2(a + 8, P0, S1);
+  fma2(a + 10, P0, P2);
+  fma2(a + 12, P0, S2);
+  fma2(a + 14, P1, P2);
+  fma2(a + 16, P1, S2);
+  fma2(a + 18, make_float2(J[0], J[2]), make_float2(J[1], J[3]));
+  fma2(a + 20, make_float2(J[4], e), make_float2(J[5], e));
+  fma2(a + 22, P0, E);
+  fma2(a + 24, P1, E);
+  fma2(a + 26, P2, E);
   a[28] += 1.f;
 }
 
@@ -406,7 +429,7 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int term,
   // lane l holding the warp sum of value l (31 shuffles instead of 5 per value).
   float w[32];
 #pragma unroll
-  for (int k = 0; k < 32; ++k) w[k] = k < kSums ? acc[k] : 0.f;
+  for (int k = 0; k < 32; ++k) w[k] = k < kSums ? acc[acc_slot(k)] : 0.f;
 #pragma unroll
   for (int half = 16, off = 16; off > 0; half >>= 1, off >>= 1) {
     const bool hi = (lane & off) != 0;
