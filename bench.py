@@ -171,6 +171,96 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
+class ServeMonitor:
+    """Samples during a served pass, to place its slow ticks: SM clock and
+    throttle reasons every 100 ms (with the sample's wall time), and the GPU's
+    compute processes every 500 ms (another process on the GPU would share it)."""
+    CLK = ("timestamp,clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+           "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+           "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        out_dir = os.environ.get("DRI_CLOCKS_DIR") or tempfile.gettempdir()
+        self.paths = [os.path.join(out_dir, f"serve_{n}_{os.getpid()}.csv") for n in ("clk", "apps")]
+        self.procs = []
+
+    def __enter__(self):
+        cmds = [["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.CLK}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                ["nvidia-smi", f"--id={self.index}", "--query-compute-apps=pid,used_memory",
+                 "--format=csv,noheader,nounits", "-lms", "500"]]
+        self.files = []
+        for path, cmd in zip(self.paths, cmds):
+            try:
+                os.makedirs(os.path.dirname(path), exist_ok=True)
+                f = open(path, "w")
+                self.files.append(f)
+                self.procs.append(subprocess.Popen(cmd, stdout=f, stderr=subprocess.DEVNULL))
+            except (OSError, FileNotFoundError):
+                pass
+        return self
+
+    def __exit__(self, *a):
+        for pr in self.procs:
+            pr.terminate()
+            pr.wait()
+        for f in self.files:
+            f.close()
+
+    def _clock_rows(self):
+        import datetime
+        rows = []
+        try:
+            lines = open(self.paths[0]).read().splitlines()
+        except OSError:
+            return rows
+        for line in lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                t = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((t, float(parts[1]), float(parts[2]), parts[3:7]))
+            except ValueError:
+                pass
+        return rows
+
+    def summary(self, t0_wall, t1_wall, stalls):
+        """Clock and process samples between the wall times t0 and t1, and the
+        clock sample nearest to each stalled tick (wall time, tick ms)."""
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = [r for r in self._clock_rows() if t0_wall <= r[0] <= t1_wall]
+        out = {"clock_samples": len(rows)}
+        if rows:
+            mhz = np.array([r[1] for r in rows])
+            out.update(sm_mhz_median=float(np.median(mhz)), sm_mhz_min=float(mhz.min()),
+                       sm_max_mhz=max(r[2] for r in rows),
+                       reasons=sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v == "Active"}),
+                       samples_below_95pct=int(np.sum(mhz < 0.95 * max(r[2] for r in rows))))
+        pids = set()
+        try:
+            for line in open(self.paths[1]):
+                parts = [x.strip() for x in line.split(",")]
+                if parts and parts[0].isdigit():
+                    pids.add(int(parts[0]))
+        except OSError:
+            pass
+        # process ids as the driver reports them (a container may number its
+        # processes differently): more than one id means another process
+        out["compute_pids"] = sorted(pids)
+        out["own_pid"] = os.getpid()
+        near = []
+        for tw, tick_ms in stalls[:10]:
+            if not rows:
+                break
+            r = min(rows, key=lambda r: abs(r[0] - tw))
+            near.append({"at_s": tw - t0_wall, "tick_ms": tick_ms, "sample_dt_s": r[0] - tw,
+                         "sm_mhz": r[1], "reasons": [names[i] for i, v in enumerate(r[3]) if v == "Active"]})
+        out["stalled_ticks"] = near
+        return out
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle timing (bounded samples)
 # ---------------------------------------------------------------------------
@@ -931,13 +1021,22 @@ def served_pass(args, dev, workers, rendered=None):
     warm_s = time.perf_counter() - t_w
     dri.dri_server_stats_read(srv, reset=True)
     thr0 = cpu_throttle()
-    for t in th:
-        t.join()
+    mon = ServeMonitor(dev.index if dev.index is not None else 0)
+    with mon:
+        t0_wall = time.time()
+        for t in th:
+            t.join()
+        t1_wall = time.time()
     thr = throttle_delta(thr0, cpu_throttle())
     wall = time.perf_counter() - t_start
     trace = dri.dri_server_trace_read(srv)             # read before the reset clears it
     st = dri.dri_server_stats_read(srv, reset=True)
     ticks = tick_summary(trace)
+    # wall time of each tick over 50 ms (the trace's first tick is the first
+    # after the stats reset, t0_wall)
+    stalls = [] if not trace else [
+        (t0_wall + (t.dequeue_ms - trace[0].dequeue_ms) / 1e3, t.done_ms - t.dequeue_ms)
+        for t in trace if t.done_ms - t.dequeue_ms > 50.0]
     bad = sum(1 for s in statuses if s != 0)
     served = {
         "streams": SERVE_STREAMS, "mix": "stream i: " + ", ".join(f"{w}x{h}" for w, h in SERVE_CLASSES)
@@ -953,6 +1052,7 @@ def served_pass(args, dev, workers, rendered=None):
         "h2d_bytes_per_s": st.frames_per_s * float(np.mean(frame_bytes)),
         "warmup_s": warm_s, "client_max_lag_ms": 1000.0 * lag[0], "client_max_lag_at_s": lag[1],
         "host_cpu_throttle": thr, "tick_phases_ms": ticks,
+        "monitor": mon.summary(t0_wall, t1_wall, stalls),
         "latency_from": "submit to result (warm-up excluded: 2 s and until the start's backlog is "
                         "drained)"}
 
