@@ -624,6 +624,51 @@ def job_throughput(units_per_rank, world, ms_max):
     return world * units_per_rank / (ms_max / 1000.0)
 
 
+MM_COUNTERS = ("pgmigrate_success", "compact_isolated", "compact_migrate_scanned", "compact_stall",
+               "thp_collapse_alloc", "numa_hint_faults")
+
+
+def mm_counters(path="/proc/vmstat"):
+    """The host kernel's page-migration and compaction counters (None where the
+    file is unreadable)."""
+    try:
+        with open(path) as f:
+            d = dict(line.split() for line in f)
+    except OSError:
+        return None
+    return {k: int(d[k]) for k in MM_COUNTERS if k in d}
+
+
+def mm_delta(a, b):
+    if a is None or b is None:
+        return None
+    return {k: b[k] - a[k] for k in b if k in a}
+
+
+def wait_mm_quiet(max_s=20.0, period=0.5):
+    """Waits until the host kernel has stopped migrating and compacting pages
+    (two consecutive samples `period` apart without a migrated page), at most
+    max_s; returns the seconds waited.  Migration unmaps the pages it moves,
+    and on this machine the GPU's reads of host memory (pinned frames, copies)
+    stalled for tens to hundreds of ms while the kernel compacted the memory
+    freed by the frame-rendering processes."""
+    t = time.perf_counter()
+    prev = mm_counters()
+    if prev is None:
+        return 0.0
+    quiet = 0
+    while time.perf_counter() - t < max_s:
+        time.sleep(period)
+        cur = mm_counters()
+        moved = cur.get("pgmigrate_success", 0) - prev.get("pgmigrate_success", 0) + \
+            cur.get("compact_isolated", 0) - prev.get("compact_isolated", 0)
+        quiet = quiet + 1 if moved == 0 else 0
+        prev = cur
+        if quiet >= 2:
+            break
+    return time.perf_counter() - t
+
+
 def cpu_throttle(root="/sys/fs/cgroup"):
     """The process's CPU-bandwidth throttling counters from its cgroup (v2
     cpu.stat / cpu.max, else v1 cpu/cpu.stat and the CFS quota): throttled
@@ -997,6 +1042,9 @@ def served_pass(args, dev, workers, rendered=None):
             if tickets[n]:
                 statuses[n] = lib.dri_server_poll(srv, ctypes.c_uint64(tickets[n]), ctypes.byref(res), -1)
 
+    # the host kernel compacts the memory the rendering processes freed: let it
+    # finish before the offered load starts (bounded; the wait is reported)
+    quiet_s = wait_mm_quiet()
     th = [threading.Thread(target=client), threading.Thread(target=poller)]
     # the client and poller are Python threads: a pass of the cyclic garbage
     # collector over the bench's objects can hold them for hundreds of ms and
@@ -1021,6 +1069,7 @@ def served_pass(args, dev, workers, rendered=None):
     warm_s = time.perf_counter() - t_w
     dri.dri_server_stats_read(srv, reset=True)
     thr0 = cpu_throttle()
+    mm0 = mm_counters()
     mon = ServeMonitor(dev.index if dev.index is not None else 0)
     with mon:
         t0_wall = time.time()
@@ -1028,6 +1077,7 @@ def served_pass(args, dev, workers, rendered=None):
             t.join()
         t1_wall = time.time()
     thr = throttle_delta(thr0, cpu_throttle())
+    mm = mm_delta(mm0, mm_counters())
     wall = time.perf_counter() - t_start
     trace = dri.dri_server_trace_read(srv)             # read before the reset clears it
     st = dri.dri_server_stats_read(srv, reset=True)
@@ -1051,7 +1101,8 @@ def served_pass(args, dev, workers, rendered=None):
                   "request",
         "h2d_bytes_per_s": st.frames_per_s * float(np.mean(frame_bytes)),
         "warmup_s": warm_s, "client_max_lag_ms": 1000.0 * lag[0], "client_max_lag_at_s": lag[1],
-        "host_cpu_throttle": thr, "tick_phases_ms": ticks,
+        "host_cpu_throttle": thr, "host_mm_counters": mm, "mm_quiet_wait_s": quiet_s,
+        "tick_phases_ms": ticks,
         "monitor": mon.summary(t0_wall, t1_wall, stalls),
         "latency_from": "submit to result (warm-up excluded: 2 s and until the start's backlog is "
                         "drained)"}

@@ -64,3 +64,41 @@ def test_tick_summary_phases():
     assert abs(s["gap"]["max"] - 0.2) < 1e-9
     assert s["slowest"]["requests"] == 9 and abs(s["slowest"]["at_ms"] - 11.2) < 1e-9
     assert bench.tick_summary([]) is None
+
+
+def test_mm_counters_and_quiet_wait(tmp_path, monkeypatch):
+    p = str(tmp_path / "vmstat")
+    _write(p, "nr_free_pages 10\npgmigrate_success 7\ncompact_isolated 3\ncompact_stall 0\n")
+    a = bench.mm_counters(p)
+    assert a == {"pgmigrate_success": 7, "compact_isolated": 3, "compact_stall": 0}
+    _write(p, "nr_free_pages 9\npgmigrate_success 19\ncompact_isolated 5\ncompact_stall 1\n")
+    assert bench.mm_delta(a, bench.mm_counters(p)) == {"pgmigrate_success": 12, "compact_isolated": 2,
+                                                       "compact_stall": 1}
+    assert bench.mm_counters(str(tmp_path / "missing")) is None
+    assert bench.mm_delta(None, a) is None
+    # the wait ends after two quiet samples, or at its bound while pages keep moving
+    seq = iter([{"pgmigrate_success": n, "compact_isolated": 0} for n in (0, 5, 9, 9, 9, 9)])
+    monkeypatch.setattr(bench, "mm_counters", lambda path="/proc/vmstat": next(seq))
+    waited = bench.wait_mm_quiet(max_s=5.0, period=0.01)
+    assert 0.03 <= waited < 1.0
+    moving = iter({"pgmigrate_success": n, "compact_isolated": 0} for n in range(10 ** 6))
+    monkeypatch.setattr(bench, "mm_counters", lambda path="/proc/vmstat": next(moving))
+    assert 0.1 <= bench.wait_mm_quiet(max_s=0.1, period=0.01) < 0.5
+
+
+def test_serve_monitor_summary(tmp_path, monkeypatch):
+    import datetime
+    monkeypatch.setenv("DRI_CLOCKS_DIR", str(tmp_path))
+    m = bench.ServeMonitor(0)
+    t = datetime.datetime(2026, 1, 2, 3, 4, 5, 100000).timestamp()
+    _write(m.paths[0], "2026/01/02 03:04:05.100, 2070, 2070, Not Active, Not Active, Not Active, Not Active\n"
+                       "2026/01/02 03:04:05.200, 1500, 2070, Active, Not Active, Not Active, Not Active\n"
+                       "2026/01/02 03:04:09.000, 2070, 2070, Not Active, Not Active, Not Active, Not Active\n")
+    _write(m.paths[1], "4321, 500\n1234, 900\n")
+    out = m.summary(t - 0.05, t + 1.0, [(t + 0.21, 80.0)])
+    assert out["clock_samples"] == 2                    # the third sample is after the pass
+    assert out["sm_mhz_min"] == 1500.0 and out["samples_below_95pct"] == 1
+    assert out["reasons"] == ["hw_slowdown"]
+    assert out["compute_pids"] == [1234, 4321]
+    (st,) = out["stalled_ticks"]
+    assert st["sm_mhz"] == 1500.0 and st["reasons"] == ["hw_slowdown"] and abs(st["sample_dt_s"] + 0.11) < 1e-3
