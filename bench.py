@@ -1194,6 +1194,14 @@ def precision_study(seq, frames, imu, dev, n_frames):
                        f"frame 1 against frame 0 at the ground-truth states",
            "oracle": "exact FP64 (maps not rounded)", "solve": "FP64 on the GPU in every variant",
            "normalisation": "max |dH_ij|/sqrt(H_ii H_jj), max |db_i|/sqrt(H_ii C); bar 1e-5",
+           "parity_bars": {
+               "fp32 maps (flags 0, 2)": "systems 1e-5 normalised, pose 1e-6 rad / 1e-6 m, against "
+                                         "the FP64 oracle (tests)",
+               "fp16 maps (flags 1, 3)": "systems 2^-11 normalised, pose 1e-5 rad / 1e-5 m (10x the "
+                                         "FP32 pose bar), against an oracle that rounds the stored "
+                                         "normals and gradients to FP16 as the library does (tests); "
+                                         "FP32- and FP64-computed normals can round to neighbouring "
+                                         "half-precision values"},
            "oracle_track_s": t_oracle, "variants": {}}
     for name, flags in PRECISION_VARIANTS:
         cfg = dri_config(seq, flags)
