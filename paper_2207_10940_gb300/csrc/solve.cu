@@ -784,8 +784,7 @@ template <int N, int T, int NS = 0>
 __device__ bool ep_ldlt_solve(const double* A, const double* b, double* x, double* colbuf,
                               double* Lsm, double* piv, const double* Padd = nullptr,
                               const double* gadd = nullptr) {
-  constexpr int kTri = N * (N + 1) / 2;
-  constexpr int kEnt = kTri + N;                     // lower triangle + the b column
+  constexpr int kEnt = N * (N + 1) / 2 + N;          // lower triangle + the b column
   constexpr int kOwn = (kEnt + T - 1) / T;
   const int t = threadIdx.x;
   int ei[kOwn], ej[kOwn];
@@ -794,14 +793,18 @@ __device__ bool ep_ldlt_solve(const double* A, const double* b, double* x, doubl
   for (int o = 0; o < kOwn; ++o) {
     const int e = t + o * T;
     int i = -1, j = -1;
-    if (e < kTri) {                                  // row-major lower triangle
-      i = (int)((sqrtf(8.0f * e + 1.0f) - 1.0f) * 0.5f);
-      while (i * (i + 1) / 2 > e) --i;
-      while ((i + 1) * (i + 2) / 2 <= e) ++i;
-      j = e - i * (i + 1) / 2;
-    } else if (e < kEnt) {
-      i = e - kTri;
-      j = N;
+    if (e < kEnt) {
+      // entries dealt out by lifetime: group g (column c = N - 1 - g) holds
+      // (c..N-1, c) and the right-hand side's (c, N), g + 2 entries, updated
+      // by pivots 0..c-1; groups in order of decreasing c, so the entries a
+      // pivot still updates are a prefix of the threads and fill the fewest
+      // warps (an FP64 warp instruction costs the same with 1 or 32 lanes)
+      int g = (int)((sqrtf(9.0f + 8.0f * e) - 3.0f) * 0.5f);
+      while (g * (g + 3) / 2 > e) --g;
+      while ((g + 1) * (g + 4) / 2 <= e) ++g;
+      const int r = e - g * (g + 3) / 2, c = N - 1 - g;
+      i = r <= g ? c + r : c;
+      j = r <= g ? c : N;
     }
     ei[o] = i;
     ej[o] = j;
