@@ -143,7 +143,9 @@ typedef struct {
     double bias_relin_g;           /* first order: re-integrate past |db_g|, rad/s    */
     double bias_relin_a;           /* first order: re-integrate past |db_a|, m/s^2    */
     int32_t track_mode;            /* DRI_TRACK_INERTIAL (default) | _RGBD_ONLY | _GYRO_ONLY */
-    int32_t reserved;
+    int32_t count_margins;         /* 1: fill dri_track_result.n_margin (the pixel kernel
+                                      of each level's last iteration counts them: ~2% of a
+                                      batched frame's pixel-kernel time); 0 (default): zeros */
     double rgbd_lambda;            /* RGB-D-only: photometric weight (default 1)      */
     double occlusion_thr;          /* > 0: photometric depth-consistency test, m; 0 off */
     int32_t icp_depth_weight;      /* 1: ICP weight W_ICP / z^4 (sigma_d at 1 m); 0 off */
@@ -165,14 +167,24 @@ typedef struct {
 } dri_state;
 
 /* Result of one tracked frame.  n_icp / n_rgb are the valid correspondence
- * counts of the last iteration at each level; cost is Eq. 6 at the last
- * linearisation (data + IMU terms, prior excluded); status is the frame's
- * DRI_* code (DRI_OK, or DRI_ELOST with x1 = the previous state). */
+ * counts of the last iteration at each level.  n_margin counts, for that
+ * iteration, the pixel decisions of the ICP term plus those of the photometric
+ * term that lay within the rounding margins of FP32 arithmetic: a projection
+ * within 1e-4 px of a rounding or image-bound boundary, or a depth-range, z > 0,
+ * distance, normal-angle or occlusion test within a relative 1e-5 of its
+ * threshold (normal angle with FP16 maps: 4 * 2^-11 in cos).  Such a pixel may
+ * be decided either way by implementations that round differently; decisions
+ * made while the maps were built (the normals' own tests) are not counted.
+ * Counted when the stream's config has count_margins = 1 (in a batch: when any
+ * of its streams has), else zero.  cost is Eq. 6 at the last linearisation (data + IMU terms, prior excluded);
+ * status is the frame's DRI_* code (DRI_OK, or DRI_ELOST with x1 = the
+ * previous state). */
 typedef struct {
     dri_state x1;
     dri_state x0;
     int32_t n_icp[DRI_MAX_LEVELS];
     int32_t n_rgb[DRI_MAX_LEVELS];
+    int32_t n_margin[DRI_MAX_LEVELS];
     double cost;
     int32_t status;
     int32_t initialised;           /* 1 if this call only initialised the stream     */
@@ -189,6 +201,7 @@ typedef struct {
     double cost_icp, cost_rgb, cost_imu;
     double e_imu[18];              /* IMU error x^1(x0) boxminus x1                   */
     int64_t n_icp, n_rgb;
+    int64_t n_margin_icp, n_margin_rgb;  /* margin decisions per term (see dri_track_result) */
 } dri_linearisation;
 
 /* Fills *cfg with defaults for a width x height stream: intrinsics scaled from
@@ -414,10 +427,12 @@ int dri_set_state(dri_stream s, const dri_state* x1, const double* H_prior, cons
  * on pyramid level `level` of the uploaded frame against the stream's
  * reference, prior and IMU, without changing the stream.  W_IMU is taken at x0.
  * flags (nullable, host, width_l * height_l bytes) receives per pixel
- * bit 0 = ICP correspondence valid, bit 1 = photometric valid and, for a
- * valid ICP correspondence, its reference pixel (x_i, y_i) as x_i mod 4 in
- * bits 2-3 and y_i mod 4 in bits 4-5.  The terms are evaluated by the same
- * pixel kernel (and rows per thread) that dri_track runs for the stream. */
+ * bit 0 = ICP correspondence valid, bit 1 = photometric valid, for a valid
+ * ICP correspondence its reference pixel (x_i, y_i) as x_i mod 4 in bits 2-3
+ * and y_i mod 4 in bits 4-5, bit 6 = the ICP term's decision was a margin
+ * decision, bit 7 = the photometric term's (as counted by
+ * dri_track_result.n_margin).  The terms are evaluated by the same pixel
+ * kernel (and rows per thread) that dri_track runs for the stream. */
 int dri_linearise(dri_stream s, int32_t level, const dri_state* x0, const dri_state* x1,
                   dri_linearisation* out, uint8_t* flags);
 
@@ -477,9 +492,10 @@ int dri_profile_read(dri_stream s, dri_profile* out);
  * at (x_ref) and the states x0, x1 to linearise at.  Output (device memory):
  * *out receives the ICP and photometric fields of dri_linearisation exactly as
  * dri_linearise fills them for a one-level stream (H_icp, b_icp, H_rgb, b_rgb,
- * cost_icp, cost_rgb, n_icp, n_rgb; H, b, e_imu and cost_imu are zeroed);
- * flags (nullable, device, width * height bytes) the per-pixel validity and
- * association bits, encoded as by dri_linearise.
+ * cost_icp, cost_rgb, n_icp, n_rgb, n_margin_icp, n_margin_rgb; H, b, e_imu and
+ * cost_imu are zeroed);
+ * flags (nullable, device, width * height bytes) the per-pixel validity,
+ * association and margin bits, encoded as by dri_linearise.
  * Work is enqueued on cuda_stream; the call does not wait.
  *
  * DRI_EINVAL for a NULL argument, an option value a stream would reject, or a

@@ -122,21 +122,24 @@ def linearise(cur: FrameLevel, ref: RefLevel, R_ref, r_ref, x0, x1, cfg):
     J_icp = np.concatenate([Nr, np.cross(s1, Nr)], axis=-1)
 
     cand = dv & cur.N_valid
-    m_icp = _normal_margin(cur.depth, cur.V, cur.N, cfg) & dv
-    m_icp |= cand & (np.abs(z) <= REL_MARGIN * np.linalg.norm(pr, axis=-1))
+    # margins of the decisions made per pixel in the linearisation itself (the
+    # pixel's own depth range, z > 0, the rounding, distance and angle tests) ...
+    m_icp_px = _depth_margin(cur.depth, cfg) & dv
+    m_icp_px |= cand & (np.abs(z) <= REL_MARGIN * np.linalg.norm(pr, axis=-1))
     rx = xr + 0.5
     ry = yr + 0.5
-    m_icp |= cand & zpos & ((np.abs(rx - np.round(rx)) < PX_MARGIN) |
-                            (np.abs(ry - np.round(ry)) < PX_MARGIN))
-    # reference-side decisions at the associated pixel
-    ref_nm = _normal_margin(ref.depth, (ref.V_W - r_ref) @ R_ref, ref.N_W @ R_ref, cfg)
-    m_icp |= cand & inb & ref_nm[yc, xc]
-    m_icp |= cand & rvalid & (_near_rel(dist, cfg.icp_dist_thr) | _near_rel(cosang, cos_thr))
+    m_icp_px |= cand & zpos & ((np.abs(rx - np.round(rx)) < PX_MARGIN) |
+                               (np.abs(ry - np.round(ry)) < PX_MARGIN))
+    m_icp_px |= cand & rvalid & (_near_rel(dist, cfg.icp_dist_thr) | _near_rel(cosang, cos_thr))
     if getattr(cfg, "fp16_maps", False):
         # normals stored in half precision: an implementation that rounds a normal
         # computed in FP32 may land one half-precision unit (2^-11 relative) away
         # from the rounding of the FP64 normal, which moves cos by up to ~2 * 2^-11
-        m_icp |= cand & rvalid & (np.abs(cosang - cos_thr) <= FP16_COS_MARGIN)
+        m_icp_px |= cand & rvalid & (np.abs(cosang - cos_thr) <= FP16_COS_MARGIN)
+    # ... and of those made while the normal maps were built (the live pixel's
+    # and the associated reference pixel's)
+    ref_nm = _normal_margin(ref.depth, (ref.V_W - r_ref) @ R_ref, ref.N_W @ R_ref, cfg)
+    m_icp = m_icp_px | (_normal_margin(cur.depth, cur.V, cur.N, cfg) & dv) | (cand & inb & ref_nm[yc, xc])
 
     # ---------------- photometric (Eq. 3) ----------------
     p0 = (pW - r0) @ R0                  # R_0^T (p_W - r_0)
@@ -195,6 +198,8 @@ def linearise(cur: FrameLevel, ref: RefLevel, R_ref, r_ref, x0, x1, cfg):
         H_rgb=W_rgb * Jr.T @ Jr, b_rgb=-W_rgb * Jr.T @ er, cost_rgb=W_rgb * float(er @ er),
         n_rgb=int(rgb_valid.sum()),
         icp_valid=icp_valid, rgb_valid=rgb_valid, icp_margin=m_icp, rgb_margin=m_rgb,
+        # the photometric margins are all decided per pixel in the linearisation
+        icp_margin_px=m_icp_px, rgb_margin_px=m_rgb,
         # per-pixel values (also where invalid) for finite-difference checks
         px=dict(e_icp=e_icp, J_icp=J_icp, e_rgb=e_rgb, J_rgb=J_rgb, xi=xi, yi=yi, xp=xp, yp=yp,
                 G0=G0),

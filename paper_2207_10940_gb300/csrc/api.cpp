@@ -64,6 +64,7 @@ int valid_config(const dri_stream_config* c) {
   if (c->gravity_dof != 0 && c->gravity_dof != DRI_GRAVITY_2DOF && c->gravity_dof != DRI_GRAVITY_3D)
     return DRI_EINVAL;
   if (c->gravity_dof == DRI_GRAVITY_3D && c->track_mode != DRI_TRACK_INERTIAL) return DRI_EINVAL;
+  if (c->count_margins != 0 && c->count_margins != 1) return DRI_EINVAL;
   const double qn = c->T_CS[3] * c->T_CS[3] + c->T_CS[4] * c->T_CS[4] + c->T_CS[5] * c->T_CS[5] +
                     c->T_CS[6] * c->T_CS[6];
   if (!(std::fabs(qn - 1.0) < 1e-6)) return DRI_EINVAL;
@@ -435,6 +436,7 @@ int plan_create(dri_stream_s* const* streams, int n, int ring, bool in_workspace
   p->fp32p = (streams[0]->cfg.precision_flags & DRI_FP32_PARTIALS) != 0;
   p->opt = pixel_options(streams[0]->cfg);
   for (int i = 0; i < n; ++i) p->g3 = p->g3 || streams[i]->cfg.gravity_dof == DRI_GRAVITY_3D;
+  for (int i = 0; i < n; ++i) p->margins = p->margins || streams[i]->cfg.count_margins == 1;
   plan_set_groups(p, groups);
   // a batch plan's table has room for any group count; a stream's own plan has
   // one group and exactly the workspace's table region
@@ -708,7 +710,8 @@ int plan_enqueue(Plan* p, int phases, int64_t* kernels) {
         if (p->norm_side && l == L - 2) CK(cudaStreamWaitEvent(sg, p->ev_norm, 0));
         for (int it = 0; it < p->iters[l]; ++it) {
           --remaining;
-          const BatchArgs at = plan_args(p, track_start(p, l, g), l, 0, p->gfirst[g], p->gcount[g]);
+          BatchArgs at = plan_args(p, track_start(p, l, g), l, 0, p->gfirst[g], p->gcount[g]);
+          at.margin = p->margins && it == p->iters[l] - 1;   // the level's margin decisions
           const int nb = track_blocks(p, l, g);
           CK(launch(prof, DRI_KC_TRACK, plan_pixels(p, l) * px_scale,
                     [&] {
@@ -1257,6 +1260,7 @@ void fill_result(const dri_stream_s* s, const Ctrl* h, dri_track_result* out, bo
   for (int l = 0; l < kMaxLevels; ++l) {
     out->n_icp[l] = h->n_icp[l];
     out->n_rgb[l] = h->n_rgb[l];
+    out->n_margin[l] = h->n_margin[l];
   }
   out->cost = h->cost;
   out->status = h->status;
@@ -1415,8 +1419,8 @@ int dri_linearise(dri_stream s, int32_t level, const dri_state* x0, const dri_st
   // The pixel terms come from the batched kernel that tracking runs, over the
   // stream's own one-slot plan (its rows per thread included).  The per-pixel
   // validity bits come from the same kernel's flag-writing instantiation,
-  // launched first; the production instantiation then recomputes the sums the
-  // system is assembled from.
+  // launched first; the instantiation a level's last iteration runs (margin
+  // decisions counted) then recomputes the sums the system is assembled from.
   const BatchArgs at = plan_args(p, track_start(p, level, 0), level, 0, 0, 1);
   const int nb = track_blocks(p, level, 0);
   const double px = (double)s->geom[level].w * s->geom[level].h;
@@ -1428,9 +1432,13 @@ int dri_linearise(dri_stream s, int32_t level, const dri_state* x0, const dri_st
     CK(launch(s, DRI_KC_TRACK, px, [&] {
       return launch_track_batch(af, nb, p->fp16, p->fp32p, p->opt, launch_priority(false), false, s->stream);
     }));
+    // the flag-writing launch counted the margin decisions too: count once
+    CK(cudaMemsetAsync(s->ctrl->margin_acc, 0, sizeof(s->ctrl->margin_acc), s->stream));
   }
+  BatchArgs am = at;
+  am.margin = 1;                   // the margin decisions, counted as a level's last iteration does
   CK(launch(s, DRI_KC_TRACK, px, [&] {
-    return launch_track_batch(at, nb, p->fp16, p->fp32p, p->opt, launch_priority(false), false, s->stream);
+    return launch_track_batch(am, nb, p->fp16, p->fp32p, p->opt, launch_priority(false), false, s->stream);
   }));
   CK(launch(s, DRI_KC_SOLVE, 0.0, [&] { return launch_linearise_end(sp, s->lin_dev, s->stream); }));
   s->launches += 1 + 2 * L - 1 + 3 + (flags ? 1 : 0);

@@ -56,12 +56,14 @@ struct Ctrl {
   double cost;
   double t_state;                     // time of x
   int32_t n_icp[kMaxLevels], n_rgb[kMaxLevels];
+  int32_t n_margin[kMaxLevels];       // margin decisions of the last iteration per level
   int32_t status;                     // DRI_OK or the frame's error
   int32_t ref_index;                  // map set holding the reference
   int32_t initialised;                // reference exists
   int32_t iterations;
   uint32_t block_counter;             // last-block detection of the pixel kernel
-  uint32_t pad1[3];
+  uint32_t margin_acc[2];             // margin decisions of the running pixel kernel (ICP, photometric)
+  uint32_t pad1;
   // ---- solver state ----
   DState xbar;                        // prior mean
   DState xstart;                      // state at frame start (restored on DRI_ELOST)
@@ -196,8 +198,10 @@ struct BatchArgs {
   int32_t nslots;
   int32_t level;
   int32_t last;                       // 1 on the frame's last Gauss-Newton iteration
-  uint8_t* flags;                     // pixel kernel, parity entry only: per-pixel validity bits
-                                      // (one slot, zeroed before the launch); nullptr otherwise
+  int32_t margin;                     // pixel kernel: count margin decisions (a level's last iteration)
+  uint8_t* flags;                     // pixel kernel, parity entry only: per-pixel validity and
+                                      // margin bits (one slot, zeroed before the launch); nullptr
+                                      // otherwise
 };
 
 // Index (0 .. nslots - 1, relative to slot0) of the launch slot owning `block`.

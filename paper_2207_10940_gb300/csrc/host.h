@@ -85,6 +85,7 @@ struct Plan {
   bool fp16 = false, fp32p = false;
   int opt = 0;                      // pixel-kernel options of every slot: 1 occlusion test, 2 depth weight
   bool g3 = false;                  // some slot has the 3-D gravity form (its step's shared memory)
+  bool margins = false;             // some slot counts margin decisions (count_margins)
   bool owns_device = false;         // table / dyn / heads allocated by the plan
   int groups = 1;                   // slot groups of the Gauss-Newton loop, one CUDA stream each
   std::vector<int> gfirst, gcount;

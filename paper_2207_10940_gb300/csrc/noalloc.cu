@@ -92,6 +92,7 @@ __global__ void k_noalloc_begin(Ctrl* c, uint32_t* counters, DState xref, DState
   c->status = 0;
   c->ref_index = 0;
   c->block_counter = 0u;
+  c->margin_acc[0] = c->margin_acc[1] = 0u;
 }
 
 // Weighted world-frame systems of both terms from the folded sums (the pixel
@@ -133,6 +134,8 @@ __global__ void k_noalloc_end(const Ctrl* c, double W_icp, double W_rgb, dri_lin
     out->cost_imu = 0.0;
     out->n_icp = (int64_t)c->sums[28];
     out->n_rgb = (int64_t)c->sums[kSums + 28];
+    out->n_margin_icp = c->margin_acc[0];
+    out->n_margin_rgb = c->margin_acc[1];
   }
 }
 

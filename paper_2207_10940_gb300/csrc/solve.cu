@@ -1007,6 +1007,14 @@ __device__ __forceinline__ bool held_gyro_only(int k) {
   return (m >= 6 && m < 9) || m >= 12;
 }
 
+// Margin decisions the pixel kernel counted (its launch for a level's last
+// iteration counts them; the others add nothing): stored for the level, and
+// the accumulator cleared for the next launch.
+__device__ __forceinline__ void store_margin(Ctrl* c, int level) {
+  c->n_margin[level] = (int32_t)(c->margin_acc[0] + c->margin_acc[1]);
+  c->margin_acc[0] = c->margin_acc[1] = 0u;
+}
+
 // Assemble the joint system at (ctrl->x0, ctrl->x1) into S.H (full), S.b.
 // Entry e (0..71) of the two pixel systems rotated into W: term e / 36 (0 ICP
 // with R_ref, 1 photometric with R_0), element e % 36 of its 6x6 (and, for
@@ -1310,6 +1318,7 @@ __device__ void gn_step_pose_only(const SolveParams& sp, GnSmem& S) {
     const double* s = c->sums;
     c->n_icp[sp.level] = (int32_t)s[28];
     c->n_rgb[sp.level] = (int32_t)s[kSums + 28];
+    store_margin(c, sp.level);
     c->cost = sp.W_icp * s[27] + lam * sp.W_rgb * s[kSums + 27];
     c->iterations += 1;
   }
@@ -1406,6 +1415,7 @@ __device__ void gn_step_body(const SolveParams& sp, GnSmem& S) {
     const double* s = c->sums;
     c->n_icp[sp.level] = (int32_t)s[28];
     c->n_rgb[sp.level] = (int32_t)s[kSums + 28];
+    store_margin(c, sp.level);
     c->cost = sp.W_icp * s[27] + sp.W_rgb * s[kSums + 27] + S.cost_imu;
     c->iterations += 1;
   }
@@ -1613,6 +1623,7 @@ __device__ void gn_step_g3(const SolveParams& sp, Gn3Smem& S) {
     const double* s = c->sums;
     c->n_icp[sp.level] = (int32_t)s[28];
     c->n_rgb[sp.level] = (int32_t)s[kSums + 28];
+    store_margin(c, sp.level);
     c->cost = sp.W_icp * s[27] + sp.W_rgb * s[kSums + 27] + S.cost_imu;
     c->iterations += 1;
   }
@@ -1755,7 +1766,8 @@ __device__ void frame_begin_body(const SolveParams& sp, BeginSmem& B) {
     c->x0 = c->x;
     c->iterations = 0;
     c->cost = 0.0;
-    for (int l = 0; l < kMaxLevels; ++l) c->n_icp[l] = c->n_rgb[l] = 0;
+    for (int l = 0; l < kMaxLevels; ++l) c->n_icp[l] = c->n_rgb[l] = c->n_margin[l] = 0;
+    c->margin_acc[0] = c->margin_acc[1] = 0u;
   }
   __syncthreads();
   if (sp.track_mode == DRI_TRACK_RGBD_ONLY) {     // x1 starts at x0; no IMU term
@@ -1887,7 +1899,8 @@ __device__ void frame_init_body(const SolveParams& sp) {
     c->initialised = 1;
     c->iterations = 0;
     c->cost = 0.0;
-    for (int l = 0; l < kMaxLevels; ++l) c->n_icp[l] = c->n_rgb[l] = 0;
+    for (int l = 0; l < kMaxLevels; ++l) c->n_icp[l] = c->n_rgb[l] = c->n_margin[l] = 0;
+    c->margin_acc[0] = c->margin_acc[1] = 0u;
   }
 }
 
@@ -1900,6 +1913,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_linearise_begin(SolveParams s
     c->status = 0;
     c->x0 = x0;
     c->x1 = x1;
+    c->margin_acc[0] = c->margin_acc[1] = 0u;
   }
   __syncthreads();
   const bool ok = imu_weight_and_prediction(sp, c, B, nullptr);
@@ -1930,6 +1944,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_linearise_end(SolveParams sp,
     out->cost_imu = S.ok ? S.cost_imu : 0.0;
     out->n_icp = (int64_t)s[28];
     out->n_rgb = (int64_t)s[kSums + 28];
+    out->n_margin_icp = c->margin_acc[0];
+    out->n_margin_rgb = c->margin_acc[1];
+    c->margin_acc[0] = c->margin_acc[1] = 0u;
     if (!S.ok) c->status = DRI_ENOTREADY;
   }
 }

@@ -102,6 +102,21 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Margin decisions (the last iteration of each level, and the parity entry):
+// a pixel whose accept / reject decision in this kernel lies within 1e-4 px of
+// a rounding or bound boundary, or within a relative 1e-5 of a threshold, as
+// the oracle marks its margin pixels; an FP32 and an FP64 evaluation may
+// decide it differently.
+constexpr float kPxMargin = 1e-4f, kRelMargin = 1e-5f;
+__device__ __forceinline__ bool near_rel(float a, float thr) {
+  return fabsf(a - thr) <= kRelMargin * fabsf(thr);
+}
+// f - floor(f) within kPxMargin of 0 or 1 (f's integer part is fl)
+__device__ __forceinline__ bool near_int(float f, float fl) {
+  const float r = f - fl;
+  return r < kPxMargin || r > 1.f - kPxMargin;
+}
+
 // What a thread needs of its tile for the whole loop over its rows: the term's
 // transform (A = R^T R_1 - I, t), its column u with the pixel ray's x part and
 // the bounds of an integer displacement that stays inside the reference image,
@@ -117,6 +132,8 @@ struct TileCtx {
   float ify_cy;                 // -c_y / f_y
   int row0, kR, nrows;          // the thread's rows: row0, row0 + kR, ... (nrows of them)
   float dmin, dmax, dist2, cosmin, occ_thr;
+  float dist2_lo, dist2_hi;     // margin decisions: squared distances within 1e-5 of the threshold
+  float cos_margin;             //   and the angle test's margin
   const void* __restrict__ A1;  // live pack A
   const float* __restrict__ D1;
   const float* __restrict__ I1;
@@ -174,9 +191,11 @@ struct IcpPix {
   float ix, iy;                 // integer displacement of the associated pixel
   float mx, my, mz;             // (I + A) n1: the live normal in the reference camera
   bool ok;
+  bool cand;                    // depth in range and a normal: the tests after the gather apply
+  bool m;                       // a margin decision so far
 };
 
-template <typename T>
+template <typename T, bool MARGIN>
 __device__ __forceinline__ void icp_front(const TileCtx& c, const RowCtx& q, const float4 live,
                                           IcpPix& x) {
   // live = (n1, d); a zero normal is rejected by the angle test (cos_min > 0)
@@ -193,6 +212,15 @@ __device__ __forceinline__ void icp_front(const TileCtx& c, const RowCtx& q, con
   // NaN and out-of-range displacements fail these comparisons
   x.ok = q.in && d >= c.dmin && d <= c.dmax && z > 0.f && x.ix >= c.lox && x.ix < c.hix &&
          x.iy >= q.loy && x.iy < q.hiy;
+  if (MARGIN) {
+    const bool dv = q.in && d >= c.dmin && d <= c.dmax;
+    x.cand = dv && (live.x != 0.f || live.y != 0.f || live.z != 0.f);
+    const float pz = d + x.w.Dz, px = x.w.px + x.w.Dx, py = x.w.py + x.w.Dy;
+    // |z| <= 1e-5 |p| as squares (1e-10 = kRelMargin^2)
+    x.m = (dv && (near_rel(d, c.dmin) || near_rel(d, c.dmax))) ||
+          (x.cand && pz * pz <= 1e-10f * fmaf(px, px, fmaf(py, py, pz * pz))) ||
+          (x.cand && pz > 0.f && (near_int(sx + 0.5f, x.ix) || near_int(sy + 0.5f, x.iy)));
+  }
   x.mx = fmaf(c.A[0], live.x, fmaf(c.A[1], live.y, fmaf(c.A[2], live.z, live.x)));
   x.my = fmaf(c.A[3], live.x, fmaf(c.A[4], live.y, fmaf(c.A[5], live.z, live.y)));
   x.mz = fmaf(c.A[6], live.x, fmaf(c.A[7], live.y, fmaf(c.A[8], live.z, live.z)));
@@ -205,9 +233,9 @@ __device__ __forceinline__ void icp_front(const TileCtx& c, const RowCtx& q, con
   }
 }
 
-template <bool DW, bool FLAGS>
+template <bool DW, bool FLAGS, bool MARGIN>
 __device__ __forceinline__ void icp_back(const TileCtx& c, const RowCtx& q, const IcpPix& x,
-                                         float* acc) {
+                                         float* acc, int& nm) {
   const float Nx = x.ref.x, Ny = x.ref.y, Nz = x.ref.z, dr = x.ref.w;
   // reference vertex V = d_ref K^-1 [x_i, y_i, 1]^T
   const float Vx = dr * ((c.ucx + x.ix) * c.g.ifx);
@@ -216,9 +244,16 @@ __device__ __forceinline__ void icp_back(const TileCtx& c, const RowCtx& q, cons
   const float dist2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
   const float cosang = fmaf(x.mx, Nx, fmaf(x.my, Ny, x.mz * Nz));
   const bool ok = x.ok && dist2 < c.dist2 && cosang > c.cosmin;
-  if (FLAGS && ok) {           // bit 0, and the association in bits 2-5
+  bool m = false;
+  if (MARGIN) {                // distance and angle tests at a valid reference pixel
+    const bool rvalid = x.ok && (Nx != 0.f || Ny != 0.f || Nz != 0.f);   // a reference normal
+    m = x.m || (x.cand && rvalid &&
+                ((dist2 >= c.dist2_lo && dist2 <= c.dist2_hi) || fabsf(cosang - c.cosmin) <= c.cos_margin));
+    nm += m ? 1 : 0;
+  }
+  if (FLAGS && (ok || m)) {    // bit 0 valid, the association in bits 2-5, bit 6 margin
     const unsigned xi = (unsigned)(c.u + (int)x.ix), yi = (unsigned)(q.v + (int)x.iy);
-    const unsigned bits = 1u | (xi & 3u) << 2 | (yi & 3u) << 4;
+    const unsigned bits = (ok ? 1u | (xi & 3u) << 2 | (yi & 3u) << 4 : 0u) | (m ? 1u << 6 : 0u);
     atomicOr(reinterpret_cast<unsigned int*>(c.flags + (q.o & ~3)), bits << (8 * (q.o & 3)));
   }
   if (!ok) return;
@@ -245,9 +280,10 @@ struct RgbPix {
   float iz, z;
   float i1;                     // live intensity
   bool ok;
+  bool m;                       // a margin decision so far
 };
 
-template <typename T>
+template <typename T, bool MARGIN>
 __device__ __forceinline__ void rgb_front(const TileCtx& c, const RowCtx& q, float d, float i1,
                                           RgbPix& x) {
   x.w = warp_point(c, q.ry, d);
@@ -259,6 +295,16 @@ __device__ __forceinline__ void rgb_front(const TileCtx& c, const RowCtx& q, flo
   // the bilinear support [x, x + 1] x [y, y + 1] inside the image
   x.ok = q.in && d >= c.dmin && d <= c.dmax && x.z > 0.f && fx >= c.lox && fx < c.hix - 1.f &&
          fy >= q.loy && fy < q.hiy - 1.f;
+  if (MARGIN) {
+    const bool dv = q.in && d >= c.dmin && d <= c.dmax;
+    const float px = x.w.px + x.w.Dx, py = x.w.py + x.w.Dy;
+    // x = u + sx, so |x| = |sx - lox| and |x - (w - 1)| = |sx - (hix - 1)|
+    x.m = (dv && (near_rel(d, c.dmin) || near_rel(d, c.dmax))) ||
+          (dv && x.z * x.z <= 1e-10f * fmaf(px, px, fmaf(py, py, x.z * x.z))) ||
+          (dv && x.z > 0.f &&
+           (fabsf(sx - c.lox) <= kPxMargin || fabsf(sx - (c.hix - 1.f)) <= kPxMargin ||
+            fabsf(sy - q.loy) <= kPxMargin || fabsf(sy - (q.hiy - 1.f)) <= kPxMargin));
+  }
   x.ax = sx - fx;
   x.ay = sy - fy;
   x.xr = c.ucx + sx;
@@ -279,10 +325,11 @@ __device__ __forceinline__ void rgb_front(const TileCtx& c, const RowCtx& q, flo
   }
 }
 
-template <typename T, bool OCC, bool FLAGS>
+template <typename T, bool OCC, bool FLAGS, bool MARGIN>
 __device__ __forceinline__ void rgb_back(const TileCtx& c, const RowCtx& q, const RgbPix& x,
-                                         float* acc) {
+                                         float* acc, int& nm) {
   bool ok = x.ok;
+  bool m = MARGIN && x.m;
   if (OCC && ok) {               // depth consistency at the nearest reference pixel
     const bool right = x.ax >= 0.5f, down = x.ay >= 0.5f;
     float dr;
@@ -293,10 +340,15 @@ __device__ __forceinline__ void rgb_back(const TileCtx& c, const RowCtx& q, cons
       dr = __ldg(c.D0 + q.o + (int)(floorf(sy) + (down ? 1.f : 0.f)) * c.g.w +
                  (int)(floorf(sx) + (right ? 1.f : 0.f)));
     }
+    if (MARGIN)                  // the nearest pixel's rounding and the depth gap's threshold
+      m = m || fabsf(x.ax - 0.5f) < kPxMargin || fabsf(x.ay - 0.5f) < kPxMargin ||
+          (dr > 0.f && near_rel(fabsf(x.z - dr), c.occ_thr));
     if (dr > 0.f && fabsf(x.z - dr) > c.occ_thr) ok = false;
   }
-  if (FLAGS && ok)
-    atomicOr(reinterpret_cast<unsigned int*>(c.flags + (q.o & ~3)), 2u << (8 * (q.o & 3)));
+  if (MARGIN) nm += m ? 1 : 0;
+  if (FLAGS && (ok || m))        // bit 1 valid, bit 7 margin
+    atomicOr(reinterpret_cast<unsigned int*>(c.flags + (q.o & ~3)),
+             ((ok ? 2u : 0u) | (m ? 1u << 7 : 0u)) << (8 * (q.o & 3)));
   if (!ok) return;
   const float w00 = (1.f - x.ax) * (1.f - x.ay), w01 = x.ax * (1.f - x.ay);
   const float w10 = (1.f - x.ax) * x.ay, w11 = x.ax * x.ay;
@@ -329,8 +381,8 @@ __device__ __forceinline__ void prefetch_ahead(const TileCtx& c, int r, bool icp
 // half before the current row's back half, so that its gather is in flight
 // meanwhile, measured slower: the state carried between the halves costs
 // registers -- fewer resident warps or spills -- and moves.)
-template <typename T, bool DW, bool FLAGS>
-__device__ __forceinline__ void icp_rows(const TileCtx& c, float* acc) {
+template <typename T, bool DW, bool FLAGS, bool MARGIN>
+__device__ __forceinline__ void icp_rows(const TileCtx& c, float* acc, int& nm) {
   auto live = [&](const RowCtx& q) {
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
     if (q.in) a = Packs<T>::load_a(c.A1, c.D1, q.o);
@@ -342,15 +394,15 @@ __device__ __forceinline__ void icp_rows(const TileCtx& c, float* acc) {
     const float4 ln = r + 1 < c.nrows ? live(row_ctx(c, r + 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
     prefetch_ahead<T>(c, r, true);
     IcpPix x;
-    icp_front<T>(c, q, l, x);
-    icp_back<DW, FLAGS>(c, q, x, acc);
+    icp_front<T, MARGIN>(c, q, l, x);
+    icp_back<DW, FLAGS, MARGIN>(c, q, x, acc, nm);
     l = ln;
   }
 }
 
 // The photometric term over the thread's rows, as icp_rows.
-template <typename T, bool OCC, bool FLAGS>
-__device__ __forceinline__ void rgb_rows(const TileCtx& c, float* acc) {
+template <typename T, bool OCC, bool FLAGS, bool MARGIN>
+__device__ __forceinline__ void rgb_rows(const TileCtx& c, float* acc, int& nm) {
   auto live = [&](const RowCtx& q) {
     float2 a = make_float2(0.f, 0.f);
     if (q.in) a = make_float2(Packs<T>::depth(c.A1, c.D1, q.o), __ldg(c.I1 + q.o));
@@ -362,8 +414,8 @@ __device__ __forceinline__ void rgb_rows(const TileCtx& c, float* acc) {
     const float2 ln = r + 1 < c.nrows ? live(row_ctx(c, r + 1)) : make_float2(0.f, 0.f);
     prefetch_ahead<T>(c, r, false);
     RgbPix x;
-    rgb_front<T>(c, q, l.x, l.y, x);
-    rgb_back<T, OCC, FLAGS>(c, q, x, acc);
+    rgb_front<T, MARGIN>(c, q, l.x, l.y, x);
+    rgb_back<T, OCC, FLAGS, MARGIN>(c, q, x, acc, nm);
     l = ln;
   }
 }
@@ -375,7 +427,7 @@ __device__ __forceinline__ void rgb_rows(const TileCtx& c, float* acc) {
 // photometric occlusion test and the depth-dependent ICP weight.
 constexpr int kOptOcc = 1, kOptDepthWeight = 2;
 
-template <typename T, typename P, bool FLAGS, bool SPLIT, int OPT>
+template <typename T, typename P, bool FLAGS, bool MARGIN, bool SPLIT, int OPT>
 __device__ __forceinline__ void track_tile(const TrackParams& p, const int term, const int bx,
                                            const int by, const int bid) {
   Ctrl* __restrict__ ctrl = p.ctrl;
@@ -409,6 +461,14 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int term,
   c.dmax = p.depth_max;
   c.dist2 = p.icp_dist2;
   c.cosmin = p.icp_cos;
+  {
+    const float thr = sqrtf(p.icp_dist2);
+    c.dist2_lo = (thr * (1.f - kRelMargin)) * (thr * (1.f - kRelMargin));
+    c.dist2_hi = (thr * (1.f + kRelMargin)) * (thr * (1.f + kRelMargin));
+  }
+  // FP16 normals: a stored normal may be one half-precision unit from the
+  // rounding of an FP64-computed one, which moves cos by up to ~2 * 2^-11
+  c.cos_margin = sizeof(T) == 2 ? 4.f * 0.00048828125f : kRelMargin * fabsf(p.icp_cos);
   c.occ_thr = p.occ_thr;
   c.A1 = p.m.packA[cs];
   c.D1 = p.m.depth[cs];
@@ -421,8 +481,13 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int term,
   float acc[kSums];
 #pragma unroll
   for (int k = 0; k < kSums; ++k) acc[k] = 0.f;
-  if (icp) icp_rows<T, (OPT & kOptDepthWeight) != 0, FLAGS>(c, acc);
-  else rgb_rows<T, (OPT & kOptOcc) != 0, FLAGS>(c, acc);
+  int nm = 0;
+  if (icp) icp_rows<T, (OPT & kOptDepthWeight) != 0, FLAGS, MARGIN>(c, acc, nm);
+  else rgb_rows<T, (OPT & kOptOcc) != 0, FLAGS, MARGIN>(c, acc, nm);
+  if (MARGIN) {                      // the warp's margin decisions, one integer add
+    const unsigned sum = __reduce_add_sync(0xffffffffu, (unsigned)nm);
+    if (lane == 0 && sum) atomicAdd(&ctrl->margin_acc[icp ? 0 : 1], sum);
+  }
 
   // ---------------- reduction ----------------
   // Warp: transpose-reduce.  Padded to 32 values, five halving exchanges leave
@@ -501,7 +566,7 @@ __device__ __forceinline__ void track_tile(const TrackParams& p, const int term,
 template <typename T, typename P, bool FLAGS, int OPT>
 __global__ void __launch_bounds__(kTrackThreadsX * kTrackThreadsY)
 k_track(TrackParams p) {
-  track_tile<T, P, FLAGS, false, OPT>(p, 0, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x);
+  track_tile<T, P, FLAGS, FLAGS, false, OPT>(p, 0, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // Tiles of every tracking slot at one level: block -> (slot, tile, term)
@@ -510,7 +575,7 @@ k_track(TrackParams p) {
 // more spill reloads) and than two columns per thread.
 // FLAGS (parity entry only): the same kernel that also or-s each pixel's
 // validity bits into a.flags (the slot's level image, zeroed before the launch).
-template <typename T, typename P, int OPT, bool FLAGS>
+template <typename T, typename P, int OPT, bool FLAGS, bool MARGIN>
 __global__ void __launch_bounds__(kTrackThreadsX * kTrackThreadsY, 3)
 k_track_batch(const BatchArgs a) {
   const int i = batch_slot(a, blockIdx.x);
@@ -530,7 +595,7 @@ k_track_batch(const BatchArgs a) {
   const int t = blockIdx.x - __ldg(a.start + i);
   const int gx = (p.g.w + kTrackThreadsX - 1) / kTrackThreadsX;
   const int tile = t >> 1;                    // the two terms of a tile are neighbours
-  track_tile<T, P, FLAGS, true, OPT>(p, t & 1, tile % gx, tile / gx, t);
+  track_tile<T, P, FLAGS, MARGIN, true, OPT>(p, t & 1, tile % gx, tile / gx, t);
 }
 
 }  // namespace
@@ -602,17 +667,18 @@ cudaError_t launch_track_batch(const BatchArgs& a, int blocks, bool fp16, bool f
   attr[1].val.priority = priority;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-#define DRI_TRACK_BATCH_F(T, P, F)                                                       \
+#define DRI_TRACK_BATCH_F(T, P, F, M)                                                    \
   do {                                                                                   \
-    if (opt == 0) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 0, F>, a);         \
-    if (opt == 1) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 1, F>, a);         \
-    if (opt == 2) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 2, F>, a);         \
-    return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 3, F>, a);                       \
+    if (opt == 0) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 0, F, M>, a);      \
+    if (opt == 1) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 1, F, M>, a);      \
+    if (opt == 2) return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 2, F, M>, a);      \
+    return cudaLaunchKernelEx(&cfg, k_track_batch<T, P, 3, F, M>, a);                    \
   } while (0)
 #define DRI_TRACK_BATCH(T, P)                                                            \
   do {                                                                                   \
-    if (a.flags) DRI_TRACK_BATCH_F(T, P, true);                                          \
-    DRI_TRACK_BATCH_F(T, P, false);                                                      \
+    if (a.flags) DRI_TRACK_BATCH_F(T, P, true, true);                                    \
+    if (a.margin) DRI_TRACK_BATCH_F(T, P, false, true);                                  \
+    DRI_TRACK_BATCH_F(T, P, false, false);                                               \
   } while (0)
   if (fp16) {
     if (fp32_partials) DRI_TRACK_BATCH(__half, float);

@@ -56,7 +56,7 @@ class dri_stream_config(ctypes.Structure):
         ("min_valid", ctypes.c_int32), ("precision_flags", ctypes.c_int32),
         ("max_imu", ctypes.c_int32), ("imu_mode", ctypes.c_int32),
         ("bias_relin_g", ctypes.c_double), ("bias_relin_a", ctypes.c_double),
-        ("track_mode", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("track_mode", ctypes.c_int32), ("count_margins", ctypes.c_int32),
         ("rgbd_lambda", ctypes.c_double), ("occlusion_thr", ctypes.c_double),
         ("icp_depth_weight", ctypes.c_int32), ("gravity_dof", ctypes.c_int32),
     ]
@@ -78,6 +78,7 @@ class dri_track_result(ctypes.Structure):
     _fields_ = [
         ("x1", dri_state), ("x0", dri_state),
         ("n_icp", ctypes.c_int32 * DRI_MAX_LEVELS), ("n_rgb", ctypes.c_int32 * DRI_MAX_LEVELS),
+        ("n_margin", ctypes.c_int32 * DRI_MAX_LEVELS),
         ("cost", ctypes.c_double), ("status", ctypes.c_int32), ("initialised", ctypes.c_int32),
     ]
 
@@ -90,6 +91,7 @@ class dri_linearisation(ctypes.Structure):
         ("cost_icp", ctypes.c_double), ("cost_rgb", ctypes.c_double), ("cost_imu", ctypes.c_double),
         ("e_imu", ctypes.c_double * 18),
         ("n_icp", ctypes.c_int64), ("n_rgb", ctypes.c_int64),
+        ("n_margin_icp", ctypes.c_int64), ("n_margin_rgb", ctypes.c_int64),
     ]
 
 

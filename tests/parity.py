@@ -168,6 +168,25 @@ def new_stream(dcfg, x_init):
                       torch.cuda.Stream())
 
 
+def check_margins(out, flags, lin, what=""):
+    """The kernel's margin decisions (flag bits 6 ICP, 7 photometric): their
+    counts equal the bits (the counting and the flag-writing launches are one
+    kernel), and per pixel they are the oracle's margins of the decisions the
+    linearisation makes (icp_margin_px, rgb_margin_px) except where a pixel's
+    margin quantity lies within FP32 rounding of the margin's own edge: a
+    pixel's distance to a rounding boundary carries ~1e-6 px of FP32 error, so
+    with two edges per axis and two axes about 8e-6 of the pixels sit that
+    close to an edge, bounded here by max(4, 1e-5 x pixels) per term."""
+    gm_i, gm_r = (flags & 64) != 0, (flags & 128) != 0
+    assert out.n_margin_icp == gm_i.sum() and out.n_margin_rgb == gm_r.sum(), \
+        (what, out.n_margin_icp, gm_i.sum(), out.n_margin_rgb, gm_r.sum())
+    bar = max(4, 1e-5 * flags.size)
+    for name, g, o in (("ICP", gm_i, lin["icp_margin_px"]), ("photometric", gm_r, lin["rgb_margin_px"])):
+        diff = int((g != o).sum())
+        assert diff <= bar, \
+            f"{what} {name} margins: {diff} pixels differ (kernel {g.sum()}, oracle {o.sum()})"
+
+
 def compare_linearisation(out, flags, lin, H, b, cost, cur, ref, x0, x1, cfg, rel=REL, what=""):
     """A dri_linearise result (and its flag bytes) against the oracle's
     linearisation `lin` and assembled system (H, b, cost) at the same state:
@@ -181,6 +200,7 @@ def compare_linearisation(out, flags, lin, H, b, cost, cur, ref, x0, x1, cfg, re
     assert bad_i == 0, f"{what}: ICP validity differs at {bad_i} non-margin pixels"
     assert bad_r == 0, f"{what}: photometric validity differs at {bad_r} non-margin pixels"
     assert out.n_icp == gi.sum() and out.n_rgb == gr.sum()
+    check_margins(out, flags, lin, what)
     al = margin_allowance(lin, flags, cur, ref, x0, x1, cfg)
     check_system(np.array(out.H_icp).reshape(6, 6), out.b_icp, lin["H_icp"], lin["b_icp"],
                  lin["cost_icp"], rel=rel, what=f"{what} ICP", allow=al["icp"])

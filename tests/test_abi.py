@@ -62,3 +62,39 @@ def test_fp16_maps_shrink_the_workspace(lib):
     b = dri.dri_config_default(640, 480)
     b.precision_flags = dri.DRI_FP16_MAPS
     assert dri.dri_stream_workspace_bytes(b) < dri.dri_stream_workspace_bytes(a)
+
+
+STRUCTS = ("dri_stream_config", "dri_imu_sample", "dri_state", "dri_track_result", "dri_linearisation",
+           "dri_profile", "dri_batch_options", "dri_server_stats", "dri_server_tick")
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors in dri.py have the C header's size and field offsets
+    (a small C program compiled against include/dri.h prints them)."""
+    import shutil
+    import subprocess
+    from paper_2207_10940_gb300 import dri
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "dri.h"', "int main(void) {"]
+    for name in STRUCTS:
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in getattr(dri, name)._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    c_layout = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        *key, value = line.split()
+        c_layout[tuple(key)] = int(value)
+    for name in STRUCTS:
+        cls = getattr(dri, name)
+        assert c_layout[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert c_layout[(name, field)] == getattr(cls, field).offset, (name, field)

@@ -100,3 +100,6 @@ def test_gravity_form_is_validated_on_the_host(dri):
     cfg = dri.dri_config_default(320, 240)
     cfg.icp_angle_thr_deg = 90.0             # the angle test must reject zero normals
     _einval(dri, dri.dri_stream_workspace_bytes, cfg)
+    cfg = dri.dri_config_default(320, 240)
+    cfg.count_margins = 2                    # an option, 0 or 1
+    _einval(dri, dri.dri_stream_workspace_bytes, cfg)
