@@ -103,3 +103,14 @@ def test_gravity_form_is_validated_on_the_host(dri):
     cfg = dri.dri_config_default(320, 240)
     cfg.count_margins = 2                    # an option, 0 or 1
     _einval(dri, dri.dri_stream_workspace_bytes, cfg)
+
+
+def test_empty_and_null_batches_are_rejected(dri):
+    """dri_track_batch takes at least one stream: an empty, negative or NULL
+    list is DRI_EINVAL before any CUDA call."""
+    lib = dri.load_library()
+    out = (dri.dri_track_result * 1)()
+    arr = (ctypes.c_void_p * 1)()
+    assert lib.dri_track_batch(None, 1, out) == dri.DRI_EINVAL
+    assert lib.dri_track_batch(arr, 0, out) == dri.DRI_EINVAL
+    assert lib.dri_track_batch(arr, -1, out) == dri.DRI_EINVAL
