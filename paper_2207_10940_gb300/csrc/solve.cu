@@ -31,8 +31,11 @@
 // to the end of the interval (state-transition blocks from suffix sums of u_k dt_k
 // and u_k w_k).  These equal the sequential recursion exactly (same algebra,
 // other rounding order).  W_IMU's block structure (a 9x9 block and a diagonal)
-// is used in the assembly; the 34x34 system is Jacobi scaled and solved by an
-// LDL^T factorisation whose trailing updates run over all threads.
+// is used in the assembly.  The step solves the reduced 26-dimensional system
+// (x1's biases and gravity eliminated in closed form) with an element-parallel
+// LDL^T on four warps; its 14 components that no pixel term touches are
+// eliminated before the pixel sums arrive, the 12 pose components after
+// (gn_step_body).  The 3-D gravity form solves its whole 36-dimensional system.
 //
 // All arithmetic here is FP64.  One block of kSolveThreads threads runs each
 // stream's kernel; a batched launch has one block per slot.
